@@ -1,0 +1,74 @@
+"""Model operators of the paper, assembled from their definitions (FP64).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Grid ordering: a grid with axis sizes (nx, ny[, nz]) is flattened with x
+fastest, i.e. index = (z*ny + y)*nx + x.  Kronecker products are therefore
+written with the slowest axis first.
+
+* Finite-difference Laplacian (Section 5.2: "standard 5-point FD
+  discretization"; the 3D 7-point analogue): the 1D second difference
+  (-u[j-1] + 2u[j] - u[j+1]) / h^2 with homogeneous Dirichlet ends, combined as
+  a Kronecker sum over the axes.
+* Bilinear (Q1) finite elements (Section 5.1: "standard bilinear finite
+  elements", stiffness A and mass B): on a tensor mesh the Q1 element matrices
+  factor into 1D linear-element matrices, so A = K (x) M + M (x) K and
+  B = M (x) M with K = tridiag(-1, 2, -1)/h and M = tridiag(1, 4, 1) h/6 on
+  the interior nodes.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def second_difference_1d(N: int, h: float) -> sp.csr_matrix:
+    """(-u[j-1] + 2u[j] - u[j+1]) / h^2 on N interior points, Dirichlet ends."""
+    main = np.full(N, 2.0)
+    off = np.full(N - 1, -1.0)
+    return (sp.diags([off, main, off], [-1, 0, 1], format="csr") / h**2).tocsr()
+
+
+def kron_sum(mats_slow_to_fast):
+    """Kronecker sum  sum_d I (x) .. (x) M_d (x) .. (x) I  (first matrix = slowest axis)."""
+    sizes = [m.shape[0] for m in mats_slow_to_fast]
+    total = None
+    for d, m in enumerate(mats_slow_to_fast):
+        left = int(np.prod(sizes[:d])) if d > 0 else 1
+        right = int(np.prod(sizes[d + 1:])) if d + 1 < len(sizes) else 1
+        term = sp.kron(sp.kron(sp.identity(left, format="csr"), m, format="csr"),
+                       sp.identity(right, format="csr"), format="csr")
+        total = term if total is None else total + term
+    return total.tocsr()
+
+
+def laplacian_dirichlet(dims, h: float) -> sp.csr_matrix:
+    """Negative FD Laplacian, Dirichlet, on a grid with axis sizes dims = (nx, ny[, nz])."""
+    mats = [second_difference_1d(N, h) for N in reversed(dims)]  # slowest axis first
+    return kron_sum(mats)
+
+
+def q1_1d(N: int, h: float):
+    """1D linear-element stiffness and mass on N interior nodes of a uniform mesh."""
+    K = sp.diags([np.full(N - 1, -1.0), np.full(N, 2.0), np.full(N - 1, -1.0)],
+                 [-1, 0, 1], format="csr") / h
+    M = sp.diags([np.full(N - 1, 1.0), np.full(N, 4.0), np.full(N - 1, 1.0)],
+                 [-1, 0, 1], format="csr") * (h / 6.0)
+    return K.tocsr(), M.tocsr()
+
+
+def q1_fe_2d(elems: int):
+    """Stiffness A and mass B of bilinear elements for -Laplace on the unit square
+    with `elems` elements per side, homogeneous Dirichlet (Section 5.1)."""
+    h = 1.0 / elems
+    K, M = q1_1d(elems - 1, h)
+    A = (sp.kron(K, M) + sp.kron(M, K)).tocsr()
+    B = sp.kron(M, M).tocsr()
+    return A, B
+
+
+def model_operator(workload):
+    """(A, B) of a workload description; B is None for the standard problem."""
+    if workload.kind in ("lap2d", "lap3d"):
+        return laplacian_dirichlet(workload.dims, workload.h), None
+    raise ValueError("unknown operator kind %r" % workload.kind)

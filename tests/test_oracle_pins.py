@@ -1,0 +1,330 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics
+(closed-form spectra, the paper's printed eigenvalues, algebraic identities of
+the V-cycle, the Petrov-Galerkin condition, dense brute force).  CPU only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import workloads as wl
+from oracle import avmg, operators, plhr
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def fd_closed_form(dims, h):
+    """Dirichlet FD Laplacian spectrum: sum_d (4/h^2) sin^2(i_d pi / (2(N_d + 1)))."""
+    vals = np.zeros(1)
+    for N in dims:
+        mu = 4.0 / h**2 * np.sin(np.arange(1, N + 1) * np.pi / (2.0 * (N + 1))) ** 2
+        vals = (vals[:, None] + mu[None, :]).ravel()
+    return np.sort(vals)
+
+
+def sine_mode(dims, modes):
+    """Analytic eigenvector of the Dirichlet FD Laplacian (x fastest)."""
+    vecs = [np.sin(np.arange(1, N + 1) * m * np.pi / (N + 1)) for N, m in zip(dims, modes)]
+    out = vecs[-1]
+    for v in reversed(vecs[:-1]):
+        out = np.kron(out, v)
+    return out
+
+
+# ---------------------------------------------------------------- operators
+
+@pytest.mark.parametrize("dims", [(5, 7), (3, 4, 5), (6, 6, 6)])
+def test_fd_laplacian_matches_closed_form(dims):
+    h = 1.0 / (max(dims) + 1)
+    L = operators.laplacian_dirichlet(dims, h).toarray()
+    assert np.allclose(L, L.T)
+    ev = np.linalg.eigvalsh(L)
+    assert np.allclose(ev, fd_closed_form(dims, h), rtol=1e-12, atol=1e-9)
+
+
+def test_fd_laplacian_mode_ordering_x_fastest():
+    dims, h = (4, 5, 6), 0.1
+    L = operators.laplacian_dirichlet(dims, h)
+    u = sine_mode(dims, (1, 2, 3))
+    # eigenvalue of the tensor mode: (2 - 2cos(m pi/(N+1)))/h^2 per axis
+    lam = sum((2.0 - 2.0 * math.cos(m * math.pi / (N + 1))) / h**2 for N, m in zip(dims, (1, 2, 3)))
+    assert np.allclose(L @ u, lam * u, rtol=1e-12, atol=1e-9)
+
+
+def test_q1_fe_reproduces_printed_eigenvalues():
+    """Section 5.1: lambda_31 ~ 497.5521 and lambda_66 ~ 979.7072 for 50x50
+    bilinear elements (golden values copied from the paper's text)."""
+    with open(os.path.join(GOLDEN, "fe_q1_50x50.json")) as f:
+        g = json.load(f)
+    A, B = operators.q1_fe_2d(g["elements_per_side"])
+    assert A.shape[0] == g["n"]
+    ev = sla.eigh(A.toarray(), B.toarray(), eigvals_only=True)
+    tol = 0.5 * 10.0 ** (-g["printed_decimals"])
+    for idx, val in g["eigenvalues_1based"].items():
+        assert abs(ev[int(idx) - 1] - val) <= tol + 1e-12
+
+
+def test_q1_fe_closed_form_small_mesh():
+    """Tensor Q1: lambda = mu_i + mu_j, mu = (6/h^2)(1 - cos t)/(2 + cos t)."""
+    e = 9
+    h = 1.0 / e
+    A, B = operators.q1_fe_2d(e)
+    ev = sla.eigh(A.toarray(), B.toarray(), eigvals_only=True)
+    t = np.arange(1, e) * np.pi * h
+    mu = 6.0 / h**2 * (1 - np.cos(t)) / (2 + np.cos(t))
+    cf = np.sort((mu[:, None] + mu[None, :]).ravel())
+    assert np.allclose(ev, cf, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- AV-MG
+
+def test_restriction_prolongation_identities():
+    dims = (4, 6, 8)
+    R = avmg.restriction(dims)
+    P = 8.0 * R.T
+    assert np.allclose((R @ P).toarray(), np.eye(R.shape[0]))
+    ones = np.ones(int(np.prod(dims)))
+    assert np.allclose(R @ ones, 1.0)
+    # child (x=3, y=5, z=7) belongs to coarse cell (1, 2, 3)
+    x = np.zeros(int(np.prod(dims)))
+    x[(7 * 6 + 5) * 4 + 3] = 8.0
+    c = R @ x
+    assert np.argmax(c) == (3 * 3 + 2) * 2 + 1 and abs(c.max() - 1.0) < 1e-15
+
+
+def test_avmg_single_level_is_exact_absolute_inverse():
+    """levels = 1: T = |L - sigma I|^{-1}; on an analytic sine mode
+    T u = u / |lambda - sigma|."""
+    dims, h, sigma = (6, 5, 4), 1.0 / 7.0, 300.0
+    T = avmg.AVMG(dims, h, sigma, levels=1)
+    for modes in [(1, 1, 1), (2, 3, 1), (6, 5, 4), (3, 2, 2)]:
+        u = sine_mode(dims, modes)
+        lam = sum((2.0 - 2.0 * math.cos(m * math.pi / (N + 1))) / h**2 for N, m in zip(dims, modes))
+        assert np.allclose(T(u), u / abs(lam - sigma), rtol=1e-10, atol=1e-14)
+
+
+def _dense(op, n):
+    return np.column_stack([op(e) for e in np.eye(n)])
+
+
+@pytest.mark.parametrize("sigma", [40.0, 900.0])
+def test_polynomial_level_spectrum(sigma):
+    """B_l = p_2(L_l - sigma I) has eigenvalues p_2(lambda_i - sigma) with
+    p_2(x) = (x^2 + c^2)/(2c); B_l = L_l below the resolution threshold."""
+    dims, h = (4, 4, 4), 1.0 / 5.0
+    lev = avmg.Level(dims, h, sigma)
+    B = _dense(lev.apply_B, 64)
+    ev = np.linalg.eigvalsh(0.5 * (B + B.T))
+    lam = fd_closed_form(dims, h)
+    if math.sqrt(sigma) * h < 2 * math.pi / 10:
+        assert not lev.use_poly
+        ref = lam
+    else:
+        assert lev.use_poly
+        c = 0.5 * max(sigma, 12.0 / h**2 - sigma)   # Gershgorin: [-sigma, 12/h^2 - sigma]
+        ref = np.sort(((lam - sigma) ** 2 + c * c) / (2 * c))
+        assert ev.min() >= c / 2 * (1 - 1e-12)
+    assert np.allclose(ev, ref, rtol=1e-11)
+    assert ev.max() <= lev.beta * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("sigma", [60.0, 700.0])
+def test_two_level_vcycle_algebraic_form(sigma):
+    """Two-grid Algorithm 4 equals the closed form
+    T = B^{-1}(I - E^{2nu}) + E^nu P T_c R E^nu,  E = I - omega B,
+    with P = 2^d R^T and T_c = |L_0 - sigma I|^{-1}."""
+    dims, h, nu = (4, 4, 6), 1.0 / 7.0, 2
+    T = avmg.AVMG(dims, h, sigma, levels=2, nu=nu)
+    n = int(np.prod(dims))
+    Td = _dense(T, n)
+    fine = T.levels[1]
+    B = _dense(fine.apply_B, n)
+    om = 1.0 / fine.beta
+    E = np.eye(n) - om * B
+    En = np.linalg.matrix_power(E, nu)
+    R = T.R[1].toarray()
+    P = 8.0 * R.T
+    Lc = operators.laplacian_dirichlet(tuple(N // 2 for N in dims), 2 * h).toarray() - sigma * np.eye(R.shape[0])
+    w, Q = np.linalg.eigh(Lc)
+    Tc = Q @ np.diag(1.0 / np.abs(w)) @ Q.T
+    ref = np.linalg.solve(B, np.eye(n) - En @ En) + En @ P @ Tc @ R @ En
+    assert np.allclose(Td, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("levels,sigma", [(2, 60.0), (3, 700.0), (3, 1500.0)])
+def test_vcycle_symmetric_positive_definite(levels, sigma):
+    dims, h = (8, 8, 8), 1.0 / 9.0
+    T = avmg.AVMG(dims, h, sigma, levels=levels)
+    Td = _dense(T, 512)
+    assert np.abs(Td - Td.T).max() <= 1e-12 * np.abs(Td).max()
+    assert np.linalg.eigvalsh(0.5 * (Td + Td.T)).min() > 0
+
+
+# ---------------------------------------------------------------- extraction
+
+def _random_borth_basis(n, m, B, rng):
+    Z = rng.standard_normal((n, m))
+    G = Z.T @ (Z if B is None else B @ Z)
+    Rc = np.linalg.cholesky(G).T
+    return Z @ np.linalg.inv(Rc)
+
+
+def test_tharmonic_identity_T_gives_real_spectrum():
+    """T = I, B = I: G_R = Z*(A - sI)Z is symmetric and G_L = Z*(A - sI)^2 Z is
+    positive definite, so every xi is real (standard harmonic RR)."""
+    rng = np.random.default_rng(1)
+    A = operators.laplacian_dirichlet((10, 10), 1 / 11).toarray()
+    sigma = 500.0
+    Z = _random_borth_basis(100, 12, None, rng)
+    U = A @ Z - sigma * Z
+    xi, Y = plhr.tharmonic_extract(0.5 * (U.T @ U + U.T @ U), U.T @ Z)
+    assert np.all(np.abs(np.imag(xi)) <= 1e-10 * np.abs(xi))
+
+
+@pytest.mark.parametrize("generalized", [False, True])
+def test_tharmonic_petrov_galerkin_condition(generalized):
+    """Eq. orth_gen: Z*(A - sB) T (A - theta B) Z y = 0 for theta = sigma + xi."""
+    rng = np.random.default_rng(2)
+    if generalized:
+        A, B = operators.q1_fe_2d(9)
+        A, B = A.toarray(), B.toarray()
+    else:
+        A = operators.laplacian_dirichlet((8, 8), 1 / 9).toarray()
+        B = np.eye(64)
+    n = A.shape[0]
+    sigma = 250.0
+    M = rng.standard_normal((n, n))
+    T = M @ M.T / n + np.eye(n)           # SPD preconditioner
+    Z = _random_borth_basis(n, 9, B, rng)
+    U = A @ Z - sigma * B @ Z
+    Q = T @ U
+    GL = U.T @ Q
+    GR = Q.T @ B @ Z
+    xi, Y = plhr.tharmonic_extract(0.5 * (GL + GL.T), GR)
+    for j in range(len(xi)):
+        theta = sigma + xi[j]
+        v = Z @ Y[:, j]
+        pg = Z.T @ (A - sigma * B) @ T @ (A @ v - theta * (B @ v))
+        scale = np.linalg.norm(Z.T @ (A - sigma * B) @ T @ (A - sigma * B) @ Z, 2) * (1 + abs(xi[j]))
+        assert np.linalg.norm(pg) <= 1e-10 * scale
+
+
+def test_real_spectrum_ordering_pairs_conjugates():
+    xi = np.array([3.0, 1 + 1j, -0.5, 1 - 1j, 2.0 - 0.1j, 2.0 + 0.1j, -1.5])
+    order, partner = plhr.order_real_spectrum(xi)
+    seq = list(xi[order])
+    assert seq[0] == -0.5
+    assert seq[1] == 1 + 1j and seq[2] == 1 - 1j          # |1+i| = 1.414 < 1.5
+    assert seq[3] == -1.5
+    assert seq[4] == 2.0 + 0.1j and seq[5] == 2.0 - 0.1j
+    assert seq[6] == 3.0
+    assert partner[1] == 3 and partner[3] == 1 and partner[0] == -1
+
+
+def test_select_real_cut_pair_keeps_real_part():
+    xi = np.array([0.1, 0.2 + 0.3j, 0.2 - 0.3j, 5.0])
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+    Y = np.column_stack([rng.standard_normal(4), y, np.conj(y), rng.standard_normal(4)])
+    Yp, tags, chosen = plhr.select_real(xi, Y, 2)           # cut between the pair
+    assert [t[0] for t in tags] == ["real", "cut"]
+    yr = plhr.rotate_principal(y)
+    assert np.allclose(Yp[:, 1], np.real(yr))
+    assert abs(np.real(yr) @ np.imag(yr)) < 1e-14
+    assert np.linalg.norm(np.real(yr)) >= np.linalg.norm(np.imag(yr))
+    Yp3, tags3, _ = plhr.select_real(xi, Y, 3)
+    assert [t[0] for t in tags3] == ["real", "pairR", "pairI"]
+
+
+# ---------------------------------------------------------------- whole solver
+
+def test_bplhr_2d_identity_T_matches_closed_form():
+    w = wl.lap2d_small(16, k=4, gap_index=20)
+    r = plhr.solve_workload(w, maxit=2000)
+    assert r.converged
+    lam = fd_closed_form(w.dims, w.h)
+    ref = lam[np.lexsort((lam, np.abs(lam - w.sigma)))][: w.k]
+    assert np.allclose(np.sort(r.eigvals), np.sort(ref), rtol=1e-10)
+    assert np.all(r.residuals <= w.tol)
+    V = r.eigvecs
+    assert np.abs(V.T @ V - np.eye(w.k)).max() <= 1e-12
+
+
+def test_bplhr_3d_avmg_matches_closed_form():
+    w = wl.lap3d_small(8, levels=2, k=4, gap_index=30)
+    r = plhr.solve_workload(w, maxit=500)
+    assert r.converged
+    lam = fd_closed_form(w.dims, w.h)
+    ref = lam[np.lexsort((lam, np.abs(lam - w.sigma)))][: w.k]
+    assert np.allclose(np.sort(r.eigvals), np.sort(ref), rtol=1e-10)
+    assert np.all(r.residuals <= w.tol)
+
+
+def test_bplhr_generalized_fe_with_perturbed_exact_preconditioner():
+    """Section 5.1 setting in small: Q1 FE pencil (B != I), T = |A - sB|^{-1} + E
+    with a small SPD perturbation E; eigenpairs vs dense eigh(A, B)."""
+    A, B = operators.q1_fe_2d(12)
+    Ad, Bd = A.toarray(), B.toarray()
+    n = Ad.shape[0]
+    sigma = 497.0
+    w, X = sla.eigh(Ad, Bd)
+    # |A - sB|^{-1} = X |Lambda - s|^{-1} X^T for B-orthonormal X
+    Tex = X @ np.diag(1.0 / np.abs(w - sigma)) @ X.T
+    rng = np.random.default_rng(4)
+    M = rng.standard_normal((n, n))
+    E = M @ M.T
+    E *= 1e-3 * np.linalg.norm(Tex, 2) / np.linalg.norm(E, 2)
+    T = Tex + E
+    k = 4
+    V0 = wl.start_block(n, k + 1, 99)
+    r = plhr.bplhr(A, B, lambda Xb: T @ Xb, sigma, k, V0, tol=1e-9, maxit=300)
+    assert r.converged
+    ref = w[np.lexsort((w, np.abs(w - sigma)))][:k]
+    assert np.allclose(np.sort(r.eigvals), np.sort(ref), rtol=1e-10)
+    V = r.eigvecs
+    assert np.abs(V.T @ Bd @ V - np.eye(k)).max() <= 1e-12
+
+
+def test_real_arithmetic_equals_complex_when_spectrum_real():
+    """Alg. 3 reduces to Alg. 2 when every projected eigenvector is real: with
+    T = I and B = I all xi are real, so both runs must produce the same Ritz
+    values."""
+    w = wl.lap2d_small(12, k=3, gap_index=12)
+    A, _ = operators.model_operator(w)
+    V0 = w.v0()
+    hr = plhr.bplhr(A, None, None, w.sigma, w.k, V0, tol=1e-14, maxit=12).history
+    hc = plhr.bplhr(A, None, None, w.sigma, w.k, V0.astype(np.complex128), tol=1e-14,
+                    maxit=12, real=False).history
+    for a, b in zip(hr, hc):
+        assert np.allclose(a["lam"], b["lam"], rtol=1e-9)
+
+
+def test_plain_and_carried_images_agree():
+    """The carried images AZ, BZ, T(A - sB)Z equal explicit products."""
+    w = wl.lap3d_small(8, levels=2, k=3, gap_index=25)
+    A, _ = operators.model_operator(w)
+    T = avmg.preconditioner(w)
+    h1 = plhr.bplhr(A, None, T, w.sigma, w.k, w.v0(), tol=1e-14, maxit=10).history
+    h2 = plhr.bplhr(A, None, T, w.sigma, w.k, w.v0(), tol=1e-14, maxit=10, plain=True).history
+    for a, b in zip(h1, h2):
+        assert np.allclose(a["lam"], b["lam"], rtol=1e-9)
+
+
+def test_complex_hermitian_problem_matches_dense():
+    """Alg. 2 (complex arithmetic) on a small complex Hermitian problem:
+    a 2D Laplacian plus a Hermitian imaginary coupling."""
+    rng = np.random.default_rng(5)
+    n = 64
+    A0 = operators.laplacian_dirichlet((8, 8), 1 / 9).toarray()
+    K = rng.standard_normal((n, n))
+    A = A0 + 5j * (K - K.T)
+    sigma = 400.0
+    w = np.linalg.eigvalsh(A)
+    k = 3
+    V0 = wl.start_block(n, k, 17, complex_=True)
+    r = plhr.bplhr(A, None, None, sigma, k, V0, tol=1e-10, maxit=3000, real=False)
+    assert r.converged
+    ref = w[np.lexsort((w, np.abs(w - sigma)))][:k]
+    assert np.allclose(np.sort(r.eigvals), np.sort(ref), rtol=1e-10)

@@ -1,0 +1,175 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module holds no arithmetic of the eigensolver: it only describes the
+workloads (grid sizes, mesh widths, shifts, block sizes, multigrid depth) and
+draws the seeded starting blocks.  Both the oracle and the GPU path receive
+the same arrays from here.
+
+Starting block V0 (the paper recommends a random initial guess, Section 3.2):
+element (i, j) of an n x kc block is the (i*kc + j + 1)-th output of the
+SplitMix64 generator (G. Steele, D. Lea, C. Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) started from ``seed``; the 64-bit
+output x is mapped to (x >> 11) * 2**-53 - 0.5, uniform in [-0.5, 0.5).
+The C library implements the same published generator for the case where the
+caller passes no starting block.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+SEED_BASE = 20140801
+
+
+def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
+    """Outputs start+1 .. start+count of SplitMix64 seeded with ``seed`` (uint64)."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + idx * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform_block(n: int, kc: int, seed: int, start: int = 0) -> np.ndarray:
+    """n x kc float64 block, entries uniform in [-0.5, 0.5) (row-major draw order)."""
+    x = splitmix64(seed, n * kc, start)
+    u = (x >> np.uint64(11)).astype(np.float64) * (2.0 ** -53) - 0.5
+    return u.reshape(n, kc)
+
+
+def start_block(n: int, kc: int, seed: int, complex_: bool = False) -> np.ndarray:
+    """Seeded starting block V0 (n x kc).  Complex blocks draw the imaginary
+    part from the outputs that follow the real part's n*kc outputs."""
+    re = uniform_block(n, kc, seed)
+    if not complex_:
+        return re
+    im = uniform_block(n, kc, seed, start=n * kc)
+    return re + 1j * im
+
+
+@dataclass
+class Workload:
+    """One seeded eigenproblem: operator description + solver parameters."""
+    name: str
+    kind: str                 # "lap2d" (5-point) or "lap3d" (7-point), Dirichlet
+    dims: tuple               # grid points per axis, x fastest: (nx, ny[, nz])
+    h: float                  # mesh width
+    sigma: float              # target shift
+    k: int                    # wanted eigenpairs
+    tol: float                # relative residual tolerance
+    prec: str = "none"        # "none" (T = I) or "avmg"
+    mg_levels: int = 1
+    mg_nu: int = 2
+    maxit: int = 1000
+    seed: int = SEED_BASE
+    real: bool = True
+    note: str = ""
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(np.prod(self.dims))
+
+    @property
+    def kprime(self) -> int:
+        # real arithmetic runs one extra column so a conjugate pair is never cut
+        return self.k + 1 if self.real else self.k
+
+    def v0(self) -> np.ndarray:
+        return start_block(self.n, self.kprime, self.seed, complex_=not self.real)
+
+
+def lap_closed_form(dims, h) -> np.ndarray:
+    """Sorted eigenvalues of the Dirichlet finite-difference Laplacian on a
+    tensor grid: sum over axes of (4/h^2) sin^2(i pi / (2(N+1))), i = 1..N.
+    Used only to place shifts (midpoints of gaps); tests pin the operators
+    against it independently."""
+    mus = [4.0 / h**2 * np.sin(np.arange(1, N + 1) * np.pi / (2.0 * (N + 1))) ** 2 for N in dims]
+    tot = mus[0]
+    for m in mus[1:]:
+        tot = (tot[:, None] + m[None, :]).ravel()
+    return np.sort(tot)
+
+
+def _mid_gap(dims, h, lo_index: int) -> float:
+    lam = lap_closed_form(dims, h)
+    return 0.5 * (lam[lo_index] + lam[lo_index + 1])
+
+
+def config1() -> Workload:
+    """2D 5-point Laplacian, 32x32 Dirichlet interior grid, h = 1/33, B = I,
+    sigma midway between the 100th and 101st eigenvalues, k = 4, T = I."""
+    dims, h = (32, 32), 1.0 / 33.0
+    return Workload(name="lap2d_32x32_k4", kind="lap2d", dims=dims, h=h,
+                    sigma=_mid_gap(dims, h, 99), k=4, tol=1e-8, prec="none", maxit=20000,
+                    seed=SEED_BASE + 1)
+
+
+# 3D 7-point Laplacian, 128^3 interior, h = 1/129: the shift is the midpoint of
+# the eigenvalues 1064.0220711725 (mode (6,6,6)) and 1073.1201516674 (modes
+# (3,6,8) and permutations); 471 eigenvalues lie below it and the 10 nearest
+# form complete multiplets (3 + 1 + 6), the 11th is 12.18 away.
+def config2() -> Workload:
+    dims, h = (128, 128, 128), 1.0 / 129.0
+    sigma = 0.5 * (_lap3_mode((6, 6, 6), h) + _lap3_mode((3, 6, 8), h))
+    return Workload(name="lap3d_128cube_k10", kind="lap3d", dims=dims, h=h,
+                    sigma=sigma, k=10, tol=1e-8, prec="avmg", mg_levels=4,
+                    mg_nu=2, seed=SEED_BASE + 2)
+
+
+def _lap3_mode(mode, h) -> float:
+    return sum(4.0 / h**2 * math.sin(i * math.pi * h / 2.0) ** 2 for i in mode)
+
+
+def lap3d_small(N: int = 32, levels: int = 3, k: int = 4, gap_index: int | None = None,
+                seed: int = SEED_BASE + 12) -> Workload:
+    """Reduced 3D Laplacian with the same structure as the 128^3 problem, for
+    parity runs the oracle finishes in seconds.  The shift sits in the widest
+    gap around the requested index such that the k nearest eigenvalues are
+    complete multiplets."""
+    h = 1.0 / (N + 1)
+    lam = lap_closed_form((N, N, N), h)
+    target = gap_index if gap_index is not None else 60
+    sigma = _clean_shift(lam, target, k)
+    return Workload(name=f"lap3d_{N}cube_k{k}", kind="lap3d", dims=(N, N, N), h=h,
+                    sigma=sigma, k=k, tol=1e-8, prec="avmg", mg_levels=levels,
+                    mg_nu=2, seed=seed)
+
+
+def lap2d_small(N: int = 16, k: int = 4, gap_index: int = 20, prec: str = "none",
+                levels: int = 1, seed: int = SEED_BASE + 11) -> Workload:
+    h = 1.0 / (N + 1)
+    lam = lap_closed_form((N, N), h)
+    sigma = _clean_shift(lam, gap_index, k)
+    return Workload(name=f"lap2d_{N}sq_k{k}", kind="lap2d", dims=(N, N), h=h,
+                    sigma=sigma, k=k, tol=1e-8, prec=prec, mg_levels=levels,
+                    mg_nu=2, seed=seed)
+
+
+def _clean_shift(lam: np.ndarray, target: int, k: int) -> float:
+    """Midpoint of a gap near index ``target`` such that the k eigenvalues
+    nearest the midpoint do not split a multiplet (ties within 1e-9 relative)."""
+    best = None
+    for lo in range(max(0, target - 40), min(len(lam) - 1, target + 40)):
+        if lam[lo + 1] - lam[lo] <= 1e-9 * lam[lo + 1]:
+            continue
+        s = 0.5 * (lam[lo] + lam[lo + 1])
+        d = np.sort(np.abs(lam - s))
+        if d[k] - d[k - 1] > 1e-6 * s:  # k-th and (k+1)-th distances differ
+            score = (d[k] - d[k - 1]) / s
+            if best is None or score > best[0]:
+                best = (score, s)
+    if best is None:
+        raise ValueError("no clean shift near index %d" % target)
+    return float(best[1])
+
+
+CONFIGS = {"config1": config1, "config2": config2}
