@@ -1,0 +1,210 @@
+/*
+ * plhr.h - C ABI of the GB300 block PLHR library (libplhr.so).
+ *
+ * Block PLHR computes the k eigenpairs of the Hermitian problem
+ *     A v = lambda B v,   A = A^*,  B = B^* > 0,
+ * whose eigenvalues are closest to a real interior shift sigma
+ * (Vecharynski & Knyazev, "Preconditioned locally harmonic residual method
+ * for computing interior eigenpairs of certain classes of Hermitian
+ * matrices", Section 1, Eq. eqn:eigp), using a Hermitian positive definite
+ * preconditioner T ~ |A - sigma B|^{-1} (Section 5) and the T-harmonic
+ * Rayleigh-Ritz extraction of Algorithm 2 / Algorithm 3 (Section 4).
+ *
+ * Conventions for every entry point
+ *   - Blocks of vectors are n x ncols, row-major, FP64, in device memory:
+ *     element (i, j) sits at ptr[i * ld + j], ld >= ncols.  Grid vectors are
+ *     flattened with x fastest: i = (z * ny + y) * nx + x.
+ *   - The caller owns every pointer it passes; the library never frees or
+ *     retains them.  Opaque objects (plhr_op, plhr_prec) are owned by the
+ *     library and released with their destroy call.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Entry points
+ *     that only enqueue work return before it completes.
+ *   - Errors are returned as plhr_status; nothing aborts, traps or prints.
+ *     Invalid arguments give PLHR_EINVAL before any work is enqueued; a
+ *     failing CUDA call gives PLHR_ECUDA (plhr_last_error() has the text).
+ *   - Every entry point needs the CUDA device that holds the pointers to be
+ *     current on the calling thread.
+ */
+#ifndef PLHR_H
+#define PLHR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PLHR_OK = 0,
+    PLHR_ENOTCONV = 1,   /* maxit reached; outputs hold the best current pairs */
+    PLHR_EINVAL = 2,     /* invalid argument (null pointer, size, descriptor) */
+    PLHR_EBREAKDOWN = 3, /* projected problem not solvable (G_L not positive definite) */
+    PLHR_ENAN = 4,       /* NaN or Inf met in the iteration */
+    PLHR_ENOMEM = 5,     /* device workspace allocation failed */
+    PLHR_ECUDA = 6       /* CUDA runtime error */
+} plhr_status;
+
+/* ------------------------------------------------------------------ operators
+ * A model operator given by a stencil on a tensor grid with homogeneous
+ * Dirichlet boundary conditions.  LAP5_2D / LAP7_3D are the negative
+ * finite-difference Laplacians of Section 5.2 ("standard 5-point FD
+ * discretization"; the 7-point 3D analogue):
+ *     (L u)_i = scale * sum_axes (2 u_i - u_{i-e} - u_{i+e}) / h^2,
+ * values outside the grid taken as zero. */
+typedef enum {
+    PLHR_STENCIL_LAP5_2D = 1,
+    PLHR_STENCIL_LAP7_3D = 2
+} plhr_stencil_kind;
+
+typedef struct {
+    int kind;          /* plhr_stencil_kind */
+    int64_t dims[3];   /* grid points per axis (x, y, z); dims[2] = 1 for 2D */
+    double h;          /* mesh width, > 0 */
+    double scale;      /* multiplier of the stencil, > 0 (1 for -Laplacian) */
+} plhr_stencil_desc;
+
+typedef struct plhr_op plhr_op;
+
+/* Create a stencil operator.  *out is set only on PLHR_OK. */
+plhr_status plhr_op_stencil(plhr_op** out, const plhr_stencil_desc* desc);
+/* Number of rows n of the operator (0 for NULL). */
+int64_t plhr_op_size(const plhr_op* op);
+void plhr_op_destroy(plhr_op* op);
+
+/* Y = op X for an n x ncols block (ncols >= 0).  X and Y must not overlap. */
+plhr_status plhr_op_apply(const plhr_op* op, int ncols, const double* X, int64_t ldx,
+                          double* Y, int64_t ldy, void* stream);
+
+/* ------------------------------------------------------------- preconditioner
+ * T ~ |L - sigma I|^{-1}: the absolute-value multigrid V-cycle of Appendix A,
+ * Algorithm 4 ("AV-MG"), for a stencil Laplacian L.  On level l the smoother
+ * works with B_l = L_l when sqrt(sigma) h_l < delta, otherwise with the
+ * polynomial B_l = p_2(L_l - sigma I_l) = ((L_l - sigma I_l)^2 + c_l^2 I)/(2 c_l);
+ * nu Richardson steps w <- w + omega_l (r - B_l w) before and after the
+ * coarse-grid correction; cell-centred coarsening by two per axis (average
+ * of the 2^d children, piecewise-constant prolongation); the exact
+ * |L_0 - sigma I_0|^{-1} on the coarsest grid.  T is symmetric positive
+ * definite. */
+typedef struct {
+    int levels;        /* number of grids, >= 1 (1 = exact |L - sigma I|^{-1}) */
+    int nu;            /* smoothing steps before and after, >= 1 */
+    double delta;      /* resolution threshold for B_l = L_l (default 2 pi / 10) */
+    int transfer;      /* 0: piecewise-constant prolongation / averaging restriction;
+                          1: trilinear cell-centred prolongation (1D weights 3/4, 1/4),
+                             restriction P^T / 2^d */
+    int coarse;        /* coarsest |L_0 - sigma I_0|^{-1}: 0 = L_0 the Laplacian
+                          rediscretised with h_0 = 2^(levels-1) h; 1 = L_0 with the
+                          cell-centred sine modes as eigenvectors and the fine grid's
+                          eigenvalues of the same modes */
+} plhr_mg_opts;
+
+typedef struct plhr_prec plhr_prec;
+
+void plhr_mg_opts_default(plhr_mg_opts* o);
+/* Build the hierarchy for the stencil operator A (LAP5_2D or LAP7_3D; every
+ * axis size divisible by 2^(levels-1)).  opts NULL = defaults. */
+plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma,
+                           const plhr_mg_opts* opts);
+void plhr_prec_destroy(plhr_prec* T);
+/* W = T R for an n x ncols block.  R and W must not overlap.  Uses device
+ * workspace owned by T (grown on demand; calls on one T must not overlap). */
+plhr_status plhr_prec_apply(plhr_prec* T, int ncols, const double* R, int64_t ldr,
+                            double* W, int64_t ldw, void* stream);
+
+/* -------------------------------------------------------------------- solver */
+typedef enum {
+    PLHR_PRECISION_F64 = 0,   /* every step in FP64 */
+    PLHR_PRECISION_MIXED = 1  /* FP32 operator/preconditioner, FP64 projection */
+} plhr_precision;
+
+typedef struct {
+    int maxit;                 /* iteration cap (default 1000) */
+    int precision;             /* plhr_precision */
+    int real_arithmetic;       /* 1: Algorithm 3 with k' = k + 1 columns (default) */
+    int s_vectors;             /* 1: trial space [V W S P] (default); 0: [V W P] */
+    int soft_lock;             /* 1: converged columns add no W, S columns (default) */
+    const double* v_init;      /* device n x k' starting block, or NULL (seeded) */
+    int64_t ld_init;
+    uint64_t seed;             /* SplitMix64 seed used when v_init == NULL */
+    double* history;           /* host, history_cap * (2 k' + 3) doubles, or NULL: per
+                                  iteration [it, Ritz values (k'), rel. residuals (k'),
+                                  trial-basis columns kept, trial-basis size] ordered by
+                                  distance to sigma */
+    int history_cap;
+    int guard;                 /* extra block columns beyond k (real arithmetic: k' = k + guard,
+                                  default 1 as the paper suggests: "(at least) by 1"); more guard
+                                  columns make it less likely that a wanted pair of a degenerate
+                                  cluster is left out; 4 (k + guard) <= 64 */
+} plhr_options;
+
+typedef struct {
+    int iterations;            /* iterations taken */
+    int converged;             /* 1 when all k relative residuals <= tol */
+    double max_rel_residual;   /* max over the k returned pairs (explicit A V, B V) */
+    double setup_seconds;      /* host wall time before the first iteration */
+    double solve_seconds;      /* host wall time of the iteration loop */
+    int history_len;           /* records written to options.history */
+} plhr_info;
+
+void plhr_options_default(plhr_options* o);
+
+/* Compute the k eigenpairs of A v = lambda B v nearest sigma.
+ *   B        NULL = identity.
+ *   T        NULL = identity (no preconditioning).
+ *   tol      relative residual ||A v - lambda B v|| / (max(|lambda|, 1) ||B v||).
+ *   eigvals  host, k doubles, ordered by |lambda - sigma| (ties: smaller first).
+ *   eigvecs  device n x k block (ldv >= k), B-orthonormal Ritz vectors.
+ * Returns PLHR_OK on convergence, PLHR_ENOTCONV after maxit iterations (the
+ * outputs then hold the current approximations).  The call synchronises
+ * `stream` once per iteration. */
+plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sigma, int k,
+                       plhr_prec* T, double tol, const plhr_options* opt,
+                       double* eigvals, double* eigvecs, int64_t ldv,
+                       plhr_info* info, void* stream);
+
+/* ------------------------------------------------- projected problem (device)
+ * One extraction step of the T-harmonic Rayleigh-Ritz procedure (Section 3.1,
+ * Eq. THarm_evp, solved through Eq. THarm_evp_sinv) with the selection of
+ * Algorithm 3 steps 7-10, on device data.  The trial basis is Z D (m columns,
+ * D = diag(colscale)), its first nv columns the V block; inputs are the
+ * m x m row-major Grams Gzz = (ZD)^T B (ZD), Guq = (UD)^T (QD),
+ * Gqz = (QD)^T B (ZD) with U = (A - sigma B) Z and Q = T U.  Z is
+ * B-orthonormalised implicitly (Cholesky of the column-normalised Gzz; columns
+ * whose pivot^2 < 1e-12 are dropped), the pencil G_L y = xi G_R y is reduced
+ * with G_L = L L^T and solved by Hessenberg/Francis QR, the k' = kp
+ * eigenvectors of smallest |xi| are selected with conjugate pairs kept
+ * together (a pair cut at position kp keeps its real part), and the outputs are
+ * coefficients on the raw columns: P_new = Z C_P (Cp, m x kp) and
+ * V_new = V C_VV + P_new (Cvv, nv x kp).  tags/partner (kp ints): column kind
+ * 0 real, 1 real part of a pair, 2 cut column, 3 imaginary part, and the pair
+ * partner column; xi: 2 kp doubles (re, im of each selected unit);
+ * status (device, 3 ints): [0 ok / 1 G_L not positive definite / 2 QR did not
+ * converge / 3 rank loss, columns kept, units selected]; clk (device, 16 long
+ * long, optional): clock64 stamps of the stages.  m <= 64, kp <= 16. */
+plhr_status plhr_tharm_extract(int m, int kp, int nv, const double* Gzz, const double* Guq,
+                               const double* Gqz, const double* colscale, double* Cp, double* Cvv,
+                               int* tags, int* partner, double* xi, int* status, long long* clk,
+                               void* stream);
+
+/* ---------------------------------------------------------------- utilities */
+const char* plhr_status_string(plhr_status s);
+/* Number of CUDA kernels the library has launched in this process. */
+long long plhr_kernel_launches(void);
+/* Phase timing with CUDA events recorded on the launching stream, around the
+ * solver's phases: 0 stencil products, 1 preconditioner applications,
+ * 2 Gram pass, 3 coefficient updates, 4 small dense device stages,
+ * 5 residual pass.  Off by default; enabling adds two events per phase call. */
+void plhr_profile_enable(int on);
+/* ms[6], calls[6] (either may be NULL): accumulated milliseconds and calls per
+ * phase since the last reset; reset != 0 clears the accumulators.  Waits for
+ * the recorded events. */
+void plhr_profile_read(double* ms, long long* calls, int reset);
+/* Text of the last error recorded on the calling thread ("" if none). */
+const char* plhr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLHR_H */

@@ -1,0 +1,301 @@
+"""GB300 block PLHR: interior eigenpairs of Hermitian problems (Vecharynski &
+Knyazev, arXiv 1408.0042) on one GPU.
+
+This module is a thin ctypes binding of libplhr.so (C ABI in include/plhr.h):
+it only marshals arguments.  Every step of the solver runs in the library's
+CUDA kernels; there is no CPU fallback, and importing an entry point without a
+built library raises.  PyTorch supplies device memory and streams.
+
+    import paper_1408_0042_gb300 as plhr
+    A = plhr.Operator.laplacian((128, 128, 128), h=1/129)
+    T = plhr.AVMG(A, sigma, levels=4, nu=2)
+    lam, V, info = plhr.solve(A, sigma, k=10, T=T, tol=1e-8)
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libplhr.so")
+
+PLHR_OK, PLHR_ENOTCONV, PLHR_EINVAL, PLHR_EBREAKDOWN, PLHR_ENAN, PLHR_ENOMEM, PLHR_ECUDA = range(7)
+LAP5_2D, LAP7_3D = 1, 2
+PRECISION_F64, PRECISION_MIXED = 0, 1
+
+
+class StencilDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dims", ctypes.c_int64 * 3), ("h", ctypes.c_double),
+                ("scale", ctypes.c_double)]
+
+
+class MGOpts(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("nu", ctypes.c_int), ("delta", ctypes.c_double),
+                ("transfer", ctypes.c_int), ("coarse", ctypes.c_int)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("maxit", ctypes.c_int), ("precision", ctypes.c_int), ("real_arithmetic", ctypes.c_int),
+                ("s_vectors", ctypes.c_int), ("soft_lock", ctypes.c_int),
+                ("v_init", ctypes.c_void_p), ("ld_init", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("history", ctypes.c_void_p), ("history_cap", ctypes.c_int), ("guard", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("max_rel_residual", ctypes.c_double), ("setup_seconds", ctypes.c_double),
+                ("solve_seconds", ctypes.c_double), ("history_len", ctypes.c_int)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/plhr.h
+_SIGS = {
+    "plhr_op_stencil": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(StencilDesc)]),
+    "plhr_op_size": (ctypes.c_int64, [ctypes.c_void_p]),
+    "plhr_op_destroy": (None, [ctypes.c_void_p]),
+    "plhr_op_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "plhr_mg_opts_default": (None, [ctypes.POINTER(MGOpts)]),
+    "plhr_prec_avmg": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_double,
+                                      ctypes.POINTER(MGOpts)]),
+    "plhr_prec_destroy": (None, [ctypes.c_void_p]),
+    "plhr_prec_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "plhr_options_default": (None, [ctypes.POINTER(Options)]),
+    "plhr_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(Options),
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(Info),
+                                  ctypes.c_void_p]),
+    "plhr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "plhr_kernel_launches": (ctypes.c_longlong, []),
+    "plhr_profile_enable": (None, [ctypes.c_int]),
+    "plhr_profile_read": (None, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "plhr_last_error": (ctypes.c_char_p, []),
+    "plhr_tharm_extract": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 11
+                           + [ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libplhr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libplhr.so is not built (%s); run `python -m paper_1408_0042_gb300.build`" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class PlhrError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load_library()
+        msg = "%s: %s (%s)" % (where, lib.plhr_status_string(status).decode(), lib.plhr_last_error().decode())
+        super().__init__(msg)
+        self.status = status
+
+
+def _check(status, where):
+    if status != PLHR_OK:
+        raise PlhrError(status, where)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_block(X, n, name):
+    import torch
+    if not isinstance(X, torch.Tensor) or not X.is_cuda or X.dtype != torch.float64 or X.dim() != 2:
+        raise ValueError("%s must be a 2-D float64 CUDA tensor" % name)
+    if X.shape[0] != n:
+        raise ValueError("%s has %d rows, operator has %d" % (name, X.shape[0], n))
+    if X.stride(1) != 1 or (X.shape[0] > 1 and X.stride(0) < X.shape[1]):
+        raise ValueError("%s must be row-major with unit column stride" % name)
+
+
+class Operator:
+    """A stencil operator (Dirichlet FD Laplacian, 5-point in 2D, 7-point in 3D)."""
+
+    def __init__(self, handle, dims, h, scale):
+        self._h = handle
+        self.dims = tuple(dims)
+        self.h = h
+        self.scale = scale
+
+    @classmethod
+    def laplacian(cls, dims, h, scale=1.0):
+        lib = load_library()
+        d = StencilDesc()
+        if len(dims) == 2:
+            d.kind = LAP5_2D
+            d.dims[:] = [dims[0], dims[1], 1]
+        elif len(dims) == 3:
+            d.kind = LAP7_3D
+            d.dims[:] = list(dims)
+        else:
+            raise ValueError("dims must have 2 or 3 entries")
+        d.h = h
+        d.scale = scale
+        out = ctypes.c_void_p()
+        _check(lib.plhr_op_stencil(ctypes.byref(out), ctypes.byref(d)), "plhr_op_stencil")
+        return cls(out, dims, h, scale)
+
+    @property
+    def n(self):
+        return int(load_library().plhr_op_size(self._h))
+
+    def apply(self, X, out=None, stream=None):
+        import torch
+        _check_block(X, self.n, "X")
+        if out is None:
+            out = torch.empty_like(X)
+        _check_block(out, self.n, "out")
+        _check(load_library().plhr_op_apply(self._h, X.shape[1], ctypes.c_void_p(X.data_ptr()), X.stride(0),
+                                            ctypes.c_void_p(out.data_ptr()), out.stride(0), _stream_ptr(stream)),
+               "plhr_op_apply")
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.plhr_op_destroy(self._h)
+            self._h = None
+
+
+class AVMG:
+    """Absolute-value multigrid preconditioner T ~ |L - sigma I|^{-1} (Alg. 4)."""
+
+    def __init__(self, A: Operator, sigma: float, levels: int = 1, nu: int = 2,
+                 delta: float = 2 * math.pi / 10, transfer: int = 0, coarse: int = 0):
+        lib = load_library()
+        o = MGOpts()
+        lib.plhr_mg_opts_default(ctypes.byref(o))
+        o.levels, o.nu, o.delta, o.transfer, o.coarse = levels, nu, delta, transfer, coarse
+        out = ctypes.c_void_p()
+        _check(lib.plhr_prec_avmg(ctypes.byref(out), A._h, sigma, ctypes.byref(o)), "plhr_prec_avmg")
+        self._h = out
+        self.n = A.n
+        self.sigma = sigma
+
+    def apply(self, R, out=None, stream=None):
+        import torch
+        _check_block(R, self.n, "R")
+        if out is None:
+            out = torch.empty_like(R)
+        _check_block(out, self.n, "out")
+        _check(load_library().plhr_prec_apply(self._h, R.shape[1], ctypes.c_void_p(R.data_ptr()), R.stride(0),
+                                              ctypes.c_void_p(out.data_ptr()), out.stride(0), _stream_ptr(stream)),
+               "plhr_prec_apply")
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.plhr_prec_destroy(self._h)
+            self._h = None
+
+
+def tharm_extract(Gzz, Guq, Gqz, colscale, kp, nv, stream=None, clocks=False):
+    """Device T-harmonic extraction step (see include/plhr.h) on torch CUDA
+    float64 m x m Grams.  Returns dict with Cp (m x kp), Cvv (nv x kp), tags,
+    partner, xi (units x 2), status, and optional stage clocks."""
+    import torch
+    lib = load_library()
+    m = Gzz.shape[0]
+    dev = Gzz.device
+    Cp = torch.zeros((m, kp), dtype=torch.float64, device=dev)
+    Cvv = torch.zeros((nv, kp), dtype=torch.float64, device=dev)
+    tags = torch.zeros(kp, dtype=torch.int32, device=dev)
+    partner = torch.zeros(kp, dtype=torch.int32, device=dev)
+    xi = torch.zeros(2 * kp, dtype=torch.float64, device=dev)
+    status = torch.zeros(3, dtype=torch.int32, device=dev)
+    clk = torch.zeros(16, dtype=torch.int64, device=dev) if clocks else None
+    args = [Gzz, Guq, Gqz, colscale, Cp, Cvv, tags, partner, xi, status]
+    ptrs = [ctypes.c_void_p(t.contiguous().data_ptr()) for t in args]
+    _check(lib.plhr_tharm_extract(m, kp, nv, *ptrs, ctypes.c_void_p(clk.data_ptr()) if clk is not None else None,
+                                  _stream_ptr(stream)), "plhr_tharm_extract")
+    torch.cuda.synchronize()
+    st = status.cpu().numpy()
+    out = {"Cp": Cp.cpu().numpy(), "Cvv": Cvv.cpu().numpy(), "tags": tags.cpu().numpy(),
+           "partner": partner.cpu().numpy(), "xi": xi.cpu().numpy()[: 2 * int(st[2])].reshape(-1, 2),
+           "status": int(st[0]), "kept": int(st[1]), "units": int(st[2])}
+    if clk is not None:
+        out["clocks"] = clk.cpu().numpy()
+    return out
+
+
+PHASES = ("stencil", "preconditioner", "gram", "update", "dense", "residual")
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load_library().plhr_kernel_launches())
+
+
+def profile_enable(on: bool = True) -> None:
+    load_library().plhr_profile_enable(1 if on else 0)
+
+
+def profile_read(reset: bool = False) -> dict:
+    """Accumulated CUDA-event time (ms) and calls per solver phase."""
+    ms = (ctypes.c_double * 6)()
+    calls = (ctypes.c_longlong * 6)()
+    load_library().plhr_profile_read(ms, calls, 1 if reset else 0)
+    return {name: {"ms": ms[i], "calls": calls[i]} for i, name in enumerate(PHASES)}
+
+
+def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float = 1e-8, maxit: int = 1000,
+          v_init=None, seed: int = 20140801, history: bool = False, precision: int = PRECISION_F64,
+          stream=None, raise_on_notconv: bool = False, guard: int = 1):
+    """k eigenpairs of A v = lambda v nearest sigma with k + guard block
+    columns.  Returns (eigvals (numpy, k), eigvecs (torch n x k float64,
+    CUDA), info dict)."""
+    import torch
+    lib = load_library()
+    n = A.n
+    kp = k + guard
+    opt = Options()
+    lib.plhr_options_default(ctypes.byref(opt))
+    opt.maxit = maxit
+    opt.precision = precision
+    opt.seed = seed
+    opt.guard = guard
+    if v_init is not None:
+        _check_block(v_init, n, "v_init")
+        if v_init.shape[1] < kp:
+            raise ValueError("v_init needs k + guard columns")
+        opt.v_init = v_init.data_ptr()
+        opt.ld_init = v_init.stride(0)
+    hist = None
+    rl = 2 * kp + 3
+    if history:
+        hist = np.zeros((maxit + 2) * rl, dtype=np.float64)
+        opt.history = hist.ctypes.data
+        opt.history_cap = maxit + 2
+    vals = np.zeros(k, dtype=np.float64)
+    vecs = torch.empty((n, k), dtype=torch.float64, device="cuda")
+    info = Info()
+    st = lib.plhr_solve(A._h, None, sigma, k, T._h if T is not None else None, tol, ctypes.byref(opt),
+                        vals.ctypes.data, ctypes.c_void_p(vecs.data_ptr()), k, ctypes.byref(info),
+                        _stream_ptr(stream))
+    if st not in (PLHR_OK, PLHR_ENOTCONV) or (raise_on_notconv and st == PLHR_ENOTCONV):
+        raise PlhrError(st, "plhr_solve")
+    out = {"status": st, "iterations": info.iterations, "converged": bool(info.converged),
+           "max_rel_residual": info.max_rel_residual, "setup_seconds": info.setup_seconds,
+           "solve_seconds": info.solve_seconds}
+    if hist is not None:
+        rec = hist[: info.history_len * rl].reshape(info.history_len, rl)
+        out["history"] = [{"it": int(r[0]), "lam": r[1:1 + k].copy(), "rel": r[1 + kp:1 + kp + k].copy(),
+                           "lam_all": r[1:1 + kp].copy(), "rel_all": r[1 + kp:1 + 2 * kp].copy(),
+                           "kept": int(r[1 + 2 * kp]), "m": int(r[2 + 2 * kp])} for r in rec]
+    return vals, vecs, out

@@ -1,0 +1,49 @@
+// Tall-skinny block kernels (residual, multi-Gram, coefficient update).
+#pragma once
+
+#include "plhr_internal.h"
+
+namespace plhr {
+
+int reduce_blocks();
+int residual_blocks(int kp);
+int gram_max_m();
+
+// R = sc_j (AV_j - lam_j V_j); out[0:kp] = sum R^2, out[kp:2kp] = sum (sc V)^2.
+// partial: residual_blocks(kp) * 2 * kp doubles.
+cudaError_t residual_norms(int64_t n, int kp, const double* V, int64_t ldv, const double* AV, int64_t ldav,
+                           const double* lam, const double* sc, double* R, int64_t ldr, double* partial,
+                           double* out, cudaStream_t s);
+
+// Over nb blocks per family (Z, AZ, Q), columns scaled by colscale:
+// out = [Z^T Z | U^T Q | Q^T Z] (3 m x m, row-major), U = AZ - sigma Z.
+// Q == nullptr means Q = U (preconditioner T = I).
+// partial: reduce_blocks() * 3 * m * m doubles.
+cudaError_t multi_gram(int64_t n, int nb, const Blk<const double>* Z, const Blk<const double>* AZ,
+                       const Blk<const double>* Q, double sigma, const double* colscale, double* partial,
+                       double* out, cudaStream_t s);
+
+// Family F = [F_0 .. F_{nb-1}] (m columns): Pout = F C_P, Vout = F_0 C_VV + F C_P
+// (in place allowed: Vout may be F_0, Pout may be F_{nb-1}).  When dotV is
+// given, out[0:kp] = sum Vout .* dotV, out[kp:2kp] = sum dotV .^ 2.
+cudaError_t block_update(int64_t n, int nb, const Blk<const double>* F, int kp, const double* Cp,
+                         const double* Cvv, double* Vout, int64_t ldvo, double* Pout, int64_t ldpo,
+                         const double* dotV, int64_t lddv, double* partial, double* out, cudaStream_t s);
+
+// Y = X C for X n x kx (ldx), C kx x ky (row-major); in place allowed when
+// ky <= kx and Y == X (rows are staged).
+cudaError_t block_times_small(int64_t n, const double* X, int64_t ldx, int kx, const double* C, int ky, double* Y,
+                              int64_t ldy, cudaStream_t s);
+
+// Gather columns: Y[:, j] = X[:, idx[j]] for j < nc (device idx).
+cudaError_t gather_columns(int64_t n, const double* X, int64_t ldx, const int* idx, int nc, double* Y, int64_t ldy,
+                           cudaStream_t s);
+
+// out[j] = sum_i X_ij Y_ij, out[kc + j] = sum_i X_ij^2 (partial: residual_blocks(kc) * 2 kc)
+cudaError_t column_dots(int64_t n, int kc, const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                        double* partial, double* out, cudaStream_t s);
+
+// Seeded starting block: element (i, j) = (SplitMix64 output i*kc + j + 1 >> 11) * 2^-53 - 0.5.
+cudaError_t seeded_block(int64_t n, int kc, uint64_t seed, double* X, int64_t ldx, cudaStream_t s);
+
+}  // namespace plhr

@@ -1,0 +1,247 @@
+// C ABI: error state, stencil operators, the AV-MG preconditioner object.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "plhr_internal.h"
+
+namespace plhr {
+
+namespace {
+thread_local char g_err[512] = {0};
+}
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+int sm_count() {
+    static int cached = 0;
+    if (cached == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            cached = v;
+        else
+            cached = 132;
+    }
+    return cached;
+}
+
+}  // namespace plhr
+
+using namespace plhr;
+
+extern "C" {
+
+const char* plhr_last_error(void) { return g_err; }
+
+const char* plhr_status_string(plhr_status s) {
+    switch (s) {
+        case PLHR_OK: return "ok";
+        case PLHR_ENOTCONV: return "not converged within maxit";
+        case PLHR_EINVAL: return "invalid argument";
+        case PLHR_EBREAKDOWN: return "breakdown of the projected problem";
+        case PLHR_ENAN: return "NaN or Inf in the iteration";
+        case PLHR_ENOMEM: return "device allocation failed";
+        case PLHR_ECUDA: return "CUDA error";
+    }
+    return "unknown status";
+}
+
+plhr_status plhr_op_stencil(plhr_op** out, const plhr_stencil_desc* d) {
+    clear_error();
+    if (!out || !d) { set_error("plhr_op_stencil: null argument"); return PLHR_EINVAL; }
+    if (d->kind != PLHR_STENCIL_LAP5_2D && d->kind != PLHR_STENCIL_LAP7_3D) {
+        set_error("plhr_op_stencil: unknown kind %d", d->kind);
+        return PLHR_EINVAL;
+    }
+    if (d->dims[0] < 1 || d->dims[1] < 1 || d->dims[2] < 1 || !(d->h > 0) || !(d->scale > 0)) {
+        set_error("plhr_op_stencil: bad dims/h/scale");
+        return PLHR_EINVAL;
+    }
+    if (d->kind == PLHR_STENCIL_LAP5_2D && d->dims[2] != 1) {
+        set_error("plhr_op_stencil: 2D stencil needs dims[2] == 1");
+        return PLHR_EINVAL;
+    }
+    plhr_op* op = new plhr_op;
+    op->kind = d->kind;
+    op->g.d = d->kind == PLHR_STENCIL_LAP7_3D ? 3 : 2;
+    op->g.nx = d->dims[0];
+    op->g.ny = d->dims[1];
+    op->g.nz = d->dims[2];
+    op->g.h = d->h;
+    op->g.scale = d->scale;
+    *out = op;
+    return PLHR_OK;
+}
+
+int64_t plhr_op_size(const plhr_op* op) { return op ? op->g.n() : 0; }
+
+void plhr_op_destroy(plhr_op* op) { delete op; }
+
+plhr_status plhr_op_apply(const plhr_op* op, int ncols, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                          void* stream) {
+    clear_error();
+    if (!op || ncols < 0 || (ncols > 0 && (!X || !Y)) || ldx < ncols || ldy < ncols) {
+        set_error("plhr_op_apply: invalid argument");
+        return PLHR_EINVAL;
+    }
+    if (ncols == 0) return PLHR_OK;
+    PLHR_TRY_CUDA(lap_axpby(op->g, ncols, X, ldx, Y, ldy, 1.0, 0.0, (cudaStream_t)stream));
+    return PLHR_OK;
+}
+
+void plhr_mg_opts_default(plhr_mg_opts* o) {
+    if (!o) return;
+    o->levels = 1;
+    o->nu = 2;
+    o->delta = 2.0 * M_PI / 10.0;
+    o->transfer = 0;
+    o->coarse = 0;
+}
+
+plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma, const plhr_mg_opts* opts) {
+    clear_error();
+    plhr_mg_opts o;
+    plhr_mg_opts_default(&o);
+    if (opts) o = *opts;
+    if (!out || !A) { set_error("plhr_prec_avmg: null argument"); return PLHR_EINVAL; }
+    if (o.levels < 1 || o.nu < 1 || !(o.delta > 0) || (o.transfer != 0 && o.transfer != 1) ||
+        (o.coarse != 0 && o.coarse != 1) || !std::isfinite(sigma)) {
+        set_error("plhr_prec_avmg: bad options");
+        return PLHR_EINVAL;
+    }
+    const Grid& g = A->g;
+    const int64_t f = (int64_t)1 << (o.levels - 1);
+    if (g.nx % f || g.ny % f || (g.d == 3 && g.nz % f)) {
+        set_error("plhr_prec_avmg: axis sizes must be divisible by 2^(levels-1) = %lld", (long long)f);
+        return PLHR_EINVAL;
+    }
+    plhr_prec* T = new plhr_prec;
+    MGHierarchy& H = T->H;
+    H.dim = g.d;
+    H.nu = o.nu;
+    H.linear = o.transfer;
+    H.sigma = sigma;
+    H.lev.resize(o.levels);
+    for (int l = o.levels - 1, s = 0; l >= 0; --l, ++s) {
+        MGLevel& L = H.lev[l];
+        int64_t sc = (int64_t)1 << s;
+        L.g = g;
+        L.g.nx = g.nx / sc;
+        L.g.ny = g.ny / sc;
+        L.g.nz = g.d == 3 ? g.nz / sc : 1;
+        L.g.h = g.h * (double)sc;
+        // Gershgorin interval of L_l - sigma I: [-sigma, 4 d scale / h_l^2 - sigma]
+        double a = -sigma, b = 4.0 * g.d * L.g.inv_h2() - sigma;
+        L.poly = !(std::sqrt(std::fmax(sigma, 0.0)) * L.g.h < o.delta);
+        if (L.poly) {
+            L.c = 0.5 * std::fmax(std::fabs(a), std::fabs(b));
+            double beta = (std::fmax(a * a, b * b) + L.c * L.c) / (2.0 * L.c);
+            L.omega = 1.0 / beta;
+        } else {
+            L.c = 0.0;
+            L.omega = 1.0 / (4.0 * g.d * L.g.inv_h2());
+        }
+    }
+    // coarsest separable basis and eigenvalues per axis
+    const Grid& g0 = H.lev[0].g;
+    int64_t N0[3] = {g0.nx, g0.ny, g0.nz};
+    int64_t Nf[3] = {g.nx, g.ny, g.nz};
+    for (int ax = 0; ax < g.d; ++ax) {
+        int64_t N = N0[ax];
+        std::vector<double> S(N * N), mu(N);
+        for (int64_t m = 0; m < N; ++m) {
+            if (o.coarse == 0) {
+                mu[m] = 4.0 * g0.inv_h2() * std::pow(std::sin((m + 1) * M_PI / (2.0 * (N + 1))), 2);
+                for (int64_t p = 0; p < N; ++p)
+                    S[p * N + m] = std::sqrt(2.0 / (N + 1)) * std::sin((p + 1) * (m + 1) * M_PI / (N + 1));
+            } else {
+                mu[m] = 4.0 * g.inv_h2() * std::pow(std::sin((m + 1) * M_PI / (2.0 * (Nf[ax] + 1))), 2);
+                double nrm = (m == N - 1) ? std::sqrt(1.0 / N) : std::sqrt(2.0 / N);
+                for (int64_t p = 0; p < N; ++p) S[p * N + m] = nrm * std::sin((p + 0.5) * (m + 1) * M_PI / N);
+            }
+        }
+        if (cudaMalloc(&H.d_basis[ax], sizeof(double) * N * N) != cudaSuccess ||
+            cudaMalloc(&H.d_mu[ax], sizeof(double) * N) != cudaSuccess) {
+            set_error("plhr_prec_avmg: cudaMalloc failed");
+            plhr_prec_destroy(T);
+            return PLHR_ENOMEM;
+        }
+        if (cudaMemcpy(H.d_basis[ax], S.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(H.d_mu[ax], mu.data(), sizeof(double) * N, cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_error("plhr_prec_avmg: upload failed");
+            plhr_prec_destroy(T);
+            return PLHR_ECUDA;
+        }
+        H.n0[ax] = N;
+    }
+    int64_t n0 = g0.n();
+    if (2 * n0 * (int64_t)sizeof(double) > 200 * 1024) {
+        set_error("plhr_prec_avmg: coarsest grid of %lld points exceeds the single-CTA solve", (long long)n0);
+        plhr_prec_destroy(T);
+        return PLHR_EINVAL;
+    }
+    *out = T;
+    return PLHR_OK;
+}
+
+void plhr_prec_destroy(plhr_prec* T) {
+    if (!T) return;
+    for (int a = 0; a < 3; ++a) {
+        if (T->H.d_basis[a]) cudaFree(T->H.d_basis[a]);
+        if (T->H.d_mu[a]) cudaFree(T->H.d_mu[a]);
+    }
+    if (T->work) cudaFree(T->work);
+    delete T;
+}
+
+}  // extern "C"
+
+namespace plhr {
+plhr_status prec_reserve(plhr_prec* T, int nc, int64_t extra_doubles) {
+    int64_t need = mg_workspace_doubles(T->H, nc) + extra_doubles;
+    if (need <= T->work_doubles) return PLHR_OK;
+    if (T->work) {
+        cudaDeviceSynchronize();
+        cudaFree(T->work);
+        T->work = nullptr;
+        T->work_doubles = 0;
+    }
+    if (need == 0) return PLHR_OK;
+    if (cudaMalloc(&T->work, sizeof(double) * need) != cudaSuccess) {
+        set_error("prec workspace: cudaMalloc of %lld doubles failed", (long long)need);
+        return PLHR_ENOMEM;
+    }
+    T->work_doubles = need;
+    return PLHR_OK;
+}
+}  // namespace plhr
+
+extern "C" plhr_status plhr_prec_apply(plhr_prec* T, int ncols, const double* R, int64_t ldr, double* W, int64_t ldw,
+                                       void* stream) {
+    clear_error();
+    if (!T || ncols < 0 || (ncols > 0 && (!R || !W)) || ldr < ncols || ldw < ncols) {
+        set_error("plhr_prec_apply: invalid argument");
+        return PLHR_EINVAL;
+    }
+    if (ncols == 0) return PLHR_OK;
+    const int64_t n = T->H.lev.back().g.n();
+    const int64_t stage = (ldw == ncols) ? 0 : n * ncols;
+    PLHR_TRY(prec_reserve(T, ncols, stage));
+    cudaStream_t s = (cudaStream_t)stream;
+    double* out = (ldw == ncols) ? W : T->work + mg_workspace_doubles(T->H, ncols);
+    PLHR_TRY_CUDA(mg_vcycle(T->H, ncols, R, ldr, out, ncols, T->work, s));
+    if (ldw != ncols)
+        PLHR_TRY_CUDA(cudaMemcpy2DAsync(W, sizeof(double) * ldw, out, sizeof(double) * ncols, sizeof(double) * ncols,
+                                        n, cudaMemcpyDeviceToDevice, s));
+    return PLHR_OK;
+}

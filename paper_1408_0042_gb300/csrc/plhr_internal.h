@@ -1,0 +1,124 @@
+// Internal declarations shared by the translation units of libplhr.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "plhr.h"
+
+namespace plhr {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define PLHR_TRY_CUDA(call)                                                    \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            ::plhr::set_error("%s failed: %s (%s:%d)", #call,                  \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);     \
+            return PLHR_ECUDA;                                                 \
+        }                                                                      \
+    } while (0)
+
+#define PLHR_TRY(expr)                                                         \
+    do {                                                                       \
+        plhr_status s_ = (expr);                                               \
+        if (s_ != PLHR_OK) return s_;                                          \
+    } while (0)
+
+// Launch check: the kernel launch itself (configuration) failed.
+#define PLHR_LAUNCHED() PLHR_TRY_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------- grids
+// Tensor grid with homogeneous Dirichlet boundary, x fastest.
+struct Grid {
+    int d = 3;            // 2 or 3
+    int64_t nx = 1, ny = 1, nz = 1;
+    double h = 1.0;
+    double scale = 1.0;   // stencil multiplier
+    int64_t n() const { return nx * ny * nz; }
+    double inv_h2() const { return scale / (h * h); }
+};
+
+// A block of row-major vectors: element (i, j) at p[i * ld + j].
+template <typename T>
+struct Blk {
+    T* p = nullptr;
+    int64_t ld = 0;
+    int nc = 0;
+};
+
+inline int grid_size_for(int64_t work, int threads, int max_blocks) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+int sm_count();
+
+// Kernel launches issued by the library (all entry points, process-wide).
+void count_launches(int n);
+
+// Optional phase timing with CUDA events on the launching stream.
+enum Phase { PH_STENCIL = 0, PH_VCYCLE = 1, PH_GRAM = 2, PH_UPDATE = 3, PH_DENSE = 4, PH_OTHER = 5, PH_COUNT = 6 };
+struct PhaseScope {
+    PhaseScope(int phase, cudaStream_t s);
+    ~PhaseScope();
+    int phase;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+void profile_flush();   // accumulate finished event pairs (synchronises their events)
+
+// ---------------------------------------------------------------- stencil
+// y = alpha * L x + beta * x   (L: scaled Dirichlet Laplacian of g)
+cudaError_t lap_axpby(const Grid& g, int nc, const double* x, int64_t ldx, double* y,
+                      int64_t ldy, double alpha, double beta, cudaStream_t s);
+// ax = L x; o1 = ax - x * diag(lam) (optional); o2 = ax - sig * x (optional)
+cudaError_t lap_apply_shifts(const Grid& g, int nc, const double* x, int64_t ldx,
+                             double* ax, int64_t ldax, double* o1, int64_t ld1,
+                             const double* lam, double* o2, int64_t ld2, double sig,
+                             cudaStream_t s);
+
+// ---------------------------------------------------------------- multigrid
+struct MGLevel {
+    Grid g;
+    bool poly = false;    // B_l = p_2(L_l - sigma I) instead of L_l
+    double c = 0.0;       // p_2 parameter
+    double omega = 0.0;   // Richardson step 1 / beta_l
+};
+
+struct MGHierarchy {
+    int dim = 3;
+    int nu = 2;
+    int linear = 0;                    // 1: trilinear cell-centred transfers, 0: piecewise constant
+    double sigma = 0.0;
+    std::vector<MGLevel> lev;          // 0 = coarsest
+    // coarsest solve: w = S3 diag(1/|mu_i + mu_j + mu_k - sigma|) S3^T r with
+    // S3 = Sx (x) Sy (x) Sz (orthonormal 1D bases) and 1D eigenvalues mu
+    double* d_basis[3] = {nullptr, nullptr, nullptr};   // N_a x N_a, row-major [point][mode]
+    double* d_mu[3] = {nullptr, nullptr, nullptr};
+    int64_t n0[3] = {1, 1, 1};
+};
+
+cudaError_t mg_vcycle(const MGHierarchy& H, int nc, const double* r, int64_t ldr, double* w,
+                      int64_t ldw, double* work, cudaStream_t s);
+int64_t mg_workspace_doubles(const MGHierarchy& H, int nc);
+
+}  // namespace plhr
+
+struct plhr_op {
+    int kind;
+    plhr::Grid g;
+};
+
+struct plhr_prec {
+    plhr::MGHierarchy H;
+    double* work = nullptr;
+    int64_t work_doubles = 0;
+};

@@ -1,0 +1,431 @@
+// Block PLHR driver (Algorithm 3, real arithmetic; FP64 path).  Every step of
+// the iteration runs on the device; the host enqueues kernels and reads one
+// small status record per iteration (convergence flags, Ritz values).
+//
+// Stored state (n rows each, row-major):
+//   V, AV, QV      current block and its images A V, T(A - sigma B) V (k' columns,
+//                  stored unnormalised; `scale` holds the B-normalising factors
+//                  of Alg. 3 step 14, applied wherever V is used)
+//   P, AP, QP      conjugate directions and images (k' columns, absent at it 0)
+//   W, AW          preconditioned residuals of the active columns (Alg. 3 step 4)
+//   SQ = [S | Q_W] s-vectors (step 5) and T(A - sigma B) W, one 2 n_a-wide V-cycle
+//   AS, QS         A S and T(A - sigma B) S
+// Per iteration: 2 block products with A (W, S) and 4 applications of T
+// (W, S, Q_W, Q_S), as in the storage/cost paragraph after Algorithm 2.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "blockops.h"
+#include "dense.h"
+#include "plhr_internal.h"
+
+namespace plhr {
+plhr_status prec_reserve(plhr_prec* T, int nc, int64_t extra_doubles);
+}
+
+using namespace plhr;
+
+namespace {
+
+struct DevBuf {
+    double* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+struct HostStatus {
+    int conv, nact, nan;
+    int dense[3];
+    int rr_ok;
+    int pad;
+};
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+extern "C" void plhr_options_default(plhr_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->maxit = 1000;
+    o->precision = PLHR_PRECISION_F64;
+    o->real_arithmetic = 1;
+    o->s_vectors = 1;
+    o->soft_lock = 1;
+    o->seed = 20140801ull;
+    o->guard = 1;
+}
+
+extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sigma, int k, plhr_prec* T, double tol,
+                                  const plhr_options* opt_in, double* eigvals, double* eigvecs, int64_t ldv,
+                                  plhr_info* info, void* stream) {
+    clear_error();
+    const double t0 = now_s();
+    plhr_options opt;
+    plhr_options_default(&opt);
+    if (opt_in) opt = *opt_in;
+    if (!A || !eigvals || !eigvecs || k < 1 || ldv < k || !(tol > 0) || !std::isfinite(sigma) || opt.maxit < 0) {
+        set_error("plhr_solve: invalid argument");
+        return PLHR_EINVAL;
+    }
+    if (B != nullptr) {
+        set_error("plhr_solve: only B = identity is supported by this build");
+        return PLHR_EINVAL;
+    }
+    if (!opt.real_arithmetic || opt.precision != PLHR_PRECISION_F64 || !opt.s_vectors) {
+        set_error("plhr_solve: this build supports real arithmetic, FP64, with s-vectors");
+        return PLHR_EINVAL;
+    }
+    const int64_t n = A->g.n();
+    if (opt.guard < 0) {
+        set_error("plhr_solve: guard < 0");
+        return PLHR_EINVAL;
+    }
+    const int kp = k + opt.guard;
+    const int mmax = 4 * kp;
+    if (mmax > kDenseMaxM || mmax > gram_max_m() || kp > 32) {
+        set_error("plhr_solve: k + guard = %d too large (4 (k + guard) must be <= %d)", kp, kDenseMaxM);
+        return PLHR_EINVAL;
+    }
+    if (n < (int64_t)mmax) {
+        set_error("plhr_solve: n = %lld too small for k = %d", (long long)n, k);
+        return PLHR_EINVAL;
+    }
+    if (T && T->H.lev.back().g.n() != n) {
+        set_error("plhr_solve: preconditioner size does not match A");
+        return PLHR_EINVAL;
+    }
+    if (opt.v_init && opt.ld_init < kp) {
+        set_error("plhr_solve: ld_init < k + guard");
+        return PLHR_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Grid& g = A->g;
+
+    // ---------------------------------------------------------------- workspace
+    const int64_t nk = n * kp;
+    const int64_t big_doubles = 6 * nk /*V AV QV P AP QP*/ + nk /*R*/ + nk /*Rc*/ + nk /*W*/ + nk /*AW*/ +
+                                2 * nk /*SQ*/ + 2 * nk /*X2*/ + nk /*AS*/ + nk /*X3*/ + nk /*QS*/;
+    const int m3 = 3 * mmax * mmax;
+    const int64_t part_doubles = (int64_t)reduce_blocks() * m3 + (int64_t)residual_blocks(kp) * 2 * kp + 64;
+    const int64_t small_doubles = m3 /*grams*/ + (int64_t)dense_work_doubles() + mmax * kp /*Cp*/ + kp * kp /*Cvv*/ +
+                                  8 * 64 /*vectors*/ + kp * kp /*Crr*/ + 2 * 64 /*xi*/;
+    DevBuf big, part, small;
+    if (cudaMallocAsync(&big.p, sizeof(double) * big_doubles, s) != cudaSuccess ||
+        cudaMallocAsync(&part.p, sizeof(double) * part_doubles, s) != cudaSuccess ||
+        cudaMallocAsync(&small.p, sizeof(double) * small_doubles, s) != cudaSuccess) {
+        set_error("plhr_solve: device allocation of %.1f MB failed", 8e-6 * (double)(big_doubles + part_doubles));
+        return PLHR_ENOMEM;
+    }
+    int* ints = nullptr;
+    if (cudaMallocAsync(&ints, sizeof(int) * 512, s) != cudaSuccess) {
+        set_error("plhr_solve: device allocation failed");
+        return PLHR_ENOMEM;
+    }
+    struct IntFree { int* p; ~IntFree() { if (p) cudaFree(p); } } int_free{ints};
+    HostStatus* hs = nullptr;
+    if (cudaMallocHost(&hs, sizeof(HostStatus) + sizeof(double) * 4 * 64) != cudaSuccess) {
+        set_error("plhr_solve: pinned allocation failed");
+        return PLHR_ENOMEM;
+    }
+    struct HostFree { void* p; ~HostFree() { if (p) cudaFreeHost(p); } } host_free{hs};
+    double* h_rel = reinterpret_cast<double*>(hs + 1);
+    double* h_lam = h_rel + 64;
+    double* h_theta = h_lam + 64;
+    int* h_order = reinterpret_cast<int*>(h_theta + 64);
+
+    double* p = big.p;
+    auto take = [&](int64_t cnt) { double* r = p; p += cnt; return r; };
+    double *V = take(nk), *AV = take(nk), *QV = take(nk), *P = take(nk), *AP = take(nk), *QP = take(nk);
+    double *R = take(nk), *Rc = take(nk), *W = take(nk), *AW = take(nk), *SQ = take(2 * nk), *X2 = take(2 * nk);
+    double *AS = take(nk), *X3 = take(nk), *QS = take(nk);
+    double* gpart = part.p;
+    double* rpart = part.p + (int64_t)reduce_blocks() * m3;
+    double* q = small.p;
+    double* grams = q; q += m3;
+    double* dwork = q; q += dense_work_doubles();
+    double* Cp = q; q += mmax * kp;
+    double* Cvv = q; q += kp * kp;
+    double* sums = q; q += 64;
+    double* lam = q; q += 64;
+    double* scale = q; q += 64;
+    double* colscale = q; q += 64;
+    double* rel = q; q += 64;
+    double* lam_act = q; q += 64;
+    double* dots = q; q += 64;
+    double* theta = q; q += 64;
+    double* Crr = q; q += kp * kp;
+    double* xi = q; q += 128;
+    int* active = ints;
+    int* order = ints + 64;
+    int* tags = ints + 128;
+    int* partner = ints + 192;
+    int* dstat = ints + 256;   // [conv, nact, nan, dense0, dense1, dense2, rr_ok]
+    if (T) PLHR_TRY(prec_reserve(T, 2 * kp, 0));
+
+    // colscale = 1 everywhere (the V part is overwritten every iteration)
+    {
+        std::vector<double> ones(64, 1.0);
+        PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, ones.data(), sizeof(double) * 64, cudaMemcpyHostToDevice, s));
+        PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+
+    auto applyT = [&](int nc, const double* r, int64_t ldr, double* w) -> plhr_status {
+        // w (ld nc) = T r
+        if (nc == 0) return PLHR_OK;
+        if (!T) {
+            PLHR_TRY_CUDA(cudaMemcpy2DAsync(w, sizeof(double) * nc, r, sizeof(double) * ldr, sizeof(double) * nc, n,
+                                            cudaMemcpyDeviceToDevice, s));
+            return PLHR_OK;
+        }
+        PhaseScope ps(PH_VCYCLE, s);
+        PLHR_TRY_CUDA(mg_vcycle(T->H, nc, r, ldr, w, nc, T->work, s));
+        return PLHR_OK;
+    };
+
+    // ---------------------------------------------------------------- start (Alg. 3 steps 1-2)
+    if (opt.v_init)
+        PLHR_TRY_CUDA(cudaMemcpy2DAsync(V, sizeof(double) * kp, opt.v_init, sizeof(double) * opt.ld_init,
+                                        sizeof(double) * kp, n, cudaMemcpyDeviceToDevice, s));
+    else
+        PLHR_TRY_CUDA(seeded_block(n, kp, opt.seed, V, kp, s));
+    // AV, X3 := AV - sigma V, QV = T(AV - sigma V) (with T = I, Q = AZ - sigma Z is
+    // formed inside the Gram pass and no Q block is stored)
+    PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
+    if (T) PLHR_TRY(applyT(kp, X3, kp, QV));
+    PLHR_TRY_CUDA(column_dots(n, kp, V, kp, AV, kp, rpart, dots, s));   // v.Av, v.v
+    {
+        std::vector<int> zeros(64, 0), neg(64, -1);
+        PLHR_TRY_CUDA(cudaMemcpyAsync(tags, zeros.data(), sizeof(int) * 64, cudaMemcpyHostToDevice, s));
+        PLHR_TRY_CUDA(cudaMemcpyAsync(partner, neg.data(), sizeof(int) * 64, cudaMemcpyHostToDevice, s));
+        PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    PLHR_TRY_CUDA(dense_rq(kp, dots, tags, partner, lam, scale, s));
+    int np = 0;
+
+    // images of V and P under A: explicit stencil products after every update
+    // (no recursion, so no drift), dots for the Rayleigh quotients of V
+    auto refresh_images = [&]() -> plhr_status {
+        PhaseScope ps(PH_STENCIL, s);
+        PLHR_TRY_CUDA(lap_axpby(g, kp, V, kp, AV, kp, 1.0, 0.0, s));
+        if (np) PLHR_TRY_CUDA(lap_axpby(g, kp, P, kp, AP, kp, 1.0, 0.0, s));
+        PLHR_TRY_CUDA(column_dots(n, kp, V, kp, AV, kp, rpart, dots, s));
+        return PLHR_OK;
+    };
+
+    const double t1 = now_s();
+    plhr_status result = PLHR_ENOTCONV;
+    int it = 0;
+    int hist = 0;
+    int last_m = 0;
+    int last_kept = 0;
+    for (it = 0; it <= opt.maxit; ++it) {
+        // -------------------------------------------- residual, convergence (step 4 input)
+        {
+            PhaseScope ps(PH_OTHER, s);
+            PLHR_TRY_CUDA(residual_norms(n, kp, V, kp, AV, kp, lam, scale, R, kp, rpart, sums, s));
+        }
+        StatusArgs sa;
+        sa.kp = kp; sa.k = k; sa.sigma = sigma; sa.tol = tol;
+        sa.sums = sums; sa.lam = lam; sa.lam_act = lam_act; sa.active = active; sa.rel = rel; sa.order = order;
+        sa.hstat = dstat;
+        PLHR_TRY_CUDA(dense_status(sa, s));
+        PLHR_TRY_CUDA(cudaMemcpyAsync(hs, dstat, sizeof(int) * 7, cudaMemcpyDeviceToHost, s));
+        PLHR_TRY_CUDA(cudaMemcpyAsync(h_rel, rel, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+        PLHR_TRY_CUDA(cudaMemcpyAsync(h_lam, lam, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+        PLHR_TRY_CUDA(cudaMemcpyAsync(h_order, order, sizeof(int) * kp, cudaMemcpyDeviceToHost, s));
+        PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+        if (hs->nan) {
+            set_error("plhr_solve: NaN/Inf at iteration %d", it);
+            result = PLHR_ENAN;
+            break;
+        }
+        if (opt.history && hist < opt.history_cap) {
+            double* rec = opt.history + (int64_t)hist * (2 * kp + 3);
+            rec[0] = it;
+            for (int q2 = 0; q2 < kp; ++q2) {
+                rec[1 + q2] = h_lam[h_order[q2]];
+                rec[1 + kp + q2] = h_rel[h_order[q2]];
+            }
+            rec[1 + 2 * kp] = last_kept;
+            rec[2 + 2 * kp] = last_m;
+            ++hist;
+        }
+        if (hs->conv) {
+            // final standard Rayleigh-Ritz (Alg. 3 step 16) and acceptance on the
+            // returned vectors: explicit A V, B V
+            PLHR_TRY_CUDA(lap_axpby(g, kp, V, kp, AW, kp, 1.0, 0.0, s));
+            Blk<const double> zb[1] = {{V, kp, kp}}, ab[1] = {{AW, kp, kp}}, qb[1] = {{V, kp, kp}};
+            PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
+            PLHR_TRY_CUDA(multi_gram(n, 1, zb, ab, qb, 0.0, colscale, gpart, grams, s));
+            // grams: [V^T V | (AV)^T V | V^T V] (kp x kp blocks)
+            PLHR_TRY_CUDA(dense_rr(kp, grams + kp * kp, grams, sigma, scale, Crr, theta, dstat + 6, s));
+            PLHR_TRY_CUDA(block_times_small(n, V, kp, kp, Crr, kp, Rc, kp, s));   // all Ritz vectors
+            PLHR_TRY_CUDA(lap_axpby(g, kp, Rc, kp, AW, kp, 1.0, 0.0, s));
+            {
+                std::vector<double> ones(kp, 1.0);
+                PLHR_TRY_CUDA(cudaMemcpyAsync(dots, ones.data(), sizeof(double) * kp, cudaMemcpyHostToDevice, s));
+            }
+            PLHR_TRY_CUDA(residual_norms(n, kp, Rc, kp, AW, kp, theta, dots, R, kp, rpart, sums, s));
+            sa.lam = theta;
+            PLHR_TRY_CUDA(dense_status(sa, s));
+            PLHR_TRY_CUDA(cudaMemcpyAsync(hs, dstat, sizeof(int) * 7, cudaMemcpyDeviceToHost, s));
+            PLHR_TRY_CUDA(cudaMemcpyAsync(h_rel, rel, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+            PLHR_TRY_CUDA(cudaMemcpyAsync(h_theta, theta, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+            PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+            if (!hs->rr_ok) {
+                set_error("plhr_solve: final Rayleigh-Ritz failed");
+                result = PLHR_EBREAKDOWN;
+                break;
+            }
+            bool acc = true;
+            for (int q2 = 0; q2 < k; ++q2) acc = acc && (h_rel[q2] <= tol);
+            if (acc) {
+                result = PLHR_OK;
+                break;
+            }
+            // carry on from the rotated block (same span): V <- V C, A V explicit
+            PLHR_TRY_CUDA(cudaMemcpyAsync(V, Rc, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
+            PLHR_TRY_CUDA(cudaMemcpyAsync(AV, AW, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
+            if (T) PLHR_TRY_CUDA(block_times_small(n, QV, kp, kp, Crr, kp, QV, kp, s));
+            PLHR_TRY_CUDA(cudaMemcpyAsync(lam, theta, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
+            {
+                std::vector<double> ones(kp, 1.0);
+                PLHR_TRY_CUDA(cudaMemcpyAsync(scale, ones.data(), sizeof(double) * kp, cudaMemcpyHostToDevice, s));
+                PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+            }
+            continue;
+        }
+        if (it == opt.maxit) break;
+        const int na = hs->nact;
+        // -------------------------------------------- W = T(AV - BV Lambda), active columns
+        const double* Ract = R;
+        int64_t ldra = kp;
+        if (na < kp) {
+            PLHR_TRY_CUDA(gather_columns(n, R, kp, active, na, Rc, na, s));
+            Ract = Rc;
+            ldra = na;
+        }
+        PLHR_TRY(applyT(na, Ract, ldra, W));
+        // -------------------------------------------- S = T(AW - BW Lambda), Q_W = T(AW - sigma BW)
+        double* X2in = T ? X2 : SQ;
+        {
+            PhaseScope ps(PH_STENCIL, s);
+            PLHR_TRY_CUDA(lap_apply_shifts(g, na, W, na, AW, na, X2in, T ? 2 * na : na, lam_act,
+                                           T ? X2in + na : nullptr, 2 * na, sigma, s));
+        }
+        const double* S = SQ;
+        const int64_t lds = T ? 2 * na : na;
+        if (T) PLHR_TRY(applyT(2 * na, X2, 2 * na, SQ));
+        const double* QW = SQ + na;
+        // -------------------------------------------- A S, Q_S = T(AS - sigma BS)
+        {
+            PhaseScope ps(PH_STENCIL, s);
+            PLHR_TRY_CUDA(lap_apply_shifts(g, na, S, lds, AS, na, nullptr, 0, nullptr, T ? X3 : nullptr, na, sigma, s));
+        }
+        if (T) PLHR_TRY(applyT(na, X3, na, QS));
+        // -------------------------------------------- Grams over Z = [V W S P], AZ, Q (steps 6-7)
+        const int nb = np ? 4 : 3;
+        const int m = kp + 2 * na + np;
+        last_m = m;
+        Blk<const double> zb[4] = {{V, kp, kp}, {W, na, na}, {S, lds, na}, {P, kp, np}};
+        Blk<const double> ab[4] = {{AV, kp, kp}, {AW, na, na}, {AS, na, na}, {AP, kp, np}};
+        Blk<const double> qb[4] = {{QV, kp, kp}, {QW, 2 * na, na}, {QS, na, na}, {QP, kp, np}};
+        PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
+        DenseArgs da;
+        da.m = m; da.kp = kp; da.nv = kp;
+        da.Gzz = grams; da.Guq = grams + m * m; da.Gqz = grams + 2 * m * m;
+        da.colscale = colscale; da.work = dwork; da.Cp = Cp; da.Cvv = Cvv; da.tags = tags; da.tag_partner = partner;
+        da.xi = xi; da.out_int = dstat + 3; da.clk = nullptr;
+        for (int pass = 0; pass < 2; ++pass) {
+            {
+                PhaseScope ps(PH_GRAM, s);
+                PLHR_TRY_CUDA(multi_gram(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams, s));
+            }
+            // ---------------------------------------- projected T-harmonic problem, selection (steps 7-10)
+            {
+                PhaseScope ps(PH_DENSE, s);
+                PLHR_TRY_CUDA(dense_extract(da, s));
+            }
+            PLHR_TRY_CUDA(cudaMemcpyAsync(hs->dense, dstat + 3, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+            PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+            if (hs->dense[0] == kDenseOK || !T || pass == 1) break;
+            // recovery: the carried images T(A - sigma B)V, T(A - sigma B)P have
+            // drifted; recompute them explicitly and project again
+            PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
+            PLHR_TRY(applyT(kp, X3, kp, QV));
+            if (np) {
+                PLHR_TRY_CUDA(lap_apply_shifts(g, kp, P, kp, AP, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
+                PLHR_TRY(applyT(kp, X3, kp, QP));
+            }
+        }
+        last_kept = hs->dense[1];
+        if (hs->dense[0] != kDenseOK) {
+            set_error("plhr_solve: projected problem failed at iteration %d (code %d)", it, hs->dense[0]);
+            result = PLHR_EBREAKDOWN;
+            break;
+        }
+        // -------------------------------------------- P, V (steps 11-12), images, RQs (13-14)
+        {
+            PhaseScope ps(PH_UPDATE, s);
+            PLHR_TRY_CUDA(block_update(n, nb, zb, kp, Cp, Cvv, V, kp, P, kp, nullptr, 0, nullptr, nullptr, s));
+            if (T) PLHR_TRY_CUDA(block_update(n, nb, qb, kp, Cp, Cvv, QV, kp, QP, kp, nullptr, 0, nullptr, nullptr, s));
+        }
+        np = kp;
+        PLHR_TRY(refresh_images());
+        PLHR_TRY_CUDA(dense_rq(kp, dots, tags, partner, lam, scale, s));
+    }
+    const double t2 = now_s();
+    if (result == PLHR_OK || result == PLHR_ENOTCONV) {
+        if (result == PLHR_ENOTCONV) {
+            // final Rayleigh-Ritz on the current block
+            PLHR_TRY_CUDA(lap_axpby(g, kp, V, kp, AW, kp, 1.0, 0.0, s));
+            Blk<const double> zb[1] = {{V, kp, kp}}, ab[1] = {{AW, kp, kp}}, qb[1] = {{V, kp, kp}};
+            PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
+            PLHR_TRY_CUDA(multi_gram(n, 1, zb, ab, qb, 0.0, colscale, gpart, grams, s));
+            PLHR_TRY_CUDA(dense_rr(kp, grams + kp * kp, grams, sigma, scale, Crr, theta, dstat + 6, s));
+            PLHR_TRY_CUDA(block_times_small(n, V, kp, kp, Crr, kp, Rc, kp, s));
+            PLHR_TRY_CUDA(lap_axpby(g, kp, Rc, kp, AW, kp, 1.0, 0.0, s));
+            std::vector<double> ones(kp, 1.0);
+            PLHR_TRY_CUDA(cudaMemcpyAsync(dots, ones.data(), sizeof(double) * kp, cudaMemcpyHostToDevice, s));
+            PLHR_TRY_CUDA(residual_norms(n, kp, Rc, kp, AW, kp, theta, dots, R, kp, rpart, sums, s));
+            StatusArgs sa;
+            sa.kp = kp; sa.k = k; sa.sigma = sigma; sa.tol = tol;
+            sa.sums = sums; sa.lam = theta; sa.lam_act = lam_act; sa.active = active; sa.rel = rel; sa.order = order;
+            sa.hstat = dstat;
+            PLHR_TRY_CUDA(dense_status(sa, s));
+            PLHR_TRY_CUDA(cudaMemcpyAsync(h_rel, rel, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+            PLHR_TRY_CUDA(cudaMemcpyAsync(h_theta, theta, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+            PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+        }
+        // Rc holds the Ritz vectors ordered by |theta - sigma|: the first k are returned
+        PLHR_TRY_CUDA(cudaMemcpy2DAsync(eigvecs, sizeof(double) * ldv, Rc, sizeof(double) * kp, sizeof(double) * k, n,
+                                        cudaMemcpyDeviceToDevice, s));
+        PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+        double mx = 0.0;
+        for (int q2 = 0; q2 < k; ++q2) {
+            eigvals[q2] = h_theta[q2];
+            mx = std::fmax(mx, h_rel[q2]);
+        }
+        if (info) info->max_rel_residual = mx;
+    }
+    if (info) {
+        info->iterations = it;
+        info->converged = result == PLHR_OK ? 1 : 0;
+        info->setup_seconds = t1 - t0;
+        info->solve_seconds = t2 - t1;
+        info->history_len = hist;
+    }
+    cudaFreeAsync(big.p, s);
+    cudaFreeAsync(part.p, s);
+    cudaFreeAsync(small.p, s);
+    cudaFreeAsync(ints, s);
+    big.p = part.p = small.p = nullptr;
+    int_free.p = nullptr;
+    cudaStreamSynchronize(s);
+    profile_flush();
+    return result;
+}

@@ -69,6 +69,7 @@ class Workload:
     mg_levels: int = 1
     mg_nu: int = 2
     maxit: int = 1000
+    guard: int = 1            # block columns beyond k (real arithmetic)
     seed: int = SEED_BASE
     real: bool = True
     note: str = ""
@@ -80,8 +81,9 @@ class Workload:
 
     @property
     def kprime(self) -> int:
-        # real arithmetic runs one extra column so a conjugate pair is never cut
-        return self.k + 1 if self.real else self.k
+        # real arithmetic runs guard extra columns (at least one, so that a
+        # conjugate pair is never cut at the k-th position)
+        return self.k + self.guard if self.real else self.k
 
     def v0(self) -> np.ndarray:
         return start_block(self.n, self.kprime, self.seed, complex_=not self.real)
@@ -110,7 +112,7 @@ def config1() -> Workload:
     dims, h = (32, 32), 1.0 / 33.0
     return Workload(name="lap2d_32x32_k4", kind="lap2d", dims=dims, h=h,
                     sigma=_mid_gap(dims, h, 99), k=4, tol=1e-8, prec="none", maxit=20000,
-                    seed=SEED_BASE + 1)
+                    guard=2, seed=SEED_BASE + 1)
 
 
 # 3D 7-point Laplacian, 128^3 interior, h = 1/129: the shift is the midpoint of
@@ -122,7 +124,8 @@ def config2() -> Workload:
     sigma = 0.5 * (_lap3_mode((6, 6, 6), h) + _lap3_mode((3, 6, 8), h))
     return Workload(name="lap3d_128cube_k10", kind="lap3d", dims=dims, h=h,
                     sigma=sigma, k=10, tol=1e-8, prec="avmg", mg_levels=4,
-                    mg_nu=2, seed=SEED_BASE + 2)
+                    mg_nu=2, guard=6, seed=SEED_BASE + 2,
+                    extra={"transfer": "linear", "coarse": "fine_spectrum"})
 
 
 def _lap3_mode(mode, h) -> float:
