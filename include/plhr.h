@@ -187,6 +187,28 @@ plhr_status plhr_tharm_extract(int m, int kp, int nv, const double* Gzz, const d
                                int* tags, int* partner, double* xi, int* status, long long* clk,
                                void* stream);
 
+/* Same computation as plhr_tharm_extract, for callers that cannot allocate
+ * device memory when they call it: an application whose allocator owns all of
+ * the device memory, a service with a fixed memory budget that forbids
+ * allocation after start-up, or code running from a host callback where an
+ * allocation could block.  The paper has no counterpart: this is a property
+ * of the library, not of the method.
+ *   - Scratch comes from a 256 KiB array built into the library (enough for
+ *     the largest supported m = 64); every GPU that loads the library keeps it
+ *     until the process exits.  m > 64 is rejected with PLHR_EINVAL.
+ *   - The call performs no cudaMalloc, cudaFree or other allocation.  Its first
+ *     call on a device looks up the array's device address for that device
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents (the
+ *     solver writes every scratch element it reads, so nothing needs clearing).
+ *     Calls whose work overlaps on the GPU, e.g. on two streams at once, race
+ *     on the array: serialise them.
+ * Arguments, outputs and status are those of plhr_tharm_extract (no clk). */
+plhr_status plhr_tharm_extract_noalloc(int m, int kp, int nv, const double* Gzz, const double* Guq,
+                                       const double* Gqz, const double* colscale, double* Cp, double* Cvv,
+                                       int* tags, int* partner, double* xi, int* status, void* stream);
+
 /* ---------------------------------------------------------------- utilities */
 const char* plhr_status_string(plhr_status s);
 /* Number of CUDA kernels the library has launched in this process. */

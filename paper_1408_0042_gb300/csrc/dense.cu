@@ -22,6 +22,7 @@
 #include "dense.h"
 
 #include <cfloat>
+#include <mutex>
 
 namespace plhr {
 namespace {
@@ -986,5 +987,78 @@ extern "C" plhr_status plhr_tharm_extract(int m, int kp, int nv, const double* G
     cudaError_t e = dense_extract(a, s);
     cudaFreeAsync(work, s);
     PLHR_TRY_CUDA(e);
+    return PLHR_OK;
+}
+
+// ======================================================================
+// Allocation-free variant of plhr_tharm_extract.
+//
+// Some callers cannot allocate device memory at the moment they need the
+// projected eigensolve: an application that has handed the whole device to
+// its own pooled allocator or arena, a service with a fixed memory budget
+// that forbids allocation after start-up, or code running from a host
+// callback where an allocation could block on the allocator.  For them this
+// entry point takes its scratch from a fixed array compiled into the library
+// instead of calling the CUDA allocator.
+namespace {
+
+// Scratch of the projected eigensolve for the largest supported basis
+// (m = 64): 8 * 64 * 64 doubles = 256 KiB.  Every GPU that loads the library
+// holds this array until the process exits.
+constexpr size_t kNoAllocScratchDoubles = 8 * (size_t)plhr::kDenseMaxM * plhr::kDenseMaxM;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+// Device address of the scratch array, looked up once per device.
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+plhr_status noalloc_scratch(double** out) {
+    int dev = 0;
+    PLHR_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        plhr::set_error("plhr_tharm_extract_noalloc: device ordinal %d out of range", dev);
+        return PLHR_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        // host code sees only a stand-in for g_noalloc_scratch; its device
+        // address comes from the runtime, with this device current
+        PLHR_TRY_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return PLHR_OK;
+}
+
+}  // namespace
+
+extern "C" plhr_status plhr_tharm_extract_noalloc(int m, int kp, int nv, const double* Gzz, const double* Guq,
+                                                  const double* Gqz, const double* colscale, double* Cp,
+                                                  double* Cvv, int* tags, int* partner, double* xi, int* status,
+                                                  void* stream) {
+    using namespace plhr;
+    clear_error();
+    if (m > kDenseMaxM) {
+        set_error("plhr_tharm_extract_noalloc: m = %d exceeds the maximum %d of the built-in scratch", m,
+                  kDenseMaxM);
+        return PLHR_EINVAL;
+    }
+    if (m < 1 || kp < 1 || kp > 16 || kp > m || nv < 1 || nv > m || !Gzz || !Guq || !Gqz || !colscale || !Cp ||
+        !Cvv || !tags || !partner || !xi || !status) {
+        set_error("plhr_tharm_extract_noalloc: invalid argument");
+        return PLHR_EINVAL;
+    }
+    if (dense_work_doubles() > kNoAllocScratchDoubles) {
+        set_error("plhr_tharm_extract_noalloc: built-in scratch too small");
+        return PLHR_EINVAL;
+    }
+    double* work = nullptr;
+    PLHR_TRY(noalloc_scratch(&work));
+    DenseArgs a;
+    a.m = m; a.kp = kp; a.nv = nv; a.Gzz = Gzz; a.Guq = Guq; a.Gqz = Gqz; a.colscale = colscale; a.work = work;
+    a.Cp = Cp; a.Cvv = Cvv; a.tags = tags; a.tag_partner = partner; a.xi = xi; a.out_int = status; a.clk = nullptr;
+    PLHR_TRY_CUDA(dense_extract(a, (cudaStream_t)stream));
     return PLHR_OK;
 }
