@@ -28,6 +28,9 @@ namespace plhr {
 namespace {
 
 constexpr int MAXM = kDenseMaxM;
+constexpr int LDS = MAXM + 1;     // shared row stride: column accesses hit distinct banks
+constexpr int NT = 128;           // threads of the extraction CTA
+constexpr int NW = NT / 32;
 
 struct cplx {
     double re, im;
@@ -35,6 +38,8 @@ struct cplx {
 __device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 __device__ __forceinline__ cplx cadd(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
 __device__ __forceinline__ cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cplx cscale(cplx a, double s) { return {a.re * s, a.im * s}; }
+__device__ __forceinline__ double cabs1(cplx a) { return fabs(a.re) + fabs(a.im); }
 __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
     // Smith's algorithm
     if (fabs(b.re) >= fabs(b.im)) {
@@ -47,65 +52,21 @@ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
 }
 
 __device__ __forceinline__ void wsync() { __syncwarp(); }
+__device__ __forceinline__ void bsync() { __syncthreads(); }
 
-// ---------------------------------------------------------------- Cholesky with drop
-// A (n x n, ld) symmetric, overwritten: upper triangle holds R for kept
-// columns.  keep[j] = 1 if kept.  Returns number kept.  Pivot test relative
-// to the original diagonal (1 after scaling).
-__device__ int chol_drop(double* A, int n, int ld, int* keep, double tol) {
-    const int lane = threadIdx.x;
-    int nk = 0;
-    for (int j = 0; j < n; ++j) {
-        double p = A[j * ld + j];
-        bool ok = (p > tol) && isfinite(p);
-        wsync();
-        if (lane == 0) keep[j] = ok ? 1 : 0;
-        if (ok) {
-            double r = sqrt(p);
-            for (int l = j + 1 + lane; l < n; l += 32) A[j * ld + l] /= r;
-            wsync();
-            if (lane == 0) A[j * ld + j] = r;
-            // trailing update of the upper triangle
-            for (int idx = lane; idx < (n - j - 1) * (n - j - 1); idx += 32) {
-                int a = j + 1 + idx / (n - j - 1), b = j + 1 + idx % (n - j - 1);
-                if (b >= a) A[a * ld + b] -= A[j * ld + a] * A[j * ld + b];
-            }
-            ++nk;
-        } else {
-            // drop: row/column j take no further part
-            for (int l = lane; l < n; l += 32) { A[j * ld + l] = 0.0; }
-        }
-        wsync();
-    }
-    return nk;
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
-// X <- R^-T X R^-1 for upper triangular R (n x n) and square X (n x n); in place.
-__device__ void congruence_rinv(const double* R, int ldr, double* X, int ldx, int n) {
-    const int lane = threadIdx.x;
-    // solve R^T Y = X  (forward substitution down the rows), one column per lane
-    for (int c = lane; c < n; c += 32) {
-        for (int i = 0; i < n; ++i) {
-            double s = X[i * ldx + c];
-            for (int l = 0; l < i; ++l) s -= R[l * ldr + i] * X[l * ldx + c];
-            X[i * ldx + c] = s / R[i * ldr + i];
-        }
-    }
-    wsync();
-    // solve Z R = Y  row by row: z_j = (y_j - sum_{l<j} z_l R_lj) / R_jj
-    for (int r = lane; r < n; r += 32) {
-        for (int j = 0; j < n; ++j) {
-            double s = X[r * ldx + j];
-            for (int l = 0; l < j; ++l) s -= X[r * ldx + l] * R[l * ldr + j];
-            X[r * ldx + j] = s / R[j * ldr + j];
-        }
-    }
-    wsync();
-}
-
-// plain Cholesky A = L L^T (lower stored in A's lower triangle); false on failure
+// ---------------------------------------------------------------- warp Cholesky (final Rayleigh-Ritz)
+// plain Cholesky A = L L^T by one warp (lower stored in A's lower triangle)
 __device__ bool chol_lower(double* A, int n, int ld) {
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     bool ok = true;
     for (int j = 0; j < n; ++j) {
         double p = A[j * ld + j];
@@ -125,89 +86,134 @@ __device__ bool chol_lower(double* A, int n, int ld) {
     return ok;
 }
 
-// ---------------------------------------------------------------- Hessenberg + QR
-// Householder reduction of H (n x n) to upper Hessenberg; Z accumulates.
-__device__ void hessenberg(double* H, double* Z, int n, int ld, double* v) {
-    const int lane = threadIdx.x;
-    for (int i = lane; i < n * n; i += 32) Z[(i / n) * ld + i % n] = (i / n == i % n) ? 1.0 : 0.0;
-    wsync();
+// ---------------------------------------------------------------- block-wide dense kernels
+// Cholesky with column dropping of a symmetric n x n (upper triangle used):
+// A = R^T R on the kept columns; column j is dropped when its pivot is below
+// tol (the matrix is column-normalised, so the test is relative).
+__device__ int bchol_drop(double* A, int n, int* keep, double tol) {
+    const int tid = threadIdx.x;
+    int nk = 0;
+    for (int j = 0; j < n; ++j) {
+        double p = A[j * LDS + j];
+        bool ok = (p > tol) && isfinite(p);
+        bsync();
+        if (tid == 0) keep[j] = ok ? 1 : 0;
+        if (ok) {
+            double r = sqrt(p);
+            for (int l = j + 1 + tid; l < n; l += NT) A[j * LDS + l] /= r;
+            bsync();
+            if (tid == 0) A[j * LDS + j] = r;
+            const int w = n - j - 1;
+            for (int idx = tid; idx < w * w; idx += NT) {
+                int a = j + 1 + idx / w, b = j + 1 + idx % w;
+                if (b >= a) A[a * LDS + b] -= A[j * LDS + a] * A[j * LDS + b];
+            }
+            ++nk;
+        } else {
+            for (int l = tid; l < n; l += NT) A[j * LDS + l] = 0.0;
+        }
+        bsync();
+    }
+    return nk;
+}
+
+// X <- R^{-T} X R^{-1} for upper triangular R (both n x n, stride LDS)
+__device__ void bcongruence(const double* R, double* X, int n) {
+    const int tid = threadIdx.x;
+    if (tid < n) {
+        const int c = tid;
+        for (int i = 0; i < n; ++i) {
+            double s = X[i * LDS + c];
+            for (int l = 0; l < i; ++l) s -= R[l * LDS + i] * X[l * LDS + c];
+            X[i * LDS + c] = s / R[i * LDS + i];
+        }
+    }
+    bsync();
+    if (tid < n) {
+        const int r = tid;
+        for (int j = 0; j < n; ++j) {
+            double s = X[r * LDS + j];
+            for (int l = 0; l < j; ++l) s -= X[r * LDS + l] * R[l * LDS + j];
+            X[r * LDS + j] = s / R[j * LDS + j];
+        }
+    }
+    bsync();
+}
+
+// A = L L^T (lower triangle), block-wide; false when not positive definite
+__device__ bool bchol_lower(double* A, int n, int* flag) {
+    const int tid = threadIdx.x;
+    for (int j = 0; j < n; ++j) {
+        double p = A[j * LDS + j];
+        bool ok = (p > 0.0) && isfinite(p);
+        if (!ok) { bsync(); return false; }
+        double r = sqrt(p);
+        bsync();
+        for (int l = j + 1 + tid; l < n; l += NT) A[l * LDS + j] /= r;
+        bsync();
+        if (tid == 0) A[j * LDS + j] = r;
+        const int w = n - j - 1;
+        for (int idx = tid; idx < w * w; idx += NT) {
+            int a = j + 1 + idx / w, b = j + 1 + idx % w;
+            if (b <= a) A[a * LDS + b] -= A[a * LDS + j] * A[b * LDS + j];
+        }
+        bsync();
+    }
+    (void)flag;
+    return true;
+}
+
+// Householder reduction of H (n x n) to upper Hessenberg form.  The reflector
+// of step k, I - beta_k v v^T with v = (0,..,0, v_{k+1}, .., v_{n-1}), is kept
+// in row k of Vh and beta[k] (beta = 0: identity).
+__device__ void bhessenberg(double* H, double* Vh, double* beta, int n, double* red) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int k = 0; k < n - 2; ++k) {
-        // x = H[k+1:n, k]
-        double ss = 0.0;
-        for (int i = k + 1 + lane; i < n; i += 32) ss += H[i * ld + k] * H[i * ld + k];
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        // ||x||^2 for x = H[k+1:n, k]  (warp 0)
+        if (warp == 0) {
+            double ss = 0.0;
+            for (int i = k + 1 + lane; i < n; i += 32) ss += H[i * LDS + k] * H[i * LDS + k];
+            ss = warp_sum(ss);
+            if (lane == 0) red[0] = ss;
+        }
+        bsync();
+        const double ss = red[0];
+        const double x0 = H[(k + 1) * LDS + k];
         double alpha = sqrt(ss);
-        double x0 = H[(k + 1) * ld + k];
-        if (alpha == 0.0) continue;
         if (x0 > 0) alpha = -alpha;
-        // v = x - alpha e1, normalised so that P = I - 2 v v^T / (v^T v)
-        for (int i = k + 1 + lane; i < n; i += 32) v[i] = H[i * ld + k];
-        wsync();
-        if (lane == 0) v[k + 1] = x0 - alpha;
-        wsync();
-        double vv = ss - x0 * x0 + (x0 - alpha) * (x0 - alpha);
-        if (vv == 0.0) continue;
-        double beta = 2.0 / vv;
-        // H = P H : rows k+1..n-1, all columns
-        for (int c = lane; c < n; c += 32) {
-            double s = 0.0;
-            for (int i = k + 1; i < n; ++i) s += v[i] * H[i * ld + c];
-            s *= beta;
-            for (int i = k + 1; i < n; ++i) H[i * ld + c] -= s * v[i];
+        const double vv = ss - x0 * x0 + (x0 - alpha) * (x0 - alpha);
+        const bool skip = (alpha == 0.0) || (vv == 0.0);
+        const double b = skip ? 0.0 : 2.0 / vv;
+        for (int i = tid; i < n; i += NT) Vh[k * LDS + i] = (i <= k || skip) ? 0.0 : (i == k + 1 ? x0 - alpha : H[i * LDS + k]);
+        if (tid == 0) beta[k] = b;
+        bsync();
+        if (!skip) {
+            const double* v = Vh + k * LDS;
+            // H <- (I - b v v^T) H : one column per thread
+            for (int c = tid; c < n; c += NT) {
+                double s = 0.0;
+                for (int i = k + 1; i < n; ++i) s += v[i] * H[i * LDS + c];
+                s *= b;
+                for (int i = k + 1; i < n; ++i) H[i * LDS + c] -= s * v[i];
+            }
+            bsync();
+            // H <- H (I - b v v^T) : one row per thread
+            for (int r = tid; r < n; r += NT) {
+                double s = 0.0;
+                for (int i = k + 1; i < n; ++i) s += H[r * LDS + i] * v[i];
+                s *= b;
+                for (int i = k + 1; i < n; ++i) H[r * LDS + i] -= s * v[i];
+            }
+            bsync();
+            for (int i = k + 2 + tid; i < n; i += NT) H[i * LDS + k] = 0.0;
         }
-        wsync();
-        // H = H P : all rows, columns k+1..n-1
-        for (int r = lane; r < n; r += 32) {
-            double s = 0.0;
-            for (int i = k + 1; i < n; ++i) s += H[r * ld + i] * v[i];
-            s *= beta;
-            for (int i = k + 1; i < n; ++i) H[r * ld + i] -= s * v[i];
-        }
-        // Z = Z P
-        for (int r = lane; r < n; r += 32) {
-            double s = 0.0;
-            for (int i = k + 1; i < n; ++i) s += Z[r * ld + i] * v[i];
-            s *= beta;
-            for (int i = k + 1; i < n; ++i) Z[r * ld + i] -= s * v[i];
-        }
-        wsync();
-        for (int i = k + 2 + lane; i < n; i += 32) H[i * ld + k] = 0.0;
-        wsync();
+        bsync();
     }
 }
 
-// Apply the reflector I - tau u u^T (u[0] = 1, length nr = 2 or 3) to rows
-// k..k+nr-1 of H (columns c0..n-1) and columns k..k+nr-1 (rows 0..r1) of H and Z.
-__device__ void apply_refl(double* H, double* Z, int n, int ld, int k, int nr, double u1, double u2, double tau,
-                           int c0, int r1) {
-    const int lane = threadIdx.x;
-    for (int c = c0 + lane; c < n; c += 32) {
-        double s = H[k * ld + c] + u1 * H[(k + 1) * ld + c] + (nr == 3 ? u2 * H[(k + 2) * ld + c] : 0.0);
-        s *= tau;
-        H[k * ld + c] -= s;
-        H[(k + 1) * ld + c] -= s * u1;
-        if (nr == 3) H[(k + 2) * ld + c] -= s * u2;
-    }
-    wsync();
-    for (int r = lane; r <= r1; r += 32) {
-        double s = H[r * ld + k] + u1 * H[r * ld + k + 1] + (nr == 3 ? u2 * H[r * ld + k + 2] : 0.0);
-        s *= tau;
-        H[r * ld + k] -= s;
-        H[r * ld + k + 1] -= s * u1;
-        if (nr == 3) H[r * ld + k + 2] -= s * u2;
-    }
-    for (int r = lane; r < n; r += 32) {
-        double s = Z[r * ld + k] + u1 * Z[r * ld + k + 1] + (nr == 3 ? u2 * Z[r * ld + k + 2] : 0.0);
-        s *= tau;
-        Z[r * ld + k] -= s;
-        Z[r * ld + k + 1] -= s * u1;
-        if (nr == 3) Z[r * ld + k + 2] -= s * u2;
-    }
-    wsync();
-}
-
-// Householder vector for (x, y[, z]): returns u1, u2, tau with
-// (I - tau u u^T) (x, y, z)^T = (beta, 0, 0)^T, u = (1, u1, u2).
+// ---------------------------------------------------------------- eigenvalues (one warp)
+// Householder vector for (x, y[, z]): u = (1, u1, u2), tau with
+// (I - tau u u^T)(x, y, z)^T = (beta, 0, 0)^T.
 __device__ __forceinline__ void house3(double x, double y, double z, int nr, double& u1, double& u2, double& tau) {
     double nrm = sqrt(x * x + y * y + (nr == 3 ? z * z : 0.0));
     if (nrm == 0.0 || (y == 0.0 && (nr == 2 || z == 0.0))) {
@@ -221,97 +227,57 @@ __device__ __forceinline__ void house3(double x, double y, double z, int nr, dou
     tau = (beta - x) / beta;
 }
 
-// Givens rotation making the 2x2 block at (p, p+1) upper triangular when its
-// eigenvalues are real; applied to H rows/cols and Z columns.
-__device__ void split_real_2x2(double* H, double* Z, int n, int ld, int p) {
-    const int lane = threadIdx.x;
-    double a = H[p * ld + p], b = H[p * ld + p + 1], c = H[(p + 1) * ld + p], d = H[(p + 1) * ld + p + 1];
-    double hf = 0.5 * (a - d);
-    double disc = hf * hf + b * c;
-    if (disc < 0.0) return;
-    double sq = sqrt(disc);
-    // eigenvalue mu with eigenvector (b, mu - a) or (mu - d, c)
-    double mu = 0.5 * (a + d) + (hf >= 0 ? sq : -sq);
-    double x1, x2;
-    if (fabs(b) + fabs(mu - a) >= fabs(mu - d) + fabs(c)) { x1 = b; x2 = mu - a; }
-    else { x1 = mu - d; x2 = c; }
-    double r = hypot(x1, x2);
-    if (r == 0.0) return;
-    double cs = x1 / r, sn = x2 / r;
-    // G = [cs -sn; sn cs] with first column the eigenvector: H <- G^T H G
-    wsync();
-    for (int col = p + lane; col < n; col += 32) {
-        double h1 = H[p * ld + col], h2 = H[(p + 1) * ld + col];
-        H[p * ld + col] = cs * h1 + sn * h2;
-        H[(p + 1) * ld + col] = -sn * h1 + cs * h2;
-    }
-    wsync();
-    for (int row = lane; row <= p + 1; row += 32) {
-        double h1 = H[row * ld + p], h2 = H[row * ld + p + 1];
-        H[row * ld + p] = cs * h1 + sn * h2;
-        H[row * ld + p + 1] = -sn * h1 + cs * h2;
-    }
-    for (int row = lane; row < n; row += 32) {
-        double z1 = Z[row * ld + p], z2 = Z[row * ld + p + 1];
-        Z[row * ld + p] = cs * z1 + sn * z2;
-        Z[row * ld + p + 1] = -sn * z1 + cs * z2;
-    }
-    wsync();
-    if (lane == 0) H[(p + 1) * ld + p] = 0.0;
-    wsync();
-}
-
-// Francis double-shift QR on Hessenberg H (n x n) -> real Schur form, Z updated.
-// Returns false if an eigenvalue fails to converge.
-__device__ bool francis_qr(double* H, double* Z, int n, int ld) {
-    const int lane = threadIdx.x;
+// Francis double-shift QR (Golub & Van Loan Sec. 7.5) on the upper Hessenberg
+// H, eigenvalues only: every transformation is applied to the active window
+// rows/columns l..hi alone (no Schur vectors, no full Schur form), which is
+// all the eigenvalues need.  Deflated 1x1 and 2x2 diagonal blocks remain.
+// One warp; returns false if the iteration does not converge.
+__device__ bool francis_eigenvalues(double* H, int n) {
+    const int lane = threadIdx.x & 31;
     const double eps = DBL_EPSILON;
     double anorm = 0.0;
     for (int i = lane; i < n * n; i += 32) {
         int r = i / n, c = i % n;
-        if (c >= r - 1) anorm = fmax(anorm, fabs(H[r * ld + c]));
+        if (c >= r - 1) anorm = fmax(anorm, fabs(H[r * LDS + c]));
     }
-    for (int o = 16; o > 0; o >>= 1) anorm = fmax(anorm, __shfl_xor_sync(0xffffffffu, anorm, o));
+    anorm = warp_max(anorm);
     if (anorm == 0.0) anorm = 1.0;
     int hi = n - 1;
     int its = 0, total_its = 0;
     while (hi >= 0) {
-        // locate the lowest negligible subdiagonal in [1, hi]
+        // negligible subdiagonal: relative to the neighbouring diagonal, or to
+        // ||H|| (normwise backward stable).  Only the eigenvalues of largest
+        // modulus are used, and they keep full relative accuracy; the normwise
+        // test lets the many eigenvalues near zero deflate quickly.
         int l = hi;
         while (l > 0) {
-            double s = fabs(H[(l - 1) * ld + l - 1]) + fabs(H[l * ld + l]);
-            if (s == 0.0) s = anorm;
-            if (fabs(H[l * ld + l - 1]) <= eps * s) break;
+            double s = fabs(H[(l - 1) * LDS + l - 1]) + fabs(H[l * LDS + l]);
+            if (s < anorm) s = anorm;
+            if (fabs(H[l * LDS + l - 1]) <= eps * s) break;
             --l;
         }
         wsync();
-        if (l > 0 && lane == 0) H[l * ld + l - 1] = 0.0;
+        if (l > 0 && lane == 0) H[l * LDS + l - 1] = 0.0;
         wsync();
-        if (l == hi) {
-            --hi;
-            its = 0;
-            continue;
-        }
-        if (l == hi - 1) {
-            split_real_2x2(H, Z, n, ld, hi - 1);
-            hi -= 2;
+        if (l >= hi - 1) {          // 1x1 or 2x2 block converged
+            hi = l - 1;
             its = 0;
             continue;
         }
         if (its >= 40) {
-            // Stalled window: a (near-)defective cluster of numerically equal
-            // eigenvalues converges only linearly.  Deflate at the smallest
-            // subdiagonal when it is below 1e-7 ||H||: this moves eigenvalues by
-            // about that much, and only a basis of the cluster is needed.
+            // a stalled window holds a (near-)defective cluster of numerically
+            // equal eigenvalues, which converges only linearly; deflate at the
+            // smallest subdiagonal when it is below 1e-7 ||H|| (the eigenvalues
+            // move by about that much; only a basis of the cluster is needed)
             int jm = l + 1;
-            double vm = fabs(H[(l + 1) * ld + l]);
+            double vm = fabs(H[(l + 1) * LDS + l]);
             for (int j = l + 2; j <= hi; ++j) {
-                double v = fabs(H[j * ld + j - 1]);
+                double v = fabs(H[j * LDS + j - 1]);
                 if (v < vm) { vm = v; jm = j; }
             }
             if (vm <= 1e-7 * anorm) {
                 wsync();
-                if (lane == 0) H[jm * ld + jm - 1] = 0.0;
+                if (lane == 0) H[jm * LDS + jm - 1] = 0.0;
                 wsync();
                 its = 0;
                 continue;
@@ -321,42 +287,56 @@ __device__ bool francis_qr(double* H, double* Z, int n, int ld) {
         ++its;
         double s, t;
         if (its % 10 == 0) {
-            // exceptional shift
-            double w = fabs(H[hi * ld + hi - 1]) + fabs(H[(hi - 1) * ld + hi - 2]);
+            double w = fabs(H[hi * LDS + hi - 1]) + fabs(H[(hi - 1) * LDS + hi - 2]);
             s = 1.5 * w;
             t = w * w;
         } else {
-            double a = H[(hi - 1) * ld + hi - 1], b = H[(hi - 1) * ld + hi], c = H[hi * ld + hi - 1],
-                   d = H[hi * ld + hi];
+            double a = H[(hi - 1) * LDS + hi - 1], b = H[(hi - 1) * LDS + hi], c = H[hi * LDS + hi - 1],
+                   d = H[hi * LDS + hi];
             s = a + d;
             t = a * d - b * c;
         }
-        // first column of (H - s1 I)(H - s2 I) at rows l, l+1, l+2
-        double h00 = H[l * ld + l], h01 = H[l * ld + l + 1], h10 = H[(l + 1) * ld + l],
-               h11 = H[(l + 1) * ld + l + 1], h21 = H[(l + 2) * ld + l + 1];
+        double h00 = H[l * LDS + l], h01 = H[l * LDS + l + 1], h10 = H[(l + 1) * LDS + l],
+               h11 = H[(l + 1) * LDS + l + 1], h21 = H[(l + 2) * LDS + l + 1];
         double x = h00 * h00 + h01 * h10 - s * h00 + t;
         double y = h10 * (h00 + h11 - s);
         double z = h10 * h21;
+        // every lane has read the shift and the first bulge column before any
+        // lane writes (lanes of a warp need not run in lockstep)
+        wsync();
         for (int k = l; k <= hi - 1; ++k) {
-            int nr = (k < hi - 1) ? 3 : 2;
+            const int nr = (k < hi - 1) ? 3 : 2;
             double u1, u2, tau;
             house3(x, y, z, nr, u1, u2, tau);
             if (tau != 0.0) {
-                int c0 = k > l ? k - 1 : l;
-                int r1 = (k + 3 < hi) ? k + 3 : hi;
-                apply_refl(H, Z, n, ld, k, nr, u1, u2, tau, c0, r1);
-                // rows above the active block, for the full Schur form
-                (void)r1;
+                const int c0 = k > l ? k - 1 : l;
+                for (int c = c0 + lane; c <= hi; c += 32) {
+                    double sv = H[k * LDS + c] + u1 * H[(k + 1) * LDS + c] + (nr == 3 ? u2 * H[(k + 2) * LDS + c] : 0.0);
+                    sv *= tau;
+                    H[k * LDS + c] -= sv;
+                    H[(k + 1) * LDS + c] -= sv * u1;
+                    if (nr == 3) H[(k + 2) * LDS + c] -= sv * u2;
+                }
+                wsync();
+                const int r1 = (k + 3 < hi) ? k + 3 : hi;
+                for (int r = l + lane; r <= r1; r += 32) {
+                    double sv = H[r * LDS + k] + u1 * H[r * LDS + k + 1] + (nr == 3 ? u2 * H[r * LDS + k + 2] : 0.0);
+                    sv *= tau;
+                    H[r * LDS + k] -= sv;
+                    H[r * LDS + k + 1] -= sv * u1;
+                    if (nr == 3) H[r * LDS + k + 2] -= sv * u2;
+                }
+                wsync();
             }
             if (k > l && lane == 0) {
-                H[(k + 1) * ld + k - 1] = 0.0;
-                if (nr == 3) H[(k + 2) * ld + k - 1] = 0.0;
+                H[(k + 1) * LDS + k - 1] = 0.0;
+                if (nr == 3) H[(k + 2) * LDS + k - 1] = 0.0;
             }
             wsync();
             if (k < hi - 1) {
-                x = H[(k + 1) * ld + k];
-                y = H[(k + 2) * ld + k];
-                z = (k < hi - 2) ? H[(k + 3) * ld + k] : 0.0;
+                x = H[(k + 1) * LDS + k];
+                y = H[(k + 2) * LDS + k];
+                z = (k < hi - 2) ? H[(k + 3) * LDS + k] : 0.0;
             }
             wsync();
         }
@@ -364,396 +344,482 @@ __device__ bool francis_qr(double* H, double* Z, int n, int ld) {
     return true;
 }
 
-// ---------------------------------------------------------------- eigenvectors
-// Eigenvector x (complex, length n) of quasi-triangular T for eigenvalue lam at
-// diagonal position p (p = first row of a 2x2 block for a complex lam).
-// Sequential; executed by one lane.
-__device__ void schur_eigvec(const double* T, int n, int ld, int p, bool block2, cplx lam, cplx* x,
-                             double smallnum) {
-    for (int i = 0; i < n; ++i) x[i] = {0.0, 0.0};
-    int top;
-    if (!block2) {
-        x[p] = {1.0, 0.0};
-        top = p - 1;
-    } else {
-        // (T_pp - lam) x_p + T_p,p+1 x_p+1 = 0
-        x[p] = {T[p * ld + p + 1], 0.0};
-        x[p + 1] = csub(lam, cplx{T[p * ld + p], 0.0});
-        top = p - 1;
-    }
-    int i = top;
-    while (i >= 0) {
-        bool two = (i > 0) && (T[i * ld + i - 1] != 0.0);
-        if (!two) {
-            cplx s = {0.0, 0.0};
-            for (int l = i + 1; l < n; ++l) s = cadd(s, cmul(cplx{T[i * ld + l], 0.0}, x[l]));
-            cplx d = csub(cplx{T[i * ld + i], 0.0}, lam);
-            if (fabs(d.re) + fabs(d.im) < smallnum) d = {smallnum, 0.0};
-            x[i] = cdiv(cplx{-s.re, -s.im}, d);
-            i -= 1;
-        } else {
-            // 2x2 diagonal block at rows (i-1, i)
-            int a = i - 1;
-            cplx s1 = {0.0, 0.0}, s2 = {0.0, 0.0};
-            for (int l = i + 1; l < n; ++l) {
-                s1 = cadd(s1, cmul(cplx{T[a * ld + l], 0.0}, x[l]));
-                s2 = cadd(s2, cmul(cplx{T[i * ld + l], 0.0}, x[l]));
+// ---------------------------------------------------------------- eigenvectors (one warp each)
+// Inverse iteration on the Hessenberg H0 for the eigenvalue lam: two solves of
+// (H0 - lam I) x = b (Gaussian elimination with adjacent-row pivoting, which
+// keeps the Hessenberg structure), starting from b = 1.  U (packed upper
+// triangle, complex) lives in per-warp scratch.  x is returned normalised to
+// max |x_i| = 1.
+__device__ void inverse_iteration(const double* H0, int n, cplx lam, cplx* x, cplx* U, cplx* cur, cplx* nxt,
+                                  double tiny) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < n; i += 32) x[i] = {1.0, 0.0};
+    wsync();
+    for (int iter = 0; iter < 2; ++iter) {
+        // cur = row 0 of (H0 - lam I)
+        for (int j = lane; j < n; j += 32) cur[j] = {H0[j] - (j == 0 ? lam.re : 0.0), j == 0 ? -lam.im : 0.0};
+        cplx bcur = x[0];
+        wsync();
+        for (int k = 0; k < n - 1; ++k) {
+            // nxt = row k+1 (columns >= k)
+            for (int j = k + lane; j < n; j += 32)
+                nxt[j] = {H0[(k + 1) * LDS + j] - (j == k + 1 ? lam.re : 0.0), j == k + 1 ? -lam.im : 0.0};
+            cplx bnxt = x[k + 1];
+            wsync();
+            const bool swap = cabs1(nxt[k]) > cabs1(cur[k]);
+            wsync();
+            if (swap) {
+                for (int j = k + lane; j < n; j += 32) { cplx t2 = cur[j]; cur[j] = nxt[j]; nxt[j] = t2; }
+                cplx t2 = bcur; bcur = bnxt; bnxt = t2;
             }
-            cplx m11 = csub(cplx{T[a * ld + a], 0.0}, lam), m12 = {T[a * ld + i], 0.0};
-            cplx m21 = {T[i * ld + a], 0.0}, m22 = csub(cplx{T[i * ld + i], 0.0}, lam);
-            cplx det = csub(cmul(m11, m22), cmul(m12, m21));
-            if (fabs(det.re) + fabs(det.im) < smallnum) det = {smallnum, 0.0};
-            cplx r1 = {-s1.re, -s1.im}, r2 = {-s2.re, -s2.im};
-            x[a] = cdiv(csub(cmul(m22, r1), cmul(m12, r2)), det);
-            x[i] = cdiv(csub(cmul(m11, r2), cmul(m21, r1)), det);
-            i -= 2;
+            wsync();
+            cplx piv = cur[k];
+            if (cabs1(piv) < tiny) piv = {tiny, 0.0};
+            const cplx f = cdiv(nxt[k], piv);
+            // store U row k, eliminate
+            cplx* urow = U + (k * n - (k * (k - 1)) / 2);   // row k holds columns k..n-1
+            for (int j = k + lane; j < n; j += 32) {
+                urow[j - k] = (j == k) ? piv : cur[j];
+                if (j > k) nxt[j] = csub(nxt[j], cmul(f, cur[j]));
+            }
+            x[k] = bcur;   // all lanes hold the same value; x[k] is rhs after elimination
+            bnxt = csub(bnxt, cmul(f, bcur));
+            wsync();
+            for (int j = k + 1 + lane; j < n; j += 32) cur[j] = nxt[j];
+            bcur = bnxt;
+            wsync();
         }
-        // rescale to avoid overflow
+        {
+            cplx piv = cur[n - 1];
+            if (cabs1(piv) < tiny) piv = {tiny, 0.0};
+            if (lane == 0) U[(n - 1) * n - ((n - 1) * (n - 2)) / 2] = piv;
+            x[n - 1] = bcur;
+        }
+        wsync();
+        // back substitution U x = b
+        for (int i = n - 1; i >= 0; --i) {
+            const cplx* urow = U + (i * n - (i * (i - 1)) / 2);
+            double sr = 0.0, si = 0.0;
+            for (int j = i + 1 + lane; j < n; j += 32) {
+                cplx p = cmul(urow[j - i], x[j]);
+                sr += p.re;
+                si += p.im;
+            }
+            sr = warp_sum(sr);
+            si = warp_sum(si);
+            cplx xi_ = cdiv(csub(x[i], cplx{sr, si}), urow[0]);
+            wsync();
+            if (lane == 0) x[i] = xi_;
+            wsync();
+        }
+        // normalise
         double mx = 0.0;
-        for (int l = i + 1; l < n; ++l) mx = fmax(mx, fabs(x[l].re) + fabs(x[l].im));
-        if (mx > 1e100) {
-            for (int l = 0; l < n; ++l) { x[l].re /= mx; x[l].im /= mx; }
-        }
+        for (int j = lane; j < n; j += 32) mx = fmax(mx, cabs1(x[j]));
+        mx = warp_max(mx);
+        if (!(mx > 0.0) || !isfinite(mx)) mx = 1.0;
+        for (int j = lane; j < n; j += 32) x[j] = cscale(x[j], 1.0 / mx);
+        wsync();
     }
 }
 
 // ---------------------------------------------------------------- the kernel
-// Shared-memory matrices use a row stride of MAXM + 1 doubles so that
-// column-wise accesses by the lanes of the warp fall in distinct banks.
-constexpr int LDS = MAXM + 1;
 struct Smem {
-    double H[MAXM * LDS];
-    double Z[MAXM * LDS];
-    double A[MAXM * LDS];    // scaled Z*Z -> R
-    double B[MAXM * LDS];    // G_L -> L
-    double v[MAXM];
-    double t[MAXM];          // column scale of the raw basis
+    double H[MAXM * LDS];     // C, then its Hessenberg form, then the quasi-triangular result
+    double H0[MAXM * LDS];    // Hessenberg form of C (kept for inverse iteration)
+    double Vh[MAXM * LDS];    // Householder vectors of the Hessenberg reduction
+    double A[MAXM * LDS];     // column-normalised B-Gram -> R
+    double B[MAXM * LDS];     // G_L -> L
+    double beta[MAXM];
+    double t[MAXM];           // column normalisation of the (scaled) basis
+    double red[NT];
     int keep[MAXM];
-    int kidx[MAXM];          // kept -> raw index
+    int kidx[MAXM];           // kept -> raw index
     double eig_re[MAXM], eig_im[MAXM];
-    int eig_pos[MAXM];       // diagonal position in T
-    int eig_blk[MAXM];       // 1 if from a 2x2 block
-    int order[MAXM];
-    int partner[MAXM];
-    cplx x[16 * MAXM];       // eigenvector workspace, one per selected unit
+    int order[MAXM];          // selected units: eigenvalue index
+    int kind[MAXM];           // 0 real, 2 full pair, 1 cut pair
+    int nclose[MAXM];         // earlier selected units in the same numerical cluster
+    int ints[8];
 };
 
-__global__ void __launch_bounds__(32) k_extract(DenseArgs a) {
+__global__ void __launch_bounds__(NT) k_extract(DenseArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = a.m, kp = a.kp;
-    const int ld = LDS;
-    double* G = a.work;  // global scratch: [3][m][m] of scaled, compacted matrices
-#define STAMP(i) do { if (a.clk && lane == 0) a.clk[i] = clock64(); } while (0)
+    // global scratch: complex eigenvector coefficients per selected unit, Y',
+    // and per-warp packed LU factors of the inverse iteration
+    double* Yre = a.work;                          // [unit][MAXM]
+    double* Yim = Yre + MAXM * MAXM;               // [unit][MAXM]
+    double* Yp = Yim + MAXM * MAXM;                // [col][MAXM]
+    cplx* Uw = reinterpret_cast<cplx*>(Yp + MAXM * MAXM);   // NW x (MAXM (MAXM + 1) / 2)
+    double* Wr = Yre;                              // reused after Y' is assembled
+    double* Wv = Yim;
+#define STAMP(i) do { if (a.clk && tid == 0) a.clk[i] = clock64(); } while (0)
     STAMP(0);
-    // ---- 1. scaling and Cholesky with drop of the B-Gram.  The implicit
-    // basis Z D R^{-1} amplifies Gram rounding by cond(R)^2; if G_L then fails
-    // to be positive definite, the pass is repeated with a stricter drop
-    // threshold (fewer, better conditioned columns).
-    // The Grams are of the scaled columns Z diag(colscale); t normalises them.
-    const double drop_tols[3] = {1e-12, 1e-9, 1e-6};
-    int attempt = 0;
-    int nk = 0, nvk = 0;
-retry:
-    for (int i = lane; i < m; i += 32) {
+    // ---- 1. B-orthonormalisation of Z, implicitly: Cholesky with column
+    // dropping of the column-normalised Gram (the Grams are of Z diag(colscale)).
+    // The basis Z D R^{-1} amplifies Gram rounding by cond(R)^2; if G_L then is
+    // not numerically positive definite the pass is repeated with a stricter
+    // drop threshold.
+    for (int i = tid; i < m; i += NT) {
         double g = a.Gzz[i * m + i];
         S.t[i] = (g > 0.0 && isfinite(g)) ? 1.0 / sqrt(g) : 0.0;
     }
-    wsync();
-    for (int i = lane; i < m * m; i += 32) {
-        int r = i / m, c = i % m;
-        S.A[r * ld + c] = a.Gzz[i] * S.t[r] * S.t[c];
+    bsync();
+    const double drop_tols[3] = {1e-12, 1e-9, 1e-6};
+    int nk = 0, nvk = 0;
+    bool ok = false;
+    for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
+        for (int i = tid; i < m * m; i += NT) {
+            int r = i / m, c = i % m;
+            S.A[r * LDS + c] = a.Gzz[i] * S.t[r] * S.t[c];
+        }
+        bsync();
+        bchol_drop(S.A, m, S.keep, drop_tols[attempt]);
+        if (tid == 0) {
+            int q = 0, qv = 0;
+            for (int j = 0; j < m; ++j)
+                if (S.keep[j] && S.t[j] != 0.0) {
+                    S.kidx[q++] = j;
+                    if (j < a.nv) ++qv;
+                }
+            S.ints[0] = q;
+            S.ints[1] = qv;
+        }
+        bsync();
+        nk = S.ints[0];
+        nvk = S.ints[1];
+        if (nvk < 1 || nk < kp) break;
+        // compact R (upper) in place through H
+        for (int i = tid; i < nk * nk; i += NT) {
+            int r = i / nk, c = i % nk;
+            S.H[r * LDS + c] = (c >= r) ? S.A[S.kidx[r] * LDS + S.kidx[c]] : 0.0;
+        }
+        bsync();
+        for (int i = tid; i < nk * nk; i += NT) S.A[(i / nk) * LDS + i % nk] = S.H[(i / nk) * LDS + i % nk];
+        bsync();
+        // G_L = sym(U^T Q), G_R[r][c] = q_r . z_c, on the kept, normalised columns
+        for (int i = tid; i < nk * nk; i += NT) {
+            int r = i / nk, c = i % nk;
+            int rr = S.kidx[r], cc = S.kidx[c];
+            S.B[r * LDS + c] = 0.5 * (a.Guq[rr * m + cc] + a.Guq[cc * m + rr]) * S.t[rr] * S.t[cc];
+            S.H[r * LDS + c] = a.Gqz[rr * m + cc] * S.t[rr] * S.t[cc];
+        }
+        bsync();
+        // ---- 2. the pencil in the B-orthonormal basis, via tau = 1/xi
+        bcongruence(S.A, S.B, nk);
+        bcongruence(S.A, S.H, nk);
+        for (int i = tid; i < nk * nk; i += NT) {
+            int r = i / nk, c = i % nk;
+            if (c > r) {
+                double sv = 0.5 * (S.B[r * LDS + c] + S.B[c * LDS + r]);
+                S.B[r * LDS + c] = sv;
+                S.B[c * LDS + r] = sv;
+            }
+        }
+        bsync();
+        ok = bchol_lower(S.B, nk, nullptr);
     }
-    wsync();
-    nk = chol_drop(S.A, m, ld, S.keep, drop_tols[attempt]);
-    if (lane == 0) {
-        int q = 0;
-        for (int j = 0; j < m; ++j)
-            if (S.keep[j] && S.t[j] != 0.0) S.kidx[q++] = j;
-        nk = q;
-        a.out_int[1] = nk;
-    }
-    nk = __shfl_sync(0xffffffffu, nk, 0);
-    wsync();
-    // kept count in the V block
-    nvk = 0;
-    for (int q = 0; q < nk; ++q) nvk += (S.kidx[q] < a.nv) ? 1 : 0;
-    // columns of V may be dropped (nearly parallel Ritz vectors of a converged
-    // cluster); the selection needs k' kept columns overall
-    if (nvk < 1 || nk < kp) {
-        if (lane == 0) a.out_int[0] = kDenseRankLoss;
-        return;
-    }
-    // compact R (upper) into H temporarily -> keep in A compacted
-    for (int i = lane; i < nk * nk; i += 32) {
-        int r = i / nk, c = i % nk;
-        S.H[r * ld + c] = (c >= r) ? S.A[S.kidx[r] * ld + S.kidx[c]] : 0.0;
-    }
-    wsync();
-    for (int i = lane; i < nk * nk; i += 32) S.A[(i / nk) * ld + i % nk] = S.H[(i / nk) * ld + i % nk];
-    wsync();
     STAMP(1);
-    // ---- 2. projected G_L, G_R in the orthonormal basis
-    double* GL = G;               // nk x nk, ld nk (global scratch)
-    double* GR = G + m * m;
-    for (int i = lane; i < nk * nk; i += 32) {
-        int r = i / nk, c = i % nk;
-        int rr = S.kidx[r], cc = S.kidx[c];
-        double uq = a.Guq[rr * m + cc], qu = a.Guq[cc * m + rr];
-        S.B[r * ld + c] = 0.5 * (uq + qu) * S.t[rr] * S.t[cc];      // G_L = sym(U^T Q)
-        S.H[r * ld + c] = a.Gqz[rr * m + cc] * S.t[rr] * S.t[cc];   // G_R[r][c] = q_r . z_c
-    }
-    wsync();
-    congruence_rinv(S.A, ld, S.B, ld, nk);
-    congruence_rinv(S.A, ld, S.H, ld, nk);
-    // symmetrise G_L exactly
-    for (int i = lane; i < nk * nk; i += 32) {
-        int r = i / nk, c = i % nk;
-        if (c > r) {
-            double s = 0.5 * (S.B[r * ld + c] + S.B[c * ld + r]);
-            S.B[r * ld + c] = s;
-            S.B[c * ld + r] = s;
-        }
-    }
-    wsync();
-    for (int i = lane; i < nk * nk; i += 32) { GL[i] = S.B[(i / nk) * ld + i % nk]; GR[i] = S.H[(i / nk) * ld + i % nk]; }
-    wsync();
-    // ---- Cholesky G_L = L L^T
-    bool ok = chol_lower(S.B, nk, ld);
-    if (!ok) {
-        if (attempt < 2) {
-            ++attempt;
-            wsync();
-            goto retry;
-        }
-        if (lane == 0) a.out_int[0] = kDenseBreakdown;
+    if (nvk < 1 || nk < kp) {
+        if (tid == 0) { a.out_int[0] = kDenseRankLoss; a.out_int[1] = nk; a.out_int[2] = 0; }
         return;
     }
-    STAMP(2);
-    // C = L^-1 G_R L^-T : solve L Y = G_R (columns), then C L^T = Y (rows)
-    for (int c = lane; c < nk; c += 32) {
+    if (!ok) {
+        if (tid == 0) { a.out_int[0] = kDenseBreakdown; a.out_int[1] = nk; a.out_int[2] = 0; }
+        return;
+    }
+    // C = L^{-1} G_R L^{-T}: L Y = G_R by columns, then C L^T = Y by rows
+    if (tid < nk) {
+        const int c = tid;
         for (int i = 0; i < nk; ++i) {
-            double s = S.H[i * ld + c];
-            for (int l = 0; l < i; ++l) s -= S.B[i * ld + l] * S.H[l * ld + c];
-            S.H[i * ld + c] = s / S.B[i * ld + i];
+            double sv = S.H[i * LDS + c];
+            for (int l = 0; l < i; ++l) sv -= S.B[i * LDS + l] * S.H[l * LDS + c];
+            S.H[i * LDS + c] = sv / S.B[i * LDS + i];
         }
     }
-    wsync();
-    for (int r = lane; r < nk; r += 32) {
+    bsync();
+    if (tid < nk) {
+        const int r = tid;
         for (int j = 0; j < nk; ++j) {
-            double s = S.H[r * ld + j];
-            for (int l = 0; l < j; ++l) s -= S.H[r * ld + l] * S.B[j * ld + l];
-            S.H[r * ld + j] = s / S.B[j * ld + j];
+            double sv = S.H[r * LDS + j];
+            for (int l = 0; l < j; ++l) sv -= S.H[r * LDS + l] * S.B[j * LDS + l];
+            S.H[r * LDS + j] = sv / S.B[j * LDS + j];
         }
     }
-    wsync();
+    bsync();
+    STAMP(2);
+    // ---- 3. eigenvalues of C: Hessenberg form, then Francis QR on a copy
+    bhessenberg(S.H, S.Vh, S.beta, nk, S.red);
+    for (int i = tid; i < nk * LDS; i += NT) S.H0[i] = S.H[i];
+    bsync();
     STAMP(3);
-    // ---- 3. eigenvalues of C
-    hessenberg(S.H, S.Z, nk, ld, S.v);
+    if (warp == 0) {
+        bool conv = francis_eigenvalues(S.H, nk);
+        if (lane == 0) S.ints[2] = conv ? 1 : 0;
+    }
+    bsync();
     STAMP(4);
-    ok = francis_qr(S.H, S.Z, nk, ld);
-    STAMP(5);
-    if (!ok) {
-        if (lane == 0) a.out_int[0] = kDenseNoConv;
+    if (!S.ints[2]) {
+        if (tid == 0) { a.out_int[0] = kDenseNoConv; a.out_int[1] = nk; a.out_int[2] = 0; }
         return;
     }
-    // eigenvalue list from the quasi-triangular T = H
-    if (lane == 0) {
-        int q = 0;
-        int i = 0;
+    // ---- 4. order by |xi| (xi = 1/tau), conjugate pairs adjacent, select k'
+    if (tid == 0) {
+        int q = 0, i = 0;
         while (i < nk) {
-            if (i + 1 < nk && S.H[(i + 1) * ld + i] != 0.0) {
-                double aa = S.H[i * ld + i], bb = S.H[i * ld + i + 1], cc = S.H[(i + 1) * ld + i],
-                       dd = S.H[(i + 1) * ld + i + 1];
-                double hf = 0.5 * (aa - dd);
-                double disc = hf * hf + bb * cc;
-                double re = 0.5 * (aa + dd), im = sqrt(fmax(-disc, 0.0));
-                // tau = re +- i im;  xi = 1/tau.  Record the member with Im(xi) > 0,
-                // i.e. Im(tau) < 0, first.
-                S.eig_re[q] = re; S.eig_im[q] = -im; S.eig_pos[q] = i; S.eig_blk[q] = 1; ++q;
-                S.eig_re[q] = re; S.eig_im[q] = im; S.eig_pos[q] = i; S.eig_blk[q] = 1; ++q;
+            if (i + 1 < nk && S.H[(i + 1) * LDS + i] != 0.0) {
+                double aa = S.H[i * LDS + i], bb = S.H[i * LDS + i + 1], cc = S.H[(i + 1) * LDS + i],
+                       dd = S.H[(i + 1) * LDS + i + 1];
+                double hf = 0.5 * (aa - dd), disc = hf * hf + bb * cc;
+                if (disc >= 0.0) {   // deflated block with two real eigenvalues
+                    double sq = sqrt(disc);
+                    S.eig_re[q] = 0.5 * (aa + dd) + sq; S.eig_im[q] = 0.0; ++q;
+                    S.eig_re[q] = 0.5 * (aa + dd) - sq; S.eig_im[q] = 0.0; ++q;
+                } else {
+                    // tau = re -+ i im: the member with Im(tau) < 0 has Im(xi) > 0
+                    S.eig_re[q] = 0.5 * (aa + dd); S.eig_im[q] = -sqrt(-disc); ++q;
+                    S.eig_re[q] = 0.5 * (aa + dd); S.eig_im[q] = sqrt(-disc); ++q;
+                }
                 i += 2;
             } else {
-                S.eig_re[q] = S.H[i * ld + i]; S.eig_im[q] = 0.0; S.eig_pos[q] = i; S.eig_blk[q] = 0; ++q;
+                S.eig_re[q] = S.H[i * LDS + i]; S.eig_im[q] = 0.0; ++q;
                 i += 1;
             }
         }
-        // ---- 4. ordering: units (real eigenvalue or conjugate pair) by (|xi|, Re xi)
-        // xi = 1/tau = conj(tau) / |tau|^2
+        // units: real eigenvalues and conjugate pairs (represented by Im(tau) < 0)
         int nu = 0;
-        int unit_first[MAXM];
+        int unit_e[MAXM];
         double key_abs[MAXM], key_re[MAXM];
         for (int e = 0; e < nk; ++e) {
-            if (S.eig_blk[e] && S.eig_im[e] > 0.0) continue;   // second member of a pair
-            double re = S.eig_re[e], im = S.eig_im[e];
-            double m2 = re * re + im * im;
+            if (S.eig_im[e] > 0.0) continue;
+            double re = S.eig_re[e], im = S.eig_im[e], m2 = re * re + im * im;
             double xr = m2 > 0.0 ? re / m2 : INFINITY, xim = m2 > 0.0 ? -im / m2 : 0.0;
             key_abs[nu] = m2 > 0.0 ? hypot(xr, xim) : INFINITY;
             key_re[nu] = xr;
-            unit_first[nu] = e;
+            unit_e[nu] = e;
             ++nu;
         }
-        // insertion sort (stable)
         for (int i2 = 1; i2 < nu; ++i2) {
             double ka = key_abs[i2], kr = key_re[i2];
-            int uf = unit_first[i2];
+            int ue = unit_e[i2];
             int j = i2 - 1;
             while (j >= 0 && (key_abs[j] > ka || (key_abs[j] == ka && key_re[j] > kr))) {
-                key_abs[j + 1] = key_abs[j]; key_re[j + 1] = key_re[j]; unit_first[j + 1] = unit_first[j];
+                key_abs[j + 1] = key_abs[j]; key_re[j + 1] = key_re[j]; unit_e[j + 1] = unit_e[j];
                 --j;
             }
-            key_abs[j + 1] = ka; key_re[j + 1] = kr; unit_first[j + 1] = uf;
+            key_abs[j + 1] = ka; key_re[j + 1] = kr; unit_e[j + 1] = ue;
         }
-        // expand to the first kp eigenvalues; record the selection
-        int sel = 0;
-        int nsel_units = 0;
+        int sel = 0, ns = 0;
         for (int u = 0; u < nu && sel < kp; ++u) {
-            int e = unit_first[u];
-            S.order[nsel_units] = e;
-            S.partner[nsel_units] = S.eig_blk[e] ? ((kp - sel >= 2) ? 2 : 1) : 0;  // 0 real, 2 full pair, 1 cut pair
-            sel += S.eig_blk[e] ? 2 : 1;
-            ++nsel_units;
+            int e = unit_e[u];
+            bool pair = S.eig_im[e] != 0.0;
+            S.order[ns] = e;
+            S.kind[ns] = pair ? ((kp - sel >= 2) ? 2 : 1) : 0;
+            sel += pair ? 2 : 1;
+            ++ns;
         }
-        a.out_int[2] = nsel_units;
-    }
-    wsync();
-    int nsel_units = a.out_int[2];
-    __syncwarp();
-    nsel_units = __shfl_sync(0xffffffffu, nsel_units, 0);
-    // ---- eigenvectors of C for the selected units (z = Z x), then y = L^-T z
-    // Store complex y (kept basis) into global scratch Y: [unit][nk] re, im
-    double* Yre = G + 2 * m * m;
-    double* Yim = Yre + MAXM * MAXM;
-    double anorm = 0.0;
-    for (int i = lane; i < nk * nk; i += 32) anorm = fmax(anorm, fabs(S.H[(i / nk) * ld + i % nk]));
-    for (int o = 16; o > 0; o >>= 1) anorm = fmax(anorm, __shfl_xor_sync(0xffffffffu, anorm, o));
-    const double smallnum = DBL_EPSILON * (anorm > 0 ? anorm : 1.0);
-    STAMP(6);
-    // one selected unit per lane: eigenvector x of the quasi-triangular T
-    // (back substitution), z = Z x, y = L^{-T} z, normalise, rotate pairs
-    for (int u = lane; u < nsel_units; u += 32) {
-        int e = S.order[u];
-        cplx* x = S.x + u * MAXM;
-        cplx lam = {S.eig_re[e], S.eig_im[e]};
-        schur_eigvec(S.H, nk, ld, S.eig_pos[e], S.eig_blk[e] != 0, lam, x, smallnum);
-        double* yr = Yre + u * MAXM;
-        double* yi = Yim + u * MAXM;
-        for (int r = 0; r < nk; ++r) {
-            double zr = 0.0, zi = 0.0;
-            for (int l = 0; l < nk; ++l) {
-                zr += S.Z[r * ld + l] * x[l].re;
-                zi += S.Z[r * ld + l] * x[l].im;
+        // numerical clusters among the selected: later members get a shifted
+        // inverse iteration and are orthogonalised against earlier ones
+        for (int u = 0; u < ns; ++u) {
+            int c = 0;
+            double re = S.eig_re[S.order[u]], im = S.eig_im[S.order[u]];
+            double mag = fmax(fabs(re) + fabs(im), 1e-300);
+            for (int v = 0; v < u; ++v) {
+                double d = fabs(S.eig_re[S.order[v]] - re) + fabs(S.eig_im[S.order[v]] - im);
+                if (d <= 1e-8 * mag) ++c;
             }
-            yr[r] = zr;
-            yi[r] = zi;
+            S.nclose[u] = c;
         }
-        for (int i = nk - 1; i >= 0; --i) {
-            double sr = yr[i], si = yi[i];
-            for (int l = i + 1; l < nk; ++l) {
-                sr -= S.B[l * ld + i] * yr[l];
-                si -= S.B[l * ld + i] * yi[l];
-            }
-            yr[i] = sr / S.B[i * ld + i];
-            yi[i] = si / S.B[i * ld + i];
-        }
-        double aa = 0.0, bb = 0.0, ab = 0.0;
-        for (int i = 0; i < nk; ++i) {
-            aa += yr[i] * yr[i]; bb += yi[i] * yi[i]; ab += yr[i] * yi[i];
-        }
-        double c = 1.0, sn = 0.0;
-        if (S.eig_blk[e]) {
-            double phi = 0.5 * atan2(-2.0 * ab, aa - bb);
-            c = cos(phi); sn = sin(phi);
-        }
-        double nrm = sqrt(aa + bb);
-        for (int i = 0; i < nk; ++i) {
-            double r = yr[i], im = yi[i];
-            yr[i] = (r * c - im * sn) / nrm;
-            yi[i] = (r * sn + im * c) / nrm;
-        }
-    }
-    wsync();
-    STAMP(7);
-    // ---- Y' = [Y0 YR yR~ YI] columns, in kept basis; tags
-    // column order: real units, then full pairs' real parts, then the cut
-    // column, then full pairs' imaginary parts
-    double* Yp = Yim + MAXM * MAXM;  // [kp][nk]
-    if (lane == 0) {
-        int col = 0;
-        int npair = 0;
-        for (int u = 0; u < nsel_units; ++u) if (S.partner[u] == 2) ++npair;
-        int nreal = 0;
-        for (int u = 0; u < nsel_units; ++u) if (S.partner[u] == 0) ++nreal;
-        int pr = 0;
-        bool has_cut = false;
-        for (int u = 0; u < nsel_units; ++u) if (S.partner[u] == 1) has_cut = true;
-        for (int u = 0; u < nsel_units; ++u) {
-            int kind = S.partner[u];
-            if (kind == 0) {
-                for (int i = 0; i < nk; ++i) Yp[col * MAXM + i] = Yre[u * MAXM + i];
-                a.tags[col] = 0; a.tag_partner[col] = -1;
-                ++col;
-            }
-        }
-        int base_R = nreal, base_cut = nreal + npair, base_I = nreal + npair + (has_cut ? 1 : 0);
-        for (int u = 0; u < nsel_units; ++u) {
-            int kind = S.partner[u];
-            if (kind == 2) {
-                int cr = base_R + pr, ci = base_I + pr;
-                for (int i = 0; i < nk; ++i) {
-                    Yp[cr * MAXM + i] = Yre[u * MAXM + i];
-                    Yp[ci * MAXM + i] = Yim[u * MAXM + i];
-                }
-                a.tags[cr] = 1; a.tag_partner[cr] = ci;
-                a.tags[ci] = 3; a.tag_partner[ci] = cr;
-                ++pr;
-            } else if (kind == 1) {
-                for (int i = 0; i < nk; ++i) Yp[base_cut * MAXM + i] = Yre[u * MAXM + i];
-                a.tags[base_cut] = 2; a.tag_partner[base_cut] = -1;
-            }
-        }
-        // diagnostic xi of the selected columns
-        for (int u = 0; u < nsel_units; ++u) {
+        S.ints[3] = ns;
+        for (int u = 0; u < ns; ++u) {
             int e = S.order[u];
             double re = S.eig_re[e], im = S.eig_im[e], m2 = re * re + im * im;
             a.xi[2 * u] = re / m2;
             a.xi[2 * u + 1] = -im / m2;
         }
     }
-    wsync();
-    // ---- 5. raw coefficients.  Z-hat = Z diag(colscale t) R^{-1}; R^{-1} is
-    // upper triangular and the V columns come first, so
-    //   P_new = Z-hat[:, rest] Y'_rest = Z diag(colscale t) R^{-1} [0; Y'_rest]
-    //   V_new - P_new = Z-hat[:, V] Y'_V = Z_V diag(colscale t) R_VV^{-1} Y'_V
-    double* Wr = Yp + MAXM * MAXM;   // [kp][nk]: R^{-1} [0; Y'_rest]
-    double* Wv = Wr + MAXM * MAXM;   // [kp][nk]: R_VV^{-1} Y'_V (rows < nvk)
-    for (int j = lane; j < kp; j += 32) {
-        for (int i = nk - 1; i >= 0; --i) {
-            double s = (i >= nvk) ? Yp[j * MAXM + i] : 0.0;
-            for (int l = i + 1; l < nk; ++l) s -= S.A[i * ld + l] * Wr[j * MAXM + l];
-            Wr[j * MAXM + i] = s / S.A[i * ld + i];
-        }
-        for (int i = nvk - 1; i >= 0; --i) {
-            double s = Yp[j * MAXM + i];
-            for (int l = i + 1; l < nvk; ++l) s -= S.A[i * ld + l] * Wv[j * MAXM + l];
-            Wv[j * MAXM + i] = s / S.A[i * ld + i];
+    bsync();
+    const int nsel = S.ints[3];
+    STAMP(5);
+    // ---- 5. eigenvectors of C for the selected units: inverse iteration on the
+    // Hessenberg form (one warp per unit), back to C's basis with the Householder
+    // reflectors, then y = L^{-T} z in the orthonormal basis
+    {
+        double hn = 0.0;
+        for (int i = tid; i < nk * nk; i += NT) hn = fmax(hn, fabs(S.H0[(i / nk) * LDS + i % nk]));
+        hn = warp_max(hn);
+        if (lane == 0) S.red[warp] = hn;
+        bsync();
+        double hmax = 0.0;
+        for (int w = 0; w < NW; ++w) hmax = fmax(hmax, S.red[w]);
+        const double tiny = DBL_EPSILON * (hmax > 0.0 ? hmax : 1.0);
+        cplx* Uo = Uw + warp * (MAXM * (MAXM + 1) / 2);
+        __shared__ cplx xs[NW][MAXM], cs_[NW][MAXM], ns_[NW][MAXM];
+        for (int u = warp; u < nsel; u += NW) {
+            const int e = S.order[u];
+            cplx lam = {S.eig_re[e], S.eig_im[e]};
+            if (S.nclose[u] > 0) {
+                double f = 1.0 + 1e-10 * S.nclose[u];
+                lam = cscale(lam, f);
+            }
+            cplx* x = xs[warp];
+            inverse_iteration(S.H0, nk, lam, x, Uo, cs_[warp], ns_[warp], tiny);
+            // z = Q x with Q = H_0 H_1 ... (reflectors applied last-first)
+            for (int k = nk - 3; k >= 0; --k) {
+                const double b = S.beta[k];
+                if (b == 0.0) continue;
+                const double* v = S.Vh + k * LDS;
+                double sr = 0.0, si = 0.0;
+                for (int i = k + 1 + lane; i < nk; i += 32) { sr += v[i] * x[i].re; si += v[i] * x[i].im; }
+                sr = warp_sum(sr) * b;
+                si = warp_sum(si) * b;
+                wsync();
+                for (int i = k + 1 + lane; i < nk; i += 32) { x[i].re -= sr * v[i]; x[i].im -= si * v[i]; }
+                wsync();
+            }
+            // y = L^{-T} z  (back substitution with the lower factor L)
+            double* yr = Yre + u * MAXM;
+            double* yi = Yim + u * MAXM;
+            for (int i = nk - 1; i >= 0; --i) {
+                double sr = 0.0, si = 0.0;
+                for (int l = i + 1 + lane; l < nk; l += 32) {
+                    sr += S.B[l * LDS + i] * yr[l];
+                    si += S.B[l * LDS + i] * yi[l];
+                }
+                sr = warp_sum(sr);
+                si = warp_sum(si);
+                if (lane == 0) {
+                    yr[i] = (x[i].re - sr) / S.B[i * LDS + i];
+                    yi[i] = (x[i].im - si) / S.B[i * LDS + i];
+                }
+                __threadfence_block();
+                wsync();
+            }
         }
     }
-    wsync();
-    for (int i = lane; i < m * kp; i += 32) a.Cp[i] = 0.0;
-    for (int i = lane; i < a.nv * kp; i += 32) a.Cvv[i] = 0.0;
-    wsync();
-    for (int i = lane; i < nk * kp; i += 32) {
-        int q = i / kp, j = i % kp;
-        int raw = S.kidx[q];
-        double tr = S.t[raw] * a.colscale[raw];
+    bsync();
+    STAMP(6);
+    // ---- cluster orthogonalisation, pair rotation, unit norm (warp 0, in the
+    // orthonormal basis: plain complex inner products)
+    if (warp == 0) {
+        for (int u = 0; u < nsel; ++u) {
+            double* yr = Yre + u * MAXM;
+            double* yi = Yim + u * MAXM;
+            if (S.nclose[u] > 0) {
+                const int e = S.order[u];
+                const double re = S.eig_re[e], im = S.eig_im[e];
+                const double mag = fmax(fabs(re) + fabs(im), 1e-300);
+                for (int v = 0; v < u; ++v) {
+                    const int f = S.order[v];
+                    if (fabs(S.eig_re[f] - re) + fabs(S.eig_im[f] - im) > 1e-8 * mag) continue;
+                    const double* vr = Yre + v * MAXM;
+                    const double* vi = Yim + v * MAXM;
+                    // y -= v (v^H y) / (v^H v)
+                    double pr = 0.0, pi = 0.0, vv = 0.0;
+                    for (int i = lane; i < nk; i += 32) {
+                        pr += vr[i] * yr[i] + vi[i] * yi[i];
+                        pi += vr[i] * yi[i] - vi[i] * yr[i];
+                        vv += vr[i] * vr[i] + vi[i] * vi[i];
+                    }
+                    pr = warp_sum(pr); pi = warp_sum(pi); vv = warp_sum(vv);
+                    pr /= vv; pi /= vv;
+                    for (int i = lane; i < nk; i += 32) {
+                        double ar = vr[i] * pr - vi[i] * pi, ai = vr[i] * pi + vi[i] * pr;
+                        yr[i] -= ar;
+                        yi[i] -= ai;
+                    }
+                    __threadfence_block();
+                    wsync();
+                }
+            }
+            double aa = 0.0, bb = 0.0, ab = 0.0;
+            for (int i = lane; i < nk; i += 32) { aa += yr[i] * yr[i]; bb += yi[i] * yi[i]; ab += yr[i] * yi[i]; }
+            aa = warp_sum(aa); bb = warp_sum(bb); ab = warp_sum(ab);
+            double c = 1.0, sn = 0.0;
+            if (S.kind[u] != 0) {
+                double phi = 0.5 * atan2(-2.0 * ab, aa - bb);
+                c = cos(phi); sn = sin(phi);
+            }
+            double nrm = sqrt(aa + bb);
+            if (!(nrm > 0.0)) nrm = 1.0;
+            for (int i = lane; i < nk; i += 32) {
+                double r = yr[i], im2 = yi[i];
+                yr[i] = (r * c - im2 * sn) / nrm;
+                yi[i] = (r * sn + im2 * c) / nrm;
+            }
+            __threadfence_block();
+            wsync();
+        }
+    }
+    bsync();
+    // ---- Y' = [Y0 YR yR~ YI] (kept basis), column tags
+    if (tid == 0) {
+        int nreal = 0, npair = 0;
+        bool has_cut = false;
+        for (int u = 0; u < nsel; ++u) {
+            if (S.kind[u] == 0) ++nreal;
+            else if (S.kind[u] == 2) ++npair;
+            else has_cut = true;
+        }
+        int col = 0, pr = 0;
+        const int base_R = nreal, base_cut = nreal + npair, base_I = nreal + npair + (has_cut ? 1 : 0);
+        for (int u = 0; u < nsel; ++u) {
+            const double* yr = Yre + u * MAXM;
+            const double* yi = Yim + u * MAXM;
+            if (S.kind[u] == 0) {
+                for (int i = 0; i < nk; ++i) Yp[col * MAXM + i] = yr[i];
+                a.tags[col] = 0; a.tag_partner[col] = -1;
+                ++col;
+            } else if (S.kind[u] == 2) {
+                const int cr = base_R + pr, ci = base_I + pr;
+                for (int i = 0; i < nk; ++i) { Yp[cr * MAXM + i] = yr[i]; Yp[ci * MAXM + i] = yi[i]; }
+                a.tags[cr] = 1; a.tag_partner[cr] = ci;
+                a.tags[ci] = 3; a.tag_partner[ci] = cr;
+                ++pr;
+            } else {
+                for (int i = 0; i < nk; ++i) Yp[base_cut * MAXM + i] = yr[i];
+                a.tags[base_cut] = 2; a.tag_partner[base_cut] = -1;
+            }
+        }
+    }
+    __threadfence_block();
+    bsync();
+    STAMP(7);
+    // ---- 6. raw coefficients.  Z-hat = Z diag(colscale t) R^{-1}; R^{-1} is
+    // upper triangular with the V columns first, so
+    //   P_new = Z-hat[:, rest] Y'_rest = Z diag(colscale t) R^{-1} [0; Y'_rest]
+    //   V_new - P_new = Z-hat[:, V] Y'_V = Z_V diag(colscale t) R_VV^{-1} Y'_V
+    if (tid < kp) {
+        const int j = tid;
+        for (int i = nk - 1; i >= 0; --i) {
+            double sv = (i >= nvk) ? Yp[j * MAXM + i] : 0.0;
+            for (int l = i + 1; l < nk; ++l) sv -= S.A[i * LDS + l] * Wr[j * MAXM + l];
+            Wr[j * MAXM + i] = sv / S.A[i * LDS + i];
+        }
+        for (int i = nvk - 1; i >= 0; --i) {
+            double sv = Yp[j * MAXM + i];
+            for (int l = i + 1; l < nvk; ++l) sv -= S.A[i * LDS + l] * Wv[j * MAXM + l];
+            Wv[j * MAXM + i] = sv / S.A[i * LDS + i];
+        }
+    }
+    for (int i = tid; i < m * kp; i += NT) a.Cp[i] = 0.0;
+    for (int i = tid; i < a.nv * kp; i += NT) a.Cvv[i] = 0.0;
+    __threadfence_block();
+    bsync();
+    for (int i = tid; i < nk * kp; i += NT) {
+        const int q = i / kp, j = i % kp;
+        const int raw = S.kidx[q];
+        const double tr = S.t[raw] * a.colscale[raw];
         a.Cp[raw * kp + j] = tr * Wr[j * MAXM + q];
         if (q < nvk) a.Cvv[raw * kp + j] = tr * Wv[j * MAXM + q];
     }
-    wsync();
     STAMP(8);
-    if (lane == 0) a.out_int[0] = kDenseOK;
+    if (tid == 0) {
+        a.out_int[0] = kDenseOK;
+        a.out_int[1] = nk;
+        a.out_int[2] = nsel;
+    }
 #undef STAMP
 }
 
@@ -761,13 +827,16 @@ retry:
 
 size_t dense_smem_bytes() { return sizeof(Smem); }
 
-size_t dense_work_doubles() { return 2 * (size_t)MAXM * MAXM + 6 * (size_t)MAXM * MAXM; }
+// Yre, Yim, Yp (3 MAXM^2) and the per-warp packed LU factors (NW MAXM(MAXM+1)/2
+// complex) fit in 8 MAXM^2 doubles.
+size_t dense_work_doubles() { return 8 * (size_t)MAXM * MAXM; }
+static_assert(3 * MAXM * MAXM + 2 * NW * (MAXM * (MAXM + 1) / 2) <= 8 * MAXM * MAXM, "dense scratch layout");
 
 cudaError_t dense_extract(const DenseArgs& a, cudaStream_t s) {
     size_t shm = sizeof(Smem);
     cudaError_t e = cudaFuncSetAttribute(k_extract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
-    k_extract<<<1, 32, shm, s>>>(a);
+    k_extract<<<1, NT, shm, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
