@@ -17,6 +17,7 @@ and the time is the maximum over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -51,6 +52,11 @@ def _peaks():
 
 # FP64 rate of GB300 from the profiling recipe's nominal table (1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 1.25
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_gram launch on the
+# 64^3 case (n = 262,144, m = 64): 446.1 MB, i.e. bytes per (row x trial column);
+# the traffic grows in proportion to n m (profiles/k_gram_lap3d_64cube.md).
+GRAM_DRAM_BYTES_PER_ROW_COL = 446.1e6 / (262144 * 64)
 
 
 class ClockSampler:
@@ -150,6 +156,14 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     w = wl.config2()
+    profile_case = args.profile_grid > 0
+    if profile_case:
+        # reduced grid with the same structure, a fixed number of iterations:
+        # the case the ncu captures run on
+        N = args.profile_grid
+        w = dataclasses.replace(w, name="lap3d_%dcube_k10_%dit" % (N, args.profile_iters), dims=(N, N, N),
+                                h=1.0 / (N + 1), maxit=args.profile_iters,
+                                mg_levels=max(1, int(round(math.log2(N / 16)))) + 1)
     n, k, kp = w.n, w.k, w.kprime
     t_setup = time.perf_counter()
     A = plhr.Operator.laplacian(w.dims, w.h)
@@ -161,8 +175,8 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
 
     def one(vinit):
-        return plhr.solve(A, w.sigma, k, T=T, tol=w.tol, maxit=w.maxit, v_init=vinit, raise_on_notconv=True,
-                          guard=w.guard)
+        return plhr.solve(A, w.sigma, k, T=T, tol=w.tol, maxit=w.maxit, v_init=vinit,
+                          raise_on_notconv=not profile_case, guard=w.guard)
 
     for _ in range(args.warmup):
         lam, V, info = one(v0)
@@ -194,6 +208,12 @@ def run_ours(args, world, rank, local):
     step_s = _max_over_ranks(statistics.mean(times), world)
     iters = info["iterations"]
 
+    if profile_case:
+        if rank == 0:
+            print(json.dumps({"profile_case": w.name, "seconds": step_s, "iterations": iters,
+                              "gpu_launches": launches,
+                              "phases_ms": {p: prof[p]["ms"] / max(1, args.steps) for p in prof}}), flush=True)
+        return
     # closed-form check of the returned eigenvalues
     cf = wl.lap_closed_form(w.dims, w.h)
     want = np.sort(cf[np.lexsort((cf, np.abs(cf - w.sigma)))][:k])
@@ -227,7 +247,9 @@ def run_ours(args, world, rank, local):
         achieved = flops / per / 1e12
         roof = {"kernel": "k_gram (FP64 multi-Gram Z^T Z, U^T Q, Q^T Z)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": GRAM_DRAM_BYTES_PER_ROW_COL * n * m_avg,
+                "traffic_note": "ncu dram bytes of k_gram on the 64^3 case scaled by n m",
                 "peak_src": "nominal FP64 rate of the profiling recipe"}
     elif dom == "update":
         flops = 3 * 2.0 * n * (m_avg * kp + kp * kp)
@@ -329,6 +351,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["f64"], default="f64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-grid", type=int, default=0,
+                    help="profiling case: N^3 grid of the same problem, fixed iteration count")
+    ap.add_argument("--profile-iters", type=int, default=3)
     args = ap.parse_args()
     world, rank, local = _dist()
     if world > 1 and args.impl == "ours":
