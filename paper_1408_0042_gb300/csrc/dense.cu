@@ -20,6 +20,7 @@
 //     and the longer of the two, build the real Y' = [Y0 YR yR~ YI].
 //  5. Coefficients on the raw basis: P_new = Z C_P, V_new = V C_VV + P_new.
 #include "dense.h"
+#include "dword.h"
 
 #include <cfloat>
 #include <mutex>
@@ -212,52 +213,87 @@ __device__ void bhessenberg(double* H, double* Vh, double* beta, int n, double* 
 }
 
 // ---------------------------------------------------------------- eigenvalues (one warp)
-// Householder vector for (x, y[, z]): u = (1, u1, u2), tau with
-// (I - tau u u^T)(x, y, z)^T = (beta, 0, 0)^T.
-__device__ __forceinline__ void house3(double x, double y, double z, int nr, double& u1, double& u2, double& tau) {
-    double nrm = sqrt(x * x + y * y + (nr == 3 ? z * z : 0.0));
-    if (nrm == 0.0 || (y == 0.0 && (nr == 2 || z == 0.0))) {
-        u1 = 0.0; u2 = 0.0; tau = 0.0;
+// Householder vector for (x, y[, z]) in double-word arithmetic: u = (1, u1, u2)
+// and tau with (I - tau u u^T)(x, y, z)^T = (beta, 0, 0)^T.
+__device__ __forceinline__ void house3(dw x, dw y, dw z, int nr, dw& u1, dw& u2, dw& tau) {
+    const dw zero = dw_make(0.0f);
+    if (dw_is_zero(y) && (nr == 2 || dw_is_zero(z))) {
+        u1 = zero; u2 = zero; tau = zero;
         return;
     }
-    double beta = x > 0 ? -nrm : nrm;
-    double v0 = x - beta;
-    u1 = y / v0;
-    u2 = nr == 3 ? z / v0 : 0.0;
-    tau = (beta - x) / beta;
+    // u and tau do not depend on the scale of (x, y, z): bring the largest to
+    // about 1 by a power of two (exact) so that the squares stay inside FP32's
+    // exponent range
+    {
+        const float mx = fmaxf(fabsf(x.hi), fmaxf(fabsf(y.hi), nr == 3 ? fabsf(z.hi) : 0.0f));
+        const float sc = pow2_inverse_of(mx);
+        x = dw_mul_pow2(x, sc);
+        y = dw_mul_pow2(y, sc);
+        z = dw_mul_pow2(z, sc);
+    }
+    dw ss = dw_add(dw_mul(x, x), dw_mul(y, y));
+    if (nr == 3) ss = dw_add(ss, dw_mul(z, z));
+    dw nrm = dw_sqrt(ss);
+    if (dw_is_zero(nrm)) {
+        u1 = zero; u2 = zero; tau = zero;
+        return;
+    }
+    dw beta = x.hi > 0.0f ? dw_neg(nrm) : nrm;
+    dw v0 = dw_sub(x, beta);
+    dw rv = dw_div(dw_make(1.0f), v0);
+    u1 = dw_mul(y, rv);
+    u2 = nr == 3 ? dw_mul(z, rv) : zero;
+    tau = dw_div(dw_neg(v0), beta);   // (beta - x) / beta
 }
 
 // Francis double-shift QR (Golub & Van Loan Sec. 7.5) on the upper Hessenberg
 // H, eigenvalues only: every transformation is applied to the active window
 // rows/columns l..hi alone (no Schur vectors, no full Schur form), which is
 // all the eigenvalues need.  Deflated 1x1 and 2x2 diagonal blocks remain.
-// One warp; returns false if the iteration does not converge.
-__device__ bool francis_eigenvalues(double* H, int n) {
+// One warp.  The iteration runs in double-word arithmetic on H scaled by a
+// power of two to unit norm (H is converted in place: a double and a
+// double-word value take the same 8 bytes) and is converted back at the end.
+// Returns false if the iteration does not converge; sweeps (optional) gets
+// the number of QR sweeps and of bulge steps.
+__device__ __noinline__ bool francis_eigenvalues(double* Hd, int n, long long* sweeps) {
     const int lane = threadIdx.x & 31;
-    const double eps = DBL_EPSILON;
     double anorm = 0.0;
     for (int i = lane; i < n * n; i += 32) {
         int r = i / n, c = i % n;
-        if (c >= r - 1) anorm = fmax(anorm, fabs(H[r * LDS + c]));
+        if (c >= r - 1) anorm = fmax(anorm, fabs(Hd[r * LDS + c]));
     }
     anorm = warp_max(anorm);
-    if (anorm == 0.0) anorm = 1.0;
+    const int ex = anorm > 0.0 ? ilogb(anorm) : 0;
+    const double down = ldexp(1.0, -ex), up = ldexp(1.0, ex);
+    dw* H = reinterpret_cast<dw*>(Hd);
+    wsync();
+    for (int i = lane; i < n * n; i += 32) {
+        int r = i / n, c = i % n;
+        double v = (c >= r - 1) ? Hd[r * LDS + c] * down : 0.0;
+        H[r * LDS + c] = dw_from_double(v);
+    }
+    wsync();
+    // negligible subdiagonal: relative to the neighbouring diagonal, or to
+    // ||H|| (= 1 to 2 after scaling; normwise backward stable).  Only the
+    // eigenvalues of largest modulus are used, and they keep full relative
+    // accuracy; the normwise test lets the many eigenvalues near zero deflate
+    // quickly.  eps is a few units of the double-word precision.
+    const float eps = 0x1p-46f;
+    const float hnorm = 1.0f;
+    const dw zero = dw_make(0.0f);
+    bool ok = true;
     int hi = n - 1;
-    int its = 0, total_its = 0;
+    int its = 0, total_its = 0, total_steps = 0;
     while (hi >= 0) {
-        // negligible subdiagonal: relative to the neighbouring diagonal, or to
-        // ||H|| (normwise backward stable).  Only the eigenvalues of largest
-        // modulus are used, and they keep full relative accuracy; the normwise
-        // test lets the many eigenvalues near zero deflate quickly.
         int l = hi;
         while (l > 0) {
-            double s = fabs(H[(l - 1) * LDS + l - 1]) + fabs(H[l * LDS + l]);
-            if (s < anorm) s = anorm;
-            if (fabs(H[l * LDS + l - 1]) <= eps * s) break;
+            float s = fabsf(H[(l - 1) * LDS + l - 1].hi) + fabsf(H[l * LDS + l].hi);
+            if (s < hnorm) s = hnorm;
+            if (fabsf(H[l * LDS + l - 1].hi) <= eps * s) break;
             --l;
         }
         wsync();
-        if (l > 0 && lane == 0) H[l * LDS + l - 1] = 0.0;
+        if (l > 0 && lane == 0) H[l * LDS + l - 1] = zero;
         wsync();
         if (l >= hi - 1) {          // 1x1 or 2x2 block converged
             hi = l - 1;
@@ -270,78 +306,115 @@ __device__ bool francis_eigenvalues(double* H, int n) {
             // smallest subdiagonal when it is below 1e-7 ||H|| (the eigenvalues
             // move by about that much; only a basis of the cluster is needed)
             int jm = l + 1;
-            double vm = fabs(H[(l + 1) * LDS + l]);
+            float vm = fabsf(H[(l + 1) * LDS + l].hi);
             for (int j = l + 2; j <= hi; ++j) {
-                double v = fabs(H[j * LDS + j - 1]);
+                float v = fabsf(H[j * LDS + j - 1].hi);
                 if (v < vm) { vm = v; jm = j; }
             }
-            if (vm <= 1e-7 * anorm) {
+            if (vm <= 1e-7f * hnorm) {
                 wsync();
-                if (lane == 0) H[jm * LDS + jm - 1] = 0.0;
+                if (lane == 0) H[jm * LDS + jm - 1] = zero;
                 wsync();
                 its = 0;
                 continue;
             }
         }
-        if (++total_its > 100 * n) return false;
+        if (++total_its > 100 * n) { ok = false; break; }
         ++its;
-        double s, t;
+        total_steps += hi - l;
+        dw s, t;
         if (its % 10 == 0) {
-            double w = fabs(H[hi * LDS + hi - 1]) + fabs(H[(hi - 1) * LDS + hi - 2]);
-            s = 1.5 * w;
-            t = w * w;
+            dw w = dw_add(dw_make(fabsf(H[hi * LDS + hi - 1].hi)), dw_make(fabsf(H[(hi - 1) * LDS + hi - 2].hi)));
+            s = dw_mul_f(w, 1.5f);
+            t = dw_mul(w, w);
         } else {
-            double a = H[(hi - 1) * LDS + hi - 1], b = H[(hi - 1) * LDS + hi], c = H[hi * LDS + hi - 1],
-                   d = H[hi * LDS + hi];
-            s = a + d;
-            t = a * d - b * c;
+            dw a = H[(hi - 1) * LDS + hi - 1], b = H[(hi - 1) * LDS + hi], c = H[hi * LDS + hi - 1],
+               d = H[hi * LDS + hi];
+            s = dw_add(a, d);
+            t = dw_sub(dw_mul(a, d), dw_mul(b, c));
         }
-        double h00 = H[l * LDS + l], h01 = H[l * LDS + l + 1], h10 = H[(l + 1) * LDS + l],
-               h11 = H[(l + 1) * LDS + l + 1], h21 = H[(l + 2) * LDS + l + 1];
-        double x = h00 * h00 + h01 * h10 - s * h00 + t;
-        double y = h10 * (h00 + h11 - s);
-        double z = h10 * h21;
+        dw h00 = H[l * LDS + l], h01 = H[l * LDS + l + 1], h10 = H[(l + 1) * LDS + l],
+           h11 = H[(l + 1) * LDS + l + 1], h21 = H[(l + 2) * LDS + l + 1];
+        // first column of (H - s1 I)(H - s2 I)
+        dw x = dw_add(dw_add(dw_mul(h00, dw_sub(h00, s)), dw_mul(h01, h10)), t);
+        dw y = dw_mul(h10, dw_sub(dw_add(h00, h11), s));
+        dw z = dw_mul(h10, h21);
         // every lane has read the shift and the first bulge column before any
         // lane writes (lanes of a warp need not run in lockstep)
         wsync();
         for (int k = l; k <= hi - 1; ++k) {
             const int nr = (k < hi - 1) ? 3 : 2;
-            double u1, u2, tau;
+            dw u1, u2, tau;
             house3(x, y, z, nr, u1, u2, tau);
-            if (tau != 0.0) {
+            if (!dw_is_zero(tau)) {
+                // left: rows k..k+2, columns c0..hi (a lane holds c and c + 32,
+                // both updated in one pass for instruction-level parallelism)
                 const int c0 = k > l ? k - 1 : l;
-                for (int c = c0 + lane; c <= hi; c += 32) {
-                    double sv = H[k * LDS + c] + u1 * H[(k + 1) * LDS + c] + (nr == 3 ? u2 * H[(k + 2) * LDS + c] : 0.0);
-                    sv *= tau;
-                    H[k * LDS + c] -= sv;
-                    H[(k + 1) * LDS + c] -= sv * u1;
-                    if (nr == 3) H[(k + 2) * LDS + c] -= sv * u2;
+                {
+                    const int ca = c0 + lane, cb = ca + 32;
+                    const bool va = ca <= hi, vb = cb <= hi;
+                    dw a0 = zero, a1 = zero, a2 = zero, b0 = zero, b1 = zero, b2 = zero;
+                    if (va) { a0 = H[k * LDS + ca]; a1 = H[(k + 1) * LDS + ca]; if (nr == 3) a2 = H[(k + 2) * LDS + ca]; }
+                    if (vb) { b0 = H[k * LDS + cb]; b1 = H[(k + 1) * LDS + cb]; if (nr == 3) b2 = H[(k + 2) * LDS + cb]; }
+                    dw sa = dw_mul(dw_add(dw_add(a0, dw_mul(u1, a1)), dw_mul(u2, a2)), tau);
+                    dw sb = dw_mul(dw_add(dw_add(b0, dw_mul(u1, b1)), dw_mul(u2, b2)), tau);
+                    if (va) {
+                        H[k * LDS + ca] = dw_sub(a0, sa);
+                        H[(k + 1) * LDS + ca] = dw_sub(a1, dw_mul(sa, u1));
+                        if (nr == 3) H[(k + 2) * LDS + ca] = dw_sub(a2, dw_mul(sa, u2));
+                    }
+                    if (vb) {
+                        H[k * LDS + cb] = dw_sub(b0, sb);
+                        H[(k + 1) * LDS + cb] = dw_sub(b1, dw_mul(sb, u1));
+                        if (nr == 3) H[(k + 2) * LDS + cb] = dw_sub(b2, dw_mul(sb, u2));
+                    }
                 }
                 wsync();
+                // right: columns k..k+2, rows l..min(k+3, hi)
                 const int r1 = (k + 3 < hi) ? k + 3 : hi;
-                for (int r = l + lane; r <= r1; r += 32) {
-                    double sv = H[r * LDS + k] + u1 * H[r * LDS + k + 1] + (nr == 3 ? u2 * H[r * LDS + k + 2] : 0.0);
-                    sv *= tau;
-                    H[r * LDS + k] -= sv;
-                    H[r * LDS + k + 1] -= sv * u1;
-                    if (nr == 3) H[r * LDS + k + 2] -= sv * u2;
+                {
+                    const int ra = l + lane, rb = ra + 32;
+                    const bool va = ra <= r1, vb = rb <= r1;
+                    dw a0 = zero, a1 = zero, a2 = zero, b0 = zero, b1 = zero, b2 = zero;
+                    if (va) { a0 = H[ra * LDS + k]; a1 = H[ra * LDS + k + 1]; if (nr == 3) a2 = H[ra * LDS + k + 2]; }
+                    if (vb) { b0 = H[rb * LDS + k]; b1 = H[rb * LDS + k + 1]; if (nr == 3) b2 = H[rb * LDS + k + 2]; }
+                    dw sa = dw_mul(dw_add(dw_add(a0, dw_mul(u1, a1)), dw_mul(u2, a2)), tau);
+                    dw sb = dw_mul(dw_add(dw_add(b0, dw_mul(u1, b1)), dw_mul(u2, b2)), tau);
+                    if (va) {
+                        H[ra * LDS + k] = dw_sub(a0, sa);
+                        H[ra * LDS + k + 1] = dw_sub(a1, dw_mul(sa, u1));
+                        if (nr == 3) H[ra * LDS + k + 2] = dw_sub(a2, dw_mul(sa, u2));
+                    }
+                    if (vb) {
+                        H[rb * LDS + k] = dw_sub(b0, sb);
+                        H[rb * LDS + k + 1] = dw_sub(b1, dw_mul(sb, u1));
+                        if (nr == 3) H[rb * LDS + k + 2] = dw_sub(b2, dw_mul(sb, u2));
+                    }
                 }
                 wsync();
             }
             if (k > l && lane == 0) {
-                H[(k + 1) * LDS + k - 1] = 0.0;
-                if (nr == 3) H[(k + 2) * LDS + k - 1] = 0.0;
+                H[(k + 1) * LDS + k - 1] = zero;
+                if (nr == 3) H[(k + 2) * LDS + k - 1] = zero;
             }
             wsync();
             if (k < hi - 1) {
                 x = H[(k + 1) * LDS + k];
                 y = H[(k + 2) * LDS + k];
-                z = (k < hi - 2) ? H[(k + 3) * LDS + k] : 0.0;
+                z = (k < hi - 2) ? H[(k + 3) * LDS + k] : zero;
             }
             wsync();
         }
     }
-    return true;
+    wsync();
+    for (int i = lane; i < n * n; i += 32) {
+        int r = i / n, c = i % n;
+        dw v = H[r * LDS + c];
+        Hd[r * LDS + c] = (c >= r - 1) ? dw_to_double(v) * up : 0.0;
+    }
+    if (sweeps && lane == 0) { sweeps[0] = total_its; sweeps[1] = total_steps; }
+    wsync();
+    return ok;
 }
 
 // ---------------------------------------------------------------- eigenvectors (one warp each)
@@ -555,7 +628,7 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a) {
     bsync();
     STAMP(3);
     if (warp == 0) {
-        bool conv = francis_eigenvalues(S.H, nk);
+        bool conv = francis_eigenvalues(S.H, nk, a.clk ? a.clk + 9 : nullptr);
         if (lane == 0) S.ints[2] = conv ? 1 : 0;
     }
     bsync();

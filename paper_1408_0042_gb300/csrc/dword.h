@@ -1,0 +1,129 @@
+// Double-word ("double-float") arithmetic: a value is the unevaluated sum
+// hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2, about 48 significant
+// bits.  On GB300 an FP64 warp instruction occupies the FP64 pipe for 64
+// cycles whatever the number of active lanes, while FP32 instructions issue
+// every cycle or two; latency-bound serial FP64 code (the QR iteration of the
+// small projected problem) runs several times faster in double-word form.
+//
+// The building blocks are the error-free transformations of Knuth (TwoSum),
+// Dekker (Fast2Sum) and the FMA-based exact product, combined as in
+// M. Joldes, J.-M. Muller, V. Popescu, "Tight and rigorous error bounds for
+// basic building blocks of double-word arithmetic", ACM TOMS 44(2), 2017:
+// the accurate double-word sum (relative error a small multiple of u^2), the
+// FMA-based double-word product, and Newton-type corrections for the quotient
+// and the square root.  u = 2^-24.  Every operation uses the _rn intrinsics
+// so that the compiler neither contracts nor reassociates them.
+//
+// The exponent range is FP32's: callers scale their data by a power of two
+// so that the magnitudes of interest stay far from under- and overflow.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace plhr {
+
+struct dw {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dw dw_make(float a) { return {a, 0.0f}; }
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ dw dw_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// s + e = a + b exactly when |a| >= |b| or a == 0 (Dekker)
+__device__ __forceinline__ dw dw_fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+// p + e = a * b exactly (FMA)
+__device__ __forceinline__ dw dw_two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return {p, e};
+}
+
+__device__ __forceinline__ dw dw_add(dw a, dw b) {
+    dw s = dw_two_sum(a.hi, b.hi);
+    dw t = dw_two_sum(a.lo, b.lo);
+    float c = __fadd_rn(s.lo, t.hi);
+    dw v = dw_fast_two_sum(s.hi, c);
+    float w = __fadd_rn(t.lo, v.lo);
+    return dw_fast_two_sum(v.hi, w);
+}
+
+__device__ __forceinline__ dw dw_neg(dw a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dw dw_sub(dw a, dw b) { return dw_add(a, dw_neg(b)); }
+
+__device__ __forceinline__ dw dw_mul(dw a, dw b) {
+    dw p = dw_two_prod(a.hi, b.hi);
+    float t = __fmul_rn(a.hi, b.lo);
+    t = __fmaf_rn(a.lo, b.hi, t);
+    float c = __fadd_rn(p.lo, t);
+    return dw_fast_two_sum(p.hi, c);
+}
+
+// a * b for an FP32 b
+__device__ __forceinline__ dw dw_mul_f(dw a, float b) {
+    dw p = dw_two_prod(a.hi, b);
+    float c = __fmaf_rn(a.lo, b, p.lo);
+    return dw_fast_two_sum(p.hi, c);
+}
+
+// a / b: q1 = a_hi * rcp(b_hi) with the hardware reciprocal approximation,
+// then two corrections with the exact remainder a - q b (each roughly squares
+// the relative error: 2^-22 -> 2^-44 -> full double-word precision)
+__device__ __forceinline__ dw dw_div(dw a, dw b) {
+    const float r = __fdividef(1.0f, b.hi);
+    const float q1 = __fmul_rn(a.hi, r);
+    dw rem = dw_sub(a, dw_mul_f(b, q1));
+    dw q = dw_fast_two_sum(q1, __fmul_rn(rem.hi, r));
+    dw rem2 = dw_sub(a, dw_mul(b, q));
+    return dw_add(q, dw_make(__fmul_rn(rem2.hi, r)));
+}
+
+// sqrt(a), a >= 0: s1 = a_hi * rsqrt(a_hi) (hardware approximation), then two
+// Newton corrections s += (a - s^2) / (2 s)
+__device__ __forceinline__ dw dw_sqrt(dw a) {
+    if (a.hi <= 0.0f) return {0.0f, 0.0f};
+    const float rs = rsqrtf(a.hi);
+    const float s1 = __fmul_rn(a.hi, rs);
+    const float half_inv = __fmul_rn(0.5f, rs);   // ~ 1 / (2 s)
+    dw rem = dw_sub(a, dw_two_prod(s1, s1));
+    dw s = dw_fast_two_sum(s1, __fmul_rn(rem.hi, half_inv));
+    dw rem2 = dw_sub(a, dw_mul(s, s));
+    return dw_add(s, dw_make(__fmul_rn(rem2.hi, half_inv)));
+}
+
+// a * 2^k for a power of two p = 2^k (exact unless a component leaves the
+// FP32 range)
+__device__ __forceinline__ dw dw_mul_pow2(dw a, float p) { return {__fmul_rn(a.hi, p), __fmul_rn(a.lo, p)}; }
+
+// 2^-e for the binary exponent e of |x| (x normal: x 2^-e in [1, 2));
+// zero and subnormal x give 2^100, which brings any subnormal to about 1
+__device__ __forceinline__ float pow2_inverse_of(float x) {
+    const int be = (__float_as_int(x) >> 23) & 0xff;   // biased exponent
+    if (be == 0) return 0x1p100f;
+    const int k = be > 253 ? 253 : be;                // 2^-(k - 127) stays normal
+    return __int_as_float((254 - k) << 23);
+}
+
+__device__ __forceinline__ float dw_abs_hi(dw a) { return fabsf(a.hi); }
+__device__ __forceinline__ bool dw_is_zero(dw a) { return a.hi == 0.0f; }
+
+// conversions (FP64 instructions: use outside inner loops)
+__device__ __forceinline__ dw dw_from_double(double d) {
+    float hi = __double2float_rn(d);
+    float lo = __double2float_rn(d - (double)hi);
+    return {hi, lo};
+}
+__device__ __forceinline__ double dw_to_double(dw a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace plhr
