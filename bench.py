@@ -2,13 +2,16 @@
 
 Workload: 3D 7-point Dirichlet Laplacian on a 128^3 grid (n = 2,097,152,
 h = 1/129), sigma midway between the eigenvalues 1064.022 and 1073.120
-(index ~471), k = 10 wanted pairs (k' = 11 columns, real arithmetic),
-preconditioner = 4-level AV-MG V-cycle with 2 pre/post smoothing steps.
-A step is one complete solve from the seeded starting block to
-convergence (all k relative residuals <= 1e-8 after the final Rayleigh-Ritz).
+(index ~471), k = 10 wanted pairs (k' = 16 block columns: 6 guard columns so
+that the 1073.12 sextet and the 1080.75 sextet behind it fit the block, real
+arithmetic), preconditioner = 4-level AV-MG V-cycle with 2 pre/post smoothing
+steps.  A step is one complete solve from the seeded starting block to
+convergence (all k relative residuals <= 1e-8 after the final Rayleigh-Ritz),
+by default in the mixed-precision form (FP32 blocks and V-cycles until the k
+residuals reach 1e-5, then FP64); one all-FP64 solve is timed beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision f64]
+                    [--precision mixed|f64] [--no-f64-compare]
 
 One JSON line is printed by rank 0.  Under torchrun (N > 1) every rank solves
 its own replica (the problem does not shard on one-GPU machines: replicas only)
@@ -136,13 +139,42 @@ def _barrier(world):
         dist.barrier()
 
 
-def _vcycle_bytes(n, ncols, levels):
-    """Algorithmic HBM bytes of one V-cycle on ncols FP64 columns: the finest
-    level reads r and writes w once per smoothing step (2 nu sweeps) plus the
-    residual/restriction pass, i.e. about 6 column passes, and every coarser
-    level adds 1/8 of that."""
-    per_level = 6 * n * ncols * 8
-    return per_level * sum(0.125 ** l for l in range(levels))
+def _vcycle_bytes_per_element(levels, elem_bytes):
+    """Algorithmic HBM bytes of the V-cycle schedule per finest-level element
+    (grid point x column): on each smoothing level the fused first two sweeps
+    (read r, write w: 2 passes), the residual (3), the restriction (1 + 1/8),
+    the prolongation with correction (2 + 1/8) and two post-sweeps (6), i.e.
+    14.25 passes, each coarser level 1/8 of the one above (the coarsest solve
+    is a few KB per column)."""
+    return 14.25 * elem_bytes * sum(0.125 ** l for l in range(max(1, levels - 1)))
+
+
+def _fp32_simt_peak_tflops(sm_mhz):
+    """FP32 CUDA-core peak: 152 SMs x 128 FMA lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def _rooflines(prof, w, peaks, sm_max_mhz):
+    """Achieved rate of every profiled phase from its algorithmic work and its
+    CUDA-event time; returns the entries sorted by total time."""
+    out = []
+    fp32_peak = _fp32_simt_peak_tflops(sm_max_mhz or 2070.0)
+    for ph, kernel, bound, peak, unit, per in [
+            ("gram", "k_gram (FP64 multi-Gram)", "alu", FP64_PEAK_TFLOPS, "TFLOP/s", 1e-12),
+            ("gram_f32", "k_gram_mx (FP32 products, compensated sums)", "alu", fp32_peak, "TFLOP/s", 1e-12),
+            ("update", "k_update (FP64)", "alu", FP64_PEAK_TFLOPS, "TFLOP/s", 1e-12),
+            ("update_f32", "k_update_mx (FP32 with FP64 V part)", "alu", fp32_peak, "TFLOP/s", 1e-12),
+            ("preconditioner_f32", "FP32 AV-MG V-cycle kernels", "hbm", peaks["hbm_gbs"], "GB/s",
+             _vcycle_bytes_per_element(w.mg_levels, 4) * 1e-9),
+            ("preconditioner", "FP64 AV-MG V-cycle kernels", "hbm", peaks["hbm_gbs"], "GB/s",
+             _vcycle_bytes_per_element(w.mg_levels, 8) * 1e-9)]:
+        d = prof.get(ph)
+        if not d or d["ms"] <= 0 or d["work"] <= 0:
+            continue
+        achieved = d["work"] * per / (d["ms"] / 1e3)
+        out.append({"phase": ph, "kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                    "frac": achieved / peak, "total_ms": d["ms"], "calls": d["calls"]})
+    return sorted(out, key=lambda r: -r["total_ms"])
 
 
 def run_ours(args, world, rank, local):
@@ -165,6 +197,7 @@ def run_ours(args, world, rank, local):
                                 h=1.0 / (N + 1), maxit=args.profile_iters,
                                 mg_levels=max(1, int(round(math.log2(N / 16)))) + 1)
     n, k, kp = w.n, w.k, w.kprime
+    prec = {"mixed": plhr.PRECISION_MIXED, "f64": plhr.PRECISION_F64}[args.precision]
     t_setup = time.perf_counter()
     A = plhr.Operator.laplacian(w.dims, w.h)
     T = plhr.AVMG(A, w.sigma, levels=w.mg_levels, nu=w.mg_nu, transfer=MG_TRANSFER, coarse=MG_COARSE)
@@ -174,14 +207,22 @@ def run_ours(args, world, rank, local):
     setup_s = time.perf_counter() - t_setup
     stream = torch.cuda.current_stream()
 
-    def one(vinit):
+    def one(vinit, p=prec):
         return plhr.solve(A, w.sigma, k, T=T, tol=w.tol, maxit=w.maxit, v_init=vinit,
-                          raise_on_notconv=not profile_case, guard=w.guard)
+                          raise_on_notconv=not profile_case, guard=w.guard, precision=p)
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
 
     for _ in range(args.warmup):
         lam, V, info = one(v0)
     torch.cuda.synchronize()
-    iters = info["iterations"]
 
     # ---------------------------------------------------------------- timed region
     plhr.profile_read(reset=True)
@@ -192,13 +233,8 @@ def run_ours(args, world, rank, local):
         _barrier(world)
         torch.cuda.synchronize()
         for _ in range(args.steps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            lam, V, info = one(v0)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1) / 1e3)
+            (lam, V, info), dt = timed(lambda: one(v0))
+            times.append(dt)
         torch.cuda.synchronize()
         _barrier(world)
     launches = plhr.kernel_launches() - launches0
@@ -210,10 +246,18 @@ def run_ours(args, world, rank, local):
 
     if profile_case:
         if rank == 0:
-            print(json.dumps({"profile_case": w.name, "seconds": step_s, "iterations": iters,
-                              "gpu_launches": launches,
+            print(json.dumps({"profile_case": w.name, "precision": args.precision, "seconds": step_s,
+                              "iterations": iters, "gpu_launches": launches,
                               "phases_ms": {p: prof[p]["ms"] / max(1, args.steps) for p in prof}}), flush=True)
         return
+
+    # the all-FP64 form on the same input, for the mixed-vs-FP64 comparison
+    fp64_s, fp64_iters = None, None
+    if args.precision == "mixed" and not args.no_f64_compare:
+        (_, _, info64), fp64_s = timed(lambda: one(v0, plhr.PRECISION_F64))
+        fp64_s = _max_over_ranks(fp64_s, world)
+        fp64_iters = info64["iterations"]
+
     # closed-form check of the returned eigenvalues
     cf = wl.lap_closed_form(w.dims, w.h)
     want = np.sort(cf[np.lexsort((cf, np.abs(cf - w.sigma)))][:k])
@@ -225,65 +269,52 @@ def run_ours(args, world, rank, local):
     vecs_host = torch.empty((n, k), dtype=torch.float64).pin_memory()
     for _ in range(max(1, args.steps)):
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        vdev = v0_host.to("cuda", non_blocking=True)
-        lam2, V2, _ = one(vdev)
-        vecs_host.copy_(V2, non_blocking=True)
-        vals_host.copy_(torch.from_numpy(lam2))
-        e1.record(stream)
-        e1.synchronize()
-        e2e_times.append(e0.elapsed_time(e1) / 1e3)
+
+        def e2e_step():
+            vdev = v0_host.to("cuda", non_blocking=True)
+            lam2, V2, _ = one(vdev)
+            vecs_host.copy_(V2, non_blocking=True)
+            vals_host.copy_(torch.from_numpy(lam2))
+        _, dt = timed(e2e_step)
+        e2e_times.append(dt)
     e2e_s = _max_over_ranks(statistics.mean(e2e_times), world)
 
-    # ---------------------------------------------------------------- roofline of the dominant phase
+    # ---------------------------------------------------------------- rooflines
     peaks = _peaks()
-    dom = max(("preconditioner", "gram", "update", "stencil"), key=lambda p: prof[p]["ms"])
-    m_avg = kp + 2 * kp + kp   # trial basis size of a full iteration
-    if dom == "gram":
-        flops = 2.0 * n * (m_avg * (m_avg + 1) / 2 + 2 * m_avg * m_avg)
-        per = prof["gram"]["ms"] / max(1, prof["gram"]["calls"]) / 1e3
-        achieved = flops / per / 1e12
-        roof = {"kernel": "k_gram (FP64 multi-Gram Z^T Z, U^T Q, Q^T Z)", "bound": "alu",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": GRAM_DRAM_BYTES_PER_ROW_COL * n * m_avg,
-                "traffic_note": "ncu dram bytes of k_gram on the 64^3 case scaled by n m",
-                "peak_src": "nominal FP64 rate of the profiling recipe"}
-    elif dom == "update":
-        flops = 3 * 2.0 * n * (m_avg * kp + kp * kp)
-        per = prof["update"]["ms"] / max(1, prof["update"]["calls"]) / 1e3
-        achieved = flops / per / 1e12
-        roof = {"kernel": "k_update x3 (FP64 coefficient update)", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_src": "nominal FP64 rate of the profiling recipe"}
-    else:
-        calls = max(1, prof[dom]["calls"])
-        cols = (kp + 2 * kp + kp) / 3.0
-        byt = _vcycle_bytes(n, cols, w.mg_levels) if dom == "preconditioner" else 3 * n * kp * 8
-        per = prof[dom]["ms"] / calls / 1e3
-        achieved = byt / per / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_src": peaks["src"]}
+    roofs = _rooflines(prof, w, peaks, clocks.get("sm_max_mhz"))
+    dom = dict(roofs[0]) if roofs else None
+    if dom is not None:
+        dom["traffic"] = None
+        if dom["phase"] == "gram":
+            m_avg = kp + 2 * kp + kp
+            calls = max(1, prof["gram"]["calls"])
+            dom["traffic"] = GRAM_DRAM_BYTES_PER_ROW_COL * n * m_avg
+            dom["traffic_note"] = ("ncu dram bytes of one k_gram launch on the 64^3 case scaled by n m, "
+                                   "per launch (%d launches in the timed steps)" % calls)
+        dom["peak_src"] = ("nominal FP64 rate of the profiling recipe" if dom["unit"] == "TFLOP/s" and
+                           "FP64" in dom["kernel"] else
+                           "FP32 lanes x clock" if dom["unit"] == "TFLOP/s" else peaks["src"])
 
     out = {
         "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded start block)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic (seeded start block)",
         "config": {"workload": w.name, "operator": "7-point Dirichlet Laplacian 128^3, h = 1/129",
-                   "n": n, "k": k, "k_prime": kp, "sigma": w.sigma, "tol": w.tol,
+                   "n": n, "k": k, "k_prime": kp, "sigma": w.sigma, "tol": w.tol, "precision": args.precision,
                    "preconditioner": {"kind": "AV-MG", "levels": w.mg_levels, "nu": w.mg_nu,
                                       "transfer": "trilinear", "coarse": "fine-spectrum"},
-                   "l2": "inputs larger than L2 (one 128^3 x 11 FP64 block = 185 MB)",
+                   "l2": "inputs larger than L2 (one 128^3 x 16 FP64 block = 268 MB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "iterations": iters, "setup_s": setup_s, "max_rel_residual": info["max_rel_residual"],
-        "max_rel_eig_err_vs_closed_form": eig_err,
-        "fp64_seconds": step_s, "mixed_seconds": None,
+        "iterations": iters, "mixed_iterations": info.get("mixed_iterations", 0), "setup_s": setup_s,
+        "max_rel_residual": info["max_rel_residual"], "max_rel_eig_err_vs_closed_form": eig_err,
+        "mixed_seconds": step_s if args.precision == "mixed" else None,
+        "fp64_seconds": step_s if args.precision == "f64" else fp64_s, "fp64_iterations": fp64_iters,
         "phases_ms_per_step": {p: prof[p]["ms"] / max(1, args.steps) for p in prof},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * kp * 8,
                 "d2h_bytes_per_step": n * k * 8 + k * 8},
-        "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+        "gpu_launches": launches, "roofline": dom, "rooflines": roofs[1:], "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(iters)
@@ -349,7 +380,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["f64"], default="f64")
+    ap.add_argument("--precision", choices=["mixed", "f64"], default="mixed")
+    ap.add_argument("--no-f64-compare", action="store_true",
+                    help="skip the all-FP64 solve timed beside the mixed-precision steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-grid", type=int, default=0,
                     help="profiling case: N^3 grid of the same problem, fixed iteration count")

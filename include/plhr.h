@@ -111,6 +111,10 @@ void plhr_prec_destroy(plhr_prec* T);
  * workspace owned by T (grown on demand; calls on one T must not overlap). */
 plhr_status plhr_prec_apply(plhr_prec* T, int ncols, const double* R, int64_t ldr,
                             double* W, int64_t ldw, void* stream);
+/* The same V-cycle in FP32 storage and arithmetic (the form the mixed-precision
+ * solve uses): W = T R for FP32 blocks.  Workspace as for plhr_prec_apply. */
+plhr_status plhr_prec_apply_f32(plhr_prec* T, int ncols, const float* R, int64_t ldr,
+                                float* W, int64_t ldw, void* stream);
 
 /* -------------------------------------------------------------------- solver */
 typedef enum {
@@ -136,6 +140,11 @@ typedef struct {
                                   default 1 as the paper suggests: "(at least) by 1"); more guard
                                   columns make it less likely that a wanted pair of a degenerate
                                   cluster is left out; 4 (k + guard) <= 64 */
+    double switch_tol;         /* PLHR_PRECISION_MIXED: the iteration runs W, S, P, the Q images,
+                                  the operator products on them and the V-cycles in FP32 (V and
+                                  A V stay FP64) until the relative residuals of the k pairs
+                                  nearest sigma are all below switch_tol, then continues in FP64
+                                  with the images recomputed explicitly (default 1e-5) */
 } plhr_options;
 
 typedef struct {
@@ -145,6 +154,7 @@ typedef struct {
     double setup_seconds;      /* host wall time before the first iteration */
     double solve_seconds;      /* host wall time of the iteration loop */
     int history_len;           /* records written to options.history */
+    int mixed_iterations;      /* iterations run in the FP32 form (PLHR_PRECISION_MIXED) */
 } plhr_info;
 
 void plhr_options_default(plhr_options* o);
@@ -215,14 +225,23 @@ const char* plhr_status_string(plhr_status s);
 /* Number of CUDA kernels the library has launched in this process. */
 long long plhr_kernel_launches(void);
 /* Phase timing with CUDA events recorded on the launching stream, around the
- * solver's phases: 0 stencil products, 1 preconditioner applications,
- * 2 Gram pass, 3 coefficient updates, 4 small dense device stages,
- * 5 residual pass.  Off by default; enabling adds two events per phase call. */
+ * solver's phases: 0 stencil products, 1 preconditioner applications (FP64),
+ * 2 Gram pass (FP64), 3 coefficient updates (FP64), 4 small dense device
+ * stages, 5 residual pass, 6 preconditioner applications in FP32, 7 Gram pass
+ * of the FP32 form, 8 coefficient update of the FP32 form.  Off by default;
+ * enabling adds two events per phase call. */
 void plhr_profile_enable(int on);
-/* ms[6], calls[6] (either may be NULL): accumulated milliseconds and calls per
+/* ms[9], calls[9] (either may be NULL): accumulated milliseconds and calls per
  * phase since the last reset; reset != 0 clears the accumulators.  Waits for
  * the recorded events. */
 void plhr_profile_read(double* ms, long long* calls, int reset);
+/* work[9]: algorithmic work accumulated per phase since the last reset of
+ * plhr_profile_read: stencil products and residual pass: grid points x
+ * columns; preconditioner phases: finest-level grid points x columns of the
+ * V-cycles; Gram phases: flops 2 n (m(m+1)/2 + 2 m^2) (Z^T Z upper triangle,
+ * U^T Q, Q^T Z for an n x m trial basis); update phases: flops 2 n m k' per
+ * updated family; dense: 0. */
+void plhr_profile_work(double* work);
 /* Text of the last error recorded on the calling thread ("" if none). */
 const char* plhr_last_error(void);
 

@@ -41,13 +41,15 @@ class Options(ctypes.Structure):
     _fields_ = [("maxit", ctypes.c_int), ("precision", ctypes.c_int), ("real_arithmetic", ctypes.c_int),
                 ("s_vectors", ctypes.c_int), ("soft_lock", ctypes.c_int),
                 ("v_init", ctypes.c_void_p), ("ld_init", ctypes.c_int64), ("seed", ctypes.c_uint64),
-                ("history", ctypes.c_void_p), ("history_cap", ctypes.c_int), ("guard", ctypes.c_int)]
+                ("history", ctypes.c_void_p), ("history_cap", ctypes.c_int), ("guard", ctypes.c_int),
+                ("switch_tol", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("max_rel_residual", ctypes.c_double), ("setup_seconds", ctypes.c_double),
-                ("solve_seconds", ctypes.c_double), ("history_len", ctypes.c_int)]
+                ("solve_seconds", ctypes.c_double), ("history_len", ctypes.c_int),
+                ("mixed_iterations", ctypes.c_int)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/plhr.h
@@ -63,6 +65,9 @@ _SIGS = {
     "plhr_prec_destroy": (None, [ctypes.c_void_p]),
     "plhr_prec_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "plhr_profile_work": (None, [ctypes.c_void_p]),
+    "plhr_prec_apply_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "plhr_options_default": (None, [ctypes.POINTER(Options)]),
     "plhr_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
                                   ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(Options),
@@ -199,6 +204,19 @@ class AVMG:
                "plhr_prec_apply")
         return out
 
+    def apply_f32(self, R, out=None, stream=None):
+        """The same V-cycle in FP32 (the form the mixed-precision solve uses)
+        on a float32 CUDA block."""
+        import torch
+        if R.dtype != torch.float32 or not R.is_cuda or R.dim() != 2 or R.shape[0] != self.n or R.stride(1) != 1:
+            raise ValueError("R must be a row-major float32 CUDA block with n rows")
+        if out is None:
+            out = torch.empty_like(R)
+        _check(load_library().plhr_prec_apply_f32(self._h, R.shape[1], ctypes.c_void_p(R.data_ptr()), R.stride(0),
+                                                  ctypes.c_void_p(out.data_ptr()), out.stride(0),
+                                                  _stream_ptr(stream)), "plhr_prec_apply_f32")
+        return out
+
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
             _lib.plhr_prec_destroy(self._h)
@@ -234,7 +252,8 @@ def tharm_extract(Gzz, Guq, Gqz, colscale, kp, nv, stream=None, clocks=False):
     return out
 
 
-PHASES = ("stencil", "preconditioner", "gram", "update", "dense", "residual")
+PHASES = ("stencil", "preconditioner", "gram", "update", "dense", "residual", "preconditioner_f32", "gram_f32",
+          "update_f32")
 
 
 def kernel_launches() -> int:
@@ -248,15 +267,18 @@ def profile_enable(on: bool = True) -> None:
 
 def profile_read(reset: bool = False) -> dict:
     """Accumulated CUDA-event time (ms) and calls per solver phase."""
-    ms = (ctypes.c_double * 6)()
-    calls = (ctypes.c_longlong * 6)()
-    load_library().plhr_profile_read(ms, calls, 1 if reset else 0)
-    return {name: {"ms": ms[i], "calls": calls[i]} for i, name in enumerate(PHASES)}
+    ms = (ctypes.c_double * len(PHASES))()
+    calls = (ctypes.c_longlong * len(PHASES))()
+    work = (ctypes.c_double * len(PHASES))()
+    lib = load_library()
+    lib.plhr_profile_work(work)
+    lib.plhr_profile_read(ms, calls, 1 if reset else 0)
+    return {name: {"ms": ms[i], "calls": calls[i], "work": work[i]} for i, name in enumerate(PHASES)}
 
 
 def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float = 1e-8, maxit: int = 1000,
           v_init=None, seed: int = 20140801, history: bool = False, precision: int = PRECISION_F64,
-          stream=None, raise_on_notconv: bool = False, guard: int = 1):
+          stream=None, raise_on_notconv: bool = False, guard: int = 1, switch_tol: float = 1e-5):
     """k eigenpairs of A v = lambda v nearest sigma with k + guard block
     columns.  Returns (eigvals (numpy, k), eigvecs (torch n x k float64,
     CUDA), info dict)."""
@@ -270,6 +292,7 @@ def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float =
     opt.precision = precision
     opt.seed = seed
     opt.guard = guard
+    opt.switch_tol = switch_tol
     if v_init is not None:
         _check_block(v_init, n, "v_init")
         if v_init.shape[1] < kp:
@@ -292,7 +315,7 @@ def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float =
         raise PlhrError(st, "plhr_solve")
     out = {"status": st, "iterations": info.iterations, "converged": bool(info.converged),
            "max_rel_residual": info.max_rel_residual, "setup_seconds": info.setup_seconds,
-           "solve_seconds": info.solve_seconds}
+           "solve_seconds": info.solve_seconds, "mixed_iterations": info.mixed_iterations}
     if hist is not None:
         rec = hist[: info.history_len * rl].reshape(info.history_len, rl)
         out["history"] = [{"it": int(r[0]), "lam": r[1:1 + k].copy(), "rel": r[1 + kp:1 + kp + k].copy(),

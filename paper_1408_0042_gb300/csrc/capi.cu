@@ -182,6 +182,15 @@ plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma, cons
             plhr_prec_destroy(T);
             return PLHR_ECUDA;
         }
+        std::vector<float> Sf(S.begin(), S.end()), muf(mu.begin(), mu.end());
+        if (cudaMalloc(&H.f_basis[ax], sizeof(float) * N * N) != cudaSuccess ||
+            cudaMalloc(&H.f_mu[ax], sizeof(float) * N) != cudaSuccess ||
+            cudaMemcpy(H.f_basis[ax], Sf.data(), sizeof(float) * N * N, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(H.f_mu[ax], muf.data(), sizeof(float) * N, cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_error("plhr_prec_avmg: FP32 basis upload failed");
+            plhr_prec_destroy(T);
+            return PLHR_ENOMEM;
+        }
         H.n0[ax] = N;
     }
     int64_t n0 = g0.n();
@@ -199,8 +208,11 @@ void plhr_prec_destroy(plhr_prec* T) {
     for (int a = 0; a < 3; ++a) {
         if (T->H.d_basis[a]) cudaFree(T->H.d_basis[a]);
         if (T->H.d_mu[a]) cudaFree(T->H.d_mu[a]);
+        if (T->H.f_basis[a]) cudaFree(T->H.f_basis[a]);
+        if (T->H.f_mu[a]) cudaFree(T->H.f_mu[a]);
     }
     if (T->work) cudaFree(T->work);
+    if (T->work32) cudaFree(T->work32);
     delete T;
 }
 
@@ -224,7 +236,44 @@ plhr_status prec_reserve(plhr_prec* T, int nc, int64_t extra_doubles) {
     T->work_doubles = need;
     return PLHR_OK;
 }
+plhr_status prec_reserve32(plhr_prec* T, int nc, int64_t extra_floats) {
+    int64_t need = mg_workspace_floats(T->H, nc) + extra_floats;
+    if (need <= T->work_floats) return PLHR_OK;
+    if (T->work32) {
+        cudaDeviceSynchronize();
+        cudaFree(T->work32);
+        T->work32 = nullptr;
+        T->work_floats = 0;
+    }
+    if (need == 0) return PLHR_OK;
+    if (cudaMalloc(&T->work32, sizeof(float) * need) != cudaSuccess) {
+        set_error("prec FP32 workspace: cudaMalloc of %lld floats failed", (long long)need);
+        return PLHR_ENOMEM;
+    }
+    T->work_floats = need;
+    return PLHR_OK;
+}
 }  // namespace plhr
+
+extern "C" plhr_status plhr_prec_apply_f32(plhr_prec* T, int ncols, const float* R, int64_t ldr, float* W,
+                                           int64_t ldw, void* stream) {
+    clear_error();
+    if (!T || ncols < 0 || (ncols > 0 && (!R || !W)) || ldr < ncols || ldw < ncols) {
+        set_error("plhr_prec_apply_f32: invalid argument");
+        return PLHR_EINVAL;
+    }
+    if (ncols == 0) return PLHR_OK;
+    const int64_t n = T->H.lev.back().g.n();
+    const int64_t stage = (ldw == ncols) ? 0 : n * ncols;
+    PLHR_TRY(prec_reserve32(T, ncols, stage));
+    cudaStream_t s = (cudaStream_t)stream;
+    float* out = (ldw == ncols) ? W : T->work32 + mg_workspace_floats(T->H, ncols);
+    PLHR_TRY_CUDA(mg_vcycle_f32(T->H, ncols, R, ldr, out, T->work32, s));
+    if (ldw != ncols)
+        PLHR_TRY_CUDA(cudaMemcpy2DAsync(W, sizeof(float) * ldw, out, sizeof(float) * ncols, sizeof(float) * ncols,
+                                        n, cudaMemcpyDeviceToDevice, s));
+    return PLHR_OK;
+}
 
 extern "C" plhr_status plhr_prec_apply(plhr_prec* T, int ncols, const double* R, int64_t ldr, double* W, int64_t ldw,
                                        void* stream) {

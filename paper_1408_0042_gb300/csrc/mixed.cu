@@ -1,0 +1,367 @@
+// Tall-skinny kernels of the mixed-precision iteration.  The block V and its
+// image A V stay FP64 (the residual A v - lambda v of a vector near
+// convergence needs them); W, S, P, their images and the T-harmonic images Q
+// are FP32.  The Grams of the trial basis take FP32 products of values that
+// were formed in full precision and then rounded (the V columns, U_V =
+// (A V - sigma V) s), accumulate 32-row chunks in FP32 registers and fold
+// every chunk into a per-thread double-FP32 (hi, lo) accumulator with TwoSum,
+// so the accumulation error does not grow with n.  The per-CTA partials are
+// summed in FP64 in a fixed order (deterministic).
+#include "dword.h"
+#include "mixed.h"
+
+namespace plhr {
+namespace {
+
+constexpr int kMxRows = 32;         // rows per chunk
+constexpr int kMxThreads = 256;
+constexpr int kMxTilesPerThread = 3;
+
+struct FamMx {
+    const void* p[4];
+    int64_t ld[4];
+    int nc[4];
+    int off[4];
+    int f64[4];
+};
+
+FamMx fam_mx(const BlkMx* b, int nb) {
+    FamMx F{};
+    int off = 0;
+    for (int i = 0; i < 4; ++i) {
+        if (i < nb) {
+            F.p[i] = b[i].p; F.ld[i] = b[i].ld; F.nc[i] = b[i].nc; F.off[i] = off; F.f64[i] = b[i].f64;
+            off += b[i].nc;
+        } else {
+            F.p[i] = nullptr; F.ld[i] = 0; F.nc[i] = 0; F.off[i] = off; F.f64[i] = 0;
+        }
+    }
+    return F;
+}
+
+__device__ __forceinline__ double ldv(const FamMx& F, int b, int64_t row, int c) {
+    return F.f64[b] ? static_cast<const double*>(F.p[b])[row * F.ld[b] + c]
+                    : (double)static_cast<const float*>(F.p[b])[row * F.ld[b] + c];
+}
+__device__ __forceinline__ float ldf(const FamMx& F, int b, int64_t row, int c) {
+    return F.f64[b] ? (float)static_cast<const double*>(F.p[b])[row * F.ld[b] + c]
+                    : static_cast<const float*>(F.p[b])[row * F.ld[b] + c];
+}
+
+// Stage rows row0 .. row0 + kMxRows - 1 of z = Z s, u = (AZ - sigma Z) s and
+// q = Q s (q = u when Q is absent) into [row][mp] FP32 tiles; FP64 blocks are
+// combined in FP64 and rounded once.
+__device__ void stage_mx(float* sz, float* su, float* sq, int mp, int64_t n, int64_t row0, const FamMx& Z,
+                         const FamMx& AZ, const FamMx& Q, int nb, int has_q, double sigma,
+                         const double* __restrict__ csc) {
+    for (int b = 0; b < nb; ++b) {
+        const int nc = Z.nc[b];
+        if (nc == 0) continue;
+        const int tot = kMxRows * nc;
+        const bool wide = Z.f64[b] || AZ.f64[b];
+        for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+            const int r = t / nc, c = t - r * nc;
+            const int64_t row = row0 + r;
+            const int col = Z.off[b] + c;
+            float z = 0.0f, u = 0.0f, q = 0.0f;
+            if (row < n) {
+                const double s = csc[col];
+                if (wide) {
+                    const double zd = ldv(Z, b, row, c) * s;
+                    const double ud = ldv(AZ, b, row, c) * s - sigma * zd;
+                    z = (float)zd;
+                    u = (float)ud;
+                } else {
+                    const float sf = (float)s;
+                    z = ldf(Z, b, row, c) * sf;
+                    u = ldf(AZ, b, row, c) * sf - (float)sigma * z;
+                }
+                q = has_q ? ldf(Q, b, row, c) * (float)s : u;
+            }
+            sz[r * mp + col] = z;
+            su[r * mp + col] = u;
+            sq[r * mp + col] = q;
+        }
+    }
+}
+
+// Tiles: 4x4 over three mp x mp outputs; g = 0: Z^T Z (upper tiles), g = 1:
+// U^T Q, g = 2: Q^T Z.
+__global__ void __launch_bounds__(kMxThreads, 1) k_gram_mx(int64_t n, int m, int mp, int nb, FamMx Z, FamMx AZ,
+                                                           FamMx Q, int has_q, double sigma,
+                                                           const double* __restrict__ csc,
+                                                           double* __restrict__ partial) {
+    extern __shared__ __align__(16) float shm[];
+    float* sz = shm;
+    float* su = sz + kMxRows * mp;
+    float* sq = su + kMxRows * mp;
+    const int T = mp / 4;
+    const int nt0 = T * (T + 1) / 2, nt1 = T * T;
+    const int ntiles = nt0 + 2 * nt1;
+    float acc[kMxTilesPerThread][16], hi[kMxTilesPerThread][16], lo[kMxTilesPerThread][16];
+    int tg[kMxTilesPerThread], ti[kMxTilesPerThread], tj[kMxTilesPerThread];
+    int my = 0;
+    for (int t = threadIdx.x; t < ntiles && my < kMxTilesPerThread; t += blockDim.x, ++my) {
+        if (t < nt0) {
+            int r = 0, rem = t;
+            while (rem >= T - r) { rem -= T - r; ++r; }
+            tg[my] = 0; ti[my] = r; tj[my] = r + rem;
+        } else if (t < nt0 + nt1) {
+            const int u = t - nt0;
+            tg[my] = 1; ti[my] = u / T; tj[my] = u % T;
+        } else {
+            const int u = t - nt0 - nt1;
+            tg[my] = 2; ti[my] = u / T; tj[my] = u % T;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kMxTilesPerThread; ++q)
+#pragma unroll
+        for (int e = 0; e < 16; ++e) { hi[q][e] = 0.0f; lo[q][e] = 0.0f; }
+    // zero the padding columns once (staging never writes them)
+    for (int t = threadIdx.x; t < kMxRows * mp; t += blockDim.x) {
+        if (t % mp >= m) { sz[t] = 0.0f; su[t] = 0.0f; sq[t] = 0.0f; }
+    }
+    const int64_t nchunks = (n + kMxRows - 1) / kMxRows;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        __syncthreads();
+        stage_mx(sz, su, sq, mp, n, ch * kMxRows, Z, AZ, Q, nb, has_q, sigma, csc);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kMxTilesPerThread; ++q) {
+            if (q >= my) break;
+            const float* A = tg[q] == 0 ? sz : (tg[q] == 1 ? su : sq);
+            const float* B = tg[q] == 0 ? sz : (tg[q] == 1 ? sq : sz);
+            const int i0 = ti[q] * 4, j0 = tj[q] * 4;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) acc[q][e] = 0.0f;
+#pragma unroll 4
+            for (int r = 0; r < kMxRows; ++r) {
+                const float4 a = *reinterpret_cast<const float4*>(A + r * mp + i0);
+                const float4 bb = *reinterpret_cast<const float4*>(B + r * mp + j0);
+                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[q][x * 4 + y] = fmaf(av[x], bv[y], acc[q][x * 4 + y]);
+            }
+            // fold the chunk into (hi, lo): hi + lo += acc exactly up to lo's rounding
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const dw s = dw_two_sum(hi[q][e], acc[q][e]);
+                hi[q][e] = s.hi;
+                lo[q][e] = __fadd_rn(lo[q][e], s.lo);
+            }
+        }
+    }
+    double* out = partial + (int64_t)blockIdx.x * 3 * m * m;
+#pragma unroll
+    for (int q = 0; q < kMxTilesPerThread; ++q) {
+        if (q >= my) break;
+        const int i0 = ti[q] * 4, j0 = tj[q] * 4;
+        double* G = out + (int64_t)tg[q] * m * m;
+        for (int x = 0; x < 4; ++x)
+            for (int y = 0; y < 4; ++y) {
+                const int i = i0 + x, j = j0 + y;
+                if (i < m && j < m) {
+                    const double v = (double)hi[q][x * 4 + y] + (double)lo[q][x * 4 + y];
+                    G[i * m + j] = v;
+                    if (tg[q] == 0) G[j * m + i] = v;
+                }
+            }
+    }
+}
+
+// out[j] = sum_b partial[b * width + j], fixed order, many CTAs
+__global__ void k_sum_wide(int nblocks, int width, const double* __restrict__ partial, double* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= width) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partial[(int64_t)b * width + j];
+    out[j] = t;
+}
+
+// ------------------------------------------------------------------ update
+constexpr int kUpRows = 32;
+
+// Family F = [F_0 .. F_{nb-1}] (m columns): Pout = F C_P, Vout = F_0 C_VV + F C_P.
+// With an FP64 F_0 and an FP64 Vout, the F_0 part of Vout is summed in FP64
+// (V keeps its FP64 accuracy; A amplifies FP32 rounding noise in V by ||A||);
+// all other sums are FP32.  Every output row depends only on the same input
+// row and a chunk is staged before any of its rows is written (in place
+// allowed: Vout may be F_0, Pout may be F_{nb-1}).
+__global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int nb, FamMx F,
+                                                   const double* __restrict__ Cp, const double* __restrict__ Cvv,
+                                                   void* __restrict__ Vout, int vo64, int64_t ldvo,
+                                                   void* __restrict__ Pout, int po64, int64_t ldpo) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    double* cs64 = reinterpret_cast<double*>(raw);          // [kp][kp]  C_VV + C_P (V rows)
+    double* zd = cs64 + kp * kp;                             // [rows][kp] FP64 V rows
+    float* cpf = reinterpret_cast<float*>(zd + kUpRows * kp);   // [m][kp]
+    float* csf = cpf + m * kp;                               // [kp][kp]
+    float* zf = csf + kp * kp;                               // [rows][m]
+    const bool v64 = F.f64[0] && vo64;
+    for (int t = threadIdx.x; t < m * kp; t += blockDim.x) cpf[t] = (float)Cp[t];
+    for (int t = threadIdx.x; t < kp * kp; t += blockDim.x) {
+        const double v = Cvv[t] + Cp[t];     // V rows of C_P are the first kp rows
+        cs64[t] = v;
+        csf[t] = (float)v;
+    }
+    const int64_t nchunks = (n + kUpRows - 1) / kUpRows;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t row0 = ch * kUpRows;
+        const int nrows = (int)((n - row0) < kUpRows ? (n - row0) : kUpRows);
+        __syncthreads();
+        for (int b = 0; b < nb; ++b) {
+            const int nc = F.nc[b];
+            for (int t = threadIdx.x; t < nrows * nc; t += blockDim.x) {
+                const int r = t / nc, c = t - r * nc;
+                const int64_t row = row0 + r;
+                if (b == 0 && v64) zd[r * kp + c] = ldv(F, 0, row, c);
+                zf[r * m + F.off[b] + c] = ldf(F, b, row, c);
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nrows * kp; t += blockDim.x) {
+            const int r = t / kp, j = t - r * kp;
+            const float* z = zf + r * m;
+            float prest = 0.0f, pv = 0.0f;
+            for (int i = kp; i < m; ++i) prest = fmaf(z[i], cpf[i * kp + j], prest);
+            for (int i = 0; i < kp; ++i) pv = fmaf(z[i], cpf[i * kp + j], pv);
+            const int64_t row = row0 + r;
+            const float p = pv + prest;
+            if (po64) static_cast<double*>(Pout)[row * ldpo + j] = (double)p;
+            else static_cast<float*>(Pout)[row * ldpo + j] = p;
+            if (v64) {
+                const double* zr = zd + r * kp;
+                double v = 0.0;
+                for (int i = 0; i < kp; ++i) v = fma(zr[i], cs64[i * kp + j], v);
+                static_cast<double*>(Vout)[row * ldvo + j] = v + (double)prest;
+            } else {
+                float v = 0.0f;
+                for (int i = 0; i < kp; ++i) v = fmaf(z[i], csf[i * kp + j], v);
+                v += prest;
+                if (vo64) static_cast<double*>(Vout)[row * ldvo + j] = (double)v;
+                else static_cast<float*>(Vout)[row * ldvo + j] = v;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ FP32 stencil
+constexpr int kSt = 256;
+
+struct Ln {
+    int nx, ny, nz, nc;
+    float ih2;
+};
+
+// ax = L x; o1 = ax - lam_c x (optional); o2 = ax - sig x (optional); one
+// thread per element, a CTA covers 256 elements of one x-line
+template <bool D3>
+__global__ void __launch_bounds__(kSt) k_lap32(Ln g, const float* __restrict__ x, int64_t ldx, float* __restrict__ ax,
+                                               int64_t ldax, float* __restrict__ o1, int64_t ld1,
+                                               const double* __restrict__ lam, float* __restrict__ o2, int64_t ld2,
+                                               float sig) {
+    const int t = blockIdx.x * kSt + threadIdx.x;
+    if (t >= g.nx * g.nc) return;
+    const int ix = t / g.nc, c = t - ix * g.nc;
+    const int iy = blockIdx.y, iz = blockIdx.z;
+    const int64_t row = ((int64_t)iz * g.ny + iy) * g.nx + ix;
+    const float* xp = x + row * ldx + c;
+    const int64_t sy = ldx * g.nx, sz = sy * g.ny;
+    // sum of the differences x_c - x_nb (exact for a smooth field; missing
+    // neighbours are zero), not 2d x_c - sum x_nb, which cancels
+    const float xv = xp[0];
+    float s = ((ix > 0 ? xv - xp[-ldx] : xv) + (ix < g.nx - 1 ? xv - xp[ldx] : xv)) +
+              ((iy > 0 ? xv - xp[-sy] : xv) + (iy < g.ny - 1 ? xv - xp[sy] : xv));
+    if (D3) s += (iz > 0 ? xv - xp[-sz] : xv) + (iz < g.nz - 1 ? xv - xp[sz] : xv);
+    const float a = g.ih2 * s;
+    if (ax) ax[row * ldax + c] = a;
+    if (o1) o1[row * ld1 + c] = a - (float)lam[c] * xv;
+    if (o2) o2[row * ld2 + c] = a - sig * xv;
+}
+
+// Y (FP64, ldy) = X (FP32, ldx), n x nc
+__global__ void k_widen(int64_t n, int nc, const float* __restrict__ X, int64_t ldx, double* __restrict__ Y,
+                        int64_t ldy) {
+    const int64_t total = n * nc;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / nc;
+        const int c = (int)(e - r * nc);
+        Y[r * ldy + c] = (double)X[r * ldx + c];
+    }
+}
+
+// Y (FP32, ldy) = X (FP64, ldx), n x nc
+__global__ void k_narrow(int64_t n, int nc, const double* __restrict__ X, int64_t ldx, float* __restrict__ Y,
+                         int64_t ldy) {
+    const int64_t total = n * nc;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / nc;
+        const int c = (int)(e - r * nc);
+        Y[r * ldy + c] = (float)X[r * ldx + c];
+    }
+}
+
+}  // namespace
+
+int gram_mx_blocks() { return sm_count() * 2; }
+
+cudaError_t multi_gram_mx(int64_t n, int nb, const BlkMx* Z, const BlkMx* AZ, const BlkMx* Q, double sigma,
+                          const double* colscale, double* partial, double* out, cudaStream_t s) {
+    FamMx FZ = fam_mx(Z, nb), FA = fam_mx(AZ, nb), FQ = fam_mx(Q ? Q : AZ, nb);
+    int m = 0;
+    for (int i = 0; i < nb; ++i) m += Z[i].nc;
+    const int mp = (m + 3) / 4 * 4;
+    const int T = mp / 4;
+    if (T * (T + 1) / 2 + 2 * T * T > kMxThreads * kMxTilesPerThread) return cudaErrorInvalidValue;
+    const int blocks = gram_mx_blocks();
+    const size_t shm = sizeof(float) * 3 * kMxRows * mp;
+    k_gram_mx<<<blocks, kMxThreads, shm, s>>>(n, m, mp, nb, FZ, FA, FQ, Q ? 1 : 0, sigma, colscale, partial);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int width = 3 * m * m;
+    k_sum_wide<<<(width + 127) / 128, 128, 0, s>>>(blocks, width, partial, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t block_update_mx(int64_t n, int nb, const BlkMx* F, int kp, const double* Cp, const double* Cvv,
+                            void* Vout, int vo64, int64_t ldvo, void* Pout, int po64, int64_t ldpo, cudaStream_t s) {
+    FamMx FF = fam_mx(F, nb);
+    int m = 0;
+    for (int i = 0; i < nb; ++i) m += F[i].nc;
+    const size_t shm = sizeof(double) * (kp * kp + kUpRows * kp) + sizeof(float) * (m * kp + kp * kp + kUpRows * m);
+    k_update_mx<<<gram_mx_blocks(), 256, shm, s>>>(n, m, kp, nb, FF, Cp, Cvv, Vout, vo64, ldvo, Pout, po64, ldpo);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t lap32_apply_shifts(const Grid& g, int nc, const float* x, int64_t ldx, float* ax, int64_t ldax, float* o1,
+                               int64_t ld1, const double* lam, float* o2, int64_t ld2, double sig, cudaStream_t s) {
+    if (nc <= 0) return cudaSuccess;
+    Ln L{(int)g.nx, (int)g.ny, (int)g.nz, nc, (float)g.inv_h2()};
+    dim3 gr((unsigned)((g.nx * nc + kSt - 1) / kSt), (unsigned)g.ny, (unsigned)g.nz);
+    if (g.d == 3) k_lap32<true><<<gr, kSt, 0, s>>>(L, x, ldx, ax, ldax, o1, ld1, lam, o2, ld2, (float)sig);
+    else k_lap32<false><<<gr, kSt, 0, s>>>(L, x, ldx, ax, ldax, o1, ld1, lam, o2, ld2, (float)sig);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t widen_block(int64_t n, int nc, const float* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s) {
+    if (nc <= 0) return cudaSuccess;
+    k_widen<<<grid_size_for(n * nc, 256, sm_count() * 8), 256, 0, s>>>(n, nc, X, ldx, Y, ldy);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t narrow_block(int64_t n, int nc, const double* X, int64_t ldx, float* Y, int64_t ldy, cudaStream_t s) {
+    if (nc <= 0) return cudaSuccess;
+    k_narrow<<<grid_size_for(n * nc, 256, sm_count() * 8), 256, 0, s>>>(n, nc, X, ldx, Y, ldy);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace plhr

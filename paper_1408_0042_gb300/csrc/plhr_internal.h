@@ -65,9 +65,11 @@ int sm_count();
 void count_launches(int n);
 
 // Optional phase timing with CUDA events on the launching stream.
-enum Phase { PH_STENCIL = 0, PH_VCYCLE = 1, PH_GRAM = 2, PH_UPDATE = 3, PH_DENSE = 4, PH_OTHER = 5, PH_COUNT = 6 };
+enum Phase { PH_STENCIL = 0, PH_VCYCLE = 1, PH_GRAM = 2, PH_UPDATE = 3, PH_DENSE = 4, PH_OTHER = 5,
+             PH_VCYCLE32 = 6, PH_GRAM32 = 7, PH_UPDATE32 = 8, PH_COUNT = 9 };
 struct PhaseScope {
-    PhaseScope(int phase, cudaStream_t s);
+    // work: algorithmic work of the call, in the phase's unit (see plhr_profile_work)
+    PhaseScope(int phase, cudaStream_t s, double work = 0.0);
     ~PhaseScope();
     int phase;
     cudaStream_t s;
@@ -103,12 +105,22 @@ struct MGHierarchy {
     // S3 = Sx (x) Sy (x) Sz (orthonormal 1D bases) and 1D eigenvalues mu
     double* d_basis[3] = {nullptr, nullptr, nullptr};   // N_a x N_a, row-major [point][mode]
     double* d_mu[3] = {nullptr, nullptr, nullptr};
+    float* f_basis[3] = {nullptr, nullptr, nullptr};   // FP32 copies for the FP32 V-cycle
+    float* f_mu[3] = {nullptr, nullptr, nullptr};
     int64_t n0[3] = {1, 1, 1};
 };
 
 cudaError_t mg_vcycle(const MGHierarchy& H, int nc, const double* r, int64_t ldr, double* w,
                       int64_t ldw, double* work, cudaStream_t s);
 int64_t mg_workspace_doubles(const MGHierarchy& H, int nc);
+
+// FP32 V-cycle (same cycle, FP32 storage and arithmetic); r is FP64 or FP32
+// with leading dimension ldr, w is dense (leading dimension nc).
+cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const double* r, int64_t ldr, float* w, float* work,
+                          cudaStream_t s);
+cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const float* r, int64_t ldr, float* w, float* work,
+                          cudaStream_t s);
+int64_t mg_workspace_floats(const MGHierarchy& H, int nc);
 
 }  // namespace plhr
 
@@ -121,4 +133,6 @@ struct plhr_prec {
     plhr::MGHierarchy H;
     double* work = nullptr;
     int64_t work_doubles = 0;
+    float* work32 = nullptr;      // FP32 V-cycle workspace
+    int64_t work_floats = 0;
 };

@@ -1,4 +1,4 @@
-// Block PLHR driver (Algorithm 3, real arithmetic; FP64 path).  Every step of
+// Block PLHR driver (Algorithm 3, real arithmetic; FP64 and mixed precision).  Every step of
 // the iteration runs on the device; the host enqueues kernels and reads one
 // small status record per iteration (convergence flags, Ritz values).
 //
@@ -12,6 +12,16 @@
 //   AS, QS         A S and T(A - sigma B) S
 // Per iteration: 2 block products with A (W, S) and 4 applications of T
 // (W, S, Q_W, Q_S), as in the storage/cost paragraph after Algorithm 2.
+//
+// Mixed precision (PLHR_PRECISION_MIXED): while the relative residuals of the
+// k pairs nearest sigma are above switch_tol the iteration runs in an FP32
+// form: W, A W, S, Q_W, A S, Q_S, P, A P and the V-cycles are FP32, V and A V
+// stay FP64 (A V explicit every iteration, so the residual is exact for the
+// stored V), the Grams take FP32 products with compensated accumulation, the
+// projected problem is FP64, the V part of the update is summed in FP64, and
+// Q_V, Q_P are recomputed explicitly (2 more V-cycles on k' columns) instead
+// of carried.  Then P is widened, its images and Q_V, Q_P are recomputed in
+// FP64 and the iteration continues in FP64 to the requested tolerance.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -19,10 +29,12 @@
 
 #include "blockops.h"
 #include "dense.h"
+#include "mixed.h"
 #include "plhr_internal.h"
 
 namespace plhr {
 plhr_status prec_reserve(plhr_prec* T, int nc, int64_t extra_doubles);
+plhr_status prec_reserve32(plhr_prec* T, int nc, int64_t extra_floats);
 }
 
 using namespace plhr;
@@ -41,6 +53,10 @@ struct HostStatus {
     int pad;
 };
 
+// flops of one multi-Gram pass over an n x m trial basis: Z^T Z (upper
+// triangle), U^T Q and Q^T Z
+double gram_flops(int64_t n, int m) { return 2.0 * (double)n * (m * (m + 1) / 2.0 + 2.0 * m * m); }
+
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -57,6 +73,7 @@ extern "C" void plhr_options_default(plhr_options* o) {
     o->soft_lock = 1;
     o->seed = 20140801ull;
     o->guard = 1;
+    o->switch_tol = 1e-5;
 }
 
 extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sigma, int k, plhr_prec* T, double tol,
@@ -75,8 +92,9 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         set_error("plhr_solve: only B = identity is supported by this build");
         return PLHR_EINVAL;
     }
-    if (!opt.real_arithmetic || opt.precision != PLHR_PRECISION_F64 || !opt.s_vectors) {
-        set_error("plhr_solve: this build supports real arithmetic, FP64, with s-vectors");
+    if (!opt.real_arithmetic || (opt.precision != PLHR_PRECISION_F64 && opt.precision != PLHR_PRECISION_MIXED) ||
+        !opt.s_vectors) {
+        set_error("plhr_solve: this build supports real arithmetic, FP64 or mixed precision, with s-vectors");
         return PLHR_EINVAL;
     }
     const int64_t n = A->g.n();
@@ -142,6 +160,27 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     double *V = take(nk), *AV = take(nk), *QV = take(nk), *P = take(nk), *AP = take(nk), *QP = take(nk);
     double *R = take(nk), *Rc = take(nk), *W = take(nk), *AW = take(nk), *SQ = take(2 * nk), *X2 = take(2 * nk);
     double *AS = take(nk), *X3 = take(nk), *QS = take(nk);
+    // FP32 blocks of the mixed form: W, A W, [S | Q_W], its input, A S, A S - sigma S,
+    // Q_S, P, A P, Q_P, Q_V
+    bool mx = opt.precision == PLHR_PRECISION_MIXED;
+    int mixed_its = 0;
+    struct FloatBuf {
+        float* p = nullptr;
+        ~FloatBuf() { if (p) cudaFree(p); }
+    } big32;
+    float *W32 = nullptr, *AW32 = nullptr, *SQ32 = nullptr, *X2_32 = nullptr, *AS32 = nullptr, *X3_32 = nullptr,
+          *QS32 = nullptr, *P32 = nullptr, *AP32 = nullptr, *QP32 = nullptr, *QV32 = nullptr;
+    if (mx) {
+        if (cudaMallocAsync(&big32.p, sizeof(float) * 13 * nk, s) != cudaSuccess) {
+            set_error("plhr_solve: device allocation of %.1f MB failed", 4e-6 * 13.0 * (double)nk);
+            return PLHR_ENOMEM;
+        }
+        float* f = big32.p;
+        W32 = f; f += nk; AW32 = f; f += nk; SQ32 = f; f += 2 * nk; X2_32 = f; f += 2 * nk; AS32 = f; f += nk;
+        X3_32 = f; f += nk; QS32 = f; f += nk; P32 = f; f += nk; AP32 = f; f += nk; QP32 = f; f += nk;
+        QV32 = f; f += nk;
+        if (T) PLHR_TRY(prec_reserve32(T, 2 * kp, 0));
+    }
     double* gpart = part.p;
     double* rpart = part.p + (int64_t)reduce_blocks() * m3;
     double* q = small.p;
@@ -181,8 +220,16 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
                                             cudaMemcpyDeviceToDevice, s));
             return PLHR_OK;
         }
-        PhaseScope ps(PH_VCYCLE, s);
+        PhaseScope ps(PH_VCYCLE, s, (double)n * nc);
         PLHR_TRY_CUDA(mg_vcycle(T->H, nc, r, ldr, w, nc, T->work, s));
+        return PLHR_OK;
+    };
+
+    auto applyT32 = [&](int nc, const auto* r, int64_t ldr, float* w) -> plhr_status {
+        // w (ld nc, FP32) = T r in the FP32 V-cycle
+        if (nc == 0) return PLHR_OK;
+        PhaseScope ps(PH_VCYCLE32, s, (double)n * nc);
+        PLHR_TRY_CUDA(mg_vcycle_f32(T->H, nc, r, ldr, w, T->work32, s));
         return PLHR_OK;
     };
 
@@ -195,7 +242,10 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     // AV, X3 := AV - sigma V, QV = T(AV - sigma V) (with T = I, Q = AZ - sigma Z is
     // formed inside the Gram pass and no Q block is stored)
     PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
-    if (T) PLHR_TRY(applyT(kp, X3, kp, QV));
+    if (T) {
+        if (mx) PLHR_TRY(applyT32(kp, (const double*)X3, kp, QV32));
+        else PLHR_TRY(applyT(kp, X3, kp, QV));
+    }
     PLHR_TRY_CUDA(column_dots(n, kp, V, kp, AV, kp, rpart, dots, s));   // v.Av, v.v
     {
         std::vector<int> zeros(64, 0), neg(64, -1);
@@ -209,10 +259,27 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     // images of V and P under A: explicit stencil products after every update
     // (no recursion, so no drift), dots for the Rayleigh quotients of V
     auto refresh_images = [&]() -> plhr_status {
-        PhaseScope ps(PH_STENCIL, s);
+        PhaseScope ps(PH_STENCIL, s, (double)n * (np ? 2 * kp : kp));
         PLHR_TRY_CUDA(lap_axpby(g, kp, V, kp, AV, kp, 1.0, 0.0, s));
-        if (np) PLHR_TRY_CUDA(lap_axpby(g, kp, P, kp, AP, kp, 1.0, 0.0, s));
+        if (np) {
+            if (mx) PLHR_TRY_CUDA(lap32_apply_shifts(g, kp, P32, kp, AP32, kp, nullptr, 0, nullptr, nullptr, 0, 0.0, s));
+            else PLHR_TRY_CUDA(lap_axpby(g, kp, P, kp, AP, kp, 1.0, 0.0, s));
+        }
         PLHR_TRY_CUDA(column_dots(n, kp, V, kp, AV, kp, rpart, dots, s));
+        return PLHR_OK;
+    };
+
+    // end of the FP32 form: P to FP64, then A V, A P, T(A V - sigma V) and
+    // T(A P - sigma P) explicitly in FP64
+    auto switch_to_f64 = [&]() -> plhr_status {
+        if (np) PLHR_TRY_CUDA(widen_block(n, kp, P32, kp, P, kp, s));
+        PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
+        if (T) PLHR_TRY(applyT(kp, X3, kp, QV));
+        if (np) {
+            PLHR_TRY_CUDA(lap_apply_shifts(g, kp, P, kp, AP, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
+            if (T) PLHR_TRY(applyT(kp, X3, kp, QP));
+        }
+        mx = false;
         return PLHR_OK;
     };
 
@@ -225,7 +292,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     for (it = 0; it <= opt.maxit; ++it) {
         // -------------------------------------------- residual, convergence (step 4 input)
         {
-            PhaseScope ps(PH_OTHER, s);
+            PhaseScope ps(PH_OTHER, s, (double)n * kp);
             PLHR_TRY_CUDA(residual_norms(n, kp, V, kp, AV, kp, lam, scale, R, kp, rpart, sums, s));
         }
         StatusArgs sa;
@@ -290,7 +357,12 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             // carry on from the rotated block (same span): V <- V C, A V explicit
             PLHR_TRY_CUDA(cudaMemcpyAsync(V, Rc, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
             PLHR_TRY_CUDA(cudaMemcpyAsync(AV, AW, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
-            if (T) PLHR_TRY_CUDA(block_times_small(n, QV, kp, kp, Crr, kp, QV, kp, s));
+            if (mx) {
+                mixed_its = it;
+                PLHR_TRY(switch_to_f64());
+            } else if (T) {
+                PLHR_TRY_CUDA(block_times_small(n, QV, kp, kp, Crr, kp, QV, kp, s));
+            }
             PLHR_TRY_CUDA(cudaMemcpyAsync(lam, theta, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
             {
                 std::vector<double> ones(kp, 1.0);
@@ -300,6 +372,14 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             continue;
         }
         if (it == opt.maxit) break;
+        if (mx) {
+            double worst = 0.0;
+            for (int q2 = 0; q2 < k; ++q2) worst = std::fmax(worst, h_rel[h_order[q2]]);
+            if (worst < opt.switch_tol) {
+                mixed_its = it;
+                PLHR_TRY(switch_to_f64());
+            }
+        }
         const int na = hs->nact;
         // -------------------------------------------- W = T(AV - BV Lambda), active columns
         const double* Ract = R;
@@ -309,11 +389,92 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             Ract = Rc;
             ldra = na;
         }
+        if (mx) {
+            // ---------------------------------------- the same step in the FP32 form
+            if (T) PLHR_TRY(applyT32(na, Ract, ldra, W32));
+            else PLHR_TRY_CUDA(narrow_block(n, na, Ract, ldra, W32, na, s));
+            float* X2in = T ? X2_32 : SQ32;
+            {
+                PhaseScope ps(PH_STENCIL, s, (double)n * na);
+                PLHR_TRY_CUDA(lap32_apply_shifts(g, na, W32, na, AW32, na, X2in, T ? 2 * na : na, lam_act,
+                                                 T ? X2in + na : nullptr, 2 * na, sigma, s));
+            }
+            const float* S32 = SQ32;
+            const int64_t lds = T ? 2 * na : na;
+            if (T) PLHR_TRY(applyT32(2 * na, (const float*)X2_32, 2 * na, SQ32));
+            const float* QW32 = SQ32 + na;
+            {
+                PhaseScope ps(PH_STENCIL, s, (double)n * na);
+                PLHR_TRY_CUDA(lap32_apply_shifts(g, na, S32, lds, AS32, na, nullptr, 0, nullptr, T ? X3_32 : nullptr,
+                                                 na, sigma, s));
+            }
+            if (T) PLHR_TRY(applyT32(na, (const float*)X3_32, na, QS32));
+            if (T) {
+                // Q_V = T(A V - sigma V) and Q_P = T(A P - sigma P) explicitly: carrying
+                // them through the update would mix the FP32 V-cycle's rounding of
+                // different iterations into one image, and the projected pencil
+                // (built from Q = T U) would lose consistency below ~1e-5
+                PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
+                PLHR_TRY(applyT32(kp, (const double*)X3, kp, QV32));
+                if (np) {
+                    PLHR_TRY_CUDA(lap32_apply_shifts(g, kp, P32, kp, AP32, kp, nullptr, 0, nullptr, X3_32, kp, sigma,
+                                                     s));
+                    PLHR_TRY(applyT32(kp, (const float*)X3_32, kp, QP32));
+                }
+            }
+            const int nb = np ? 4 : 3;
+            const int m = kp + 2 * na + np;
+            last_m = m;
+            BlkMx zb[4] = {{V, kp, kp, 1}, {W32, na, na, 0}, {S32, lds, na, 0}, {P32, kp, np, 0}};
+            BlkMx ab[4] = {{AV, kp, kp, 1}, {AW32, na, na, 0}, {AS32, na, na, 0}, {AP32, kp, np, 0}};
+            BlkMx qb[4] = {{QV32, kp, kp, 0}, {QW32, 2 * na, na, 0}, {QS32, na, na, 0}, {QP32, kp, np, 0}};
+            PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
+            DenseArgs da;
+            da.m = m; da.kp = kp; da.nv = kp;
+            da.Gzz = grams; da.Guq = grams + m * m; da.Gqz = grams + 2 * m * m;
+            da.colscale = colscale; da.work = dwork; da.Cp = Cp; da.Cvv = Cvv; da.tags = tags;
+            da.tag_partner = partner; da.xi = xi; da.out_int = dstat + 3; da.clk = nullptr;
+            for (int pass = 0; pass < 2; ++pass) {
+                {
+                    PhaseScope ps(PH_GRAM32, s, gram_flops(n, m));
+                    PLHR_TRY_CUDA(multi_gram_mx(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams, s));
+                }
+                {
+                    PhaseScope ps(PH_DENSE, s);
+                    PLHR_TRY_CUDA(dense_extract(da, s));
+                }
+                PLHR_TRY_CUDA(cudaMemcpyAsync(hs->dense, dstat + 3, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+                PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+                if (hs->dense[0] == kDenseOK || !T || pass == 1) break;
+                // recovery: recompute the carried images explicitly and project again
+                PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
+                PLHR_TRY(applyT32(kp, (const double*)X3, kp, QV32));
+                if (np) {
+                    PLHR_TRY_CUDA(lap32_apply_shifts(g, kp, P32, kp, AP32, kp, nullptr, 0, nullptr, X3_32, kp, sigma,
+                                                     s));
+                    PLHR_TRY(applyT32(kp, (const float*)X3_32, kp, QP32));
+                }
+            }
+            last_kept = hs->dense[1];
+            if (hs->dense[0] != kDenseOK) {
+                set_error("plhr_solve: projected problem failed at iteration %d (code %d)", it, hs->dense[0]);
+                result = PLHR_EBREAKDOWN;
+                break;
+            }
+            {
+                PhaseScope ps(PH_UPDATE32, s, 2.0 * n * m * kp);
+                PLHR_TRY_CUDA(block_update_mx(n, nb, zb, kp, Cp, Cvv, V, 1, kp, P32, 0, kp, s));
+            }
+            np = kp;
+            PLHR_TRY(refresh_images());
+            PLHR_TRY_CUDA(dense_rq(kp, dots, tags, partner, lam, scale, s));
+            continue;
+        }
         PLHR_TRY(applyT(na, Ract, ldra, W));
         // -------------------------------------------- S = T(AW - BW Lambda), Q_W = T(AW - sigma BW)
         double* X2in = T ? X2 : SQ;
         {
-            PhaseScope ps(PH_STENCIL, s);
+            PhaseScope ps(PH_STENCIL, s, (double)n * na);
             PLHR_TRY_CUDA(lap_apply_shifts(g, na, W, na, AW, na, X2in, T ? 2 * na : na, lam_act,
                                            T ? X2in + na : nullptr, 2 * na, sigma, s));
         }
@@ -323,10 +484,11 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         const double* QW = SQ + na;
         // -------------------------------------------- A S, Q_S = T(AS - sigma BS)
         {
-            PhaseScope ps(PH_STENCIL, s);
+            PhaseScope ps(PH_STENCIL, s, (double)n * na);
             PLHR_TRY_CUDA(lap_apply_shifts(g, na, S, lds, AS, na, nullptr, 0, nullptr, T ? X3 : nullptr, na, sigma, s));
         }
         if (T) PLHR_TRY(applyT(na, X3, na, QS));
+
         // -------------------------------------------- Grams over Z = [V W S P], AZ, Q (steps 6-7)
         const int nb = np ? 4 : 3;
         const int m = kp + 2 * na + np;
@@ -342,7 +504,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         da.xi = xi; da.out_int = dstat + 3; da.clk = nullptr;
         for (int pass = 0; pass < 2; ++pass) {
             {
-                PhaseScope ps(PH_GRAM, s);
+                PhaseScope ps(PH_GRAM, s, gram_flops(n, m));
                 PLHR_TRY_CUDA(multi_gram(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams, s));
             }
             // ---------------------------------------- projected T-harmonic problem, selection (steps 7-10)
@@ -370,7 +532,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         }
         // -------------------------------------------- P, V (steps 11-12), images, RQs (13-14)
         {
-            PhaseScope ps(PH_UPDATE, s);
+            PhaseScope ps(PH_UPDATE, s, (T ? 4.0 : 2.0) * n * m * kp);
             PLHR_TRY_CUDA(block_update(n, nb, zb, kp, Cp, Cvv, V, kp, P, kp, nullptr, 0, nullptr, nullptr, s));
             if (T) PLHR_TRY_CUDA(block_update(n, nb, qb, kp, Cp, Cvv, QV, kp, QP, kp, nullptr, 0, nullptr, nullptr, s));
         }
@@ -418,11 +580,14 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         info->setup_seconds = t1 - t0;
         info->solve_seconds = t2 - t1;
         info->history_len = hist;
+        info->mixed_iterations = (opt.precision == PLHR_PRECISION_MIXED) ? (mx ? it : mixed_its) : 0;
     }
     cudaFreeAsync(big.p, s);
     cudaFreeAsync(part.p, s);
     cudaFreeAsync(small.p, s);
     cudaFreeAsync(ints, s);
+    if (big32.p) cudaFreeAsync(big32.p, s);
+    big32.p = nullptr;
     big.p = part.p = small.p = nullptr;
     int_free.p = nullptr;
     cudaStreamSynchronize(s);

@@ -1,0 +1,107 @@
+"""GPU parity of the mixed-precision form (FP32 W, S, P, Q images, operator
+products on them and V-cycles; FP64 V, A V, projection and final check)
+against the FP64 oracle and the closed-form spectrum."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import avmg as oavmg
+from oracle import operators as oops
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def plhr():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1408_0042_gb300 as p
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return p
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _residuals(w, lam, V):
+    A, _ = oops.model_operator(w)
+    R = A @ V - V * lam[None, :]
+    return np.linalg.norm(R, axis=0) / (np.maximum(np.abs(lam), 1.0) * np.linalg.norm(V, axis=0))
+
+
+# FP32 storage and arithmetic: a V-cycle is a fixed linear map applied with
+# O(levels * nu) FP32 roundings per entry, each about 6e-8 of the entries it
+# combines; 2e-5 of the largest output entry bounds that for these sizes.
+@pytest.mark.parametrize("dims,levels,sigma,transfer,coarse", [
+    ((16, 16, 16), 1, 300.0, 0, 0), ((16, 16, 16), 3, 900.0, 1, 1), ((16, 16, 16), 3, 2500.0, 1, 1),
+    ((32, 24, 16), 3, 700.0, 0, 0), ((32, 24), 3, 700.0, 1, 1)])
+def test_avmg_f32_matches_oracle(plhr, dims, levels, sigma, transfer, coarse):
+    h = 1.0 / (max(dims) + 1)
+    A = plhr.Operator.laplacian(dims, h)
+    T = plhr.AVMG(A, sigma, levels=levels, nu=2, transfer=transfer, coarse=coarse)
+    R = wl.uniform_block(A.n, 5, 17)
+    W = T.apply_f32(torch.from_numpy(R).float().cuda()).double().cpu().numpy()
+    ref = oavmg.AVMG(dims, h, sigma, levels, nu=2, transfer=["constant", "linear"][transfer],
+                     coarse=["rediscretised", "fine_spectrum"][coarse])(R.astype(np.float32).astype(np.float64))
+    assert _rel(W, ref) <= 2e-5
+
+
+@pytest.mark.parametrize("case", ["lap2d_T_identity", "lap3d_avmg"])
+def test_mixed_solve_reaches_fp64_accuracy(plhr, case):
+    if case == "lap2d_T_identity":
+        w = wl.lap2d_small(16, k=4, gap_index=20)
+        maxit = 3000
+    else:
+        w = wl.lap3d_small(16, levels=3, k=4, gap_index=40)
+        maxit = 800
+    A = plhr.Operator.laplacian(w.dims, w.h)
+    T = None
+    if w.prec == "avmg":
+        T = plhr.AVMG(A, w.sigma, levels=w.mg_levels, nu=w.mg_nu)
+    v0 = torch.from_numpy(w.v0()).cuda()
+    lam, V, info = plhr.solve(A, w.sigma, w.k, T=T, tol=w.tol, maxit=maxit, v_init=v0,
+                              precision=plhr.PRECISION_MIXED)
+    assert info["converged"], info
+    assert 0 < info["mixed_iterations"] < info["iterations"], info
+    cf = wl.lap_closed_form(w.dims, w.h)
+    want = cf[np.lexsort((cf, np.abs(cf - w.sigma)))][: w.k]
+    assert np.allclose(np.sort(lam), np.sort(want), rtol=1e-10)
+    Vn = V.cpu().numpy()
+    assert np.all(_residuals(w, lam, Vn) <= w.tol * 1.0001)
+    assert np.abs(Vn.T @ Vn - np.eye(w.k)).max() <= 1e-12
+
+
+def test_mixed_switch_tol_zero_stays_fp32_until_forced(plhr):
+    """switch_tol below tol: the FP32 form runs until the final Rayleigh-Ritz
+    needs the FP64 form, and the answer is still FP64-accurate."""
+    w = wl.lap3d_small(16, levels=3, k=4, gap_index=40)
+    A = plhr.Operator.laplacian(w.dims, w.h)
+    T = plhr.AVMG(A, w.sigma, levels=w.mg_levels, nu=w.mg_nu)
+    v0 = torch.from_numpy(w.v0()).cuda()
+    lam, V, info = plhr.solve(A, w.sigma, w.k, T=T, tol=1e-5, maxit=800, v_init=v0,
+                              precision=plhr.PRECISION_MIXED, switch_tol=0.0)
+    assert info["converged"], info
+    assert np.all(_residuals(w, lam, V.cpu().numpy()) <= 1e-5 * 1.0001)
+
+
+@pytest.mark.slow
+def test_config2_mixed_full(plhr):
+    """128^3 Laplacian, k = 10, 4-level AV-MG, mixed precision: the same
+    closed-form eigenvalues and residual bound as the FP64 form."""
+    w = wl.config2()
+    A = plhr.Operator.laplacian(w.dims, w.h)
+    T = plhr.AVMG(A, w.sigma, levels=w.mg_levels, nu=w.mg_nu, transfer=1, coarse=1)
+    v0 = torch.from_numpy(w.v0()).cuda()
+    lam, V, info = plhr.solve(A, w.sigma, w.k, T=T, tol=w.tol, maxit=w.maxit, v_init=v0, guard=w.guard,
+                              precision=plhr.PRECISION_MIXED)
+    assert info["converged"], info
+    assert info["mixed_iterations"] > 0
+    cf = wl.lap_closed_form(w.dims, w.h)
+    want = cf[np.lexsort((cf, np.abs(cf - w.sigma)))][: w.k]
+    assert np.allclose(np.sort(lam), np.sort(want), rtol=1e-10)
+    Vn = V.cpu().numpy()
+    assert np.all(_residuals(w, lam, Vn) <= w.tol * 1.0001)
+    assert np.abs(Vn.T @ Vn - np.eye(w.k)).max() <= 1e-12
