@@ -80,6 +80,7 @@ _SIGS = {
     "plhr_last_error": (ctypes.c_char_p, []),
     "plhr_tharm_extract": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 11
                            + [ctypes.c_void_p]),
+    "plhr_tharm_extract_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 11),
 }
 
 _lib = None
