@@ -143,8 +143,10 @@ typedef struct {
     double switch_tol;         /* PLHR_PRECISION_MIXED: the iteration runs W, S, P, the Q images,
                                   the operator products on them and the V-cycles in FP32 (V and
                                   A V stay FP64) until the relative residuals of the k pairs
-                                  nearest sigma are all below switch_tol, then continues in FP64
-                                  with the images recomputed explicitly (default 1e-5) */
+                                  nearest sigma are all below switch_tol (or have stopped
+                                  improving for 25 iterations below 1e-5), then continues in
+                                  FP64 with the images recomputed explicitly and the columns beyond the
+                                  k nearest restarted from seeded random vectors (default 1e-5) */
 } plhr_options;
 
 typedef struct {

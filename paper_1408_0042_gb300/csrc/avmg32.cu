@@ -20,6 +20,8 @@ constexpr int kT = 256;
 struct Lv {
     int nx, ny, nz, nc;
     float ih2;
+    int nq;          // column groups per grid point (nc / VW)
+    float inv_nq;    // 1 / nq
 };
 
 struct Pos {
@@ -27,12 +29,16 @@ struct Pos {
     int64_t row;
 };
 
-// element position of this thread on level g; false when past the line end
+// Element group of this thread on level g: VW consecutive columns c.. of one
+// grid point; false past the line end.  ix = floor(t / nq) through a float
+// reciprocal: t < 2^12 and nq <= 32 keep (t + 1/2) / nq at least 1/64 away
+// from an integer, far above the rounding error.
+template <int VW>
 __device__ __forceinline__ bool pos_of(const Lv& g, Pos& p) {
     const int t = blockIdx.x * kT + threadIdx.x;
-    if (t >= g.nx * g.nc) return false;
-    p.ix = t / g.nc;
-    p.c = t - p.ix * g.nc;
+    if (t >= g.nx * g.nq) return false;
+    p.ix = (int)(((float)t + 0.5f) * g.inv_nq);
+    p.c = (t - p.ix * g.nq) * VW;
     p.iy = blockIdx.y;
     p.iz = blockIdx.z;
     p.row = ((int64_t)p.iz * g.ny + p.iy) * g.nx + p.ix;
@@ -42,88 +48,167 @@ __device__ __forceinline__ bool pos_of(const Lv& g, Pos& p) {
 template <typename T>
 __device__ __forceinline__ float ld(const T* p) { return (float)*p; }
 
-// (2d x - sum of neighbours) at x (leading dimension ld), zero outside, as
-// the sum of the differences x_c - x_nb: for a smooth field each difference is
-// exact in FP32 (the operands are within a factor 2 of each other), so the
-// result is correct to a few ulps of itself instead of ulps of 2d |x_c|
-template <bool D3, typename T>
-__device__ __forceinline__ float lap(const T* __restrict__ xp, int64_t ldx, const Lv& g, const Pos& p) {
-    const float xc = ld(xp);
-    const int64_t sy = ldx * g.nx, sz = sy * g.ny;
-    const float dxm = p.ix > 0 ? xc - ld(xp - ldx) : xc;
-    const float dxp = p.ix < g.nx - 1 ? xc - ld(xp + ldx) : xc;
-    const float dym = p.iy > 0 ? xc - ld(xp - sy) : xc;
-    const float dyp = p.iy < g.ny - 1 ? xc - ld(xp + sy) : xc;
-    float s = (dxm + dxp) + (dym + dyp);
-    if (D3) {
-        const float dzm = p.iz > 0 ? xc - ld(xp - sz) : xc;
-        const float dzp = p.iz < g.nz - 1 ? xc - ld(xp + sz) : xc;
-        s += dzm + dzp;
+// VW consecutive values (16-byte loads and stores when VW = 4)
+template <int VW>
+__device__ __forceinline__ void vld(float* o, const float* p) {
+    if (VW == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < VW; ++q) o[q] = p[q];
     }
-    return s;
+}
+template <int VW>
+__device__ __forceinline__ void vld(float* o, const double* p) {
+    if (VW == 4) {
+        const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+        o[0] = (float)a.x; o[1] = (float)a.y; o[2] = (float)b.x; o[3] = (float)b.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < VW; ++q) o[q] = (float)p[q];
+    }
+}
+template <int VW>
+__device__ __forceinline__ void vst(float* p, const float* v) {
+    if (VW == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < VW; ++q) p[q] = v[q];
+    }
+}
+
+// L x at (p, columns c..c+VW) with leading dimension ld, zero outside, as the
+// sum of the differences x_c - x_nb: for a smooth field each difference is
+// exact in FP32 (the operands are within a factor 2 of each other), so the
+// result is correct to a few ulps of itself instead of ulps of 2d |x_c|.
+// xc receives x itself.
+template <bool D3, int VW, typename T>
+__device__ __forceinline__ void lap(float* out, float* xc, const T* __restrict__ xp, int64_t ldx, const Lv& g,
+                                    const Pos& p) {
+    const int64_t sy = ldx * g.nx, sz = sy * g.ny;
+    float nb[VW];
+    vld<VW>(xc, xp);
+    float s[VW];
+#pragma unroll
+    for (int q = 0; q < VW; ++q) s[q] = 0.0f;
+    auto add_dir = [&](bool in, int64_t off) {
+        if (in) {
+            vld<VW>(nb, xp + off);
+#pragma unroll
+            for (int q = 0; q < VW; ++q) s[q] += xc[q] - nb[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < VW; ++q) s[q] += xc[q];
+        }
+    };
+    float sx[VW];
+    add_dir(p.ix > 0, -ldx);
+    add_dir(p.ix < g.nx - 1, ldx);
+#pragma unroll
+    for (int q = 0; q < VW; ++q) { sx[q] = s[q]; s[q] = 0.0f; }
+    add_dir(p.iy > 0, -sy);
+    add_dir(p.iy < g.ny - 1, sy);
+    if (D3) {
+        float sxy[VW];
+#pragma unroll
+        for (int q = 0; q < VW; ++q) { sxy[q] = sx[q] + s[q]; s[q] = 0.0f; }
+        add_dir(p.iz > 0, -sz);
+        add_dir(p.iz < g.nz - 1, sz);
+#pragma unroll
+        for (int q = 0; q < VW; ++q) out[q] = sxy[q] + s[q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < VW; ++q) out[q] = sx[q] + s[q];
+    }
 }
 
 // first two Richardson sweeps from w = 0 with B = L:  w = 2 om r - om^2 L r
-template <bool D3, typename Tr>
+template <bool D3, int VW, typename Tr>
 __global__ void __launch_bounds__(kT) k_rich2(Lv g, float om, const Tr* __restrict__ r, int64_t ldr,
                                               float* __restrict__ w) {
     Pos p;
-    if (!pos_of(g, p)) return;
-    const Tr* rp = r + p.row * ldr + p.c;
-    w[p.row * g.nc + p.c] = 2.0f * om * ld(rp) - om * om * g.ih2 * lap<D3>(rp, ldr, g, p);
+    if (!pos_of<VW>(g, p)) return;
+    float l[VW], rc[VW], o[VW];
+    lap<D3, VW>(l, rc, r + p.row * ldr + p.c, ldr, g, p);
+#pragma unroll
+    for (int q = 0; q < VW; ++q) o[q] = 2.0f * om * rc[q] - om * om * g.ih2 * l[q];
+    vst<VW>(w + p.row * g.nc + p.c, o);
 }
 
 // w = om r (one sweep from zero)
-template <typename Tr>
+template <bool D3, int VW, typename Tr>
 __global__ void __launch_bounds__(kT) k_scale(Lv g, float om, const Tr* __restrict__ r, int64_t ldr,
                                               float* __restrict__ w) {
     Pos p;
-    if (!pos_of(g, p)) return;
-    w[p.row * g.nc + p.c] = om * ld(r + p.row * ldr + p.c);
+    if (!pos_of<VW>(g, p)) return;
+    float rv[VW];
+    vld<VW>(rv, r + p.row * ldr + p.c);
+#pragma unroll
+    for (int q = 0; q < VW; ++q) rv[q] *= om;
+    vst<VW>(w + p.row * g.nc + p.c, rv);
 }
 
 // wout = win + om (r - L win)
-template <bool D3, typename Tr>
+template <bool D3, int VW, typename Tr>
 __global__ void __launch_bounds__(kT) k_rich(Lv g, float om, const float* __restrict__ win, const Tr* __restrict__ r,
                                              int64_t ldr, float* __restrict__ wout) {
     Pos p;
-    if (!pos_of(g, p)) return;
-    const float* wp = win + p.row * g.nc + p.c;
-    wout[p.row * g.nc + p.c] = wp[0] + om * (ld(r + p.row * ldr + p.c) - g.ih2 * lap<D3>(wp, g.nc, g, p));
+    if (!pos_of<VW>(g, p)) return;
+    float l[VW], wc[VW], rv[VW];
+    lap<D3, VW>(l, wc, win + p.row * g.nc + p.c, g.nc, g, p);
+    vld<VW>(rv, r + p.row * ldr + p.c);
+#pragma unroll
+    for (int q = 0; q < VW; ++q) wc[q] += om * (rv[q] - g.ih2 * l[q]);
+    vst<VW>(wout + p.row * g.nc + p.c, wc);
 }
 
 // t = L x - sig x
-template <bool D3>
+template <bool D3, int VW, typename Tr>
 __global__ void __launch_bounds__(kT) k_shifted(Lv g, float sig, const float* __restrict__ x, float* __restrict__ t) {
     Pos p;
-    if (!pos_of(g, p)) return;
-    const float* xp = x + p.row * g.nc + p.c;
-    t[p.row * g.nc + p.c] = g.ih2 * lap<D3>(xp, g.nc, g, p) - sig * xp[0];
+    if (!pos_of<VW>(g, p)) return;
+    float l[VW], xc[VW];
+    lap<D3, VW>(l, xc, x + p.row * g.nc + p.c, g.nc, g, p);
+#pragma unroll
+    for (int q = 0; q < VW; ++q) l[q] = g.ih2 * l[q] - sig * xc[q];
+    vst<VW>(t + p.row * g.nc + p.c, l);
 }
 
 // with B w = ((L - sig) t + c^2 w) / (2c), t = (L - sig) w:
 // mode 0: out = w + om (r - B w);  mode 1: out = r - B w
-template <bool D3, typename Tr>
+template <bool D3, int VW, typename Tr>
 __global__ void __launch_bounds__(kT) k_poly(Lv g, float sig, float cpar, float om, int mode,
                                              const float* __restrict__ w, const float* __restrict__ t,
                                              const Tr* __restrict__ r, int64_t ldr, float* __restrict__ out) {
     Pos p;
-    if (!pos_of(g, p)) return;
-    const float* tp = t + p.row * g.nc + p.c;
-    const float tt = g.ih2 * lap<D3>(tp, g.nc, g, p) - sig * tp[0];
-    const float wv = w[p.row * g.nc + p.c];
-    const float res = ld(r + p.row * ldr + p.c) - (tt + cpar * cpar * wv) / (2.0f * cpar);
-    out[p.row * g.nc + p.c] = mode == 0 ? wv + om * res : res;
+    if (!pos_of<VW>(g, p)) return;
+    float l[VW], tc[VW], wv[VW], rv[VW];
+    lap<D3, VW>(l, tc, t + p.row * g.nc + p.c, g.nc, g, p);
+    vld<VW>(wv, w + p.row * g.nc + p.c);
+    vld<VW>(rv, r + p.row * ldr + p.c);
+#pragma unroll
+    for (int q = 0; q < VW; ++q) {
+        const float tt = g.ih2 * l[q] - sig * tc[q];
+        const float res = rv[q] - (tt + cpar * cpar * wv[q]) / (2.0f * cpar);
+        rv[q] = mode == 0 ? wv[q] + om * res : res;
+    }
+    vst<VW>(out + p.row * g.nc + p.c, rv);
 }
 
 // out = r - L w
-template <bool D3, typename Tr>
+template <bool D3, int VW, typename Tr>
 __global__ void __launch_bounds__(kT) k_resid(Lv g, const float* __restrict__ w, const Tr* __restrict__ r, int64_t ldr,
                                               float* __restrict__ out) {
     Pos p;
-    if (!pos_of(g, p)) return;
-    out[p.row * g.nc + p.c] =
-        ld(r + p.row * ldr + p.c) - g.ih2 * lap<D3>(w + p.row * g.nc + p.c, g.nc, g, p);
+    if (!pos_of<VW>(g, p)) return;
+    float l[VW], wc[VW], rv[VW];
+    lap<D3, VW>(l, wc, w + p.row * g.nc + p.c, g.nc, g, p);
+    vld<VW>(rv, r + p.row * ldr + p.c);
+#pragma unroll
+    for (int q = 0; q < VW; ++q) rv[q] -= g.ih2 * l[q];
+    vst<VW>(out + p.row * g.nc + p.c, rv);
 }
 
 // 1D cell-centred prolongation weights from coarse cells to fine point f:
@@ -160,11 +245,11 @@ __device__ __forceinline__ int rw(int lin, int I, int nfx, int* idx, float* wt) 
 }
 
 // wf += P wc   (launched over the fine level)
-template <bool D3>
+template <bool D3, int VW, typename Tr>
 __global__ void __launch_bounds__(kT) k_prolong_add(Lv gf, Lv gc, int lin, const float* __restrict__ wc,
                                                     float* __restrict__ wf) {
     Pos p;
-    if (!pos_of(gf, p)) return;
+    if (!pos_of<VW>(gf, p)) return;
     int xi[2], yi[2], zi[2];
     float xw[2], yw[2], zw[2];
     const int nxw = pw(lin, p.ix, gc.nx, xi, xw);
@@ -172,23 +257,28 @@ __global__ void __launch_bounds__(kT) k_prolong_add(Lv gf, Lv gc, int lin, const
     int nzw = 1;
     zi[0] = 0; zw[0] = 1.0f;
     if (D3) nzw = pw(lin, p.iz, gc.nz, zi, zw);
-    float s = 0.0f;
+    float acc[VW], v[VW];
+    vld<VW>(acc, wf + p.row * gf.nc + p.c);
     for (int a = 0; a < nzw; ++a)
         for (int b = 0; b < nyw; ++b) {
             const float* line = wc + ((int64_t)zi[a] * gc.ny + yi[b]) * gc.nx * gc.nc + p.c;
-            float sl = 0.0f;
-            for (int q = 0; q < nxw; ++q) sl += xw[q] * line[(int64_t)xi[q] * gc.nc];
-            s += zw[a] * yw[b] * sl;
+            const float wyz = zw[a] * yw[b];
+            for (int q = 0; q < nxw; ++q) {
+                vld<VW>(v, line + (int64_t)xi[q] * gc.nc);
+                const float wt = wyz * xw[q];
+#pragma unroll
+                for (int e = 0; e < VW; ++e) acc[e] += wt * v[e];
+            }
         }
-    wf[p.row * gf.nc + p.c] += s;
+    vst<VW>(wf + p.row * gf.nc + p.c, acc);
 }
 
 // rc = R f   (launched over the coarse level)
-template <bool D3>
+template <bool D3, int VW, typename Tr>
 __global__ void __launch_bounds__(kT) k_restrict(Lv gf, Lv gc, int lin, const float* __restrict__ f,
                                                  float* __restrict__ rc) {
     Pos p;
-    if (!pos_of(gc, p)) return;
+    if (!pos_of<VW>(gc, p)) return;
     int xi[4], yi[4], zi[4];
     float xw[4], yw[4], zw[4];
     const int nxw = rw(lin, p.ix, gf.nx, xi, xw);
@@ -196,15 +286,21 @@ __global__ void __launch_bounds__(kT) k_restrict(Lv gf, Lv gc, int lin, const fl
     int nzw = 1;
     zi[0] = 0; zw[0] = 1.0f;
     if (D3) nzw = rw(lin, p.iz, gf.nz, zi, zw);
-    float s = 0.0f;
+    float acc[VW], v[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) acc[e] = 0.0f;
     for (int a = 0; a < nzw; ++a)
         for (int b = 0; b < nyw; ++b) {
             const float* line = f + ((int64_t)zi[a] * gf.ny + yi[b]) * gf.nx * gf.nc + p.c;
-            float sl = 0.0f;
-            for (int q = 0; q < nxw; ++q) sl += xw[q] * line[(int64_t)xi[q] * gf.nc];
-            s += zw[a] * yw[b] * sl;
+            const float wyz = zw[a] * yw[b];
+            for (int q = 0; q < nxw; ++q) {
+                vld<VW>(v, line + (int64_t)xi[q] * gf.nc);
+                const float wt = wyz * xw[q];
+#pragma unroll
+                for (int e = 0; e < VW; ++e) acc[e] += wt * v[e];
+            }
         }
-    rc[p.row * gc.nc + p.c] = s;
+    vst<VW>(rc + p.row * gc.nc + p.c, acc);
 }
 
 // Coarsest solve, one CTA per column: out = S diag(1/|mu_i + mu_j + mu_k - sig|) S^T in,
@@ -281,8 +377,26 @@ __global__ void __launch_bounds__(kT) k_coarse_sep(int d, int nx, int ny, int nz
     }
 }
 
-Lv lv(const Grid& g, int nc) { return Lv{(int)g.nx, (int)g.ny, (int)g.nz, nc, (float)g.inv_h2()}; }
-dim3 grid_of(const Grid& g, int nc) { return dim3((unsigned)((g.nx * nc + kT - 1) / kT), (unsigned)g.ny, (unsigned)g.nz); }
+Lv lv(const Grid& g, int nc, int vw) {
+    const int nq = nc / vw;
+    return Lv{(int)g.nx, (int)g.ny, (int)g.nz, nc, (float)g.inv_h2(), nq, 1.0f / (float)nq};
+}
+dim3 grid_of(const Grid& g, int nc, int vw) {
+    return dim3((unsigned)((g.nx * (nc / vw) + kT - 1) / kT), (unsigned)g.ny, (unsigned)g.nz);
+}
+
+// launch K<D3, VW, TR> on grid GR for the level of this call
+#define PLHR_L4(K, TR, GR, ...)                                                         \
+    do {                                                                                   \
+        if (d3) {                                                                          \
+            if (v4) K<true, 4, TR><<<GR, kT, 0, s>>>(__VA_ARGS__);                       \
+            else K<true, 1, TR><<<GR, kT, 0, s>>>(__VA_ARGS__);                          \
+        } else {                                                                           \
+            if (v4) K<false, 4, TR><<<GR, kT, 0, s>>>(__VA_ARGS__);                      \
+            else K<false, 1, TR><<<GR, kT, 0, s>>>(__VA_ARGS__);                         \
+        }                                                                                  \
+        count_launches(1);                                                                 \
+    } while (0)
 
 struct Bufs {
     float *w0, *w1, *tmp, *rc, *wc;
@@ -305,33 +419,29 @@ cudaError_t coarse(const MGHierarchy& H, int nc, const Tr* r, int64_t ldr, float
 
 // one smoothing sweep w_out = w_in + om (r - B w_in) on level L
 template <typename Tr>
-void sweep(const MGLevel& L, float sig, int nc, const float* win, const Tr* r, int64_t ldr, float* tmp, float* wout,
-           cudaStream_t s) {
-    const Lv g = lv(L.g, nc);
-    const dim3 gr = grid_of(L.g, nc);
+void sweep(const MGLevel& L, float sig, int nc, bool v4, const float* win, const Tr* r, int64_t ldr, float* tmp,
+           float* wout, cudaStream_t s) {
+    const Lv g = lv(L.g, nc, v4 ? 4 : 1);
+    const dim3 gr = grid_of(L.g, nc, v4 ? 4 : 1);
     const bool d3 = L.g.d == 3;
     if (!L.poly) {
-        if (d3) k_rich<true, Tr><<<gr, kT, 0, s>>>(g, (float)L.omega, win, r, ldr, wout);
-        else k_rich<false, Tr><<<gr, kT, 0, s>>>(g, (float)L.omega, win, r, ldr, wout);
-        count_launches(1);
+        PLHR_L4(k_rich, Tr, gr, g, (float)L.omega, win, r, ldr, wout);
         return;
     }
-    if (d3) k_shifted<true><<<gr, kT, 0, s>>>(g, sig, win, tmp);
-    else k_shifted<false><<<gr, kT, 0, s>>>(g, sig, win, tmp);
-    if (d3) k_poly<true, Tr><<<gr, kT, 0, s>>>(g, sig, (float)L.c, (float)L.omega, 0, win, tmp, r, ldr, wout);
-    else k_poly<false, Tr><<<gr, kT, 0, s>>>(g, sig, (float)L.c, (float)L.omega, 0, win, tmp, r, ldr, wout);
-    count_launches(2);
+    PLHR_L4(k_shifted, Tr, gr, g, sig, win, tmp);
+    PLHR_L4(k_poly, Tr, gr, g, sig, (float)L.c, (float)L.omega, 0, win, tmp, r, ldr, wout);
 }
 
 template <typename Tr>
-cudaError_t vcycle(const MGHierarchy& H, int l, int nc, const Tr* r, int64_t ldr, float* out,
+cudaError_t vcycle(const MGHierarchy& H, int l, int nc, bool v4, const Tr* r, int64_t ldr, float* out,
                    const std::vector<Bufs>& B, cudaStream_t s) {
     if (l == 0) return coarse(H, nc, r, ldr, out, s);
     const MGLevel& L = H.lev[l];
     const MGLevel& Lc = H.lev[l - 1];
     const Bufs& b = B[l];
-    const Lv g = lv(L.g, nc), gc = lv(Lc.g, nc);
-    const dim3 gr = grid_of(L.g, nc), grc = grid_of(Lc.g, nc);
+    const int vw = v4 ? 4 : 1;
+    const Lv g = lv(L.g, nc, vw), gc = lv(Lc.g, nc, vw);
+    const dim3 gr = grid_of(L.g, nc, vw), grc = grid_of(Lc.g, nc, vw);
     const bool d3 = L.g.d == 3;
     const float sig = (float)H.sigma, om = (float)L.omega;
     float* cur = b.w0;
@@ -339,48 +449,47 @@ cudaError_t vcycle(const MGHierarchy& H, int l, int nc, const Tr* r, int64_t ldr
     // pre-smoothing from w = 0
     int done;
     if (!L.poly && H.nu >= 2) {
-        if (d3) k_rich2<true, Tr><<<gr, kT, 0, s>>>(g, om, r, ldr, cur);
-        else k_rich2<false, Tr><<<gr, kT, 0, s>>>(g, om, r, ldr, cur);
+        PLHR_L4(k_rich2, Tr, gr, g, om, r, ldr, cur);
         done = 2;
     } else {
-        k_scale<Tr><<<gr, kT, 0, s>>>(g, om, r, ldr, cur);
+        PLHR_L4(k_scale, Tr, gr, g, om, r, ldr, cur);
         done = 1;
     }
-    count_launches(1);
     for (int i = done; i < H.nu; ++i) {
-        sweep(L, sig, nc, cur, r, ldr, b.tmp, nxt, s);
+        sweep(L, sig, nc, v4, cur, r, ldr, b.tmp, nxt, s);
         float* t = cur; cur = nxt; nxt = t;
     }
     // coarse-grid correction: r_c = R (r - B w)
     if (!L.poly) {
-        if (d3) k_resid<true, Tr><<<gr, kT, 0, s>>>(g, cur, r, ldr, nxt);
-        else k_resid<false, Tr><<<gr, kT, 0, s>>>(g, cur, r, ldr, nxt);
-        count_launches(1);
+        PLHR_L4(k_resid, Tr, gr, g, cur, r, ldr, nxt);
     } else {
-        if (d3) k_shifted<true><<<gr, kT, 0, s>>>(g, sig, cur, b.tmp);
-        else k_shifted<false><<<gr, kT, 0, s>>>(g, sig, cur, b.tmp);
-        if (d3) k_poly<true, Tr><<<gr, kT, 0, s>>>(g, sig, (float)L.c, om, 1, cur, b.tmp, r, ldr, nxt);
-        else k_poly<false, Tr><<<gr, kT, 0, s>>>(g, sig, (float)L.c, om, 1, cur, b.tmp, r, ldr, nxt);
-        count_launches(2);
+        PLHR_L4(k_shifted, Tr, gr, g, sig, cur, b.tmp);
+        PLHR_L4(k_poly, Tr, gr, g, sig, (float)L.c, om, 1, cur, b.tmp, r, ldr, nxt);
     }
-    if (d3) k_restrict<true><<<grc, kT, 0, s>>>(g, gc, H.linear, nxt, b.rc);
-    else k_restrict<false><<<grc, kT, 0, s>>>(g, gc, H.linear, nxt, b.rc);
-    count_launches(1);
+    PLHR_L4(k_restrict, float, grc, g, gc, H.linear, nxt, b.rc);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = vcycle<float>(H, l - 1, nc, b.rc, nc, b.wc, B, s);
+    e = vcycle<float>(H, l - 1, nc, v4, b.rc, nc, b.wc, B, s);
     if (e != cudaSuccess) return e;
-    if (d3) k_prolong_add<true><<<gr, kT, 0, s>>>(g, gc, H.linear, b.wc, cur);
-    else k_prolong_add<false><<<gr, kT, 0, s>>>(g, gc, H.linear, b.wc, cur);
-    count_launches(1);
+    PLHR_L4(k_prolong_add, float, gr, g, gc, H.linear, b.wc, cur);
     // post-smoothing; the last sweep writes out
     for (int i = 0; i < H.nu; ++i) {
         float* dst = (i == H.nu - 1) ? out : nxt;
-        sweep(L, sig, nc, cur, r, ldr, b.tmp, dst, s);
+        sweep(L, sig, nc, v4, cur, r, ldr, b.tmp, dst, s);
         nxt = cur;
         cur = dst;
     }
     return cudaGetLastError();
+}
+#undef PLHR_L4
+
+// r32 (dense, n x nc) = r (FP64, leading dimension ldr)
+__global__ void k_narrow_rhs(int64_t n, int nc, const double* __restrict__ r, int64_t ldr, float* __restrict__ r32) {
+    const int64_t total = n * nc;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e / nc;
+        r32[e] = (float)r[row * ldr + (e - row * nc)];
+    }
 }
 
 template <typename Tr>
@@ -397,20 +506,33 @@ cudaError_t run(const MGHierarchy& H, int nc, const Tr* r, int64_t ldr, float* w
         B[l].rc = p; p += ncc;
         B[l].wc = p; p += ncc;
     }
-    return vcycle<Tr>(H, top, nc, r, ldr, w, B, s);
+    // four columns per thread with 16-byte accesses when every block allows it
+    auto al16 = [](const void* q) { return ((uintptr_t)q & 15) == 0; };
+    const bool v4 = nc % 4 == 0 && ldr % 4 == 0 && al16(r) && al16(w) && al16(work);
+    return vcycle<Tr>(H, top, nc, v4, r, ldr, w, B, s);
 }
 
 }  // namespace
 
 int64_t mg_workspace_floats(const MGHierarchy& H, int nc) {
-    int64_t tot = 0;
+    // level buffers, plus an FP32 copy of an FP64 right-hand side
+    int64_t tot = H.lev.back().g.n() * nc;
     for (size_t l = 1; l < H.lev.size(); ++l) tot += 3 * H.lev[l].g.n() * nc + 2 * H.lev[l - 1].g.n() * nc;
     return tot;
 }
 
 cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const double* r, int64_t ldr, float* w, float* work,
                           cudaStream_t s) {
-    return run<double>(H, nc, r, ldr, w, work, s);
+    // an FP64 right-hand side is read by four fine-level kernels: round it to
+    // FP32 once (one pass) so that every level kernel streams FP32
+    if (nc <= 0) return cudaSuccess;
+    const int64_t n = H.lev.back().g.n();
+    float* r32 = work + (mg_workspace_floats(H, nc) - n * nc);
+    k_narrow_rhs<<<grid_size_for(n * nc, 256, sm_count() * 8), 256, 0, s>>>(n, nc, r, ldr, r32);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return run<float>(H, nc, r32, nc, w, work, s);
 }
 
 cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const float* r, int64_t ldr, float* w, float* work,

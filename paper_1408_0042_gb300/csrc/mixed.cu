@@ -3,8 +3,8 @@
 // convergence needs them); W, S, P, their images and the T-harmonic images Q
 // are FP32.  The Grams of the trial basis take FP32 products of values that
 // were formed in full precision and then rounded (the V columns, U_V =
-// (A V - sigma V) s), accumulate 32-row chunks in FP32 registers and fold
-// every chunk into a per-thread double-FP32 (hi, lo) accumulator with TwoSum,
+// (A V - sigma V) s), sum 32 rows at a time in FP32 registers and fold each
+// 32-row sum into a per-thread double-FP32 (hi, lo) accumulator with TwoSum,
 // so the accumulation error does not grow with n.  The per-CTA partials are
 // summed in FP64 in a fixed order (deterministic).
 #include "dword.h"
@@ -13,9 +13,8 @@
 namespace plhr {
 namespace {
 
-constexpr int kMxRows = 32;         // rows per chunk
+constexpr int kMxRows = 64;         // rows per staged chunk (folded every 32 rows)
 constexpr int kMxThreads = 256;
-constexpr int kMxTilesPerThread = 3;
 
 struct FamMx {
     const void* p[4];
@@ -23,6 +22,7 @@ struct FamMx {
     int nc[4];
     int off[4];
     int f64[4];
+    int is_u[4];
 };
 
 FamMx fam_mx(const BlkMx* b, int nb) {
@@ -31,9 +31,10 @@ FamMx fam_mx(const BlkMx* b, int nb) {
     for (int i = 0; i < 4; ++i) {
         if (i < nb) {
             F.p[i] = b[i].p; F.ld[i] = b[i].ld; F.nc[i] = b[i].nc; F.off[i] = off; F.f64[i] = b[i].f64;
+            F.is_u[i] = b[i].is_u;
             off += b[i].nc;
         } else {
-            F.p[i] = nullptr; F.ld[i] = 0; F.nc[i] = 0; F.off[i] = off; F.f64[i] = 0;
+            F.p[i] = nullptr; F.ld[i] = 0; F.nc[i] = 0; F.off[i] = off; F.f64[i] = 0; F.is_u[i] = 0;
         }
     }
     return F;
@@ -48,17 +49,23 @@ __device__ __forceinline__ float ldf(const FamMx& F, int b, int64_t row, int c) 
                     : static_cast<const float*>(F.p[b])[row * F.ld[b] + c];
 }
 
-// Stage rows row0 .. row0 + kMxRows - 1 of z = Z s, u = (AZ - sigma Z) s and
-// q = Q s (q = u when Q is absent) into [row][mp] FP32 tiles; FP64 blocks are
-// combined in FP64 and rounded once.
+// Stage rows row0 .. row0 + kMxRows - 1 of z = Z s, u = (AZ - sigma Z) s (u =
+// AZ s for a block flagged is_u, which already holds AZ - sigma Z) and q = Q s
+// (q = u when Q is absent) into [row][mp] FP32 tiles; FP64 blocks are combined
+// in FP64 and rounded once.
 __device__ void stage_mx(float* sz, float* su, float* sq, int mp, int64_t n, int64_t row0, const FamMx& Z,
                          const FamMx& AZ, const FamMx& Q, int nb, int has_q, double sigma,
                          const double* __restrict__ csc) {
-    for (int b = 0; b < nb; ++b) {
+    // static block indices: the family descriptors stay in registers / the
+    // parameter space instead of a local copy
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        if (b >= nb) break;
         const int nc = Z.nc[b];
         if (nc == 0) continue;
         const int tot = kMxRows * nc;
         const bool wide = Z.f64[b] || AZ.f64[b];
+        const bool isu = AZ.is_u[b];
         for (int t = threadIdx.x; t < tot; t += blockDim.x) {
             const int r = t / nc, c = t - r * nc;
             const int64_t row = row0 + r;
@@ -68,13 +75,13 @@ __device__ void stage_mx(float* sz, float* su, float* sq, int mp, int64_t n, int
                 const double s = csc[col];
                 if (wide) {
                     const double zd = ldv(Z, b, row, c) * s;
-                    const double ud = ldv(AZ, b, row, c) * s - sigma * zd;
+                    const double ud = isu ? ldv(AZ, b, row, c) * s : ldv(AZ, b, row, c) * s - sigma * zd;
                     z = (float)zd;
                     u = (float)ud;
                 } else {
                     const float sf = (float)s;
                     z = ldf(Z, b, row, c) * sf;
-                    u = ldf(AZ, b, row, c) * sf - (float)sigma * z;
+                    u = isu ? ldf(AZ, b, row, c) * sf : ldf(AZ, b, row, c) * sf - (float)sigma * z;
                 }
                 q = has_q ? ldf(Q, b, row, c) * (float)s : u;
             }
@@ -85,39 +92,59 @@ __device__ void stage_mx(float* sz, float* su, float* sq, int mp, int64_t n, int
     }
 }
 
-// Tiles: 4x4 over three mp x mp outputs; g = 0: Z^T Z (upper tiles), g = 1:
-// U^T Q, g = 2: Q^T Z.
-__global__ void __launch_bounds__(kMxThreads, 1) k_gram_mx(int64_t n, int m, int mp, int nb, FamMx Z, FamMx AZ,
-                                                           FamMx Q, int has_q, double sigma,
-                                                           const double* __restrict__ csc,
-                                                           double* __restrict__ partial) {
+__device__ __forceinline__ void outer4(float* acc, const float4& a, const float4& b) {
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x * 4 + y] = fmaf(av[x], bv[y], acc[x * 4 + y]);
+}
+
+// hi + lo += acc (TwoSum on hi, lo collects the rounding errors)
+__device__ __forceinline__ void fold(float* hi, float* lo, const float* acc) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const dw t = dw_two_sum(hi[e], acc[e]);
+        hi[e] = t.hi;
+        lo[e] = __fadd_rn(lo[e], t.lo);
+    }
+}
+
+__device__ __forceinline__ void put_tile(double* G, int m, int i0, int j0, const float* hi, const float* lo,
+                                         bool mirror) {
+    for (int x = 0; x < 4; ++x)
+        for (int y = 0; y < 4; ++y) {
+            const int i = i0 + x, j = j0 + y;
+            if (i < m && j < m) {
+                const double v = (double)hi[x * 4 + y] + (double)lo[x * 4 + y];
+                G[i * m + j] = v;
+                if (mirror) G[j * m + i] = v;
+            }
+        }
+}
+
+// 768 threads: thread t owns output g = t / 256 (0: Z^T Z, written for
+// ti <= tj and mirrored; 1: U^T Q; 2: Q^T Z) and its 4x4 tile (ti, tj) =
+// ((t % 256) / 16, t % 16).  One tile per thread keeps ~70 registers, so 24
+// warps per SM hide the latency of the staging loads.  mp <= 64.
+constexpr int kGramMxThreads = 768;
+__global__ void __launch_bounds__(kGramMxThreads, 1) k_gram_mx(int64_t n, int m, int mp, int nb, FamMx Z, FamMx AZ,
+                                                               FamMx Q, int has_q, double sigma,
+                                                               const double* __restrict__ csc,
+                                                               double* __restrict__ partial) {
     extern __shared__ __align__(16) float shm[];
     float* sz = shm;
     float* su = sz + kMxRows * mp;
     float* sq = su + kMxRows * mp;
     const int T = mp / 4;
-    const int nt0 = T * (T + 1) / 2, nt1 = T * T;
-    const int ntiles = nt0 + 2 * nt1;
-    float acc[kMxTilesPerThread][16], hi[kMxTilesPerThread][16], lo[kMxTilesPerThread][16];
-    int tg[kMxTilesPerThread], ti[kMxTilesPerThread], tj[kMxTilesPerThread];
-    int my = 0;
-    for (int t = threadIdx.x; t < ntiles && my < kMxTilesPerThread; t += blockDim.x, ++my) {
-        if (t < nt0) {
-            int r = 0, rem = t;
-            while (rem >= T - r) { rem -= T - r; ++r; }
-            tg[my] = 0; ti[my] = r; tj[my] = r + rem;
-        } else if (t < nt0 + nt1) {
-            const int u = t - nt0;
-            tg[my] = 1; ti[my] = u / T; tj[my] = u % T;
-        } else {
-            const int u = t - nt0 - nt1;
-            tg[my] = 2; ti[my] = u / T; tj[my] = u % T;
-        }
-    }
+    const int g = threadIdx.x >> 8, ti = (threadIdx.x >> 4) & 15, tj = threadIdx.x & 15;
+    const bool act = ti < T && tj < T && (g != 0 || ti <= tj);
+    // operands of this output: A^T B with A, B in {z, u, q}
+    const float* A = g == 0 ? sz : (g == 1 ? su : sq);
+    const float* B = g == 1 ? sq : sz;
+    float hi[16], lo[16];
 #pragma unroll
-    for (int q = 0; q < kMxTilesPerThread; ++q)
-#pragma unroll
-        for (int e = 0; e < 16; ++e) { hi[q][e] = 0.0f; lo[q][e] = 0.0f; }
+    for (int e = 0; e < 16; ++e) { hi[e] = 0.0f; lo[e] = 0.0f; }
     // zero the padding columns once (staging never writes them)
     for (int t = threadIdx.x; t < kMxRows * mp; t += blockDim.x) {
         if (t % mp >= m) { sz[t] = 0.0f; su[t] = 0.0f; sq[t] = 0.0f; }
@@ -127,49 +154,26 @@ __global__ void __launch_bounds__(kMxThreads, 1) k_gram_mx(int64_t n, int m, int
         __syncthreads();
         stage_mx(sz, su, sq, mp, n, ch * kMxRows, Z, AZ, Q, nb, has_q, sigma, csc);
         __syncthreads();
+        if (act) {
+            float acc[16];
 #pragma unroll
-        for (int q = 0; q < kMxTilesPerThread; ++q) {
-            if (q >= my) break;
-            const float* A = tg[q] == 0 ? sz : (tg[q] == 1 ? su : sq);
-            const float* B = tg[q] == 0 ? sz : (tg[q] == 1 ? sq : sz);
-            const int i0 = ti[q] * 4, j0 = tj[q] * 4;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) acc[q][e] = 0.0f;
+            for (int e = 0; e < 16; ++e) acc[e] = 0.0f;
+            for (int half = 0; half < kMxRows; half += 32) {
 #pragma unroll 4
-            for (int r = 0; r < kMxRows; ++r) {
-                const float4 a = *reinterpret_cast<const float4*>(A + r * mp + i0);
-                const float4 bb = *reinterpret_cast<const float4*>(B + r * mp + j0);
-                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {bb.x, bb.y, bb.z, bb.w};
+                for (int r = half; r < half + 32; ++r) {
+                    const float4 a = *reinterpret_cast<const float4*>(A + r * mp + 4 * ti);
+                    const float4 b = *reinterpret_cast<const float4*>(B + r * mp + 4 * tj);
+                    outer4(acc, a, b);
+                }
+                fold(hi, lo, acc);
 #pragma unroll
-                for (int x = 0; x < 4; ++x)
-#pragma unroll
-                    for (int y = 0; y < 4; ++y) acc[q][x * 4 + y] = fmaf(av[x], bv[y], acc[q][x * 4 + y]);
-            }
-            // fold the chunk into (hi, lo): hi + lo += acc exactly up to lo's rounding
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const dw s = dw_two_sum(hi[q][e], acc[q][e]);
-                hi[q][e] = s.hi;
-                lo[q][e] = __fadd_rn(lo[q][e], s.lo);
+                for (int e = 0; e < 16; ++e) acc[e] = 0.0f;
             }
         }
     }
-    double* out = partial + (int64_t)blockIdx.x * 3 * m * m;
-#pragma unroll
-    for (int q = 0; q < kMxTilesPerThread; ++q) {
-        if (q >= my) break;
-        const int i0 = ti[q] * 4, j0 = tj[q] * 4;
-        double* G = out + (int64_t)tg[q] * m * m;
-        for (int x = 0; x < 4; ++x)
-            for (int y = 0; y < 4; ++y) {
-                const int i = i0 + x, j = j0 + y;
-                if (i < m && j < m) {
-                    const double v = (double)hi[q][x * 4 + y] + (double)lo[q][x * 4 + y];
-                    G[i * m + j] = v;
-                    if (tg[q] == 0) G[j * m + i] = v;
-                }
-            }
-    }
+    if (!act) return;
+    double* out = partial + (int64_t)blockIdx.x * 3 * m * m + (int64_t)g * m * m;
+    put_tile(out, m, 4 * ti, 4 * tj, hi, lo, g == 0);
 }
 
 // out[j] = sum_b partial[b * width + j], fixed order, many CTAs
@@ -185,26 +189,27 @@ __global__ void k_sum_wide(int nblocks, int width, const double* __restrict__ pa
 constexpr int kUpRows = 32;
 
 // Family F = [F_0 .. F_{nb-1}] (m columns): Pout = F C_P, Vout = F_0 C_VV + F C_P.
-// With an FP64 F_0 and an FP64 Vout, the F_0 part of Vout is summed in FP64
-// (V keeps its FP64 accuracy; A amplifies FP32 rounding noise in V by ||A||);
-// all other sums are FP32.  Every output row depends only on the same input
-// row and a chunk is staged before any of its rows is written (in place
+// With an FP64 F_0 and an FP64 Vout, the F_0 part of Vout is summed in
+// double-word arithmetic (V keeps ~48-bit accuracy: A amplifies rounding noise
+// in V by ||A|| / lambda, and FP64 FMAs would make the kernel FP64-pipe
+// bound); all other sums are FP32.  Every output row depends only on the same
+// input row and a chunk is staged before any of its rows is written (in place
 // allowed: Vout may be F_0, Pout may be F_{nb-1}).
 __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int nb, FamMx F,
                                                    const double* __restrict__ Cp, const double* __restrict__ Cvv,
                                                    void* __restrict__ Vout, int vo64, int64_t ldvo,
                                                    void* __restrict__ Pout, int po64, int64_t ldpo) {
     extern __shared__ __align__(16) unsigned char raw[];
-    double* cs64 = reinterpret_cast<double*>(raw);          // [kp][kp]  C_VV + C_P (V rows)
-    double* zd = cs64 + kp * kp;                             // [rows][kp] FP64 V rows
-    float* cpf = reinterpret_cast<float*>(zd + kUpRows * kp);   // [m][kp]
+    dw* csw = reinterpret_cast<dw*>(raw);                    // [kp][kp]  C_VV + C_P (V rows), double-word
+    dw* zw = csw + kp * kp;                                  // [rows][kp] V rows, double-word
+    float* cpf = reinterpret_cast<float*>(zw + kUpRows * kp);   // [m][kp]
     float* csf = cpf + m * kp;                               // [kp][kp]
     float* zf = csf + kp * kp;                               // [rows][m]
     const bool v64 = F.f64[0] && vo64;
     for (int t = threadIdx.x; t < m * kp; t += blockDim.x) cpf[t] = (float)Cp[t];
     for (int t = threadIdx.x; t < kp * kp; t += blockDim.x) {
         const double v = Cvv[t] + Cp[t];     // V rows of C_P are the first kp rows
-        cs64[t] = v;
+        csw[t] = dw_from_double(v);
         csf[t] = (float)v;
     }
     const int64_t nchunks = (n + kUpRows - 1) / kUpRows;
@@ -212,13 +217,20 @@ __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int
         const int64_t row0 = ch * kUpRows;
         const int nrows = (int)((n - row0) < kUpRows ? (n - row0) : kUpRows);
         __syncthreads();
-        for (int b = 0; b < nb; ++b) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            if (b >= nb) break;
             const int nc = F.nc[b];
             for (int t = threadIdx.x; t < nrows * nc; t += blockDim.x) {
                 const int r = t / nc, c = t - r * nc;
                 const int64_t row = row0 + r;
-                if (b == 0 && v64) zd[r * kp + c] = ldv(F, 0, row, c);
-                zf[r * m + F.off[b] + c] = ldf(F, b, row, c);
+                if (b == 0 && v64) {
+                    const dw v = dw_from_double(ldv(F, 0, row, c));
+                    zw[r * kp + c] = v;
+                    zf[r * m + c] = v.hi;
+                } else {
+                    zf[r * m + F.off[b] + c] = ldf(F, b, row, c);
+                }
             }
         }
         __syncthreads();
@@ -233,10 +245,10 @@ __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int
             if (po64) static_cast<double*>(Pout)[row * ldpo + j] = (double)p;
             else static_cast<float*>(Pout)[row * ldpo + j] = p;
             if (v64) {
-                const double* zr = zd + r * kp;
-                double v = 0.0;
-                for (int i = 0; i < kp; ++i) v = fma(zr[i], cs64[i * kp + j], v);
-                static_cast<double*>(Vout)[row * ldvo + j] = v + (double)prest;
+                const dw* zr = zw + r * kp;
+                dw v = dw_make(prest);
+                for (int i = 0; i < kp; ++i) v = dw_add(v, dw_mul(zr[i], csw[i * kp + j]));
+                static_cast<double*>(Vout)[row * ldvo + j] = dw_to_double(v);
             } else {
                 float v = 0.0f;
                 for (int i = 0; i < kp; ++i) v = fmaf(z[i], csf[i * kp + j], v);
@@ -245,6 +257,21 @@ __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int
                 else static_cast<float*>(Vout)[row * ldvo + j] = v;
             }
         }
+    }
+}
+
+// V32 = V, U32 = A V - sigma V (formed in FP64, then rounded), X3 = A V - sigma V
+// in FP64 (optional); n x kp blocks with leading dimension kp
+__global__ void k_prepare_v(int64_t n, int kp, const double* __restrict__ V, const double* __restrict__ AV,
+                            double sigma, float* __restrict__ V32, float* __restrict__ U32,
+                            double* __restrict__ X3) {
+    const int64_t total = n * kp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const double v = V[e];
+        const double u = fma(-sigma, v, AV[e]);
+        V32[e] = (float)v;
+        U32[e] = (float)u;
+        if (X3) X3[e] = u;
     }
 }
 
@@ -306,7 +333,7 @@ __global__ void k_narrow(int64_t n, int nc, const double* __restrict__ X, int64_
 
 }  // namespace
 
-int gram_mx_blocks() { return sm_count() * 2; }
+int gram_mx_blocks() { return sm_count(); }
 
 cudaError_t multi_gram_mx(int64_t n, int nb, const BlkMx* Z, const BlkMx* AZ, const BlkMx* Q, double sigma,
                           const double* colscale, double* partial, double* out, cudaStream_t s) {
@@ -314,11 +341,10 @@ cudaError_t multi_gram_mx(int64_t n, int nb, const BlkMx* Z, const BlkMx* AZ, co
     int m = 0;
     for (int i = 0; i < nb; ++i) m += Z[i].nc;
     const int mp = (m + 3) / 4 * 4;
-    const int T = mp / 4;
-    if (T * (T + 1) / 2 + 2 * T * T > kMxThreads * kMxTilesPerThread) return cudaErrorInvalidValue;
+    if (mp > 64) return cudaErrorInvalidValue;
     const int blocks = gram_mx_blocks();
     const size_t shm = sizeof(float) * 3 * kMxRows * mp;
-    k_gram_mx<<<blocks, kMxThreads, shm, s>>>(n, m, mp, nb, FZ, FA, FQ, Q ? 1 : 0, sigma, colscale, partial);
+    k_gram_mx<<<blocks, kGramMxThreads, shm, s>>>(n, m, mp, nb, FZ, FA, FQ, Q ? 1 : 0, sigma, colscale, partial);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -333,8 +359,15 @@ cudaError_t block_update_mx(int64_t n, int nb, const BlkMx* F, int kp, const dou
     FamMx FF = fam_mx(F, nb);
     int m = 0;
     for (int i = 0; i < nb; ++i) m += F[i].nc;
-    const size_t shm = sizeof(double) * (kp * kp + kUpRows * kp) + sizeof(float) * (m * kp + kp * kp + kUpRows * m);
-    k_update_mx<<<gram_mx_blocks(), 256, shm, s>>>(n, m, kp, nb, FF, Cp, Cvv, Vout, vo64, ldvo, Pout, po64, ldpo);
+    const size_t shm = sizeof(dw) * (kp * kp + kUpRows * kp) + sizeof(float) * (m * kp + kp * kp + kUpRows * m);
+    k_update_mx<<<sm_count() * 4, 256, shm, s>>>(n, m, kp, nb, FF, Cp, Cvv, Vout, vo64, ldvo, Pout, po64, ldpo);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_v_mx(int64_t n, int kp, const double* V, const double* AV, double sigma, float* V32, float* U32,
+                         double* X3, cudaStream_t s) {
+    k_prepare_v<<<grid_size_for(n * kp, 256, sm_count() * 8), 256, 0, s>>>(n, kp, V, AV, sigma, V32, U32, X3);
     count_launches(1);
     return cudaGetLastError();
 }

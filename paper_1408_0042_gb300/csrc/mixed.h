@@ -12,6 +12,7 @@ struct BlkMx {
     int64_t ld = 0;
     int nc = 0;
     int f64 = 0;
+    int is_u = 0;    // in the AZ family: the block already holds AZ - sigma Z
 };
 
 int gram_mx_blocks();
@@ -25,6 +26,11 @@ cudaError_t multi_gram_mx(int64_t n, int nb, const BlkMx* Z, const BlkMx* AZ, co
 // Pout = F C_P, Vout = F_0 C_VV + F C_P (types by the flags; in place allowed).
 cudaError_t block_update_mx(int64_t n, int nb, const BlkMx* F, int kp, const double* Cp, const double* Cvv,
                             void* Vout, int vo64, int64_t ldvo, void* Pout, int po64, int64_t ldpo, cudaStream_t s);
+
+// V32 = V, U32 = A V - sigma V (FP64, then rounded), X3 = A V - sigma V (FP64,
+// optional); dense n x kp blocks
+cudaError_t prepare_v_mx(int64_t n, int kp, const double* V, const double* AV, double sigma, float* V32, float* U32,
+                         double* X3, cudaStream_t s);
 
 // FP32 stencil: ax = L x; o1 = ax - lam_c x; o2 = ax - sig x (each optional)
 cudaError_t lap32_apply_shifts(const Grid& g, int nc, const float* x, int64_t ldx, float* ax, int64_t ldax, float* o1,

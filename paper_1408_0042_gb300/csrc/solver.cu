@@ -164,21 +164,24 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     // Q_S, P, A P, Q_P, Q_V
     bool mx = opt.precision == PLHR_PRECISION_MIXED;
     int mixed_its = 0;
+    double best_worst = INFINITY;   // FP32 form: smallest worst residual so far and when
+    int best_it = 0;
     struct FloatBuf {
         float* p = nullptr;
         ~FloatBuf() { if (p) cudaFree(p); }
     } big32;
     float *W32 = nullptr, *AW32 = nullptr, *SQ32 = nullptr, *X2_32 = nullptr, *AS32 = nullptr, *X3_32 = nullptr,
-          *QS32 = nullptr, *P32 = nullptr, *AP32 = nullptr, *QP32 = nullptr, *QV32 = nullptr;
+          *QS32 = nullptr, *P32 = nullptr, *AP32 = nullptr, *QP32 = nullptr, *QV32 = nullptr, *V32 = nullptr,
+          *U32 = nullptr;
     if (mx) {
-        if (cudaMallocAsync(&big32.p, sizeof(float) * 13 * nk, s) != cudaSuccess) {
-            set_error("plhr_solve: device allocation of %.1f MB failed", 4e-6 * 13.0 * (double)nk);
+        if (cudaMallocAsync(&big32.p, sizeof(float) * 15 * nk, s) != cudaSuccess) {
+            set_error("plhr_solve: device allocation of %.1f MB failed", 4e-6 * 15.0 * (double)nk);
             return PLHR_ENOMEM;
         }
         float* f = big32.p;
         W32 = f; f += nk; AW32 = f; f += nk; SQ32 = f; f += 2 * nk; X2_32 = f; f += 2 * nk; AS32 = f; f += nk;
         X3_32 = f; f += nk; QS32 = f; f += nk; P32 = f; f += nk; AP32 = f; f += nk; QP32 = f; f += nk;
-        QV32 = f; f += nk;
+        QV32 = f; f += nk; V32 = f; f += nk; U32 = f; f += nk;
         if (T) PLHR_TRY(prec_reserve32(T, 2 * kp, 0));
     }
     double* gpart = part.p;
@@ -271,7 +274,20 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
 
     // end of the FP32 form: P to FP64, then A V, A P, T(A V - sigma V) and
     // T(A P - sigma P) explicitly in FP64
-    auto switch_to_f64 = [&]() -> plhr_status {
+    // ord: host column order by distance to sigma (the first k are kept)
+    auto switch_to_f64 = [&](const int* ord) -> plhr_status {
+        // guard columns (beyond the k nearest sigma) restart from fresh seeded
+        // random vectors: the FP32 form can lose a weak direction (a member of a
+        // degenerate cluster whose component sat below its rounding level), and
+        // random columns contain every eigendirection for the FP64 phase to find
+        if (kp > k) {
+            PLHR_TRY_CUDA(seeded_block(n, kp, opt.seed ^ 0x5bd1e995ull, Rc, kp, s));
+            for (int q2 = k; q2 < kp; ++q2) {
+                const int j = ord[q2];
+                PLHR_TRY_CUDA(cudaMemcpy2DAsync(V + j, sizeof(double) * kp, Rc + j, sizeof(double) * kp,
+                                                sizeof(double), n, cudaMemcpyDeviceToDevice, s));
+            }
+        }
         if (np) PLHR_TRY_CUDA(widen_block(n, kp, P32, kp, P, kp, s));
         PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
         if (T) PLHR_TRY(applyT(kp, X3, kp, QV));
@@ -280,6 +296,16 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             if (T) PLHR_TRY(applyT(kp, X3, kp, QP));
         }
         mx = false;
+        if (kp > k) {
+            // Rayleigh quotients and scales of the new columns (every column
+            // real: the pairing of the last extraction no longer applies)
+            std::vector<int> zeros(64, 0), neg(64, -1);
+            PLHR_TRY_CUDA(cudaMemcpyAsync(tags, zeros.data(), sizeof(int) * 64, cudaMemcpyHostToDevice, s));
+            PLHR_TRY_CUDA(cudaMemcpyAsync(partner, neg.data(), sizeof(int) * 64, cudaMemcpyHostToDevice, s));
+            PLHR_TRY_CUDA(column_dots(n, kp, V, kp, AV, kp, rpart, dots, s));
+            PLHR_TRY_CUDA(dense_rq(kp, dots, tags, partner, lam, scale, s));
+            PLHR_TRY_CUDA(cudaStreamSynchronize(s));   // the host vectors above
+        }
         return PLHR_OK;
     };
 
@@ -357,17 +383,18 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             // carry on from the rotated block (same span): V <- V C, A V explicit
             PLHR_TRY_CUDA(cudaMemcpyAsync(V, Rc, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
             PLHR_TRY_CUDA(cudaMemcpyAsync(AV, AW, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
-            if (mx) {
-                mixed_its = it;
-                PLHR_TRY(switch_to_f64());
-            } else if (T) {
-                PLHR_TRY_CUDA(block_times_small(n, QV, kp, kp, Crr, kp, QV, kp, s));
-            }
+            if (!mx && T) PLHR_TRY_CUDA(block_times_small(n, QV, kp, kp, Crr, kp, QV, kp, s));
             PLHR_TRY_CUDA(cudaMemcpyAsync(lam, theta, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
             {
                 std::vector<double> ones(kp, 1.0);
                 PLHR_TRY_CUDA(cudaMemcpyAsync(scale, ones.data(), sizeof(double) * kp, cudaMemcpyHostToDevice, s));
                 PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+            }
+            if (mx) {
+                mixed_its = it;
+                std::vector<int> ident(kp);
+                for (int q2 = 0; q2 < kp; ++q2) ident[q2] = q2;   // the RR sorted the columns
+                PLHR_TRY(switch_to_f64(ident.data()));
             }
             continue;
         }
@@ -375,9 +402,15 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         if (mx) {
             double worst = 0.0;
             for (int q2 = 0; q2 < k; ++q2) worst = std::fmax(worst, h_rel[h_order[q2]]);
-            if (worst < opt.switch_tol) {
+            if (worst < best_worst) {
+                best_worst = worst;
+                best_it = it;
+            }
+            // leave the FP32 form at switch_tol, or earlier when it stagnates at its
+            // rounding floor (no new minimum for 25 iterations below 1e-5)
+            if (worst < opt.switch_tol || (best_worst < 1e-5 && it - best_it >= 25)) {
                 mixed_its = it;
-                PLHR_TRY(switch_to_f64());
+                PLHR_TRY(switch_to_f64(h_order));
             }
         }
         const int na = hs->nact;
@@ -409,12 +442,13 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
                                                  na, sigma, s));
             }
             if (T) PLHR_TRY(applyT32(na, (const float*)X3_32, na, QS32));
+            // FP32 copies of V and U_V = A V - sigma V (formed in FP64) for the Gram
+            PLHR_TRY_CUDA(prepare_v_mx(n, kp, V, AV, sigma, V32, U32, T ? X3 : nullptr, s));
             if (T) {
                 // Q_V = T(A V - sigma V) and Q_P = T(A P - sigma P) explicitly: carrying
                 // them through the update would mix the FP32 V-cycle's rounding of
                 // different iterations into one image, and the projected pencil
                 // (built from Q = T U) would lose consistency below ~1e-5
-                PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
                 PLHR_TRY(applyT32(kp, (const double*)X3, kp, QV32));
                 if (np) {
                     PLHR_TRY_CUDA(lap32_apply_shifts(g, kp, P32, kp, AP32, kp, nullptr, 0, nullptr, X3_32, kp, sigma,
@@ -425,8 +459,9 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             const int nb = np ? 4 : 3;
             const int m = kp + 2 * na + np;
             last_m = m;
-            BlkMx zb[4] = {{V, kp, kp, 1}, {W32, na, na, 0}, {S32, lds, na, 0}, {P32, kp, np, 0}};
-            BlkMx ab[4] = {{AV, kp, kp, 1}, {AW32, na, na, 0}, {AS32, na, na, 0}, {AP32, kp, np, 0}};
+            BlkMx zb[4] = {{V32, kp, kp, 0}, {W32, na, na, 0}, {S32, lds, na, 0}, {P32, kp, np, 0}};
+            BlkMx ab[4] = {{U32, kp, kp, 0, 1}, {AW32, na, na, 0}, {AS32, na, na, 0}, {AP32, kp, np, 0}};
+            BlkMx ub[4] = {{V, kp, kp, 1}, {W32, na, na, 0}, {S32, lds, na, 0}, {P32, kp, np, 0}};
             BlkMx qb[4] = {{QV32, kp, kp, 0}, {QW32, 2 * na, na, 0}, {QS32, na, na, 0}, {QP32, kp, np, 0}};
             PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
             DenseArgs da;
@@ -434,36 +469,27 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             da.Gzz = grams; da.Guq = grams + m * m; da.Gqz = grams + 2 * m * m;
             da.colscale = colscale; da.work = dwork; da.Cp = Cp; da.Cvv = Cvv; da.tags = tags;
             da.tag_partner = partner; da.xi = xi; da.out_int = dstat + 3; da.clk = nullptr;
-            for (int pass = 0; pass < 2; ++pass) {
-                {
-                    PhaseScope ps(PH_GRAM32, s, gram_flops(n, m));
-                    PLHR_TRY_CUDA(multi_gram_mx(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams, s));
-                }
-                {
-                    PhaseScope ps(PH_DENSE, s);
-                    PLHR_TRY_CUDA(dense_extract(da, s));
-                }
-                PLHR_TRY_CUDA(cudaMemcpyAsync(hs->dense, dstat + 3, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
-                PLHR_TRY_CUDA(cudaStreamSynchronize(s));
-                if (hs->dense[0] == kDenseOK || !T || pass == 1) break;
-                // recovery: recompute the carried images explicitly and project again
-                PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
-                PLHR_TRY(applyT32(kp, (const double*)X3, kp, QV32));
-                if (np) {
-                    PLHR_TRY_CUDA(lap32_apply_shifts(g, kp, P32, kp, AP32, kp, nullptr, 0, nullptr, X3_32, kp, sigma,
-                                                     s));
-                    PLHR_TRY(applyT32(kp, (const float*)X3_32, kp, QP32));
-                }
-            }
-            last_kept = hs->dense[1];
-            if (hs->dense[0] != kDenseOK) {
-                set_error("plhr_solve: projected problem failed at iteration %d (code %d)", it, hs->dense[0]);
-                result = PLHR_EBREAKDOWN;
-                break;
+            {
+                PhaseScope ps(PH_GRAM32, s, gram_flops(n, m));
+                PLHR_TRY_CUDA(multi_gram_mx(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams, s));
             }
             {
+                PhaseScope ps(PH_DENSE, s);
+                PLHR_TRY_CUDA(dense_extract(da, s));
+            }
+            PLHR_TRY_CUDA(cudaMemcpyAsync(hs->dense, dstat + 3, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+            PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+            if (hs->dense[0] != kDenseOK) {
+                // the images are already explicit: leave the FP32 form and redo the
+                // step in FP64 (the next pass of the loop, from the same V)
+                mixed_its = it;
+                PLHR_TRY(switch_to_f64(h_order));
+                continue;
+            }
+            last_kept = hs->dense[1];
+            {
                 PhaseScope ps(PH_UPDATE32, s, 2.0 * n * m * kp);
-                PLHR_TRY_CUDA(block_update_mx(n, nb, zb, kp, Cp, Cvv, V, 1, kp, P32, 0, kp, s));
+                PLHR_TRY_CUDA(block_update_mx(n, nb, ub, kp, Cp, Cvv, V, 1, kp, P32, 0, kp, s));
             }
             np = kp;
             PLHR_TRY(refresh_images());

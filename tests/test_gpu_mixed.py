@@ -35,14 +35,17 @@ def _residuals(w, lam, V):
 # FP32 storage and arithmetic: a V-cycle is a fixed linear map applied with
 # O(levels * nu) FP32 roundings per entry, each about 6e-8 of the entries it
 # combines; 2e-5 of the largest output entry bounds that for these sizes.
-@pytest.mark.parametrize("dims,levels,sigma,transfer,coarse", [
-    ((16, 16, 16), 1, 300.0, 0, 0), ((16, 16, 16), 3, 900.0, 1, 1), ((16, 16, 16), 3, 2500.0, 1, 1),
-    ((32, 24, 16), 3, 700.0, 0, 0), ((32, 24), 3, 700.0, 1, 1)])
-def test_avmg_f32_matches_oracle(plhr, dims, levels, sigma, transfer, coarse):
+# nc = 5: one column per thread; nc = 8, 12: four columns per thread (16-byte
+# accesses)
+@pytest.mark.parametrize("dims,levels,sigma,transfer,coarse,nc", [
+    ((16, 16, 16), 1, 300.0, 0, 0, 5), ((16, 16, 16), 3, 900.0, 1, 1, 5), ((16, 16, 16), 3, 2500.0, 1, 1, 8),
+    ((32, 24, 16), 3, 700.0, 0, 0, 12), ((32, 24, 16), 3, 700.0, 1, 1, 8), ((32, 24), 3, 700.0, 1, 1, 5),
+    ((32, 24), 3, 700.0, 0, 0, 4)])
+def test_avmg_f32_matches_oracle(plhr, dims, levels, sigma, transfer, coarse, nc):
     h = 1.0 / (max(dims) + 1)
     A = plhr.Operator.laplacian(dims, h)
     T = plhr.AVMG(A, sigma, levels=levels, nu=2, transfer=transfer, coarse=coarse)
-    R = wl.uniform_block(A.n, 5, 17)
+    R = wl.uniform_block(A.n, nc, 17)
     W = T.apply_f32(torch.from_numpy(R).float().cuda()).double().cpu().numpy()
     ref = oavmg.AVMG(dims, h, sigma, levels, nu=2, transfer=["constant", "linear"][transfer],
                      coarse=["rediscretised", "fine_spectrum"][coarse])(R.astype(np.float32).astype(np.float64))
