@@ -115,6 +115,12 @@ plhr_status plhr_prec_apply(plhr_prec* T, int ncols, const double* R, int64_t ld
  * solve uses): W = T R for FP32 blocks.  Workspace as for plhr_prec_apply. */
 plhr_status plhr_prec_apply_f32(plhr_prec* T, int ncols, const float* R, int64_t ldr,
                                 float* W, int64_t ldw, void* stream);
+/* The same V-cycle with double-word storage and arithmetic (hi + lo FP32
+ * pairs, ~48-bit significands, run on the FP32 pipes) on FP64 blocks: the
+ * form the FP64 phase of the mixed-precision solve uses.  Same arguments,
+ * workspace and overlap rules as plhr_prec_apply. */
+plhr_status plhr_prec_apply_dw(plhr_prec* T, int ncols, const double* R, int64_t ldr,
+                               double* W, int64_t ldw, void* stream);
 
 /* -------------------------------------------------------------------- solver */
 typedef enum {

@@ -66,6 +66,8 @@ _SIGS = {
     "plhr_prec_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "plhr_profile_work": (None, [ctypes.c_void_p]),
+    "plhr_prec_apply_dw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "plhr_prec_apply_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "plhr_options_default": (None, [ctypes.POINTER(Options)]),
@@ -203,6 +205,18 @@ class AVMG:
         _check(load_library().plhr_prec_apply(self._h, R.shape[1], ctypes.c_void_p(R.data_ptr()), R.stride(0),
                                               ctypes.c_void_p(out.data_ptr()), out.stride(0), _stream_ptr(stream)),
                "plhr_prec_apply")
+        return out
+
+    def apply_dw(self, R, out=None, stream=None):
+        """The same V-cycle in double-word arithmetic on float64 CUDA blocks."""
+        import torch
+        _check_block(R, self.n, "R")
+        if out is None:
+            out = torch.empty_like(R)
+        _check_block(out, self.n, "out")
+        _check(load_library().plhr_prec_apply_dw(self._h, R.shape[1], ctypes.c_void_p(R.data_ptr()), R.stride(0),
+                                                 ctypes.c_void_p(out.data_ptr()), out.stride(0), _stream_ptr(stream)),
+               "plhr_prec_apply_dw")
         return out
 
     def apply_f32(self, R, out=None, stream=None):

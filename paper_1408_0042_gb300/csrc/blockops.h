@@ -43,6 +43,15 @@ cudaError_t gather_columns(int64_t n, const double* X, int64_t ldx, const int* i
 cudaError_t column_dots(int64_t n, int kc, const double* X, int64_t ldx, const double* Y, int64_t ldy,
                         double* partial, double* out, cudaStream_t s);
 
+// Double-word forms of multi_gram and block_update (same arguments and
+// results; inputs rounded once to hi + lo FP32 pairs, products and sums in
+// double-word arithmetic on the FP32 pipes; partial: sm_count() * 3 m^2).
+cudaError_t multi_gram_dw(int64_t n, int nb, const Blk<const double>* Z, const Blk<const double>* AZ,
+                          const Blk<const double>* Q, double sigma, const double* colscale, double* partial,
+                          double* out, cudaStream_t s);
+cudaError_t block_update_dw(int64_t n, int nb, const Blk<const double>* F, int kp, const double* Cp, const double* Cvv,
+                            double* Vout, int64_t ldvo, double* Pout, int64_t ldpo, cudaStream_t s);
+
 // Seeded starting block: element (i, j) = (SplitMix64 output i*kc + j + 1 >> 11) * 2^-53 - 0.5.
 cudaError_t seeded_block(int64_t n, int kc, uint64_t seed, double* X, int64_t ldx, cudaStream_t s);
 

@@ -182,6 +182,23 @@ plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma, cons
             plhr_prec_destroy(T);
             return PLHR_ECUDA;
         }
+        std::vector<float> Sw(2 * N * N), muw(2 * N);
+        for (int64_t q = 0; q < N * N; ++q) {
+            Sw[2 * q] = (float)S[q];
+            Sw[2 * q + 1] = (float)(S[q] - (double)Sw[2 * q]);
+        }
+        for (int64_t q = 0; q < N; ++q) {
+            muw[2 * q] = (float)mu[q];
+            muw[2 * q + 1] = (float)(mu[q] - (double)muw[2 * q]);
+        }
+        if (cudaMalloc(&H.w_basis[ax], sizeof(float) * 2 * N * N) != cudaSuccess ||
+            cudaMalloc(&H.w_mu[ax], sizeof(float) * 2 * N) != cudaSuccess ||
+            cudaMemcpy(H.w_basis[ax], Sw.data(), sizeof(float) * 2 * N * N, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(H.w_mu[ax], muw.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_error("plhr_prec_avmg: double-word basis upload failed");
+            plhr_prec_destroy(T);
+            return PLHR_ENOMEM;
+        }
         std::vector<float> Sf(S.begin(), S.end()), muf(mu.begin(), mu.end());
         if (cudaMalloc(&H.f_basis[ax], sizeof(float) * N * N) != cudaSuccess ||
             cudaMalloc(&H.f_mu[ax], sizeof(float) * N) != cudaSuccess ||
@@ -210,6 +227,8 @@ void plhr_prec_destroy(plhr_prec* T) {
         if (T->H.d_mu[a]) cudaFree(T->H.d_mu[a]);
         if (T->H.f_basis[a]) cudaFree(T->H.f_basis[a]);
         if (T->H.f_mu[a]) cudaFree(T->H.f_mu[a]);
+        if (T->H.w_basis[a]) cudaFree(T->H.w_basis[a]);
+        if (T->H.w_mu[a]) cudaFree(T->H.w_mu[a]);
     }
     if (T->work) cudaFree(T->work);
     if (T->work32) cudaFree(T->work32);
@@ -253,7 +272,28 @@ plhr_status prec_reserve32(plhr_prec* T, int nc, int64_t extra_floats) {
     T->work_floats = need;
     return PLHR_OK;
 }
+plhr_status prec_reserve_dw(plhr_prec* T, int nc) {
+    // the double-word V-cycle uses T->work (8-byte entries); it never runs at
+    // the same time as the FP64 one
+    const int64_t need = mg_workspace_dw(T->H, nc);
+    const int64_t have_nc = T->work_doubles;
+    if (need <= have_nc) return PLHR_OK;
+    return prec_reserve(T, nc, need - mg_workspace_doubles(T->H, nc));
+}
 }  // namespace plhr
+
+extern "C" plhr_status plhr_prec_apply_dw(plhr_prec* T, int ncols, const double* R, int64_t ldr, double* W,
+                                          int64_t ldw, void* stream) {
+    clear_error();
+    if (!T || ncols < 0 || (ncols > 0 && (!R || !W)) || ldr < ncols || ldw < ncols) {
+        set_error("plhr_prec_apply_dw: invalid argument");
+        return PLHR_EINVAL;
+    }
+    if (ncols == 0) return PLHR_OK;
+    PLHR_TRY(plhr::prec_reserve_dw(T, ncols));
+    PLHR_TRY_CUDA(plhr::mg_vcycle_dw(T->H, ncols, R, ldr, W, ldw, T->work, (cudaStream_t)stream));
+    return PLHR_OK;
+}
 
 extern "C" plhr_status plhr_prec_apply_f32(plhr_prec* T, int ncols, const float* R, int64_t ldr, float* W,
                                            int64_t ldw, void* stream) {

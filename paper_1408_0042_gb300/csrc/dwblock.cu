@@ -1,0 +1,225 @@
+// Double-word forms of the multi-Gram and the coefficient update on FP64
+// blocks, for the FP64 phase of the mixed-precision solve.  The inputs are
+// rounded once to double-word values (hi + lo FP32 pairs, ~48-bit
+// significands); products are formed with the FMA exact product of the high
+// parts plus the FP32 cross terms, and sums are accumulated with TwoSum on the
+// high part, so every result carries ~2^-46 relative error of the sum of
+// |terms| - FP64-class accuracy for the projected problem at a fraction of the
+// FP64 pipe's cost on GB300.  Results and partial sums are FP64; the per-CTA
+// partials are summed in FP64 in a fixed order (deterministic).
+#include "blockops.h"
+#include "dword.h"
+
+namespace plhr {
+namespace {
+
+constexpr int kDwRows = 32;
+constexpr int kDwThreads = 768;
+
+struct FamD {
+    const double* p[4];
+    int64_t ld[4];
+    int nc[4];
+    int off[4];
+};
+
+FamD fam_d(const Blk<const double>* b, int nb) {
+    FamD F{};
+    int off = 0;
+    for (int i = 0; i < 4; ++i) {
+        if (i < nb) {
+            F.p[i] = b[i].p; F.ld[i] = b[i].ld; F.nc[i] = b[i].nc; F.off[i] = off;
+            off += b[i].nc;
+        } else {
+            F.p[i] = nullptr; F.ld[i] = 0; F.nc[i] = 0; F.off[i] = off;
+        }
+    }
+    return F;
+}
+
+// acc += a * b (a, b double-word): exact product of the high parts, FP32
+// cross terms, TwoSum on the high part of the accumulator
+__device__ __forceinline__ void dw_fma_acc(float& hi, float& lo, const dw& a, const dw& b) {
+    const float ph = __fmul_rn(a.hi, b.hi);
+    const float pl = __fmaf_rn(a.hi, b.hi, -ph);
+    const float cr = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
+    const dw s = dw_two_sum(hi, ph);
+    hi = s.hi;
+    lo = __fadd_rn(lo, __fadd_rn(s.lo, __fadd_rn(pl, cr)));
+}
+
+// Stage rows row0 .. of z = Z s, u = (AZ - sigma Z) s, q = Q s (q = u when
+// q_from_u) as double-word [row][mp] tiles; U is formed in FP64 before rounding
+__device__ void stage_dw(dw* sz, dw* su, dw* sq, int mp, int64_t n, int64_t row0, const FamD& Z, const FamD& AZ,
+                         const FamD& Q, int nb, int q_from_u, double sigma, const double* __restrict__ csc) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        if (b >= nb) break;
+        const int nc = Z.nc[b];
+        if (nc == 0) continue;
+        const int tot = kDwRows * nc;
+        for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+            const int r = t / nc, c = t - r * nc;
+            const int64_t row = row0 + r;
+            const int col = Z.off[b] + c;
+            dw z = dw_make(0.0f), u = z, q = z;
+            if (row < n) {
+                const double s = csc[col];
+                const double zd = Z.p[b][row * Z.ld[b] + c] * s;
+                const double ud = AZ.p[b][row * AZ.ld[b] + c] * s - sigma * zd;
+                z = dw_from_double(zd);
+                u = dw_from_double(ud);
+                q = q_from_u ? u : dw_from_double(Q.p[b][row * Q.ld[b] + c] * s);
+            }
+            sz[r * mp + col] = z;
+            su[r * mp + col] = u;
+            sq[r * mp + col] = q;
+        }
+    }
+}
+
+// 768 threads: thread t owns output g = t / 256 (0: Z^T Z, written for ti <= tj
+// and mirrored; 1: U^T Q; 2: Q^T Z) and its 4x4 tile (ti, tj).  mp <= 64.
+__global__ void __launch_bounds__(kDwThreads, 1) k_gram_dw(int64_t n, int m, int mp, int nb, FamD Z, FamD AZ, FamD Q,
+                                                           int q_from_u, double sigma,
+                                                           const double* __restrict__ csc,
+                                                           double* __restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    dw* sz = reinterpret_cast<dw*>(raw);
+    dw* su = sz + kDwRows * mp;
+    dw* sq = su + kDwRows * mp;
+    const int T = mp / 4;
+    const int g = threadIdx.x >> 8, ti = (threadIdx.x >> 4) & 15, tj = threadIdx.x & 15;
+    const bool act = ti < T && tj < T && (g != 0 || ti <= tj);
+    const dw* A = g == 0 ? sz : (g == 1 ? su : sq);
+    const dw* B = g == 1 ? sq : sz;
+    float hi[16], lo[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) { hi[e] = 0.0f; lo[e] = 0.0f; }
+    for (int t = threadIdx.x; t < kDwRows * mp; t += blockDim.x) {
+        if (t % mp >= m) { sz[t] = dw_make(0.0f); su[t] = dw_make(0.0f); sq[t] = dw_make(0.0f); }
+    }
+    const int64_t nchunks = (n + kDwRows - 1) / kDwRows;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        __syncthreads();
+        stage_dw(sz, su, sq, mp, n, ch * kDwRows, Z, AZ, Q, nb, q_from_u, sigma, csc);
+        __syncthreads();
+        if (!act) continue;
+#pragma unroll 2
+        for (int r = 0; r < kDwRows; ++r) {
+            const float4* ap = reinterpret_cast<const float4*>(A + r * mp + 4 * ti);
+            const float4* bp = reinterpret_cast<const float4*>(B + r * mp + 4 * tj);
+            const float4 a01 = ap[0], a23 = ap[1], b01 = bp[0], b23 = bp[1];
+            const dw av[4] = {{a01.x, a01.y}, {a01.z, a01.w}, {a23.x, a23.y}, {a23.z, a23.w}};
+            const dw bv[4] = {{b01.x, b01.y}, {b01.z, b01.w}, {b23.x, b23.y}, {b23.z, b23.w}};
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) dw_fma_acc(hi[x * 4 + y], lo[x * 4 + y], av[x], bv[y]);
+        }
+    }
+    if (!act) return;
+    double* out = partial + (int64_t)blockIdx.x * 3 * m * m + (int64_t)g * m * m;
+    for (int x = 0; x < 4; ++x)
+        for (int y = 0; y < 4; ++y) {
+            const int i = 4 * ti + x, j = 4 * tj + y;
+            if (i < m && j < m) {
+                const double v = (double)hi[x * 4 + y] + (double)lo[x * 4 + y];
+                out[i * m + j] = v;
+                if (g == 0) out[j * m + i] = v;
+            }
+        }
+}
+
+__global__ void k_sum_wide_dw(int nblocks, int width, const double* __restrict__ partial, double* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= width) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partial[(int64_t)b * width + j];
+    out[j] = t;
+}
+
+// Pout = F C_P, Vout = F_0 C_VV + F C_P in double-word arithmetic on FP64
+// blocks (in place allowed: every output row depends only on the same input
+// row and a chunk is staged before any of its rows is written)
+constexpr int kDwUpRows = 16;
+__global__ void __launch_bounds__(256) k_update_dw(int64_t n, int m, int kp, int nb, FamD F,
+                                                   const double* __restrict__ Cp, const double* __restrict__ Cvv,
+                                                   double* __restrict__ Vout, int64_t ldvo, double* __restrict__ Pout,
+                                                   int64_t ldpo) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    dw* cp = reinterpret_cast<dw*>(raw);      // [m][kp]
+    dw* cv = cp + m * kp;                     // [kp][kp]
+    dw* zr = cv + kp * kp;                    // [rows][m]
+    for (int t = threadIdx.x; t < m * kp; t += blockDim.x) cp[t] = dw_from_double(Cp[t]);
+    for (int t = threadIdx.x; t < kp * kp; t += blockDim.x) cv[t] = dw_from_double(Cvv[t]);
+    const int64_t nchunks = (n + kDwUpRows - 1) / kDwUpRows;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t row0 = ch * kDwUpRows;
+        const int nrows = (int)((n - row0) < kDwUpRows ? (n - row0) : kDwUpRows);
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            if (b >= nb) break;
+            const int nc = F.nc[b];
+            for (int t = threadIdx.x; t < nrows * nc; t += blockDim.x) {
+                const int r = t / nc, c = t - r * nc;
+                zr[r * m + F.off[b] + c] = dw_from_double(F.p[b][(row0 + r) * F.ld[b] + c]);
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nrows * kp; t += blockDim.x) {
+            const int r = t / kp, j = t - r * kp;
+            const dw* z = zr + r * m;
+            float ph = 0.0f, pl = 0.0f;
+            for (int i = 0; i < m; ++i) dw_fma_acc(ph, pl, z[i], cp[i * kp + j]);
+            float vh = ph, vl = pl;
+            for (int i = 0; i < kp; ++i) dw_fma_acc(vh, vl, z[i], cv[i * kp + j]);
+            const int64_t row = row0 + r;
+            Pout[row * ldpo + j] = (double)ph + (double)pl;
+            Vout[row * ldvo + j] = (double)vh + (double)vl;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t multi_gram_dw(int64_t n, int nb, const Blk<const double>* Z, const Blk<const double>* AZ,
+                          const Blk<const double>* Q, double sigma, const double* colscale, double* partial,
+                          double* out, cudaStream_t s) {
+    FamD FZ = fam_d(Z, nb), FA = fam_d(AZ, nb), FQ = fam_d(Q ? Q : AZ, nb);
+    int m = 0;
+    for (int i = 0; i < nb; ++i) m += Z[i].nc;
+    const int mp = (m + 3) / 4 * 4;
+    if (mp > 64) return cudaErrorInvalidValue;
+    const int blocks = sm_count();
+    const size_t shm = sizeof(dw) * 3 * kDwRows * mp;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gram_dw, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(dw) * 3 * kDwRows * 64));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_gram_dw<<<blocks, kDwThreads, shm, s>>>(n, m, mp, nb, FZ, FA, FQ, Q ? 0 : 1, sigma, colscale, partial);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int width = 3 * m * m;
+    k_sum_wide_dw<<<(width + 127) / 128, 128, 0, s>>>(blocks, width, partial, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t block_update_dw(int64_t n, int nb, const Blk<const double>* F, int kp, const double* Cp, const double* Cvv,
+                            double* Vout, int64_t ldvo, double* Pout, int64_t ldpo, cudaStream_t s) {
+    FamD FF = fam_d(F, nb);
+    int m = 0;
+    for (int i = 0; i < nb; ++i) m += F[i].nc;
+    const size_t shm = sizeof(dw) * (m * kp + kp * kp + kDwUpRows * m);
+    k_update_dw<<<sm_count() * 4, 256, shm, s>>>(n, m, kp, nb, FF, Cp, Cvv, Vout, ldvo, Pout, ldpo);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace plhr

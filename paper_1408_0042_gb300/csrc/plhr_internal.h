@@ -107,6 +107,8 @@ struct MGHierarchy {
     double* d_mu[3] = {nullptr, nullptr, nullptr};
     float* f_basis[3] = {nullptr, nullptr, nullptr};   // FP32 copies for the FP32 V-cycle
     float* f_mu[3] = {nullptr, nullptr, nullptr};
+    float* w_basis[3] = {nullptr, nullptr, nullptr};   // double-word (hi, lo) copies for the
+    float* w_mu[3] = {nullptr, nullptr, nullptr};      // double-word V-cycle
     int64_t n0[3] = {1, 1, 1};
 };
 
@@ -121,6 +123,13 @@ cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const double* r, int64_t
 cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const float* r, int64_t ldr, float* w, float* work,
                           cudaStream_t s);
 int64_t mg_workspace_floats(const MGHierarchy& H, int nc);
+
+// Double-word V-cycle (same cycle; hi + lo FP32 pairs, ~48-bit arithmetic on
+// the FP32 pipes): w (FP64, ldw) = T r (FP64, ldr); work: mg_workspace_dw(H, nc)
+// 8-byte entries.
+cudaError_t mg_vcycle_dw(const MGHierarchy& H, int nc, const double* r, int64_t ldr, double* w, int64_t ldw,
+                         void* work, cudaStream_t s);
+int64_t mg_workspace_dw(const MGHierarchy& H, int nc);
 
 }  // namespace plhr
 

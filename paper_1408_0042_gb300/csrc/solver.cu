@@ -35,6 +35,7 @@
 namespace plhr {
 plhr_status prec_reserve(plhr_prec* T, int nc, int64_t extra_doubles);
 plhr_status prec_reserve32(plhr_prec* T, int nc, int64_t extra_floats);
+plhr_status prec_reserve_dw(plhr_prec* T, int nc);
 }
 
 using namespace plhr;
@@ -163,6 +164,9 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     // FP32 blocks of the mixed form: W, A W, [S | Q_W], its input, A S, A S - sigma S,
     // Q_S, P, A P, Q_P, Q_V
     bool mx = opt.precision == PLHR_PRECISION_MIXED;
+    // FP64 phase of the mixed form: V-cycle, Gram and update in double-word
+    // arithmetic on the FP64 blocks (FP64-class accuracy on the FP32 pipes)
+    const bool dwf = opt.precision == PLHR_PRECISION_MIXED;
     int mixed_its = 0;
     double best_worst = INFINITY;   // FP32 form: smallest worst residual so far and when
     int best_it = 0;
@@ -183,6 +187,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         X3_32 = f; f += nk; QS32 = f; f += nk; P32 = f; f += nk; AP32 = f; f += nk; QP32 = f; f += nk;
         QV32 = f; f += nk; V32 = f; f += nk; U32 = f; f += nk;
         if (T) PLHR_TRY(prec_reserve32(T, 2 * kp, 0));
+        if (T) PLHR_TRY(prec_reserve_dw(T, 2 * kp));
     }
     double* gpart = part.p;
     double* rpart = part.p + (int64_t)reduce_blocks() * m3;
@@ -224,7 +229,10 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             return PLHR_OK;
         }
         PhaseScope ps(PH_VCYCLE, s, (double)n * nc);
-        PLHR_TRY_CUDA(mg_vcycle(T->H, nc, r, ldr, w, nc, T->work, s));
+        if (dwf)   // FP64 phase of the mixed form: double-word V-cycle
+            PLHR_TRY_CUDA(mg_vcycle_dw(T->H, nc, r, ldr, w, nc, T->work, s));
+        else
+            PLHR_TRY_CUDA(mg_vcycle(T->H, nc, r, ldr, w, nc, T->work, s));
         return PLHR_OK;
     };
 
@@ -531,7 +539,10 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         for (int pass = 0; pass < 2; ++pass) {
             {
                 PhaseScope ps(PH_GRAM, s, gram_flops(n, m));
-                PLHR_TRY_CUDA(multi_gram(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams, s));
+                if (dwf)
+                    PLHR_TRY_CUDA(multi_gram_dw(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams, s));
+                else
+                    PLHR_TRY_CUDA(multi_gram(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams, s));
             }
             // ---------------------------------------- projected T-harmonic problem, selection (steps 7-10)
             {
@@ -559,8 +570,13 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         // -------------------------------------------- P, V (steps 11-12), images, RQs (13-14)
         {
             PhaseScope ps(PH_UPDATE, s, (T ? 4.0 : 2.0) * n * m * kp);
-            PLHR_TRY_CUDA(block_update(n, nb, zb, kp, Cp, Cvv, V, kp, P, kp, nullptr, 0, nullptr, nullptr, s));
-            if (T) PLHR_TRY_CUDA(block_update(n, nb, qb, kp, Cp, Cvv, QV, kp, QP, kp, nullptr, 0, nullptr, nullptr, s));
+            if (dwf) {
+                PLHR_TRY_CUDA(block_update_dw(n, nb, zb, kp, Cp, Cvv, V, kp, P, kp, s));
+                if (T) PLHR_TRY_CUDA(block_update_dw(n, nb, qb, kp, Cp, Cvv, QV, kp, QP, kp, s));
+            } else {
+                PLHR_TRY_CUDA(block_update(n, nb, zb, kp, Cp, Cvv, V, kp, P, kp, nullptr, 0, nullptr, nullptr, s));
+                if (T) PLHR_TRY_CUDA(block_update(n, nb, qb, kp, Cp, Cvv, QV, kp, QP, kp, nullptr, 0, nullptr, nullptr, s));
+            }
         }
         np = kp;
         PLHR_TRY(refresh_images());

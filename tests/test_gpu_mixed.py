@@ -52,6 +52,24 @@ def test_avmg_f32_matches_oracle(plhr, dims, levels, sigma, transfer, coarse, nc
     assert _rel(W, ref) <= 2e-5
 
 
+# double-word arithmetic (unit roundoff 2^-48): the V-cycle matches the FP64
+# oracle to ~1e-13 of its largest entry
+@pytest.mark.parametrize("dims,levels,sigma,transfer,coarse,nc", [
+    ((16, 16, 16), 1, 300.0, 0, 0, 3), ((16, 16, 16), 3, 900.0, 1, 1, 5), ((16, 16, 16), 3, 2500.0, 1, 1, 4),
+    ((32, 24, 16), 3, 700.0, 0, 0, 7), ((32, 24), 3, 700.0, 1, 1, 5)])
+def test_avmg_dw_matches_oracle(plhr, dims, levels, sigma, transfer, coarse, nc):
+    h = 1.0 / (max(dims) + 1)
+    A = plhr.Operator.laplacian(dims, h)
+    T = plhr.AVMG(A, sigma, levels=levels, nu=2, transfer=transfer, coarse=coarse)
+    R = wl.uniform_block(A.n, nc, 19)
+    Rd = torch.full((A.n, nc + 2), float("nan"), dtype=torch.float64, device="cuda")
+    Rd[:, :nc] = torch.from_numpy(R).cuda()
+    W = T.apply_dw(Rd[:, :nc]).cpu().numpy()
+    ref = oavmg.AVMG(dims, h, sigma, levels, nu=2, transfer=["constant", "linear"][transfer],
+                     coarse=["rediscretised", "fine_spectrum"][coarse])(R)
+    assert _rel(W, ref) <= 1e-12
+
+
 @pytest.mark.parametrize("case", ["lap2d_T_identity", "lap3d_avmg"])
 def test_mixed_solve_reaches_fp64_accuracy(plhr, case):
     if case == "lap2d_T_identity":
