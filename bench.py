@@ -154,20 +154,31 @@ def _fp32_simt_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def _rooflines(prof, w, peaks, sm_max_mhz):
+def _rooflines(prof, w, peaks, sm_max_mhz, mixed):
     """Achieved rate of every profiled phase from its algorithmic work and its
-    CUDA-event time; returns the entries sorted by total time."""
+    CUDA-event time; returns the entries sorted by total time.  In the mixed
+    form the FP64 phase runs the Gram, the update and the V-cycle in
+    double-word arithmetic on FP32 pipes: a double-word multiply-add costs 13
+    FP32 instructions, so its compute roof is the FP32 rate x 2 / 13 in
+    FP64-equivalent flops."""
     out = []
     fp32_peak = _fp32_simt_peak_tflops(sm_max_mhz or 2070.0)
-    for ph, kernel, bound, peak, unit, per in [
-            ("gram", "k_gram (FP64 multi-Gram)", "alu", FP64_PEAK_TFLOPS, "TFLOP/s", 1e-12),
+    dw_peak = fp32_peak * 2.0 / 13.0
+    if mixed:
+        f64_rows = [("gram", "k_gram_dw (double-word multi-Gram)", "alu", dw_peak, "TFLOP/s", 1e-12),
+                    ("update", "k_update_dw (double-word update)", "alu", dw_peak, "TFLOP/s", 1e-12),
+                    ("preconditioner", "double-word AV-MG V-cycle kernels", "hbm", peaks["hbm_gbs"], "GB/s",
+                     _vcycle_bytes_per_element(w.mg_levels, 8) * 1e-9)]
+    else:
+        f64_rows = [("gram", "k_gram (FP64 multi-Gram)", "alu", FP64_PEAK_TFLOPS, "TFLOP/s", 1e-12),
+                    ("update", "k_update (FP64)", "alu", FP64_PEAK_TFLOPS, "TFLOP/s", 1e-12),
+                    ("preconditioner", "FP64 AV-MG V-cycle kernels", "hbm", peaks["hbm_gbs"], "GB/s",
+                     _vcycle_bytes_per_element(w.mg_levels, 8) * 1e-9)]
+    for ph, kernel, bound, peak, unit, per in f64_rows + [
             ("gram_f32", "k_gram_mx (FP32 products, compensated sums)", "alu", fp32_peak, "TFLOP/s", 1e-12),
-            ("update", "k_update (FP64)", "alu", FP64_PEAK_TFLOPS, "TFLOP/s", 1e-12),
-            ("update_f32", "k_update_mx (FP32 with FP64 V part)", "alu", fp32_peak, "TFLOP/s", 1e-12),
+            ("update_f32", "k_update_mx (FP32 with double-word V part)", "alu", fp32_peak, "TFLOP/s", 1e-12),
             ("preconditioner_f32", "FP32 AV-MG V-cycle kernels", "hbm", peaks["hbm_gbs"], "GB/s",
-             _vcycle_bytes_per_element(w.mg_levels, 4) * 1e-9),
-            ("preconditioner", "FP64 AV-MG V-cycle kernels", "hbm", peaks["hbm_gbs"], "GB/s",
-             _vcycle_bytes_per_element(w.mg_levels, 8) * 1e-9)]:
+             _vcycle_bytes_per_element(w.mg_levels, 4) * 1e-9)]:
         d = prof.get(ph)
         if not d or d["ms"] <= 0 or d["work"] <= 0:
             continue
@@ -209,7 +220,8 @@ def run_ours(args, world, rank, local):
 
     def one(vinit, p=prec):
         return plhr.solve(A, w.sigma, k, T=T, tol=w.tol, maxit=w.maxit, v_init=vinit,
-                          raise_on_notconv=not profile_case, guard=w.guard, precision=p)
+                          raise_on_notconv=not profile_case, guard=w.guard, precision=p,
+                          switch_tol=args.switch_tol)
 
     def timed(fn):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -281,19 +293,19 @@ def run_ours(args, world, rank, local):
 
     # ---------------------------------------------------------------- rooflines
     peaks = _peaks()
-    roofs = _rooflines(prof, w, peaks, clocks.get("sm_max_mhz"))
+    roofs = _rooflines(prof, w, peaks, clocks.get("sm_max_mhz"), args.precision == "mixed")
     dom = dict(roofs[0]) if roofs else None
     if dom is not None:
         dom["traffic"] = None
-        if dom["phase"] == "gram":
+        if dom["phase"] == "gram" and args.precision == "f64":
             m_avg = kp + 2 * kp + kp
-            calls = max(1, prof["gram"]["calls"])
             dom["traffic"] = GRAM_DRAM_BYTES_PER_ROW_COL * n * m_avg
             dom["traffic_note"] = ("ncu dram bytes of one k_gram launch on the 64^3 case scaled by n m, "
-                                   "per launch (%d launches in the timed steps)" % calls)
-        dom["peak_src"] = ("nominal FP64 rate of the profiling recipe" if dom["unit"] == "TFLOP/s" and
-                           "FP64" in dom["kernel"] else
-                           "FP32 lanes x clock" if dom["unit"] == "TFLOP/s" else peaks["src"])
+                                   "per launch (%d launches in the timed steps)" % prof["gram"]["calls"])
+        dom["peak_src"] = ("measured (MEASURED_PEAKS.json hbm_gbs)" if dom["unit"] == "GB/s" else
+                           "nominal FP64 rate of the profiling recipe" if "FP64" in dom["kernel"] else
+                           "FP32 lanes x clock x 2 / 13 (double-word multiply-add)" if "double-word" in dom["kernel"]
+                           else "FP32 lanes x clock")
 
     out = {
         "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -303,6 +315,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic (seeded start block)",
         "config": {"workload": w.name, "operator": "7-point Dirichlet Laplacian 128^3, h = 1/129",
                    "n": n, "k": k, "k_prime": kp, "sigma": w.sigma, "tol": w.tol, "precision": args.precision,
+                   "switch_tol": args.switch_tol if args.precision == "mixed" else None,
                    "preconditioner": {"kind": "AV-MG", "levels": w.mg_levels, "nu": w.mg_nu,
                                       "transfer": "trilinear", "coarse": "fine-spectrum"},
                    "l2": "inputs larger than L2 (one 128^3 x 16 FP64 block = 268 MB)",
@@ -381,6 +394,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "f64"], default="mixed")
+    ap.add_argument("--switch-tol", type=float, default=1e-5,
+                    help="mixed form: residual level where the FP32 phase hands over to the double-word phase")
     ap.add_argument("--no-f64-compare", action="store_true",
                     help="skip the all-FP64 solve timed beside the mixed-precision steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")

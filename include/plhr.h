@@ -199,8 +199,11 @@ plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sigma, int k,
  * partner column; xi: 2 kp doubles (re, im of each selected unit);
  * status (device, 3 ints): [0 ok / 1 G_L not positive definite / 2 QR did not
  * converge / 3 rank loss, columns kept, units selected]; clk (device, 16 long
- * long, optional): clock64 stamps of the stages in [0..8], the number of QR
- * sweeps in [9] and of bulge-chase steps in [10].  m <= 64, kp <= 16. */
+ * long, optional): clock64 stamps of the stages in [0..8] (the stage runs as
+ * three launches: [0..2] and [5..8] come from the first and last, [3], [4]
+ * bracket the QR iteration in the middle one; SM clocks of different launches
+ * are not comparable), the number of QR sweeps in [9] and of bulge-chase
+ * steps in [10].  m <= 64, kp <= 16. */
 plhr_status plhr_tharm_extract(int m, int kp, int nv, const double* Gzz, const double* Guq,
                                const double* Gqz, const double* colscale, double* Cp, double* Cvv,
                                int* tags, int* partner, double* xi, int* status, long long* clk,

@@ -38,23 +38,17 @@ __device__ __forceinline__ bool pos_of(const Ld& g, Pos& p) {
     return true;
 }
 
-// L x at p (leading dimension nc), zero outside, as the sum of the
-// differences x_c - x_nb; xc receives x itself
+// L x at p (leading dimension nc), zero outside: 2d x_c - sum of the
+// neighbours (48 bits leave ample room for the cancellation); xc receives x
 template <bool D3>
 __device__ __forceinline__ dw lapd(dw& xc, const dw* __restrict__ xp, const Ld& g, const Pos& p) {
-    const int64_t ld = g.nc, sy = ld * g.nx, sz = sy * g.ny;
+    const int ld = g.nc, sy = ld * g.nx, sz = sy * g.ny;
     xc = xp[0];
-    const dw dxm = p.ix > 0 ? dw_sub(xc, xp[-ld]) : xc;
-    const dw dxp = p.ix < g.nx - 1 ? dw_sub(xc, xp[ld]) : xc;
-    const dw dym = p.iy > 0 ? dw_sub(xc, xp[-sy]) : xc;
-    const dw dyp = p.iy < g.ny - 1 ? dw_sub(xc, xp[sy]) : xc;
-    dw s = dw_add(dw_add(dxm, dxp), dw_add(dym, dyp));
-    if (D3) {
-        const dw dzm = p.iz > 0 ? dw_sub(xc, xp[-sz]) : xc;
-        const dw dzp = p.iz < g.nz - 1 ? dw_sub(xc, xp[sz]) : xc;
-        s = dw_add(s, dw_add(dzm, dzp));
-    }
-    return s;
+    const dw zero = dw_make(0.0f);
+    dw s = dw_add(p.ix > 0 ? xp[-ld] : zero, p.ix < g.nx - 1 ? xp[ld] : zero);
+    s = dw_add(s, dw_add(p.iy > 0 ? xp[-sy] : zero, p.iy < g.ny - 1 ? xp[sy] : zero));
+    if (D3) s = dw_add(s, dw_add(p.iz > 0 ? xp[-sz] : zero, p.iz < g.nz - 1 ? xp[sz] : zero));
+    return dw_sub(dw_mul_f(xc, D3 ? 6.0f : 4.0f), s);
 }
 
 // w = 2 om r - om^2 L r  (first two sweeps from w = 0, B = L)

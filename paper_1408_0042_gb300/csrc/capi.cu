@@ -222,6 +222,7 @@ plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma, cons
 
 void plhr_prec_destroy(plhr_prec* T) {
     if (!T) return;
+    cudaDeviceSynchronize();   // queued V-cycles may still read the hierarchy and workspace
     for (int a = 0; a < 3; ++a) {
         if (T->H.d_basis[a]) cudaFree(T->H.d_basis[a]);
         if (T->H.d_mu[a]) cudaFree(T->H.d_mu[a]);

@@ -31,7 +31,6 @@ namespace {
 constexpr int MAXM = kDenseMaxM;
 constexpr int LDS = MAXM + 1;     // shared row stride: column accesses hit distinct banks
 constexpr int NT = 128;           // threads of the extraction CTA
-constexpr int NW = NT / 32;
 
 struct cplx {
     double re, im;
@@ -514,20 +513,44 @@ struct Smem {
     int ints[8];
 };
 
-__global__ void __launch_bounds__(NT) k_extract(DenseArgs a) {
+// words of the shared-memory state saved to global memory between the launches
+constexpr int kStateWords = (int)(sizeof(Smem) / sizeof(int));
+static_assert(sizeof(Smem) % sizeof(int) == 0, "state copy granularity");
+// Yre, Yim, Yp (MAXM^2 each) and one packed complex LU factor (MAXM (MAXM+1) / 2)
+// per selected unit (at most MAXKP)
+constexpr int MAXKP = 16;
+constexpr size_t kLuComplex = (size_t)MAXM * (MAXM + 1) / 2;
+constexpr size_t kWorkMainDoubles = 3 * (size_t)MAXM * MAXM + 2 * MAXKP * kLuComplex;
+constexpr size_t kDenseWorkDoubles = kWorkMainDoubles + (sizeof(Smem) + sizeof(double) - 1) / sizeof(double);
+
+__device__ __forceinline__ Smem* state_of(const DenseArgs& a) {
+    return reinterpret_cast<Smem*>(a.work + kWorkMainDoubles);
+}
+
+// The dense stage runs as five launches: phase 0 of k_extract (up to the
+// Hessenberg form, state saved to global scratch), k_francis (one warp: the
+// eigenvalues), phase 1 (selection, state saved), k_eigvec (one CTA per
+// selected unit, in parallel), phase 2 (orthogonalisation, Y', coefficients).
+// The eigenvalue iteration measured 2x slower per bulge step when run inside
+// the large kernel than as its own launch on the same data and code, and the
+// eigenvectors ran four rounds on four warps of one SM.
+__global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = a.m, kp = a.kp;
+    int* gst = reinterpret_cast<int*>(state_of(a));
+    int* sst = reinterpret_cast<int*>(&S);
+    int nk = 0, nvk = 0;
     // global scratch: complex eigenvector coefficients per selected unit, Y',
     // and per-warp packed LU factors of the inverse iteration
     double* Yre = a.work;                          // [unit][MAXM]
     double* Yim = Yre + MAXM * MAXM;               // [unit][MAXM]
     double* Yp = Yim + MAXM * MAXM;                // [col][MAXM]
-    cplx* Uw = reinterpret_cast<cplx*>(Yp + MAXM * MAXM);   // NW x (MAXM (MAXM + 1) / 2)
     double* Wr = Yre;                              // reused after Y' is assembled
     double* Wv = Yim;
 #define STAMP(i) do { if (a.clk && tid == 0) a.clk[i] = clock64(); } while (0)
+  if (phase == 0) {
     STAMP(0);
     // ---- 1. B-orthonormalisation of Z, implicitly: Cholesky with column
     // dropping of the column-normalised Gram (the Grams are of Z diag(colscale)).
@@ -540,7 +563,6 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a) {
     }
     bsync();
     const double drop_tols[3] = {1e-12, 1e-9, 1e-6};
-    int nk = 0, nvk = 0;
     bool ok = false;
     for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
         for (int i = tid; i < m * m; i += NT) {
@@ -595,11 +617,11 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a) {
     }
     STAMP(1);
     if (nvk < 1 || nk < kp) {
-        if (tid == 0) { a.out_int[0] = kDenseRankLoss; a.out_int[1] = nk; a.out_int[2] = 0; }
+        if (tid == 0) { a.out_int[0] = kDenseRankLoss; a.out_int[1] = nk; a.out_int[2] = 0; state_of(a)->ints[6] = 1; }
         return;
     }
     if (!ok) {
-        if (tid == 0) { a.out_int[0] = kDenseBreakdown; a.out_int[1] = nk; a.out_int[2] = 0; }
+        if (tid == 0) { a.out_int[0] = kDenseBreakdown; a.out_int[1] = nk; a.out_int[2] = 0; state_of(a)->ints[6] = 1; }
         return;
     }
     // C = L^{-1} G_R L^{-T}: L Y = G_R by columns, then C L^T = Y by rows
@@ -625,16 +647,20 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a) {
     // ---- 3. eigenvalues of C: Hessenberg form, then Francis QR on a copy
     bhessenberg(S.H, S.Vh, S.beta, nk, S.red);
     for (int i = tid; i < nk * LDS; i += NT) S.H0[i] = S.H[i];
+    if (tid == 0) S.ints[6] = 0;
     bsync();
-    STAMP(3);
-    if (warp == 0) {
-        bool conv = francis_eigenvalues(S.H, nk, a.clk ? a.clk + 9 : nullptr);
-        if (lane == 0) S.ints[2] = conv ? 1 : 0;
-    }
+    for (int i = tid; i < kStateWords; i += NT) gst[i] = sst[i];
+    return;
+  }
+    // ---- phases 1, 2: reload the state (the eigenvalues are in S.H, S.ints[2])
+    for (int i = tid; i < kStateWords; i += NT) sst[i] = gst[i];
     bsync();
-    STAMP(4);
+    if (S.ints[6]) return;            // an earlier phase stopped (status already written)
+    nk = S.ints[0];
+    nvk = S.ints[1];
+  if (phase == 1) {
     if (!S.ints[2]) {
-        if (tid == 0) { a.out_int[0] = kDenseNoConv; a.out_int[1] = nk; a.out_int[2] = 0; }
+        if (tid == 0) { a.out_int[0] = kDenseNoConv; a.out_int[1] = nk; a.out_int[2] = 0; state_of(a)->ints[6] = 1; }
         return;
     }
     // ---- 4. order by |xi| (xi = 1/tau), conjugate pairs adjacent, select k'
@@ -713,64 +739,12 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a) {
         }
     }
     bsync();
+    for (int i = tid; i < kStateWords; i += NT) gst[i] = sst[i];   // selection saved for k_eigvec
+    return;
+  }
     const int nsel = S.ints[3];
     STAMP(5);
-    // ---- 5. eigenvectors of C for the selected units: inverse iteration on the
-    // Hessenberg form (one warp per unit), back to C's basis with the Householder
-    // reflectors, then y = L^{-T} z in the orthonormal basis
-    {
-        double hn = 0.0;
-        for (int i = tid; i < nk * nk; i += NT) hn = fmax(hn, fabs(S.H0[(i / nk) * LDS + i % nk]));
-        hn = warp_max(hn);
-        if (lane == 0) S.red[warp] = hn;
-        bsync();
-        double hmax = 0.0;
-        for (int w = 0; w < NW; ++w) hmax = fmax(hmax, S.red[w]);
-        const double tiny = DBL_EPSILON * (hmax > 0.0 ? hmax : 1.0);
-        cplx* Uo = Uw + warp * (MAXM * (MAXM + 1) / 2);
-        __shared__ cplx xs[NW][MAXM], cs_[NW][MAXM], ns_[NW][MAXM];
-        for (int u = warp; u < nsel; u += NW) {
-            const int e = S.order[u];
-            cplx lam = {S.eig_re[e], S.eig_im[e]};
-            if (S.nclose[u] > 0) {
-                double f = 1.0 + 1e-10 * S.nclose[u];
-                lam = cscale(lam, f);
-            }
-            cplx* x = xs[warp];
-            inverse_iteration(S.H0, nk, lam, x, Uo, cs_[warp], ns_[warp], tiny);
-            // z = Q x with Q = H_0 H_1 ... (reflectors applied last-first)
-            for (int k = nk - 3; k >= 0; --k) {
-                const double b = S.beta[k];
-                if (b == 0.0) continue;
-                const double* v = S.Vh + k * LDS;
-                double sr = 0.0, si = 0.0;
-                for (int i = k + 1 + lane; i < nk; i += 32) { sr += v[i] * x[i].re; si += v[i] * x[i].im; }
-                sr = warp_sum(sr) * b;
-                si = warp_sum(si) * b;
-                wsync();
-                for (int i = k + 1 + lane; i < nk; i += 32) { x[i].re -= sr * v[i]; x[i].im -= si * v[i]; }
-                wsync();
-            }
-            // y = L^{-T} z  (back substitution with the lower factor L)
-            double* yr = Yre + u * MAXM;
-            double* yi = Yim + u * MAXM;
-            for (int i = nk - 1; i >= 0; --i) {
-                double sr = 0.0, si = 0.0;
-                for (int l = i + 1 + lane; l < nk; l += 32) {
-                    sr += S.B[l * LDS + i] * yr[l];
-                    si += S.B[l * LDS + i] * yi[l];
-                }
-                sr = warp_sum(sr);
-                si = warp_sum(si);
-                if (lane == 0) {
-                    yr[i] = (x[i].re - sr) / S.B[i * LDS + i];
-                    yi[i] = (x[i].im - si) / S.B[i * LDS + i];
-                }
-                __threadfence_block();
-                wsync();
-            }
-        }
-    }
+    // ---- 5. (k_eigvec) eigenvectors of the selected units are in Yre, Yim
     bsync();
     STAMP(6);
     // ---- cluster orthogonalisation, pair rotation, unit norm (warp 0, in the
@@ -896,21 +870,107 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a) {
 #undef STAMP
 }
 
+// Eigenvector of one selected unit (CTA u, one warp): inverse iteration on the
+// saved Hessenberg form H0, back to C's basis with the Householder reflectors,
+// then y = L^{-T} z in the orthonormal basis, into Yre[u], Yim[u].  The units
+// run as separate CTAs on separate SMs (the FP64 work of one unit is serial).
+__global__ void __launch_bounds__(32) k_eigvec(DenseArgs a) {
+    extern __shared__ __align__(16) double sh0[];   // H0, MAXM x LDS
+    const Smem* G = state_of(a);
+    if (G->ints[6]) return;
+    const int u = blockIdx.x;
+    const int nsel = G->ints[3], nk = G->ints[0];
+    if (u >= nsel) return;
+    const int lane = threadIdx.x;
+    __shared__ cplx x[MAXM], cur[MAXM], nxt[MAXM];
+    double hn = 0.0;
+    for (int i = lane; i < nk * LDS; i += 32) {
+        const double v = G->H0[i];
+        sh0[i] = v;
+        if (i % LDS < nk) hn = fmax(hn, fabs(v));
+    }
+    hn = warp_max(hn);
+    const double tiny = DBL_EPSILON * (hn > 0.0 ? hn : 1.0);
+    __syncwarp();
+    const int e = G->order[u];
+    cplx lam = {G->eig_re[e], G->eig_im[e]};
+    if (G->nclose[u] > 0) lam = cscale(lam, 1.0 + 1e-10 * G->nclose[u]);
+    cplx* U = reinterpret_cast<cplx*>(a.work + 3 * (size_t)MAXM * MAXM) + (size_t)u * kLuComplex;
+    inverse_iteration(sh0, nk, lam, x, U, cur, nxt, tiny);
+    // z = Q x with Q = H_0 H_1 ... (reflectors applied last-first)
+    for (int k = nk - 3; k >= 0; --k) {
+        const double b = G->beta[k];
+        if (b == 0.0) continue;
+        const double* v = G->Vh + k * LDS;
+        double sr = 0.0, si = 0.0;
+        for (int i = k + 1 + lane; i < nk; i += 32) { sr += v[i] * x[i].re; si += v[i] * x[i].im; }
+        sr = warp_sum(sr) * b;
+        si = warp_sum(si) * b;
+        __syncwarp();
+        for (int i = k + 1 + lane; i < nk; i += 32) { x[i].re -= sr * v[i]; x[i].im -= si * v[i]; }
+        __syncwarp();
+    }
+    // y = L^{-T} z  (back substitution with the lower factor L)
+    double* yr = a.work + (size_t)u * MAXM;
+    double* yi = a.work + (size_t)MAXM * MAXM + (size_t)u * MAXM;
+    for (int i = nk - 1; i >= 0; --i) {
+        double sr = 0.0, si = 0.0;
+        for (int l = i + 1 + lane; l < nk; l += 32) {
+            sr += G->B[l * LDS + i] * yr[l];
+            si += G->B[l * LDS + i] * yi[l];
+        }
+        sr = warp_sum(sr);
+        si = warp_sum(si);
+        if (lane == 0) {
+            yr[i] = (x[i].re - sr) / G->B[i * LDS + i];
+            yi[i] = (x[i].im - si) / G->B[i * LDS + i];
+        }
+        __threadfence_block();
+        __syncwarp();
+    }
+}
+
+// Eigenvalues of the saved Hessenberg form (one warp; see k_extract).  The
+// stage clocks 3 and 4 and the sweep counts come from this launch.
+__global__ void __launch_bounds__(32) k_francis(DenseArgs a) {
+    extern __shared__ __align__(16) double shh[];
+    Smem* G = state_of(a);
+    if (G->ints[6]) return;
+    const int nk = G->ints[0];
+    const int lane = threadIdx.x;
+    for (int i = lane; i < nk * LDS; i += 32) shh[i] = G->H[i];
+    __syncwarp();
+    if (a.clk && lane == 0) a.clk[3] = clock64();
+    const bool conv = francis_eigenvalues(shh, nk, a.clk ? a.clk + 9 : nullptr);
+    if (a.clk && lane == 0) a.clk[4] = clock64();
+    for (int i = lane; i < nk * LDS; i += 32) G->H[i] = shh[i];
+    if (lane == 0) G->ints[2] = conv ? 1 : 0;
+}
+
 }  // namespace
 
 size_t dense_smem_bytes() { return sizeof(Smem); }
 
-// Yre, Yim, Yp (3 MAXM^2) and the per-warp packed LU factors (NW MAXM(MAXM+1)/2
-// complex) fit in 8 MAXM^2 doubles.
-size_t dense_work_doubles() { return 8 * (size_t)MAXM * MAXM; }
-static_assert(3 * MAXM * MAXM + 2 * NW * (MAXM * (MAXM + 1) / 2) <= 8 * MAXM * MAXM, "dense scratch layout");
+// Yre, Yim, Yp (3 MAXM^2), one packed complex LU factor per selected unit, and
+// the shared-memory state passed between the launches.
+size_t dense_work_doubles() { return kDenseWorkDoubles; }
+static_assert(kWorkMainDoubles >= 3 * (size_t)MAXM * MAXM + 2 * MAXKP * kLuComplex, "dense scratch layout");
 
 cudaError_t dense_extract(const DenseArgs& a, cudaStream_t s) {
     size_t shm = sizeof(Smem);
     cudaError_t e = cudaFuncSetAttribute(k_extract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
-    k_extract<<<1, NT, shm, s>>>(a);
-    count_launches(1);
+    const size_t shf = sizeof(double) * MAXM * LDS;
+    e = cudaFuncSetAttribute(k_francis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_eigvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf);
+    if (e != cudaSuccess) return e;
+    k_extract<<<1, NT, shm, s>>>(a, 0);
+    k_francis<<<1, 32, shf, s>>>(a);
+    k_extract<<<1, NT, shm, s>>>(a, 1);
+    k_eigvec<<<a.kp, 32, shf, s>>>(a);
+    k_extract<<<1, NT, shm, s>>>(a, 2);
+    count_launches(5);
     return cudaGetLastError();
 }
 
@@ -1147,7 +1207,7 @@ namespace {
 // Scratch of the projected eigensolve for the largest supported basis
 // (m = 64): 8 * 64 * 64 doubles = 256 KiB.  Every GPU that loads the library
 // holds this array until the process exits.
-constexpr size_t kNoAllocScratchDoubles = 8 * (size_t)plhr::kDenseMaxM * plhr::kDenseMaxM;
+constexpr size_t kNoAllocScratchDoubles = plhr::kDenseWorkDoubles;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
 // Device address of the scratch array, looked up once per device.

@@ -55,7 +55,7 @@ __device__ __forceinline__ float ldf(const FamMx& F, int b, int64_t row, int c) 
 // in FP64 and rounded once.
 __device__ void stage_mx(float* sz, float* su, float* sq, int mp, int64_t n, int64_t row0, const FamMx& Z,
                          const FamMx& AZ, const FamMx& Q, int nb, int has_q, double sigma,
-                         const double* __restrict__ csc) {
+                         const double* __restrict__ csc, const float* __restrict__ cscf, float sigf) {
     // static block indices: the family descriptors stay in registers / the
     // parameter space instead of a local copy
 #pragma unroll
@@ -72,18 +72,18 @@ __device__ void stage_mx(float* sz, float* su, float* sq, int mp, int64_t n, int
             const int col = Z.off[b] + c;
             float z = 0.0f, u = 0.0f, q = 0.0f;
             if (row < n) {
-                const double s = csc[col];
+                const float sf = cscf[col];
                 if (wide) {
+                    const double s = csc[col];
                     const double zd = ldv(Z, b, row, c) * s;
                     const double ud = isu ? ldv(AZ, b, row, c) * s : ldv(AZ, b, row, c) * s - sigma * zd;
                     z = (float)zd;
                     u = (float)ud;
                 } else {
-                    const float sf = (float)s;
                     z = ldf(Z, b, row, c) * sf;
-                    u = isu ? ldf(AZ, b, row, c) * sf : ldf(AZ, b, row, c) * sf - (float)sigma * z;
+                    u = isu ? ldf(AZ, b, row, c) * sf : ldf(AZ, b, row, c) * sf - sigf * z;
                 }
-                q = has_q ? ldf(Q, b, row, c) * (float)s : u;
+                q = has_q ? ldf(Q, b, row, c) * sf : u;
             }
             sz[r * mp + col] = z;
             su[r * mp + col] = u;
@@ -136,6 +136,9 @@ __global__ void __launch_bounds__(kGramMxThreads, 1) k_gram_mx(int64_t n, int m,
     float* sz = shm;
     float* su = sz + kMxRows * mp;
     float* sq = su + kMxRows * mp;
+    float* cscf = sq + kMxRows * mp;        // [mp] FP32 column scales
+    for (int t = threadIdx.x; t < m; t += blockDim.x) cscf[t] = (float)csc[t];
+    const float sigf = (float)sigma;
     const int T = mp / 4;
     const int g = threadIdx.x >> 8, ti = (threadIdx.x >> 4) & 15, tj = threadIdx.x & 15;
     const bool act = ti < T && tj < T && (g != 0 || ti <= tj);
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(kGramMxThreads, 1) k_gram_mx(int64_t n, int m,
     const int64_t nchunks = (n + kMxRows - 1) / kMxRows;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         __syncthreads();
-        stage_mx(sz, su, sq, mp, n, ch * kMxRows, Z, AZ, Q, nb, has_q, sigma, csc);
+        stage_mx(sz, su, sq, mp, n, ch * kMxRows, Z, AZ, Q, nb, has_q, sigma, csc, cscf, sigf);
         __syncthreads();
         if (act) {
             float acc[16];
@@ -343,7 +346,15 @@ cudaError_t multi_gram_mx(int64_t n, int nb, const BlkMx* Z, const BlkMx* AZ, co
     const int mp = (m + 3) / 4 * 4;
     if (mp > 64) return cudaErrorInvalidValue;
     const int blocks = gram_mx_blocks();
-    const size_t shm = sizeof(float) * 3 * kMxRows * mp;
+    const size_t shm = sizeof(float) * (3 * kMxRows * mp + mp);
+    // above the 48 KB default at mp = 64: raise the kernel's limit to the largest size
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gram_mx, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(float) * (3 * kMxRows * 64 + 64)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     k_gram_mx<<<blocks, kGramMxThreads, shm, s>>>(n, m, mp, nb, FZ, FA, FQ, Q ? 1 : 0, sigma, colscale, partial);
     count_launches(1);
     cudaError_t e = cudaGetLastError();

@@ -151,6 +151,10 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         return PLHR_ENOMEM;
     }
     struct HostFree { void* p; ~HostFree() { if (p) cudaFreeHost(p); } } host_free{hs};
+    // on every exit, wait for the work queued on the stream before any buffer
+    // above (or the FP32 ones below) is released: an error return can happen
+    // with kernels of the current iteration still in flight
+    struct StreamDrain { cudaStream_t s; ~StreamDrain() { cudaStreamSynchronize(s); } } drain_before_free{s};
     double* h_rel = reinterpret_cast<double*>(hs + 1);
     double* h_lam = h_rel + 64;
     double* h_theta = h_lam + 64;
@@ -172,8 +176,14 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     int best_it = 0;
     struct FloatBuf {
         float* p = nullptr;
-        ~FloatBuf() { if (p) cudaFree(p); }
+        cudaStream_t s = nullptr;
+        ~FloatBuf() {
+            if (!p) return;
+            cudaStreamSynchronize(s);   // destroyed before drain_before_free: wait here too
+            cudaFree(p);
+        }
     } big32;
+    big32.s = s;
     float *W32 = nullptr, *AW32 = nullptr, *SQ32 = nullptr, *X2_32 = nullptr, *AS32 = nullptr, *X3_32 = nullptr,
           *QS32 = nullptr, *P32 = nullptr, *AP32 = nullptr, *QP32 = nullptr, *QV32 = nullptr, *V32 = nullptr,
           *U32 = nullptr;
