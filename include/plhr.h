@@ -69,6 +69,16 @@ typedef struct plhr_op plhr_op;
 /* Create a stencil operator.  *out is set only on PLHR_OK. */
 plhr_status plhr_op_stencil(plhr_op** out, const plhr_stencil_desc* desc);
 /* Number of rows n of the operator (0 for NULL). */
+/* Real-space Hamiltonian H = -1/2 Lap_h + diag(V) on a d-dimensional grid
+ * (d = 2, 3; dims[2] ignored for d = 2) with mesh width h: the 5/7-point
+ * Laplacian above with scale 1/2, neighbours outside the grid zero
+ * (periodic = 0) or wrapped around (periodic = 1), and the potential V given
+ * as a device array of n doubles (x fastest) that the caller keeps alive and
+ * unchanged while the operator is in use.  The role of the Hamiltonians of
+ * Section 5.3 in the synthetic differentiation workload.  Supported by
+ * plhr_op_apply and by plhr_solve in PLHR_PRECISION_F64. */
+plhr_status plhr_op_hamiltonian(plhr_op** out, int d, const int64_t* dims, double h, int periodic,
+                                const double* potential);
 int64_t plhr_op_size(const plhr_op* op);
 void plhr_op_destroy(plhr_op* op);
 
@@ -166,6 +176,14 @@ typedef struct {
 } plhr_info;
 
 void plhr_options_default(plhr_options* o);
+
+/* Gradient of sum_k w_k lambda_k with respect to the potential of a
+ * Hamiltonian: g (device, n) = sum_k w_k V(:,k)^2 for B-orthonormal
+ * eigenvectors V (device n x k, leading dimension ldv >= k, as plhr_solve
+ * returns them) and host weights w (k values, 1 <= k <= 64): first-order
+ * perturbation theory (Hellmann-Feynman), d lambda_k / d V_i = v_k(i)^2. */
+plhr_status plhr_eigval_grad(int64_t n, int k, const double* V, int64_t ldv, const double* weights, double* g,
+                             void* stream);
 
 /* Compute the k eigenpairs of A v = lambda B v nearest sigma.
  *   B        NULL = identity.

@@ -10,6 +10,11 @@ written with the slowest axis first.
   discretization"; the 3D 7-point analogue): the 1D second difference
   (-u[j-1] + 2u[j] - u[j+1]) / h^2 with homogeneous Dirichlet ends, combined as
   a Kronecker sum over the axes.
+* Real-space Hamiltonian H = -1/2 Lap + diag(V) (the role of the Hamiltonians
+  of Section 5.3 in the synthetic differentiation workload): the same
+  Kronecker sum with the 1D second difference closed periodically
+  (u[-1] = u[N-1], u[N] = u[0]) or with Dirichlet ends, times 1/2, plus the
+  potential on the diagonal.
 * Bilinear (Q1) finite elements (Section 5.1: "standard bilinear finite
   elements", stiffness A and mass B): on a tensor mesh the Q1 element matrices
   factor into 1D linear-element matrices, so A = K (x) M + M (x) K and
@@ -46,6 +51,23 @@ def laplacian_dirichlet(dims, h: float) -> sp.csr_matrix:
     """Negative FD Laplacian, Dirichlet, on a grid with axis sizes dims = (nx, ny[, nz])."""
     mats = [second_difference_1d(N, h) for N in reversed(dims)]  # slowest axis first
     return kron_sum(mats)
+
+
+def second_difference_periodic_1d(N: int, h: float) -> sp.csr_matrix:
+    """(-u[j-1] + 2u[j] - u[j+1]) / h^2 on N points of a periodic line."""
+    D = sp.lil_matrix((N, N))
+    for j in range(N):
+        D[j, j] += 2.0
+        D[j, (j - 1) % N] -= 1.0
+        D[j, (j + 1) % N] -= 1.0
+    return (D.tocsr() / h**2).tocsr()
+
+
+def hamiltonian(dims, h: float, V, periodic: bool = True) -> sp.csr_matrix:
+    """H = -1/2 Lap + diag(V) on the grid dims = (nx, ny[, nz]); V flattened x fastest."""
+    one_d = second_difference_periodic_1d if periodic else second_difference_1d
+    lap = kron_sum([one_d(N, h) for N in reversed(dims)])
+    return (0.5 * lap + sp.diags(np.asarray(V, dtype=np.float64).ravel(), 0)).tocsr()
 
 
 def q1_1d(N: int, h: float):

@@ -56,6 +56,10 @@ class Info(ctypes.Structure):
 _SIGS = {
     "plhr_op_stencil": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(StencilDesc)]),
     "plhr_op_size": (ctypes.c_int64, [ctypes.c_void_p]),
+    "plhr_op_hamiltonian": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
+    "plhr_eigval_grad": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "plhr_op_destroy": (None, [ctypes.c_void_p]),
     "plhr_op_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
@@ -159,6 +163,25 @@ class Operator:
         out = ctypes.c_void_p()
         _check(lib.plhr_op_stencil(ctypes.byref(out), ctypes.byref(d)), "plhr_op_stencil")
         return cls(out, dims, h, scale)
+
+    @classmethod
+    def hamiltonian(cls, dims, h, potential, periodic=True):
+        """H = -1/2 Lap + diag(V) (periodic or Dirichlet) with V a float64 CUDA
+        tensor of prod(dims) values, x fastest; the operator keeps a reference."""
+        import torch
+        lib = load_library()
+        if not (isinstance(potential, torch.Tensor) and potential.is_cuda and potential.dtype == torch.float64):
+            raise ValueError("potential must be a float64 CUDA tensor")
+        pot = potential.contiguous().reshape(-1)
+        if pot.numel() != int(np.prod(dims)):
+            raise ValueError("potential has %d values for a grid of %d" % (pot.numel(), int(np.prod(dims))))
+        d3 = (ctypes.c_int64 * 3)(*(list(dims) + [1] * (3 - len(dims))))
+        out = ctypes.c_void_p()
+        _check(lib.plhr_op_hamiltonian(ctypes.byref(out), len(dims), d3, h, 1 if periodic else 0,
+                                       ctypes.c_void_p(pot.data_ptr())), "plhr_op_hamiltonian")
+        op = cls(out, tuple(dims), h, 0.5)
+        op._potential = pot
+        return op
 
     @property
     def n(self):
@@ -337,3 +360,51 @@ def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float =
                            "lam_all": r[1:1 + kp].copy(), "rel_all": r[1 + kp:1 + 2 * kp].copy(),
                            "kept": int(r[1 + 2 * kp]), "m": int(r[2 + 2 * kp])} for r in rec]
     return vals, vecs, out
+
+
+def eigval_grad(vecs, weights, stream=None):
+    """g = sum_k w_k v_k^2 (device): the gradient of sum_k w_k lambda_k with
+    respect to the potential of a Hamiltonian, for B-orthonormal eigenvectors
+    vecs (n x k float64 CUDA)."""
+    import torch
+    if vecs.dtype != torch.float64 or not vecs.is_cuda or vecs.dim() != 2 or vecs.stride(1) != 1:
+        raise ValueError("vecs must be a row-major float64 CUDA block")
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).ravel())
+    if w.size != vecs.shape[1]:
+        raise ValueError("one weight per eigenvector")
+    g = torch.empty(vecs.shape[0], dtype=torch.float64, device=vecs.device)
+    _check(load_library().plhr_eigval_grad(vecs.shape[0], vecs.shape[1], ctypes.c_void_p(vecs.data_ptr()),
+                                           vecs.stride(0), w.ctypes.data, ctypes.c_void_p(g.data_ptr()),
+                                           _stream_ptr(stream)), "plhr_eigval_grad")
+    return g
+
+
+def _hamiltonian_eig_class():
+    import torch
+
+    class HamiltonianEig(torch.autograd.Function):
+        """lambda (k, float64 CUDA) = the k eigenvalues nearest sigma of
+        H(V) = -1/2 Lap + diag(V); backward gives dL/dV = sum_k (dL/dlambda_k)
+        v_k^2 on the device (Hellmann-Feynman)."""
+
+        @staticmethod
+        def forward(ctx, V, dims, h, periodic, sigma, k, tol, maxit, guard, T):
+            op = Operator.hamiltonian(dims, h, V.detach().reshape(-1).contiguous(), periodic)
+            lam, vecs, info = solve(op, sigma, k, T=T, tol=tol, maxit=maxit, guard=guard, raise_on_notconv=True)
+            ctx.save_for_backward(vecs)
+            ctx.vshape = V.shape
+            return torch.from_numpy(lam).to(V.device)
+
+        @staticmethod
+        def backward(ctx, glam):
+            (vecs,) = ctx.saved_tensors
+            g = eigval_grad(vecs, glam.detach().cpu().numpy())
+            return (g.reshape(ctx.vshape),) + (None,) * 9
+
+    return HamiltonianEig
+
+
+def hamiltonian_eigvals(V, dims, h, sigma, k, periodic=True, tol=1e-10, maxit=5000, guard=2, T=None):
+    """Differentiable k eigenvalues nearest sigma of H(V) = -1/2 Lap + diag(V)
+    (V: float64 CUDA tensor with prod(dims) values, requires_grad allowed)."""
+    return _hamiltonian_eig_class().apply(V, tuple(dims), h, periodic, sigma, k, tol, maxit, guard, T)

@@ -83,6 +83,31 @@ plhr_status plhr_op_stencil(plhr_op** out, const plhr_stencil_desc* d) {
     return PLHR_OK;
 }
 
+plhr_status plhr_op_hamiltonian(plhr_op** out, int d, const int64_t* dims, double h, int periodic,
+                                const double* potential) {
+    clear_error();
+    if (!out || !dims || (d != 2 && d != 3) || !(h > 0)) {
+        set_error("plhr_op_hamiltonian: invalid argument");
+        return PLHR_EINVAL;
+    }
+    if (dims[0] < 1 || dims[1] < 1 || (d == 3 && dims[2] < 1)) {
+        set_error("plhr_op_hamiltonian: bad dims");
+        return PLHR_EINVAL;
+    }
+    plhr_op* op = new plhr_op;
+    op->kind = d == 3 ? PLHR_STENCIL_LAP7_3D : PLHR_STENCIL_LAP5_2D;
+    op->g.d = d;
+    op->g.nx = dims[0];
+    op->g.ny = dims[1];
+    op->g.nz = d == 3 ? dims[2] : 1;
+    op->g.h = h;
+    op->g.scale = 0.5;
+    op->g.periodic = periodic ? 1 : 0;
+    op->g.pot = potential;
+    *out = op;
+    return PLHR_OK;
+}
+
 int64_t plhr_op_size(const plhr_op* op) { return op ? op->g.n() : 0; }
 
 void plhr_op_destroy(plhr_op* op) { delete op; }

@@ -34,14 +34,18 @@ void clear_error();
 #define PLHR_LAUNCHED() PLHR_TRY_CUDA(cudaGetLastError())
 
 // ---------------------------------------------------------------- grids
-// Tensor grid with homogeneous Dirichlet boundary, x fastest.
+// Tensor grid, x fastest, homogeneous Dirichlet boundary (or periodic), with
+// an optional diagonal potential.
 struct Grid {
     int d = 3;            // 2 or 3
     int64_t nx = 1, ny = 1, nz = 1;
     double h = 1.0;
     double scale = 1.0;   // stencil multiplier
+    int periodic = 0;     // 1: periodic wrap instead of zero Dirichlet values
+    const double* pot = nullptr;   // optional diagonal term (device, n values): A = scale L + diag(pot)
     int64_t n() const { return nx * ny * nz; }
     double inv_h2() const { return scale / (h * h); }
+    bool plain() const { return !periodic && pot == nullptr; }   // the Dirichlet Laplacian
 };
 
 // A block of row-major vectors: element (i, j) at p[i * ld + j].

@@ -99,6 +99,10 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         return PLHR_EINVAL;
     }
     const int64_t n = A->g.n();
+    if (opt.precision == PLHR_PRECISION_MIXED && !A->g.plain()) {
+        set_error("plhr_solve: the mixed-precision form supports the Dirichlet Laplacian only");
+        return PLHR_EINVAL;
+    }
     if (opt.guard < 0) {
         set_error("plhr_solve: guard < 0");
         return PLHR_EINVAL;

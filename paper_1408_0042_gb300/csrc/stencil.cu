@@ -1,5 +1,6 @@
-// Stencil products with the Dirichlet finite-difference Laplacian (Section 5.2:
-// 5-point in 2D, 7-point in 3D), on blocks of vectors stored row-major
+// Stencil products with the finite-difference Laplacian (Section 5.2: 5-point
+// in 2D, 7-point in 3D; Dirichlet, or periodic with a diagonal potential for
+// the real-space Hamiltonian -1/2 Lap + V), on blocks of vectors stored row-major
 // [grid point][column].  One thread per (grid point, column) pair: a warp
 // covers 32 consecutive doubles of the block, so every neighbour access of a
 // warp (x +- 1: +-ld, y +- 1: +-ld*nx, z +- 1: +-ld*nx*ny) is one contiguous
@@ -11,20 +12,35 @@ namespace {
 
 struct Geo {
     int64_t nx, ny, nz, sx, sy, sz;   // sizes and row strides (in rows)
+    int periodic;
+    const double* pot;                // diagonal term or null
 };
 
+// sum over axes of (2 x_c - x_- - x_+); neighbours outside the grid are zero
+// (Dirichlet) or wrap around (periodic)
 template <bool D3>
 __device__ __forceinline__ double lap_at(const double* __restrict__ xp, int64_t ld, int64_t ix,
                                          int64_t iy, int64_t iz, const Geo& g) {
     double xc = xp[0];
     double s = (D3 ? 6.0 : 4.0) * xc;
-    if (ix > 0) s -= xp[-ld];
-    if (ix < g.nx - 1) s -= xp[ld];
-    if (iy > 0) s -= xp[-ld * g.sy];
-    if (iy < g.ny - 1) s -= xp[ld * g.sy];
+    if (!g.periodic) {
+        if (ix > 0) s -= xp[-ld];
+        if (ix < g.nx - 1) s -= xp[ld];
+        if (iy > 0) s -= xp[-ld * g.sy];
+        if (iy < g.ny - 1) s -= xp[ld * g.sy];
+        if (D3) {
+            if (iz > 0) s -= xp[-ld * g.sz];
+            if (iz < g.nz - 1) s -= xp[ld * g.sz];
+        }
+        return s;
+    }
+    // periodic: offsets of the wrapped neighbours (in rows)
+    const int64_t xm = ix > 0 ? -1 : g.nx - 1, xq = ix < g.nx - 1 ? 1 : -(g.nx - 1);
+    const int64_t ym = iy > 0 ? -g.sy : (g.ny - 1) * g.sy, yq = iy < g.ny - 1 ? g.sy : -(g.ny - 1) * g.sy;
+    s -= xp[ld * xm] + xp[ld * xq] + xp[ld * ym] + xp[ld * yq];
     if (D3) {
-        if (iz > 0) s -= xp[-ld * g.sz];
-        if (iz < g.nz - 1) s -= xp[ld * g.sz];
+        const int64_t zm = iz > 0 ? -g.sz : (g.nz - 1) * g.sz, zq = iz < g.nz - 1 ? g.sz : -(g.nz - 1) * g.sz;
+        s -= xp[ld * zm] + xp[ld * zq];
     }
     return s;
 }
@@ -39,8 +55,9 @@ __global__ void __launch_bounds__(256) k_lap_axpby(Geo g, int nc, double ih2, co
         int c = (int)(e - row * nc);
         int64_t ix = row % g.nx, t = row / g.nx, iy = t % g.ny, iz = t / g.ny;
         const double* xp = x + row * ldx + c;
-        double lx = lap_at<D3>(xp, ldx, ix, iy, iz, g);
-        y[row * ldy + c] = alpha * ih2 * lx + beta * xp[0];
+        double lx = ih2 * lap_at<D3>(xp, ldx, ix, iy, iz, g);
+        if (g.pot) lx += g.pot[row] * xp[0];
+        y[row * ldy + c] = alpha * lx + beta * xp[0];
     }
 }
 
@@ -59,6 +76,7 @@ __global__ void __launch_bounds__(256) k_lap_shifts(Geo g, int nc, double ih2, c
         const double* xp = x + row * ldx + c;
         double a = ih2 * lap_at<D3>(xp, ldx, ix, iy, iz, g);
         double xv = xp[0];
+        if (g.pot) a += g.pot[row] * xv;
         if (ax) ax[row * ldax + c] = a;
         if (o1) o1[row * ld1 + c] = a - lam[c] * xv;
         if (o2) o2[row * ld2 + c] = a - sig * xv;
@@ -69,6 +87,8 @@ Geo geo_of(const Grid& g) {
     Geo o;
     o.nx = g.nx; o.ny = g.ny; o.nz = g.nz;
     o.sx = 1; o.sy = g.nx; o.sz = g.nx * g.ny;
+    o.periodic = g.periodic;
+    o.pot = g.pot;
     return o;
 }
 

@@ -1,0 +1,119 @@
+"""GPU parity of the Hamiltonian operator H(V) = -1/2 Lap + diag(V), of block
+PLHR on it, and of the eigenvalue gradient with respect to V (the
+differentiation extension): against dense eigensolves of the oracle's
+operator and central finite differences of the GPU eigenvalues."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import operators as oops
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def plhr():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1408_0042_gb300 as p
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return p
+
+
+@pytest.mark.parametrize("dims,periodic,nc", [((6, 5, 4), True, 3), ((7, 6), True, 2), ((6, 5, 4), False, 4),
+                                              ((16, 12, 10), True, 5)])
+def test_hamiltonian_apply_matches_oracle(plhr, dims, periodic, nc):
+    n = int(np.prod(dims))
+    V = wl.uniform_block(n, 1, 31).ravel() * 3.0
+    h = 0.7
+    op = plhr.Operator.hamiltonian(dims, h, torch.from_numpy(V).cuda(), periodic=periodic)
+    X = wl.uniform_block(n, nc, 32)
+    Y = op.apply(torch.from_numpy(X).cuda()).cpu().numpy()
+    ref = oops.hamiltonian(dims, h, V, periodic=periodic) @ X
+    assert np.abs(Y - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def _problem(k=4, index=24):
+    """8^3 periodic grid with 4 seeded wells; sigma in the widest gap near the
+    given index such that the k nearest eigenvalues are simple."""
+    p = wl.hamiltonian_small(8, 4, k=k)
+    lam, Y = np.linalg.eigh(oops.hamiltonian(p["dims"], 1.0, p["V"]).toarray())
+    best = None
+    for i in range(index - 6, index + 6):
+        sig = 0.5 * (lam[i] + lam[i + 1])
+        d = np.abs(lam - sig)
+        o = np.argsort(d)
+        near = np.sort(o[:k])
+        gaps = np.diff(lam[near[0] - 1:near[-1] + 2])
+        score = min(gaps.min(), d[o[k]] - d[o[k - 1]])
+        if best is None or score > best[0]:
+            best = (score, sig, near)
+    _, sigma, near = best
+    return p, sigma, lam, Y, near
+
+
+def test_solve_and_gradient_match_dense_reference(plhr):
+    p, sigma, lam, Y, near = _problem()
+    k = p["k"]
+    Vt = torch.from_numpy(p["V"]).cuda()
+    op = plhr.Operator.hamiltonian(p["dims"], 1.0, Vt)
+    ev, vecs, info = plhr.solve(op, sigma, k, tol=1e-11, maxit=6000, guard=2)
+    assert info["converged"], info
+    assert np.allclose(np.sort(ev), lam[near], rtol=1e-11)
+    w = np.array([1.0, -0.5, 2.0, 0.25])
+    order = np.argsort(ev)          # weights attach to the eigenvalues sorted ascending
+    vs = vecs[:, torch.from_numpy(order).cuda()].contiguous()
+    g = plhr.eigval_grad(vs, w).cpu().numpy()
+    ref = (Y[:, near] ** 2) @ w
+    assert np.abs(g - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_gradient_matches_finite_differences_of_gpu_eigenvalues(plhr):
+    """Central differences of the GPU eigenvalues at sampled grid points agree
+    with the Hellmann-Feynman gradient to 1e-5 relative."""
+    p, sigma, lam, Y, near = _problem()
+    k = p["k"]
+    V = p["V"]
+    eps = 1e-4 * np.abs(V).max()
+
+    def eig(Vn):
+        op = plhr.Operator.hamiltonian(p["dims"], 1.0, torch.from_numpy(Vn).cuda())
+        ev, vecs, info = plhr.solve(op, sigma, k, tol=1e-12, maxit=6000, guard=2)
+        assert info["converged"]
+        o = np.argsort(ev)
+        return ev[o], vecs[:, torch.from_numpy(o).cuda()].contiguous()
+
+    ev0, vecs0 = eig(V)
+    w = np.ones(k)
+    grads = [plhr.eigval_grad(vecs0[:, j:j + 1].contiguous(), [1.0]).cpu().numpy() for j in range(k)]
+    rng = np.random.default_rng(5)
+    for i in rng.choice(V.size, 4, replace=False):
+        e = np.zeros_like(V); e[i] = eps
+        lp, _ = eig(V + e)
+        lm, _ = eig(V - e)
+        fd = (lp - lm) / (2 * eps)
+        an = np.array([grads[j][i] for j in range(k)])
+        assert np.allclose(fd, an, rtol=1e-5, atol=1e-7 * np.abs(an).max()), (i, fd, an)
+
+
+def test_autograd_function_backward(plhr):
+    p, sigma, lam, Y, near = _problem()
+    V = torch.from_numpy(p["V"]).cuda().requires_grad_(True)
+    ev = plhr.hamiltonian_eigvals(V, p["dims"], 1.0, sigma, p["k"], tol=1e-11, maxit=6000, guard=2)
+    w = torch.tensor([0.5, 1.5, -1.0, 2.0], dtype=torch.float64, device="cuda")
+    loss = (w * torch.sort(ev).values).sum()
+    loss.backward()
+    order = np.argsort(ev.detach().cpu().numpy())
+    ref = (Y[:, near] ** 2) @ w.cpu().numpy()
+    # the sort above maps w to ascending eigenvalues, as near[] is ascending
+    assert np.abs(V.grad.cpu().numpy() - ref).max() <= 1e-9 * np.abs(ref).max()
+    assert order.shape == (p["k"],)
+
+
+def test_mixed_precision_rejects_hamiltonian(plhr):
+    p, sigma, lam, Y, near = _problem()
+    op = plhr.Operator.hamiltonian(p["dims"], 1.0, torch.from_numpy(p["V"]).cuda())
+    with pytest.raises(plhr.PlhrError):
+        plhr.solve(op, sigma, p["k"], precision=plhr.PRECISION_MIXED)

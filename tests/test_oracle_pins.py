@@ -333,3 +333,43 @@ def test_complex_hermitian_problem_matches_dense():
     assert np.allclose(np.sort(r.eigvals), np.sort(ref), rtol=1e-10)
     V = r.eigvecs
     assert np.abs(V.conj().T @ V - np.eye(k)).max() <= 1e-12
+
+
+# ---------------------------------------------------------------- Hamiltonian and its gradient
+
+def test_periodic_hamiltonian_free_particle_closed_form():
+    """V = 0, periodic, h = 1: eigenvalues sum_d (1 - cos(2 pi m_d / N_d))."""
+    from oracle import operators as ops
+    dims = (5, 4, 3)
+    H = ops.hamiltonian(dims, 1.0, np.zeros(int(np.prod(dims))), periodic=True).toarray()
+    lam = np.sort(np.linalg.eigvalsh(H))
+    ms = [np.arange(N) for N in dims]
+    cf = sum(np.meshgrid(*[1.0 - np.cos(2 * np.pi * m / N) for m, N in zip(ms, dims)], indexing="ij"))
+    assert np.allclose(lam, np.sort(cf.ravel()), atol=1e-12)
+
+
+def test_dirichlet_hamiltonian_constant_potential_shifts_half_laplacian():
+    from oracle import operators as ops
+    dims, h, c = (6, 5), 0.2, -1.75
+    H = ops.hamiltonian(dims, h, np.full(30, c), periodic=False).toarray()
+    L = ops.laplacian_dirichlet(dims, h).toarray()
+    assert np.allclose(np.linalg.eigvalsh(H), 0.5 * np.linalg.eigvalsh(L) + c, atol=1e-10)
+
+
+def test_hellmann_feynman_gradient_matches_finite_differences():
+    """d lambda_k / d V_i = v_k(i)^2 for a normalised eigenvector of a simple
+    eigenvalue: checked against central differences of dense eigenvalues."""
+    from oracle import operators as ops
+    p = wl.hamiltonian_small(4, 3, dim=3)
+    dims, V = p["dims"], p["V"]
+    lam, Y = np.linalg.eigh(ops.hamiltonian(dims, 1.0, V).toarray())
+    ks = [10, 11, 30]
+    assert np.min(np.abs(np.diff(lam[min(ks) - 1:max(ks) + 2]))) > 1e-6   # simple eigenvalues
+    eps = 1e-5
+    for i in (0, 17, 40):
+        e = np.zeros_like(V); e[i] = eps
+        lp = np.linalg.eigvalsh(ops.hamiltonian(dims, 1.0, V + e).toarray())
+        lm = np.linalg.eigvalsh(ops.hamiltonian(dims, 1.0, V - e).toarray())
+        for k in ks:
+            fd = (lp[k] - lm[k]) / (2 * eps)
+            assert abs(fd - Y[i, k] ** 2) <= 1e-8, (i, k, fd, Y[i, k] ** 2)

@@ -176,3 +176,42 @@ def _clean_shift(lam: np.ndarray, target: int, k: int) -> float:
 
 
 CONFIGS = {"config1": config1, "config2": config2}
+
+
+def gaussian_potential(dims, nwells: int, seed: int, depth=(-4.0, -1.0), width=(0.5, 1.5)) -> np.ndarray:
+    """Seeded potential on a periodic grid with unit spacing (x fastest):
+    V(x) = sum_j d_j exp(-|x - c_j|^2 / (2 w_j^2)) with minimum-image
+    distances, centres uniform in the box, depths d_j and widths w_j uniform in
+    the given ranges (grid units).  The well draws come from one SplitMix64
+    stream: per well (c_x, c_y[, c_z], d, w)."""
+    dims = tuple(dims)
+    nd = len(dims)
+    u = uniform_block(nwells, nd + 2, seed) + 0.5          # uniform [0, 1)
+    axes = [np.arange(N, dtype=np.float64) for N in dims]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]   # x fastest when raveled
+    V = np.zeros(grids[0].shape)
+    for j in range(nwells):
+        r2 = np.zeros_like(V)
+        for a, N in enumerate(dims):
+            c = u[j, a] * N
+            dx = np.abs(grids[a] - c)
+            dx = np.minimum(dx, N - dx)
+            r2 += dx * dx
+        d = depth[0] + (depth[1] - depth[0]) * u[j, nd]
+        w = width[0] + (width[1] - width[0]) * u[j, nd + 1]
+        V += d * np.exp(-r2 / (2.0 * w * w))
+    return V.ravel()
+
+
+def hamiltonian_small(N: int = 10, nwells: int = 6, k: int = 4, seed: int = SEED_BASE + 5, dim: int = 3):
+    """Differentiation test problem: H(V) = -1/2 Lap + V on an N^dim periodic
+    grid (h = 1) with a seeded Gaussian-well potential (the structure of the
+    64^3, 32-well workload at a size a dense eigensolver finishes quickly)."""
+    dims = (N,) * dim
+    return {"dims": dims, "h": 1.0, "V": gaussian_potential(dims, nwells, seed), "k": k, "seed": seed}
+
+
+def config5_potential():
+    """64^3 periodic grid, 32 seeded Gaussian wells (h = 1)."""
+    dims = (64, 64, 64)
+    return dims, gaussian_potential(dims, 32, SEED_BASE + 5)
