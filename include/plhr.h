@@ -112,8 +112,9 @@ typedef struct {
 typedef struct plhr_prec plhr_prec;
 
 void plhr_mg_opts_default(plhr_mg_opts* o);
-/* Build the hierarchy for the stencil operator A (LAP5_2D or LAP7_3D; every
- * axis size divisible by 2^(levels-1)).  opts NULL = defaults. */
+/* Build the hierarchy for the stencil operator A (LAP5_2D or LAP7_3D from
+ * plhr_op_stencil, Dirichlet; every axis size divisible by 2^(levels-1);
+ * PLHR_EINVAL for a Hamiltonian operator).  opts NULL = defaults. */
 plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma,
                            const plhr_mg_opts* opts);
 void plhr_prec_destroy(plhr_prec* T);
@@ -184,6 +185,30 @@ void plhr_options_default(plhr_options* o);
  * perturbation theory (Hellmann-Feynman), d lambda_k / d V_i = v_k(i)^2. */
 plhr_status plhr_eigval_grad(int64_t n, int k, const double* V, int64_t ldv, const double* weights, double* g,
                              void* stream);
+
+/* Gradient with respect to the potential of a loss L on the eigenvectors of
+ * a Hamiltonian operator A (plhr_op_hamiltonian; B = I): given k
+ * orthonormal eigenvectors V (device n x k, leading dimension ldv >= k, as
+ * plhr_solve returns them), their eigenvalues lam (HOST, k values) and
+ * G = dL/dV (device n x k, leading dimension ldg >= k), first-order
+ * perturbation theory gives
+ *     grad (device, n) = sum_c V(:,c) .* b_c,
+ *     b_c = sum_{j != c} V(:,j) (V(:,j)^T G(:,c)) / (lam_c - lam_j) - a_c,
+ * where a_c solves (A - lam_c I) a_c = P G(:,c) on the orthogonal
+ * complement of the block (P = I - V V^T).  The k systems are solved
+ * together by MINRES on P (A - lam_c I) P, unpreconditioned, to relative
+ * residual tol (at most maxit iterations; the count taken is written to
+ * *iterations when non-null).  Pairs with |lam_c - lam_j| <= 1e-12 max(1,
+ * |lam_0|) contribute no in-block term (a repeated eigenvalue has no
+ * eigenvector derivative inside its eigenspace).  1 <= k <= 16.  The call
+ * synchronises the stream (it reads two inner products per iteration) and
+ * allocates its own device workspace (9 n x k doubles).  PLHR_EINVAL on bad
+ * arguments, PLHR_ENOMEM when the workspace cannot be allocated, PLHR_ENAN
+ * on a non-finite inner product, PLHR_ENOTCONV when maxit is reached (grad
+ * then holds the result of the last iterate). */
+plhr_status plhr_eigvec_adjoint(const plhr_op* A, int k, const double* lam, const double* V, int64_t ldv,
+                                const double* G, int64_t ldg, double tol, int maxit, double* grad,
+                                int* iterations, void* stream);
 
 /* Compute the k eigenpairs of A v = lambda B v nearest sigma.
  *   B        NULL = identity.

@@ -13,4 +13,6 @@ Modules:
   operators  - finite-difference and finite-element model operators
   avmg       - the absolute-value multigrid preconditioner (Appendix A, Alg. 4)
   plhr       - block PLHR (Section 4, Alg. 2 and Alg. 3)
+  grad       - potential gradients of eigenvalues and eigenvector losses
+                 of H(V) = -1/2 Lap + diag(V) (dense perturbation formulas)
 """

@@ -60,6 +60,10 @@ _SIGS = {
                                            ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
     "plhr_eigval_grad": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "plhr_eigvec_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                           ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.c_void_p]),
     "plhr_op_destroy": (None, [ctypes.c_void_p]),
     "plhr_op_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
@@ -379,6 +383,32 @@ def eigval_grad(vecs, weights, stream=None):
     return g
 
 
+def eigvec_adjoint(op, lam, vecs, G, tol=1e-12, maxit=None, stream=None, return_iterations=False):
+    """dL/dV (device, n) of a loss L on the orthonormal eigenvectors vecs
+    (n x k float64 CUDA, eigenvalues lam) of a Hamiltonian operator, given
+    G = dL/dvecs (n x k float64 CUDA): first-order perturbation theory with
+    the component outside the block from MINRES on P (H - lam_c) P."""
+    import torch
+    for name, t in (("vecs", vecs), ("G", G)):
+        if t.dtype != torch.float64 or not t.is_cuda or t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError(name + " must be a row-major float64 CUDA block")
+    if G.shape != vecs.shape:
+        raise ValueError("G must have the shape of vecs")
+    lam = np.ascontiguousarray(np.asarray(lam, dtype=np.float64).ravel())
+    if lam.size != vecs.shape[1]:
+        raise ValueError("one eigenvalue per eigenvector")
+    n = vecs.shape[0]
+    if maxit is None:
+        maxit = max(1000, min(20000, 2 * n))
+    g = torch.empty(n, dtype=torch.float64, device=vecs.device)
+    its = ctypes.c_int(0)
+    _check(load_library().plhr_eigvec_adjoint(op._h, vecs.shape[1], lam.ctypes.data, ctypes.c_void_p(vecs.data_ptr()),
+                                              vecs.stride(0), ctypes.c_void_p(G.data_ptr()), G.stride(0), tol,
+                                              int(maxit), ctypes.c_void_p(g.data_ptr()), ctypes.byref(its),
+                                              _stream_ptr(stream)), "plhr_eigvec_adjoint")
+    return (g, its.value) if return_iterations else g
+
+
 def _hamiltonian_eig_class():
     import torch
 
@@ -402,6 +432,47 @@ def _hamiltonian_eig_class():
             return (g.reshape(ctx.vshape),) + (None,) * 9
 
     return HamiltonianEig
+
+
+def _hamiltonian_eigh_class():
+    import torch
+
+    class HamiltonianEigh(torch.autograd.Function):
+        """(lambda, vecs): the k eigenpairs nearest sigma of H(V) = -1/2 Lap +
+        diag(V); backward gives dL/dV = sum_k (dL/dlambda_k) v_k^2 plus the
+        eigenvector adjoint term of dL/dvecs, both on the device."""
+
+        @staticmethod
+        def forward(ctx, V, dims, h, periodic, sigma, k, tol, maxit, guard, T, adj_tol):
+            Vf = V.detach().reshape(-1).contiguous()
+            op = Operator.hamiltonian(dims, h, Vf, periodic)
+            lam, vecs, info = solve(op, sigma, k, T=T, tol=tol, maxit=maxit, guard=guard, raise_on_notconv=True)
+            ctx.save_for_backward(Vf, vecs)
+            ctx.lam = lam
+            ctx.meta = (ctx.needs_input_grad, V.shape, tuple(dims), h, periodic, adj_tol)
+            return torch.from_numpy(lam).to(V.device), vecs
+
+        @staticmethod
+        def backward(ctx, glam, gvecs):
+            Vf, vecs = ctx.saved_tensors
+            _, vshape, dims, h, periodic, adj_tol = ctx.meta
+            g = torch.zeros(Vf.shape[0], dtype=torch.float64, device=Vf.device)
+            if glam is not None:
+                g += eigval_grad(vecs, glam.detach().cpu().numpy())
+            if gvecs is not None:
+                op = Operator.hamiltonian(dims, h, Vf, periodic)
+                g += eigvec_adjoint(op, ctx.lam, vecs, gvecs.detach().contiguous(), tol=adj_tol)
+            return (g.reshape(vshape),) + (None,) * 10
+
+    return HamiltonianEigh
+
+
+def hamiltonian_eigh(V, dims, h, sigma, k, periodic=True, tol=1e-10, maxit=5000, guard=2, T=None, adj_tol=1e-12):
+    """Differentiable k eigenpairs (lambda, vecs) nearest sigma of
+    H(V) = -1/2 Lap + diag(V).  Losses on vecs should not depend on the sign
+    of each eigenvector (densities, |v|^2 weights), which the solver does not
+    fix."""
+    return _hamiltonian_eigh_class().apply(V, tuple(dims), h, periodic, sigma, k, tol, maxit, guard, T, adj_tol)
 
 
 def hamiltonian_eigvals(V, dims, h, sigma, k, periodic=True, tol=1e-10, maxit=5000, guard=2, T=None):

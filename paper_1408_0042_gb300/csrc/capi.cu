@@ -145,6 +145,11 @@ plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma, cons
         return PLHR_EINVAL;
     }
     const Grid& g = A->g;
+    if (!g.plain()) {
+        // the level operators are rediscretised Dirichlet Laplacians
+        set_error("plhr_prec_avmg: A must be a Dirichlet Laplacian (plhr_op_stencil)");
+        return PLHR_EINVAL;
+    }
     const int64_t f = (int64_t)1 << (o.levels - 1);
     if (g.nx % f || g.ny % f || (g.d == 3 && g.nz % f)) {
         set_error("plhr_prec_avmg: axis sizes must be divisible by 2^(levels-1) = %lld", (long long)f);

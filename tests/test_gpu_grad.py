@@ -117,3 +117,98 @@ def test_mixed_precision_rejects_hamiltonian(plhr):
     op = plhr.Operator.hamiltonian(p["dims"], 1.0, torch.from_numpy(p["V"]).cuda())
     with pytest.raises(plhr.PlhrError):
         plhr.solve(op, sigma, p["k"], precision=plhr.PRECISION_MIXED)
+
+
+# ---------------------------------------------------------------- eigenvector adjoint
+
+def _density_loss_grad(vecs_np, m):
+    """L = sum_c sum_i m_i v_c(i)^2 and G = dL/dv (sign invariant loss)."""
+    return float(np.sum(m[:, None] * vecs_np ** 2)), 2.0 * m[:, None] * vecs_np
+
+
+def test_eigvec_adjoint_matches_dense_reference(plhr):
+    from oracle import grad as og
+    p, sigma, lam, Y, near = _problem()
+    k = p["k"]
+    op = plhr.Operator.hamiltonian(p["dims"], 1.0, torch.from_numpy(p["V"]).cuda())
+    ev, vecs, info = plhr.solve(op, sigma, k, tol=1e-12, maxit=6000, guard=2)
+    assert info["converged"]
+    m = wl.uniform_block(p["V"].size, 1, 41).ravel() ** 2 + 0.1
+    _, G = _density_loss_grad(vecs.cpu().numpy(), m)
+    g, its = plhr.eigvec_adjoint(op, ev, vecs, torch.from_numpy(G).cuda(), tol=1e-13, return_iterations=True)
+    H = oops.hamiltonian(p["dims"], 1.0, p["V"]).toarray()
+    _, Gref = _density_loss_grad(Y[:, near], m)
+    ref, _, _ = og.eigvec_grad(H, list(near), Gref)
+    g = g.cpu().numpy()
+    assert 0 < its < 20000
+    assert np.abs(g - ref).max() <= 1e-8 * np.abs(ref).max(), (np.abs(g - ref).max(), np.abs(ref).max())
+
+
+def test_eigvec_adjoint_single_vector_and_degenerate_inputs(plhr):
+    """k = 1 (no in-block term); a zero G gives a zero gradient after no
+    iterations; G = v (the norm) gives zero; k > 16 is rejected."""
+    from oracle import grad as og
+    p, _, lam, Y, near4 = _problem()
+    c = int(near4[1])
+    # a shift close to one eigenvalue (a midpoint would tie two of them)
+    sigma = lam[c] + 0.1 * min(lam[c + 1] - lam[c], lam[c] - lam[c - 1])
+    near = [c]
+    op = plhr.Operator.hamiltonian(p["dims"], 1.0, torch.from_numpy(p["V"]).cuda())
+    ev, vecs, info = plhr.solve(op, sigma, 1, tol=1e-12, maxit=6000, guard=2)
+    assert info["converged"]
+    m = wl.uniform_block(p["V"].size, 1, 43).ravel() + 1.0
+    _, G = _density_loss_grad(vecs.cpu().numpy(), m)
+    g = plhr.eigvec_adjoint(op, ev, vecs, torch.from_numpy(G).cuda(), tol=1e-13).cpu().numpy()
+    H = oops.hamiltonian(p["dims"], 1.0, p["V"]).toarray()
+    _, Gref = _density_loss_grad(Y[:, near], m)
+    ref, _, _ = og.eigvec_grad(H, list(near), Gref)
+    assert np.abs(g - ref).max() <= 1e-8 * np.abs(ref).max()
+    z, its = plhr.eigvec_adjoint(op, ev, vecs, torch.zeros_like(vecs), return_iterations=True)
+    assert its == 0 and float(z.abs().max()) == 0.0
+    gn = plhr.eigvec_adjoint(op, ev, vecs, vecs.clone(), tol=1e-13).cpu().numpy()
+    assert np.abs(gn).max() <= 1e-10
+    big = torch.zeros(vecs.shape[0], 17, dtype=torch.float64, device="cuda")
+    with pytest.raises(plhr.PlhrError):
+        plhr.eigvec_adjoint(op, np.arange(17.0), big, big)
+
+
+def test_eigvec_adjoint_matches_finite_differences_of_gpu_eigenvectors(plhr):
+    p, sigma, lam, Y, near = _problem()
+    k = p["k"]
+    V = p["V"]
+    m = wl.uniform_block(V.size, 1, 45).ravel() ** 2 + 0.1
+    eps = 1e-4 * np.abs(V).max()
+
+    def loss(Vn):
+        op = plhr.Operator.hamiltonian(p["dims"], 1.0, torch.from_numpy(Vn).cuda())
+        ev, vecs, info = plhr.solve(op, sigma, k, tol=1e-13, maxit=8000, guard=2)
+        assert info["converged"]
+        L, G = _density_loss_grad(vecs.cpu().numpy(), m)
+        return L, op, ev, vecs, G
+
+    L0, op, ev, vecs, G = loss(V)
+    g = plhr.eigvec_adjoint(op, ev, vecs, torch.from_numpy(G).cuda(), tol=1e-13).cpu().numpy()
+    rng = np.random.default_rng(9)
+    for i in rng.choice(V.size, 4, replace=False):
+        e = np.zeros_like(V); e[i] = eps
+        fd = (loss(V + e)[0] - loss(V - e)[0]) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-4 * abs(g[i]) + 1e-6 * np.abs(g).max(), (i, fd, g[i])
+
+
+def test_eigh_autograd_backward(plhr):
+    """Loss on eigenvalues and eigenvector densities together: V.grad equals
+    the Hellmann-Feynman term plus the dense eigenvector-gradient formula."""
+    from oracle import grad as og
+    p, sigma, lam, Y, near = _problem()
+    V = torch.from_numpy(p["V"]).cuda().requires_grad_(True)
+    ev, vecs = plhr.hamiltonian_eigh(V, p["dims"], 1.0, sigma, p["k"], tol=1e-12, maxit=6000, guard=2)
+    m = torch.from_numpy(wl.uniform_block(p["V"].size, 1, 47).ravel() ** 2 + 0.1).cuda()
+    o = torch.argsort(ev)
+    w = torch.tensor([0.5, 1.5, -1.0, 2.0], dtype=torch.float64, device="cuda")
+    loss = (w * ev[o]).sum() + (m[:, None] * vecs ** 2).sum()
+    loss.backward()
+    H = oops.hamiltonian(p["dims"], 1.0, p["V"]).toarray()
+    _, Gref = _density_loss_grad(Y[:, near], m.cpu().numpy())
+    ref, _, _ = og.eigvec_grad(H, list(near), Gref)
+    ref = ref + og.eigval_grad(Y[:, near], w.cpu().numpy())
+    assert np.abs(V.grad.cpu().numpy() - ref).max() <= 1e-8 * np.abs(ref).max()

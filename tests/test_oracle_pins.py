@@ -373,3 +373,60 @@ def test_hellmann_feynman_gradient_matches_finite_differences():
         for k in ks:
             fd = (lp[k] - lm[k]) / (2 * eps)
             assert abs(fd - Y[i, k] ** 2) <= 1e-8, (i, k, fd, Y[i, k] ** 2)
+
+
+def _eigvec_loss(H, idx, m, p):
+    """L = sum_c sum_i m_i |y_c(i)|^p (sign invariant) and G = dL/dY."""
+    lam, Y = np.linalg.eigh(H)
+    Yc = Y[:, idx]
+    L = float(np.sum(m[:, None] * np.abs(Yc) ** p))
+    G = p * m[:, None] * np.abs(Yc) ** (p - 1) * np.sign(Yc)
+    return L, G
+
+
+def test_eigvec_gradient_matches_finite_differences():
+    """The dense eigenvector-gradient formula against central differences of
+    sign-invariant losses (a quadratic and a quartic density weight) on a 4^3
+    periodic Hamiltonian, for three eigenvectors with simple eigenvalues."""
+    from oracle import grad as og
+    from oracle import operators as ops
+    p = wl.hamiltonian_small(4, 3, dim=3)
+    dims, V = p["dims"], p["V"]
+    H = ops.hamiltonian(dims, 1.0, V).toarray()
+    lam = np.linalg.eigvalsh(H)
+    idx = [10, 11, 30]
+    assert np.min(np.abs(np.diff(lam[min(idx) - 1:max(idx) + 2]))) > 1e-6
+    m = wl.uniform_block(V.size, 1, 77).ravel() ** 2 + 0.1
+    eps = 1e-5
+    for power in (2, 4):
+        _, G = _eigvec_loss(H, idx, m, power)
+        g, _, _ = og.eigvec_grad(H, idx, G)
+        for i in (0, 17, 40, 63):
+            e = np.zeros_like(V); e[i] = eps
+            Lp, _ = _eigvec_loss(ops.hamiltonian(dims, 1.0, V + e).toarray(), idx, m, power)
+            Lm, _ = _eigvec_loss(ops.hamiltonian(dims, 1.0, V - e).toarray(), idx, m, power)
+            fd = (Lp - Lm) / (2 * eps)
+            assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i])), (power, i, fd, g[i])
+
+
+def test_eigvec_gradient_of_norm_is_zero_and_second_derivative_symmetric():
+    """Two facts independent of finite differences: (1) L = 1/2 |y_c|^2 is
+    constant under any perturbation, so its gradient vanishes; (2) with
+    L = y_c(l)^2 = d lambda_c / d V_l the gradient at i is the mixed second
+    derivative d^2 lambda_c / dV_i dV_l, symmetric in (i, l)."""
+    from oracle import grad as og
+    from oracle import operators as ops
+    p = wl.hamiltonian_small(4, 3, dim=3)
+    H = ops.hamiltonian(p["dims"], 1.0, p["V"]).toarray()
+    lam, Y = np.linalg.eigh(H)
+    c = 11
+    g, _, _ = og.eigvec_grad(H, [c], Y[:, [c]])
+    assert np.abs(g).max() <= 1e-12
+    n = H.shape[0]
+    hess = np.zeros((n, n))
+    for l in range(n):
+        G = np.zeros((n, 1)); G[l, 0] = 2.0 * Y[l, c]
+        hess[:, l], _, _ = og.eigvec_grad(H, [c], G)
+    assert np.abs(hess - hess.T).max() <= 1e-10 * np.abs(hess).max()
+    # and the row sums vanish: a constant shift of V moves no eigenvector
+    assert np.abs(hess.sum(axis=0)).max() <= 1e-10 * np.abs(hess).max()
