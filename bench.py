@@ -363,7 +363,174 @@ def cpu_baseline(gpu_iterations):
                       "scaled by the GPU iteration count %d" % (per, total, gpu_iterations)}
 
 
-def run_reference(args, world, rank, local):
+GRAD_METRIC = ("seconds per forward + backward: k = 8 eigenpairs nearest sigma and dL/dV of "
+               "sum_k w_k lambda_k + sum_k |m (.) v_k|^2, 64^3 Hamiltonian")
+
+
+def run_grad(args, world, rank, local):
+    """The differentiation workload: a step is the forward solve (TPA-
+    preconditioned block PLHR, FP64, tol 1e-10) plus the backward pass
+    (eigenvalue gradient and the eigenvector adjoint) for one potential."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1408_0042_gb300 as plhr
+    import workloads as wl
+
+    torch.cuda.set_device(local)
+    c = wl.config5()
+    dims, sigma, k = c["dims"], c["sigma"], c["k"]
+    n = int(np.prod(dims))
+    guard, tol, adj_tol = 2, 1e-10, 1e-10
+    kp = k + guard
+    V_host = torch.from_numpy(c["V"]).pin_memory()
+    Vd = V_host.cuda()
+    v0 = torch.from_numpy(wl.start_block(n, kp, c["seed"])).cuda()
+    wt = torch.from_numpy(c["w"]).cuda()
+    mt = torch.from_numpy(c["mask"]).cuda()
+    adj_prec = args.adjoint_prec
+
+    def step(Vdev):
+        op = plhr.Operator.hamiltonian(dims, 1.0, Vdev)
+        T = plhr.TPA(op, sigma)
+        lam, vecs, info = plhr.solve(op, sigma, k, T=T, tol=tol, maxit=2000, guard=guard, v_init=v0,
+                                     raise_on_notconv=True)
+        order = np.argsort(lam)                      # w attaches to the eigenvalues in ascending order
+        wk = np.empty(k)
+        wk[order] = c["w"]
+        g = plhr.eigval_grad(vecs, wk)
+        G = (2.0 * mt[:, None] * vecs).contiguous()  # dL/dv_k of the density term
+        ga, its = plhr.eigvec_adjoint(op, lam, vecs, G, tol=adj_tol, T=T if adj_prec == "tpa" else None,
+                                      return_iterations=True)
+        g += ga
+        loss = float(np.dot(wk, lam)) + float((mt[:, None] * vecs * vecs).sum())
+        return g, lam, info, its, loss
+
+    def timed_parts(Vdev):
+        # forward and backward times of one step (CUDA events on the stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        op = plhr.Operator.hamiltonian(dims, 1.0, Vdev)
+        T = plhr.TPA(op, sigma)
+        lam, vecs, info = plhr.solve(op, sigma, k, T=T, tol=tol, maxit=2000, guard=guard, v_init=v0)
+        ev[1].record(stream)
+        G = (2.0 * mt[:, None] * vecs).contiguous()
+        plhr.eigval_grad(vecs, np.ones(k))
+        plhr.eigvec_adjoint(op, lam, vecs, G, tol=adj_tol, T=T if adj_prec == "tpa" else None)
+        ev[2].record(stream)
+        ev[2].synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+
+    for _ in range(args.warmup):
+        step(Vd)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    plhr.profile_read(reset=True)
+    plhr.profile_enable(True)
+    launches0 = plhr.kernel_launches()
+    times = []
+    with ClockSampler(local) as clk:
+        _barrier(world)
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g, lam, info, its, loss = step(Vd)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+        _barrier(world)
+    launches = plhr.kernel_launches() - launches0
+    plhr.profile_enable(False)
+    prof = plhr.profile_read(reset=True)
+    clocks = clk.summary()
+    step_s = _max_over_ranks(statistics.mean(times), world)
+
+    fwd_s, bwd_s = timed_parts(Vd)
+    # check of the answer: the 8 nearest eigenvalues from a Lanczos solve of
+    # the oracle's operator (workloads/select_shift_ham64.py)
+    lam_ref = np.array(wl.HAM64_LAMBDA_REF)
+    eig_err = float(np.abs(np.sort(lam) - lam_ref).max())
+
+    # end to end: V from pinned host memory, the gradient back to the host
+    g_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Vdev = V_host.to("cuda", non_blocking=True)
+        g2, _, _, _, _ = step(Vdev)
+        g_host.copy_(g2, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = _max_over_ranks(statistics.mean(e2e), world)
+
+    # rooflines of the phases the library times; the TPA application is FP64
+    # dense per-axis transforms: 2 (forward, inverse) x 2 flops x (nx + ny + nz)
+    # per element (grid point x column)
+    fp64 = FP64_PEAK_TFLOPS
+    per_elem = 4.0 * sum(dims)
+    roofs = []
+    for ph, kernel, per in (("preconditioner", "k_axis (TPA transforms, FP64)", per_elem * 1e-12),
+                            ("gram", "k_gram (FP64 multi-Gram)", 1e-12),
+                            ("update", "k_update (FP64)", 1e-12)):
+        d = prof.get(ph)
+        if not d or d["ms"] <= 0 or d["work"] <= 0:
+            continue
+        a = d["work"] * per / (d["ms"] / 1e3)
+        roofs.append({"phase": ph, "kernel": kernel, "bound": "alu", "achieved": a, "peak": fp64, "unit": "TFLOP/s",
+                      "frac": a / fp64, "total_ms": d["ms"], "calls": d["calls"], "traffic": None,
+                      "peak_src": "nominal FP64 rate of the profiling recipe"})
+    roofs.sort(key=lambda r: -r["total_ms"])
+    out = {
+        "metric": GRAD_METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded potential and start block)",
+        "config": {"workload": "ham64_k8_grad", "operator": "-1/2 Lap + V, 64^3 periodic, h = 1, 32 Gaussian wells",
+                   "n": n, "k": k, "k_prime": kp, "sigma": sigma, "tol": tol, "adjoint_tol": adj_tol,
+                   "preconditioner": "TPA (forward)" + (", TPA (adjoint)" if adj_prec == "tpa" else ""),
+                   "l2": "inputs larger than L2 (the 9 n x k adjoint blocks and the 64 n x k' trial blocks)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iterations": info["iterations"], "adjoint_iterations": its, "max_rel_residual": info["max_rel_residual"],
+        "max_abs_eig_err_vs_lanczos": eig_err, "forward_s": fwd_s, "backward_s": bwd_s, "loss": loss,
+        "phases_ms_per_step": {p: prof[p]["ms"] / max(1, args.steps) for p in prof},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
+        "gpu_launches": launches, "roofline": roofs[0] if roofs else None, "rooflines": roofs[1:],
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = grad_cpu_baseline(info["iterations"])
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def grad_cpu_baseline(gpu_iterations):
+    """The oracle's forward solve of the 64^3 workload (TPA by FFT), one
+    iteration timed and scaled by the GPU iteration count.  The oracle's
+    adjoint is the full-spectrum formula (a dense eigendecomposition of the
+    262,144 x 262,144 operator), so the backward pass has no CPU baseline."""
+    import numpy as np
+
+    import workloads as wl
+    from oracle import operators, plhr, spectral
+
+    c = wl.config5()
+    H = operators.hamiltonian(c["dims"], 1.0, c["V"])
+    T = spectral.TPA(c["dims"], 1.0, spectral.default_energy(c["sigma"], c["V"], c["dims"], 1.0))
+    n = H.shape[0]
+    marks = []
+    t0 = time.perf_counter()
+    plhr.bplhr(H, None, T, c["sigma"], c["k"], wl.start_block(n, c["k"] + 2, c["seed"]), tol=1e-10, maxit=1,
+               callback=lambda rec: marks.append(time.perf_counter()))
+    per = (marks[-1] - marks[0]) / max(1, len(marks) - 1)
+    return {"value": per * gpu_iterations, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "1 oracle iteration of the forward solve (%.1f s/iteration, %.1f s with setup), scaled by "
+                      "the GPU iteration count %d; forward only" % (per, time.perf_counter() - t0, gpu_iterations)}
+
     if rank != 0:
         return
     import workloads as wl
@@ -402,6 +569,10 @@ def main():
     ap.add_argument("--profile-grid", type=int, default=0,
                     help="profiling case: N^3 grid of the same problem, fixed iteration count")
     ap.add_argument("--profile-iters", type=int, default=3)
+    ap.add_argument("--workload", choices=["lap3d_128cube_k10", "ham64_k8_grad"], default="lap3d_128cube_k10",
+                    help="ham64_k8_grad: forward + backward of the 64^3 differentiation workload")
+    ap.add_argument("--adjoint-prec", choices=["none", "tpa"], default="none",
+                    help="preconditioner of the adjoint MINRES in the ham64_k8_grad workload")
     args = ap.parse_args()
     world, rank, local = _dist()
     if world > 1 and args.impl == "ours":
@@ -412,6 +583,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, world, rank, local)
+        elif args.workload == "ham64_k8_grad":
+            run_grad(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

@@ -79,6 +79,17 @@ plhr_status plhr_op_stencil(plhr_op** out, const plhr_stencil_desc* desc);
  * plhr_op_apply and by plhr_solve in PLHR_PRECISION_F64. */
 plhr_status plhr_op_hamiltonian(plhr_op** out, int d, const int64_t* dims, double h, int periodic,
                                 const double* potential);
+/* A general sparse symmetric operator A (n x n, FP64) in CSR form: row i
+ * holds val[p] at column col[p] for rowptr[i] <= p < rowptr[i+1]
+ * (rowptr: n + 1 int64 values starting at 0; col: int32 in [0, n)).  The
+ * arrays are host memory, or device memory when is_device != 0; they are
+ * copied (the caller may free them afterwards) and the structure is checked
+ * on the host (PLHR_EINVAL on a decreasing rowptr or a column out of range).
+ * Symmetry is the caller's promise: it is not checked.  Usable by
+ * plhr_op_apply, plhr_solve (PLHR_PRECISION_F64) and plhr_eigvec_adjoint;
+ * not by AV-MG or TPA (use plhr_prec_diag, plhr_prec_callback or T = NULL). */
+plhr_status plhr_op_csr(plhr_op** out, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                        int is_device);
 int64_t plhr_op_size(const plhr_op* op);
 void plhr_op_destroy(plhr_op* op);
 
@@ -117,19 +128,49 @@ void plhr_mg_opts_default(plhr_mg_opts* o);
  * PLHR_EINVAL for a Hamiltonian operator).  opts NULL = defaults. */
 plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma,
                            const plhr_mg_opts* opts);
+/* The Teter-Payne-Allan preconditioner of Section 5.3 (Teter, Payne, Allan,
+ * Phys. Rev. B 40, 12255, 1989) on the grid of A: a positive diagonal matrix
+ * in the basis of the grid's kinetic modes,
+ *     T = S diag(K(mu / energy)) S^T,
+ *     K(x) = (27 + 18x + 12x^2 + 8x^3) / (27 + 18x + 12x^2 + 8x^3 + 16x^4),
+ * S the orthonormal eigenvectors of A's stencil part (real Fourier modes on
+ * a periodic grid, sine modes on a Dirichlet grid), mu their eigenvalues.  T
+ * is symmetric positive definite and the same for every column.  energy <= 0
+ * selects sigma - min(potential) when positive, else the mean of mu.  Any
+ * stencil or Hamiltonian operator whose axis sizes are at most 144; the
+ * potential is read once here.  Usable by plhr_solve (PLHR_PRECISION_F64),
+ * plhr_prec_apply and plhr_eigvec_adjoint. */
+plhr_status plhr_prec_tpa(plhr_prec** out, const plhr_op* A, double sigma, double energy);
+/* The reference energy a TPA preconditioner uses (0 for other kinds). */
+double plhr_prec_tpa_energy(const plhr_prec* T);
+/* T = diag(d) for n positive finite values d (host, or device when
+ * is_device != 0; copied, so the caller may free d afterwards).  PLHR_EINVAL
+ * when an entry is not positive and finite. */
+plhr_status plhr_prec_diag(plhr_prec** out, int64_t n, const double* d, int is_device);
+/* A caller-supplied preconditioner: the library calls
+ *     fn(ctx, ncols, R, ldr, W, ldw, stream)
+ * to form W = T R (device n x ncols blocks, row-major; W dense, ldw == ncols)
+ * on the solver's stream and continues only when it returns PLHR_OK (any
+ * other status ends the calling solve or apply with that status).  T must be
+ * symmetric positive definite and the same operator on every call (the
+ * T-harmonic images are carried by linear updates). */
+typedef plhr_status (*plhr_apply_fn)(void* ctx, int ncols, const double* R, int64_t ldr, double* W, int64_t ldw,
+                                     void* stream);
+plhr_status plhr_prec_callback(plhr_prec** out, int64_t n, plhr_apply_fn fn, void* ctx);
 void plhr_prec_destroy(plhr_prec* T);
 /* W = T R for an n x ncols block.  R and W must not overlap.  Uses device
  * workspace owned by T (grown on demand; calls on one T must not overlap). */
 plhr_status plhr_prec_apply(plhr_prec* T, int ncols, const double* R, int64_t ldr,
                             double* W, int64_t ldw, void* stream);
 /* The same V-cycle in FP32 storage and arithmetic (the form the mixed-precision
- * solve uses): W = T R for FP32 blocks.  Workspace as for plhr_prec_apply. */
+ * solve uses): W = T R for FP32 blocks.  Workspace as for plhr_prec_apply.
+ * AV-MG only (PLHR_EINVAL for a TPA preconditioner). */
 plhr_status plhr_prec_apply_f32(plhr_prec* T, int ncols, const float* R, int64_t ldr,
                                 float* W, int64_t ldw, void* stream);
 /* The same V-cycle with double-word storage and arithmetic (hi + lo FP32
  * pairs, ~48-bit significands, run on the FP32 pipes) on FP64 blocks: the
  * form the FP64 phase of the mixed-precision solve uses.  Same arguments,
- * workspace and overlap rules as plhr_prec_apply. */
+ * workspace and overlap rules as plhr_prec_apply.  AV-MG only. */
 plhr_status plhr_prec_apply_dw(plhr_prec* T, int ncols, const double* R, int64_t ldr,
                                double* W, int64_t ldw, void* stream);
 
@@ -196,9 +237,11 @@ plhr_status plhr_eigval_grad(int64_t n, int k, const double* V, int64_t ldv, con
  *     b_c = sum_{j != c} V(:,j) (V(:,j)^T G(:,c)) / (lam_c - lam_j) - a_c,
  * where a_c solves (A - lam_c I) a_c = P G(:,c) on the orthogonal
  * complement of the block (P = I - V V^T).  The k systems are solved
- * together by MINRES on P (A - lam_c I) P, unpreconditioned, to relative
- * residual tol (at most maxit iterations; the count taken is written to
- * *iterations when non-null).  Pairs with |lam_c - lam_j| <= 1e-12 max(1,
+ * together by MINRES on P (A - lam_c I) P, preconditioned by P T P when T is
+ * non-null (T symmetric positive definite: plhr_prec_tpa, or AV-MG for a
+ * Laplacian; its workspace grows to k columns), to relative residual tol in
+ * the preconditioned norm (at most maxit iterations; the count taken is
+ * written to *iterations when non-null).  Pairs with |lam_c - lam_j| <= 1e-12 max(1,
  * |lam_0|) contribute no in-block term (a repeated eigenvalue has no
  * eigenvector derivative inside its eigenspace).  1 <= k <= 16.  The call
  * synchronises the stream (it reads two inner products per iteration) and
@@ -206,13 +249,17 @@ plhr_status plhr_eigval_grad(int64_t n, int k, const double* V, int64_t ldv, con
  * arguments, PLHR_ENOMEM when the workspace cannot be allocated, PLHR_ENAN
  * on a non-finite inner product, PLHR_ENOTCONV when maxit is reached (grad
  * then holds the result of the last iterate). */
-plhr_status plhr_eigvec_adjoint(const plhr_op* A, int k, const double* lam, const double* V, int64_t ldv,
-                                const double* G, int64_t ldg, double tol, int maxit, double* grad,
+plhr_status plhr_eigvec_adjoint(const plhr_op* A, plhr_prec* T, int k, const double* lam, const double* V,
+                                int64_t ldv, const double* G, int64_t ldg, double tol, int maxit, double* grad,
                                 int* iterations, void* stream);
 
 /* Compute the k eigenpairs of A v = lambda B v nearest sigma.
+ *   A        stencil (plhr_op_stencil), Hamiltonian (plhr_op_hamiltonian) or
+ *            CSR (plhr_op_csr); PLHR_PRECISION_MIXED takes the Dirichlet
+ *            Laplacian with AV-MG or T = NULL only.
  *   B        NULL = identity.
- *   T        NULL = identity (no preconditioning).
+ *   T        NULL = identity (no preconditioning); AV-MG, TPA, diagonal or
+ *            callback, symmetric positive definite.
  *   tol      relative residual ||A v - lambda B v|| / (max(|lambda|, 1) ||B v||).
  *   eigvals  host, k doubles, ordered by |lambda - sigma| (ties: smaller first).
  *   eigvecs  device n x k block (ldv >= k), B-orthonormal Ritz vectors.

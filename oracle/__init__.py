@@ -13,6 +13,7 @@ Modules:
   operators  - finite-difference and finite-element model operators
   avmg       - the absolute-value multigrid preconditioner (Appendix A, Alg. 4)
   plhr       - block PLHR (Section 4, Alg. 2 and Alg. 3)
+  spectral   - the Teter-Payne-Allan preconditioner of Section 5.3 on a grid
   grad       - potential gradients of eigenvalues and eigenvector losses
                  of H(V) = -1/2 Lap + diag(V) (dense perturbation formulas)
 """

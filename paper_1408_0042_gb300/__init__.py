@@ -60,7 +60,16 @@ _SIGS = {
                                            ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
     "plhr_eigval_grad": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
-    "plhr_eigvec_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+    "plhr_prec_tpa": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_double,
+                                     ctypes.c_double]),
+    "plhr_prec_tpa_energy": (ctypes.c_double, [ctypes.c_void_p]),
+    "plhr_prec_diag": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int]),
+    "plhr_prec_callback": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    "plhr_op_csr": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_int]),
+    "plhr_eigvec_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p,
                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
                                            ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                            ctypes.c_void_p]),
@@ -169,6 +178,23 @@ class Operator:
         return cls(out, dims, h, scale)
 
     @classmethod
+    def csr(cls, A):
+        """A general sparse symmetric operator from a scipy sparse matrix (or
+        anything with .tocsr()); the arrays are copied to the device."""
+        lib = load_library()
+        A = A.tocsr()
+        n = A.shape[0]
+        if A.shape != (n, n):
+            raise ValueError("A must be square")
+        rowptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        col = np.ascontiguousarray(A.indices, dtype=np.int32)
+        val = np.ascontiguousarray(A.data, dtype=np.float64)
+        out = ctypes.c_void_p()
+        _check(lib.plhr_op_csr(ctypes.byref(out), n, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data, 0),
+               "plhr_op_csr")
+        return cls(out, (n,), 1.0, 1.0)
+
+    @classmethod
     def hamiltonian(cls, dims, h, potential, periodic=True):
         """H = -1/2 Lap + diag(V) (periodic or Dirichlet) with V a float64 CUDA
         tensor of prod(dims) values, x fastest; the operator keeps a reference."""
@@ -257,6 +283,112 @@ class AVMG:
         _check(load_library().plhr_prec_apply_f32(self._h, R.shape[1], ctypes.c_void_p(R.data_ptr()), R.stride(0),
                                                   ctypes.c_void_p(out.data_ptr()), out.stride(0),
                                                   _stream_ptr(stream)), "plhr_prec_apply_f32")
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.plhr_prec_destroy(self._h)
+            self._h = None
+
+
+class _PrecBase:
+    def apply(self, R, out=None, stream=None):
+        import torch
+        _check_block(R, self.n, "R")
+        if out is None:
+            out = torch.empty_like(R)
+        _check_block(out, self.n, "out")
+        _check(load_library().plhr_prec_apply(self._h, R.shape[1], ctypes.c_void_p(R.data_ptr()), R.stride(0),
+                                              ctypes.c_void_p(out.data_ptr()), out.stride(0), _stream_ptr(stream)),
+               "plhr_prec_apply")
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.plhr_prec_destroy(self._h)
+            self._h = None
+
+
+class DiagPrec(_PrecBase):
+    """T = diag(d) for positive d (numpy array or CUDA tensor, copied)."""
+
+    def __init__(self, d):
+        import torch
+        lib = load_library()
+        out = ctypes.c_void_p()
+        if isinstance(d, torch.Tensor) and d.is_cuda:
+            dd = d.detach().to(torch.float64).contiguous()
+            _check(lib.plhr_prec_diag(ctypes.byref(out), dd.numel(), ctypes.c_void_p(dd.data_ptr()), 1),
+                   "plhr_prec_diag")
+            self.n = dd.numel()
+        else:
+            dh = np.ascontiguousarray(np.asarray(d, dtype=np.float64).ravel())
+            _check(lib.plhr_prec_diag(ctypes.byref(out), dh.size, dh.ctypes.data, 0), "plhr_prec_diag")
+            self.n = dh.size
+        self._h = out
+
+
+_APPLY_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p)
+
+
+class _DeviceView:
+    """A CUDA array interface over a raw row-major float64 device block."""
+
+    def __init__(self, ptr, rows, cols, ld):
+        self.__cuda_array_interface__ = {"shape": (rows, cols), "typestr": "<f8", "data": (ptr, False),
+                                         "strides": (8 * ld, 8), "version": 2, "stream": None}
+
+
+class CallbackPrec(_PrecBase):
+    """A preconditioner given as a Python function fn(R, W) that writes T R
+    into W (n x c float64 CUDA tensors viewing the library's buffers) on the
+    current stream; T must be symmetric positive definite and fixed."""
+
+    def __init__(self, n, fn):
+        import torch
+        lib = load_library()
+
+        def tramp(ctx, ncols, R, ldr, W, ldw, stream):
+            try:
+                r = torch.as_tensor(_DeviceView(R, n, ncols, ldr), device="cuda")
+                w = torch.as_tensor(_DeviceView(W, n, ncols, ldw), device="cuda")
+                fn(r, w)
+                return PLHR_OK
+            except Exception:   # reported to the library as an invalid-argument failure
+                return PLHR_EINVAL
+
+        self._fn = _APPLY_FN(tramp)
+        out = ctypes.c_void_p()
+        _check(lib.plhr_prec_callback(ctypes.byref(out), n, ctypes.cast(self._fn, ctypes.c_void_p), None),
+               "plhr_prec_callback")
+        self._h = out
+        self.n = n
+
+
+class TPA:
+    """Teter-Payne-Allan preconditioner (Section 5.3) on the grid of A:
+    T = S diag(K(mu / energy)) S^T over the grid's kinetic modes; energy <= 0
+    takes sigma - min(potential) (or the mean kinetic energy)."""
+
+    def __init__(self, A: Operator, sigma: float, energy: float = 0.0):
+        lib = load_library()
+        out = ctypes.c_void_p()
+        _check(lib.plhr_prec_tpa(ctypes.byref(out), A._h, sigma, energy), "plhr_prec_tpa")
+        self._h = out
+        self.n = A.n
+        self.sigma = sigma
+        self.energy = lib.plhr_prec_tpa_energy(out)
+
+    def apply(self, R, out=None, stream=None):
+        import torch
+        _check_block(R, self.n, "R")
+        if out is None:
+            out = torch.empty_like(R)
+        _check_block(out, self.n, "out")
+        _check(load_library().plhr_prec_apply(self._h, R.shape[1], ctypes.c_void_p(R.data_ptr()), R.stride(0),
+                                              ctypes.c_void_p(out.data_ptr()), out.stride(0), _stream_ptr(stream)),
+               "plhr_prec_apply")
         return out
 
     def __del__(self):
@@ -383,11 +515,12 @@ def eigval_grad(vecs, weights, stream=None):
     return g
 
 
-def eigvec_adjoint(op, lam, vecs, G, tol=1e-12, maxit=None, stream=None, return_iterations=False):
+def eigvec_adjoint(op, lam, vecs, G, tol=1e-12, maxit=None, T=None, stream=None, return_iterations=False):
     """dL/dV (device, n) of a loss L on the orthonormal eigenvectors vecs
     (n x k float64 CUDA, eigenvalues lam) of a Hamiltonian operator, given
     G = dL/dvecs (n x k float64 CUDA): first-order perturbation theory with
-    the component outside the block from MINRES on P (H - lam_c) P."""
+    the component outside the block from MINRES on P (H - lam_c) P,
+    preconditioned by P T P when T (TPA or AV-MG) is given."""
     import torch
     for name, t in (("vecs", vecs), ("G", G)):
         if t.dtype != torch.float64 or not t.is_cuda or t.dim() != 2 or t.stride(1) != 1:
@@ -402,7 +535,8 @@ def eigvec_adjoint(op, lam, vecs, G, tol=1e-12, maxit=None, stream=None, return_
         maxit = max(1000, min(20000, 2 * n))
     g = torch.empty(n, dtype=torch.float64, device=vecs.device)
     its = ctypes.c_int(0)
-    _check(load_library().plhr_eigvec_adjoint(op._h, vecs.shape[1], lam.ctypes.data, ctypes.c_void_p(vecs.data_ptr()),
+    _check(load_library().plhr_eigvec_adjoint(op._h, T._h if T is not None else None, vecs.shape[1], lam.ctypes.data,
+                                              ctypes.c_void_p(vecs.data_ptr()),
                                               vecs.stride(0), ctypes.c_void_p(G.data_ptr()), G.stride(0), tol,
                                               int(maxit), ctypes.c_void_p(g.data_ptr()), ctypes.byref(its),
                                               _stream_ptr(stream)), "plhr_eigvec_adjoint")
@@ -443,36 +577,43 @@ def _hamiltonian_eigh_class():
         eigenvector adjoint term of dL/dvecs, both on the device."""
 
         @staticmethod
-        def forward(ctx, V, dims, h, periodic, sigma, k, tol, maxit, guard, T, adj_tol):
+        def forward(ctx, V, dims, h, periodic, sigma, k, tol, maxit, guard, prec, energy, adj_tol):
             Vf = V.detach().reshape(-1).contiguous()
             op = Operator.hamiltonian(dims, h, Vf, periodic)
+            T = TPA(op, sigma, energy) if prec == "tpa" else None
             lam, vecs, info = solve(op, sigma, k, T=T, tol=tol, maxit=maxit, guard=guard, raise_on_notconv=True)
             ctx.save_for_backward(Vf, vecs)
             ctx.lam = lam
-            ctx.meta = (ctx.needs_input_grad, V.shape, tuple(dims), h, periodic, adj_tol)
+            ctx.meta = (V.shape, tuple(dims), h, periodic, sigma, prec, energy, adj_tol)
             return torch.from_numpy(lam).to(V.device), vecs
 
         @staticmethod
         def backward(ctx, glam, gvecs):
             Vf, vecs = ctx.saved_tensors
-            _, vshape, dims, h, periodic, adj_tol = ctx.meta
+            vshape, dims, h, periodic, sigma, prec, energy, adj_tol = ctx.meta
             g = torch.zeros(Vf.shape[0], dtype=torch.float64, device=Vf.device)
             if glam is not None:
                 g += eigval_grad(vecs, glam.detach().cpu().numpy())
             if gvecs is not None:
                 op = Operator.hamiltonian(dims, h, Vf, periodic)
-                g += eigvec_adjoint(op, ctx.lam, vecs, gvecs.detach().contiguous(), tol=adj_tol)
-            return (g.reshape(vshape),) + (None,) * 10
+                T = TPA(op, sigma, energy) if prec == "tpa" else None
+                g += eigvec_adjoint(op, ctx.lam, vecs, gvecs.detach().contiguous(), tol=adj_tol, T=T)
+            return (g.reshape(vshape),) + (None,) * 11
 
     return HamiltonianEigh
 
 
-def hamiltonian_eigh(V, dims, h, sigma, k, periodic=True, tol=1e-10, maxit=5000, guard=2, T=None, adj_tol=1e-12):
+def hamiltonian_eigh(V, dims, h, sigma, k, periodic=True, tol=1e-10, maxit=5000, guard=2, prec=None, energy=0.0,
+                     adj_tol=1e-12):
     """Differentiable k eigenpairs (lambda, vecs) nearest sigma of
-    H(V) = -1/2 Lap + diag(V).  Losses on vecs should not depend on the sign
-    of each eigenvector (densities, |v|^2 weights), which the solver does not
-    fix."""
-    return _hamiltonian_eigh_class().apply(V, tuple(dims), h, periodic, sigma, k, tol, maxit, guard, T, adj_tol)
+    H(V) = -1/2 Lap + diag(V); prec="tpa" preconditions the forward solve and
+    the adjoint MINRES with the Teter-Payne-Allan T (energy <= 0: default).
+    Losses on vecs should not depend on the sign of each eigenvector
+    (densities, |v|^2 weights), which the solver does not fix."""
+    if prec not in (None, "tpa"):
+        raise ValueError("prec must be None or 'tpa'")
+    return _hamiltonian_eigh_class().apply(V, tuple(dims), h, periodic, sigma, k, tol, maxit, guard, prec, energy,
+                                           adj_tol)
 
 
 def hamiltonian_eigvals(V, dims, h, sigma, k, periodic=True, tol=1e-10, maxit=5000, guard=2, T=None):

@@ -8,8 +8,10 @@
 // P g_k on the orthogonal complement of the block (P = I - V V^T).  The k
 // shifted systems are solved together by MINRES (Paige & Saunders 1975; the
 // short recurrence for symmetric indefinite systems) on the projected
-// operator P (H - lambda_k) P, one set of recurrence scalars per column; the
-// host reads the two inner products of each step.
+// operator P (H - lambda_k) P, one set of recurrence scalars per column, with
+// the optional symmetric positive definite preconditioner P T P (PMINRES,
+// the solver the paper's Section 2 discusses for these singular consistent
+// systems); the host reads the two inner products of each step.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -106,9 +108,13 @@ int nblocks(int64_t work) { return grid_size_for(work, 256, sm_count() * 8); }
 
 using namespace plhr;
 
-extern "C" plhr_status plhr_eigvec_adjoint(const plhr_op* A, int k, const double* lam, const double* V, int64_t ldv,
-                                           const double* G, int64_t ldg, double tol, int maxit, double* grad,
-                                           int* iterations, void* stream) {
+namespace plhr {
+plhr_status prec_reserve(plhr_prec* T, int nc, int64_t extra_doubles);
+}
+
+extern "C" plhr_status plhr_eigvec_adjoint(const plhr_op* A, plhr_prec* T, int k, const double* lam, const double* V,
+                                           int64_t ldv, const double* G, int64_t ldg, double tol, int maxit,
+                                           double* grad, int* iterations, void* stream) {
     clear_error();
     if (!A || k < 1 || k > kMaxK || !lam || !V || !G || !grad || ldv < k || ldg < k || !(tol > 0) || maxit < 1) {
         set_error("plhr_eigvec_adjoint: invalid argument (1 <= k <= %d)", kMaxK);
@@ -117,6 +123,13 @@ extern "C" plhr_status plhr_eigvec_adjoint(const plhr_op* A, int k, const double
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = A->g.n();
     const int64_t nk = n * k;
+    if (T) {
+        if (prec_size(T) != n) {
+            set_error("plhr_eigvec_adjoint: preconditioner size does not match A");
+            return PLHR_EINVAL;
+        }
+        PLHR_TRY(prec_reserve(T, k, 0));
+    }
     const int cross_blocks = sm_count() * 2;
     const int res_blocks = residual_blocks(k);
     // device workspace: 9 n x k blocks, the k x k cross matrix and partials
@@ -165,6 +178,15 @@ extern "C" plhr_status plhr_eigvec_adjoint(const plhr_op* A, int k, const double
     };
     Coef one{}, zero{};
     for (int c = 0; c < kMaxK; ++c) { one.a[c] = 1.0; zero.a[c] = 0.0; }
+    // Y = P T X (or P X = X without T; X is in the complement already)
+    auto precond = [&](const double* X, double* Y) -> plhr_status {
+        if (!T) {
+            PLHR_TRY_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
+            return PLHR_OK;
+        }
+        PLHR_TRY(prec_apply64(T, k, X, k, Y, T->work, s));
+        return project(Y);
+    };
 
     // in-block part of b: V C with C[j][c] = (v_j^T g_c) / (lambda_c - lambda_j), j != c
     PLHR_TRY_CUDA(cudaMemcpy2DAsync(r1, sizeof(double) * k, G, sizeof(double) * ldg, sizeof(double) * k, n,
@@ -194,12 +216,15 @@ extern "C" plhr_status plhr_eigvec_adjoint(const plhr_op* A, int k, const double
     PLHR_TRY(coldots(r1, r1, hd.data()));
     for (int c = 0; c < k; ++c) gnorm[c] = std::sqrt(std::fmax(hd[c], 0.0));
     PLHR_TRY(project(r1));                                   // r1 = P g
+    PLHR_TRY(coldots(r1, r1, hd.data()));
+    std::vector<double> pnorm(k);
+    for (int c = 0; c < k; ++c) pnorm[c] = std::sqrt(std::fmax(hd[c], 0.0));
     PLHR_TRY_CUDA(cudaMemcpyAsync(r2, r1, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
-    PLHR_TRY_CUDA(cudaMemcpyAsync(y, r1, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
+    PLHR_TRY(precond(r1, y));                                // y = P T r1
     PLHR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nk, s));
     PLHR_TRY_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * nk, s));
     PLHR_TRY_CUDA(cudaMemsetAsync(w2, 0, sizeof(double) * nk, s));
-    PLHR_TRY(coldots(r1, r1, hd.data()));
+    PLHR_TRY(coldots(r1, y, hd.data()));
     std::vector<double> beta1(k), beta(k), oldb(k, 0.0), dbar(k, 0.0), epsln(k, 0.0), phibar(k), cs(k, -1.0),
         sn(k, 0.0), alfa(k);
     // a column whose projected right-hand side is at rounding level of g_c
@@ -210,7 +235,7 @@ extern "C" plhr_status plhr_eigvec_adjoint(const plhr_op* A, int k, const double
         beta1[c] = std::sqrt(std::fmax(hd[c], 0.0));
         beta[c] = beta1[c];
         phibar[c] = beta1[c];
-        done[c] = !(beta1[c] > 1e-14 * gnorm[c]);
+        done[c] = !(pnorm[c] > 1e-14 * gnorm[c]) || !(beta1[c] > 0.0);
         if (!done[c]) all_zero = false;
     }
     int itn = 0;
@@ -238,9 +263,10 @@ extern "C" plhr_status plhr_eigvec_adjoint(const plhr_op* A, int k, const double
         }
         k_lin3<<<nblocks(nk), 256, 0, s>>>(n, k, one, y, c2, r2, zero, nullptr, y);
         count_launches(1);
-        std::swap(r1, r2);                                    // r1 <- r2, r2 <- y (copied below)
-        PLHR_TRY_CUDA(cudaMemcpyAsync(r2, y, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
-        PLHR_TRY(coldots(r2, r2, hd.data()));
+        std::swap(r1, r2);                                    // r1 <- r2, r2 <- y
+        std::swap(r2, y);
+        PLHR_TRY(precond(r2, y));                             // y = P T r2
+        PLHR_TRY(coldots(r2, y, hd.data()));
         Coef dn{}, dc{}, ph{};
         converged = true;
         for (int c = 0; c < k; ++c) {

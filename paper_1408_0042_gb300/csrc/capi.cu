@@ -110,7 +110,16 @@ plhr_status plhr_op_hamiltonian(plhr_op** out, int d, const int64_t* dims, doubl
 
 int64_t plhr_op_size(const plhr_op* op) { return op ? op->g.n() : 0; }
 
-void plhr_op_destroy(plhr_op* op) { delete op; }
+void plhr_op_destroy(plhr_op* op) {
+    if (!op) return;
+    if (op->csr.rowptr || op->csr.col || op->csr.val) {
+        cudaDeviceSynchronize();   // queued products may still read the arrays
+        if (op->csr.rowptr) cudaFree(op->csr.rowptr);
+        if (op->csr.col) cudaFree(op->csr.col);
+        if (op->csr.val) cudaFree(op->csr.val);
+    }
+    delete op;
+}
 
 plhr_status plhr_op_apply(const plhr_op* op, int ncols, const double* X, int64_t ldx, double* Y, int64_t ldy,
                           void* stream) {
@@ -254,6 +263,9 @@ void plhr_prec_destroy(plhr_prec* T) {
     if (!T) return;
     cudaDeviceSynchronize();   // queued V-cycles may still read the hierarchy and workspace
     for (int a = 0; a < 3; ++a) {
+        if (T->sp.d_S[a]) cudaFree(T->sp.d_S[a]);
+        if (T->sp.d_St[a]) cudaFree(T->sp.d_St[a]);
+        if (T->sp.d_mu[a]) cudaFree(T->sp.d_mu[a]);
         if (T->H.d_basis[a]) cudaFree(T->H.d_basis[a]);
         if (T->H.d_mu[a]) cudaFree(T->H.d_mu[a]);
         if (T->H.f_basis[a]) cudaFree(T->H.f_basis[a]);
@@ -261,6 +273,7 @@ void plhr_prec_destroy(plhr_prec* T) {
         if (T->H.w_basis[a]) cudaFree(T->H.w_basis[a]);
         if (T->H.w_mu[a]) cudaFree(T->H.w_mu[a]);
     }
+    if (T->diag) cudaFree(T->diag);
     if (T->work) cudaFree(T->work);
     if (T->work32) cudaFree(T->work32);
     delete T;
@@ -270,7 +283,7 @@ void plhr_prec_destroy(plhr_prec* T) {
 
 namespace plhr {
 plhr_status prec_reserve(plhr_prec* T, int nc, int64_t extra_doubles) {
-    int64_t need = mg_workspace_doubles(T->H, nc) + extra_doubles;
+    int64_t need = prec_workspace_doubles(T, nc) + extra_doubles;
     if (need <= T->work_doubles) return PLHR_OK;
     if (T->work) {
         cudaDeviceSynchronize();
@@ -320,6 +333,10 @@ extern "C" plhr_status plhr_prec_apply_dw(plhr_prec* T, int ncols, const double*
         set_error("plhr_prec_apply_dw: invalid argument");
         return PLHR_EINVAL;
     }
+    if (T->kind != PREC_AVMG) {
+        set_error("plhr_prec_apply_dw: double-word form exists for AV-MG only");
+        return PLHR_EINVAL;
+    }
     if (ncols == 0) return PLHR_OK;
     PLHR_TRY(plhr::prec_reserve_dw(T, ncols));
     PLHR_TRY_CUDA(plhr::mg_vcycle_dw(T->H, ncols, R, ldr, W, ldw, T->work, (cudaStream_t)stream));
@@ -331,6 +348,10 @@ extern "C" plhr_status plhr_prec_apply_f32(plhr_prec* T, int ncols, const float*
     clear_error();
     if (!T || ncols < 0 || (ncols > 0 && (!R || !W)) || ldr < ncols || ldw < ncols) {
         set_error("plhr_prec_apply_f32: invalid argument");
+        return PLHR_EINVAL;
+    }
+    if (T->kind != PREC_AVMG) {
+        set_error("plhr_prec_apply_f32: FP32 form exists for AV-MG only");
         return PLHR_EINVAL;
     }
     if (ncols == 0) return PLHR_OK;
@@ -354,12 +375,12 @@ extern "C" plhr_status plhr_prec_apply(plhr_prec* T, int ncols, const double* R,
         return PLHR_EINVAL;
     }
     if (ncols == 0) return PLHR_OK;
-    const int64_t n = T->H.lev.back().g.n();
+    const int64_t n = prec_size(T);
     const int64_t stage = (ldw == ncols) ? 0 : n * ncols;
     PLHR_TRY(prec_reserve(T, ncols, stage));
     cudaStream_t s = (cudaStream_t)stream;
-    double* out = (ldw == ncols) ? W : T->work + mg_workspace_doubles(T->H, ncols);
-    PLHR_TRY_CUDA(mg_vcycle(T->H, ncols, R, ldr, out, ncols, T->work, s));
+    double* out = (ldw == ncols) ? W : T->work + prec_workspace_doubles(T, ncols);
+    PLHR_TRY(prec_apply64(T, ncols, R, ldr, out, T->work, s));
     if (ldw != ncols)
         PLHR_TRY_CUDA(cudaMemcpy2DAsync(W, sizeof(double) * ldw, out, sizeof(double) * ncols, sizeof(double) * ncols,
                                         n, cudaMemcpyDeviceToDevice, s));

@@ -48,10 +48,11 @@ __device__ __forceinline__ void dw_fma_acc(float& hi, float& lo, const dw& a, co
     lo = __fadd_rn(lo, __fadd_rn(s.lo, __fadd_rn(pl, cr)));
 }
 
-// Stage rows row0 .. of z = Z s, u = (AZ - sigma Z) s, q = Q s (q = u when
-// q_from_u) as double-word [row][mp] tiles; U is formed in FP64 before rounding
+// Stage rows row0 .. of z = Z, u = AZ - sigma Z, q = Q (q = u when q_from_u)
+// as double-word [row][mp] tiles; U is formed by one FP64 FMA before the split
+// (the column scales are applied to the finished Grams)
 __device__ void stage_dw(dw* sz, dw* su, dw* sq, int mp, int64_t n, int64_t row0, const FamD& Z, const FamD& AZ,
-                         const FamD& Q, int nb, int q_from_u, double sigma, const double* __restrict__ csc) {
+                         const FamD& Q, int nb, int q_from_u, double sigma) {
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         if (b >= nb) break;
@@ -64,12 +65,11 @@ __device__ void stage_dw(dw* sz, dw* su, dw* sq, int mp, int64_t n, int64_t row0
             const int col = Z.off[b] + c;
             dw z = dw_make(0.0f), u = z, q = z;
             if (row < n) {
-                const double s = csc[col];
-                const double zd = Z.p[b][row * Z.ld[b] + c] * s;
-                const double ud = AZ.p[b][row * AZ.ld[b] + c] * s - sigma * zd;
-                z = dw_from_double(zd);
-                u = dw_from_double(ud);
-                q = q_from_u ? u : dw_from_double(Q.p[b][row * Q.ld[b] + c] * s);
+                const double zd = Z.p[b][row * Z.ld[b] + c];
+                const double ud = fma(-sigma, zd, AZ.p[b][row * AZ.ld[b] + c]);
+                z = dw_from_double_fast(zd);
+                u = dw_from_double_fast(ud);
+                q = q_from_u ? u : dw_from_double_fast(Q.p[b][row * Q.ld[b] + c]);
             }
             sz[r * mp + col] = z;
             su[r * mp + col] = u;
@@ -82,7 +82,6 @@ __device__ void stage_dw(dw* sz, dw* su, dw* sq, int mp, int64_t n, int64_t row0
 // and mirrored; 1: U^T Q; 2: Q^T Z) and its 4x4 tile (ti, tj).  mp <= 64.
 __global__ void __launch_bounds__(kDwThreads, 1) k_gram_dw(int64_t n, int m, int mp, int nb, FamD Z, FamD AZ, FamD Q,
                                                            int q_from_u, double sigma,
-                                                           const double* __restrict__ csc,
                                                            double* __restrict__ partial) {
     extern __shared__ __align__(16) unsigned char raw[];
     dw* sz = reinterpret_cast<dw*>(raw);
@@ -102,7 +101,7 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_gram_dw(int64_t n, int m, int
     const int64_t nchunks = (n + kDwRows - 1) / kDwRows;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         __syncthreads();
-        stage_dw(sz, su, sq, mp, n, ch * kDwRows, Z, AZ, Q, nb, q_from_u, sigma, csc);
+        stage_dw(sz, su, sq, mp, n, ch * kDwRows, Z, AZ, Q, nb, q_from_u, sigma);
         __syncthreads();
         if (!act) continue;
 #pragma unroll 2
@@ -131,12 +130,17 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_gram_dw(int64_t n, int m, int
         }
 }
 
-__global__ void k_sum_wide_dw(int nblocks, int width, const double* __restrict__ partial, double* __restrict__ out) {
+// out = D (sum of the per-CTA partials) D for each of the three m x m Grams
+// (D = diag(csc), the column scales)
+__global__ void k_sum_wide_dw(int nblocks, int m, const double* __restrict__ csc, const double* __restrict__ partial,
+                              double* __restrict__ out) {
+    const int width = 3 * m * m;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= width) return;
     double t = 0.0;
     for (int b = 0; b < nblocks; ++b) t += partial[(int64_t)b * width + j];
-    out[j] = t;
+    const int idx = j % (m * m);
+    out[j] = t * (csc[idx / m] * csc[idx % m]);
 }
 
 // Pout = F C_P, Vout = F_0 C_VV + F C_P in double-word arithmetic on FP64
@@ -164,7 +168,7 @@ __global__ void __launch_bounds__(256) k_update_dw(int64_t n, int m, int kp, int
             const int nc = F.nc[b];
             for (int t = threadIdx.x; t < nrows * nc; t += blockDim.x) {
                 const int r = t / nc, c = t - r * nc;
-                zr[r * m + F.off[b] + c] = dw_from_double(F.p[b][(row0 + r) * F.ld[b] + c]);
+                zr[r * m + F.off[b] + c] = dw_from_double_fast(F.p[b][(row0 + r) * F.ld[b] + c]);
             }
         }
         __syncthreads();
@@ -201,12 +205,12 @@ cudaError_t multi_gram_dw(int64_t n, int nb, const Blk<const double>* Z, const B
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_gram_dw<<<blocks, kDwThreads, shm, s>>>(n, m, mp, nb, FZ, FA, FQ, Q ? 0 : 1, sigma, colscale, partial);
+    k_gram_dw<<<blocks, kDwThreads, shm, s>>>(n, m, mp, nb, FZ, FA, FQ, Q ? 0 : 1, sigma, partial);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int width = 3 * m * m;
-    k_sum_wide_dw<<<(width + 127) / 128, 128, 0, s>>>(blocks, width, partial, out);
+    k_sum_wide_dw<<<(width + 127) / 128, 128, 0, s>>>(blocks, m, colscale, partial, out);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -126,4 +126,22 @@ __device__ __forceinline__ dw dw_from_double(double d) {
 }
 __device__ __forceinline__ double dw_to_double(dw a) { return (double)a.hi + (double)a.lo; }
 
+// The same split without FP64 instructions (GB300 issues FP64 at 1/64 of the
+// FP32 rate): hi is x truncated to 24 significant bits, assembled from the
+// sign, exponent and top mantissa bits of the IEEE-754 encoding; lo is the
+// remaining 29-bit mantissa converted to FP32 (rounded) and scaled by the
+// power of two 2^(e - 52).  x = hi + lo to ~2^-48 relative; |lo| < ulp(hi).
+// Zero, values below 2^-74 or above 2^127, Inf and NaN take the FP64 route.
+__device__ __forceinline__ dw dw_from_double_fast(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+    if (e < -74 || e > 127) return dw_from_double(x);
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const unsigned long long mant = b & 0xfffffffffffffull;
+    const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29));
+    const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);
+    const float lo = __fmul_rn(__uint2float_rn((unsigned)(mant & 0x1fffffffu)), scale);
+    return {hi, __uint_as_float(__float_as_uint(lo) ^ sign)};
+}
+
 }  // namespace plhr

@@ -34,8 +34,20 @@ void clear_error();
 #define PLHR_LAUNCHED() PLHR_TRY_CUDA(cudaGetLastError())
 
 // ---------------------------------------------------------------- grids
+enum { OP_KIND_CSR = 100 };   // plhr_op::kind of a CSR operator (stencil kinds are plhr_stencil_kind)
+
+// A general sparse symmetric operator in CSR form (device arrays owned by the
+// plhr_op that holds them).
+struct CsrData {
+    int64_t n = 0, nnz = 0;
+    int64_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+};
+
 // Tensor grid, x fastest, homogeneous Dirichlet boundary (or periodic), with
-// an optional diagonal potential.
+// an optional diagonal potential.  With csr set the operator is that sparse
+// matrix instead (nx = n, no stencil).
 struct Grid {
     int d = 3;            // 2 or 3
     int64_t nx = 1, ny = 1, nz = 1;
@@ -43,9 +55,10 @@ struct Grid {
     double scale = 1.0;   // stencil multiplier
     int periodic = 0;     // 1: periodic wrap instead of zero Dirichlet values
     const double* pot = nullptr;   // optional diagonal term (device, n values): A = scale L + diag(pot)
+    const CsrData* csr = nullptr;  // general sparse operator instead of the stencil
     int64_t n() const { return nx * ny * nz; }
     double inv_h2() const { return scale / (h * h); }
-    bool plain() const { return !periodic && pot == nullptr; }   // the Dirichlet Laplacian
+    bool plain() const { return !periodic && pot == nullptr && csr == nullptr; }   // the Dirichlet Laplacian
 };
 
 // A block of row-major vectors: element (i, j) at p[i * ld + j].
@@ -91,6 +104,13 @@ cudaError_t lap_apply_shifts(const Grid& g, int nc, const double* x, int64_t ldx
                              const double* lam, double* o2, int64_t ld2, double sig,
                              cudaStream_t s);
 
+// the same two entry points for a CSR operator (csr.cu)
+cudaError_t csr_axpby(const CsrData& A, int nc, const double* x, int64_t ldx, double* y, int64_t ldy, double alpha,
+                      double beta, cudaStream_t s);
+cudaError_t csr_apply_shifts(const CsrData& A, int nc, const double* x, int64_t ldx, double* ax, int64_t ldax,
+                             double* o1, int64_t ld1, const double* lam, double* o2, int64_t ld2, double sig,
+                             cudaStream_t s);
+
 // ---------------------------------------------------------------- multigrid
 struct MGLevel {
     Grid g;
@@ -120,6 +140,24 @@ cudaError_t mg_vcycle(const MGHierarchy& H, int nc, const double* r, int64_t ldr
                       int64_t ldw, double* work, cudaStream_t s);
 int64_t mg_workspace_doubles(const MGHierarchy& H, int nc);
 
+// ---------------------------------------------------------------- TPA preconditioner
+// T = S diag(K(mu / energy)) S^T with S the separable orthonormal modes of the
+// grid's kinetic operator (spectral.cu)
+struct SpecPrec {
+    int d = 3;
+    int64_t nx = 1, ny = 1, nz = 1;
+    double energy = 1.0;
+    double* d_S[3] = {nullptr, nullptr, nullptr};    // N_a x N_a, [point][mode]
+    double* d_St[3] = {nullptr, nullptr, nullptr};   // transposes
+    double* d_mu[3] = {nullptr, nullptr, nullptr};   // kinetic energy per 1D mode
+    int64_t n() const { return nx * ny * nz; }
+};
+cudaError_t spectral_apply(const SpecPrec& P, int nc, const double* r, int64_t ldr, double* w, double* work,
+                           cudaStream_t s);
+int64_t spectral_workspace_doubles(const SpecPrec& P, int nc);
+
+enum { PREC_AVMG = 0, PREC_TPA = 1, PREC_DIAG = 2, PREC_CALLBACK = 3 };
+
 // FP32 V-cycle (same cycle, FP32 storage and arithmetic); r is FP64 or FP32
 // with leading dimension ldr, w is dense (leading dimension nc).
 cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const double* r, int64_t ldr, float* w, float* work,
@@ -140,12 +178,37 @@ int64_t mg_workspace_dw(const MGHierarchy& H, int nc);
 struct plhr_op {
     int kind;
     plhr::Grid g;
+    plhr::CsrData csr;   // owned arrays of a CSR operator (g.csr points here)
 };
 
 struct plhr_prec {
-    plhr::MGHierarchy H;
+    int kind = plhr::PREC_AVMG;
+    plhr::MGHierarchy H;          // PREC_AVMG
+    plhr::SpecPrec sp;            // PREC_TPA
+    double* diag = nullptr;       // PREC_DIAG: positive diagonal (device, owned)
+    plhr_apply_fn fn = nullptr;   // PREC_CALLBACK: the caller's T
+    void* ctx = nullptr;
+    int64_t n_user = 0;           // size for PREC_DIAG / PREC_CALLBACK
     double* work = nullptr;
     int64_t work_doubles = 0;
     float* work32 = nullptr;      // FP32 V-cycle workspace
     int64_t work_floats = 0;
 };
+
+namespace plhr {
+// FP64 application of either preconditioner kind: w (dense, ld nc) = T r;
+// work: prec_workspace_doubles(T, nc) doubles
+inline int64_t prec_size(const plhr_prec* T) {
+    if (T->kind == PREC_TPA) return T->sp.n();
+    if (T->kind == PREC_DIAG || T->kind == PREC_CALLBACK) return T->n_user;
+    return T->H.lev.back().g.n();
+}
+inline int64_t prec_workspace_doubles(const plhr_prec* T, int nc) {
+    if (T->kind == PREC_TPA) return spectral_workspace_doubles(T->sp, nc);
+    if (T->kind == PREC_DIAG || T->kind == PREC_CALLBACK) return 0;
+    return mg_workspace_doubles(T->H, nc);
+}
+// any kind (precs.cu); sets the error message on failure
+plhr_status prec_apply64(const plhr_prec* T, int nc, const double* r, int64_t ldr, double* w, double* work,
+                         cudaStream_t s);
+}  // namespace plhr

@@ -99,8 +99,8 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         return PLHR_EINVAL;
     }
     const int64_t n = A->g.n();
-    if (opt.precision == PLHR_PRECISION_MIXED && !A->g.plain()) {
-        set_error("plhr_solve: the mixed-precision form supports the Dirichlet Laplacian only");
+    if (opt.precision == PLHR_PRECISION_MIXED && (!A->g.plain() || (T && T->kind != PREC_AVMG))) {
+        set_error("plhr_solve: the mixed-precision form supports the Dirichlet Laplacian with AV-MG or T = I only");
         return PLHR_EINVAL;
     }
     if (opt.guard < 0) {
@@ -117,7 +117,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         set_error("plhr_solve: n = %lld too small for k = %d", (long long)n, k);
         return PLHR_EINVAL;
     }
-    if (T && T->H.lev.back().g.n() != n) {
+    if (T && prec_size(T) != n) {
         set_error("plhr_solve: preconditioner size does not match A");
         return PLHR_EINVAL;
     }
@@ -246,7 +246,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         if (dwf)   // FP64 phase of the mixed form: double-word V-cycle
             PLHR_TRY_CUDA(mg_vcycle_dw(T->H, nc, r, ldr, w, nc, T->work, s));
         else
-            PLHR_TRY_CUDA(mg_vcycle(T->H, nc, r, ldr, w, nc, T->work, s));
+            PLHR_TRY(prec_apply64(T, nc, r, ldr, w, T->work, s));
         return PLHR_OK;
     };
 

@@ -430,3 +430,57 @@ def test_eigvec_gradient_of_norm_is_zero_and_second_derivative_symmetric():
     assert np.abs(hess - hess.T).max() <= 1e-10 * np.abs(hess).max()
     # and the row sums vanish: a constant shift of V moves no eigenvector
     assert np.abs(hess.sum(axis=0)).max() <= 1e-10 * np.abs(hess).max()
+
+
+# ---------------------------------------------------------------- TPA preconditioner (Section 5.3)
+
+def test_tpa_factor_limits():
+    """K(0) = 1 with K = 1 - 16 x^4 / 27 + O(x^5) near 0, K ~ 1 / (2x) for large
+    x, and K decreasing: the properties the Teter-Payne-Allan polynomial is
+    built to have."""
+    from oracle import spectral as sp_
+    assert sp_.tpa_factor(0.0) == 1.0
+    x = 1e-2
+    assert abs((1.0 - sp_.tpa_factor(x)) / x**4 - 16.0 / 27.0) < 1e-2
+    for x in (1e3, 1e5):
+        assert abs(sp_.tpa_factor(x) * 2.0 * x - 1.0) < 2.0 / x
+    xs = np.linspace(0.0, 50.0, 2001)
+    assert np.all(np.diff(sp_.tpa_factor(xs)) < 0)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_tpa_acts_on_plane_waves_by_its_factor(periodic):
+    """A single mode of the grid (a Fourier or sine wave, written out here) is
+    an eigenvector of T with eigenvalue K(mu / E), mu its kinetic energy from
+    the closed form."""
+    from oracle import spectral as sp_
+    dims, h, E = (8, 6, 4), 0.5, 1.7
+    T = sp_.TPA(dims, h, E, periodic=periodic)
+    z, y, x = np.meshgrid(*[np.arange(N) for N in reversed(dims)], indexing="ij")
+    for m in [(1, 2, 0), (3, 1, 1), (4, 3, 2)]:
+        if periodic:
+            phase = 2 * np.pi * (m[0] * x / dims[0] + m[1] * y / dims[1] + m[2] * z / dims[2])
+            wave = np.cos(phase + 0.3)
+            mu = 0.5 * sum((2 - 2 * np.cos(2 * np.pi * mq / N)) / h**2 for mq, N in zip(m, dims))
+        else:
+            wave = (np.sin((m[0] + 1) * (x + 1) * np.pi / (dims[0] + 1)) * np.sin((m[1] + 1) * (y + 1) * np.pi / (dims[1] + 1))
+                    * np.sin((m[2] + 1) * (z + 1) * np.pi / (dims[2] + 1)))
+            mu = 0.5 * sum((2 - 2 * np.cos((mq + 1) * np.pi / (N + 1))) / h**2 for mq, N in zip(m, dims))
+        w = wave.ravel()
+        xq = mu / E
+        K = (27 + 18 * xq + 12 * xq**2 + 8 * xq**3) / (27 + 18 * xq + 12 * xq**2 + 8 * xq**3 + 16 * xq**4)
+        assert np.allclose(T(w), K * w, atol=1e-13)
+
+
+def test_tpa_symmetric_positive_definite_and_commutes_with_kinetic_operator():
+    from oracle import operators as ops
+    from oracle import spectral as sp_
+    dims, h = (6, 5, 4), 1.0
+    n = int(np.prod(dims))
+    for periodic in (True, False):
+        T = sp_.TPA(dims, h, 2.5, periodic=periodic)
+        Tm = T(np.eye(n))
+        assert np.abs(Tm - Tm.T).max() <= 1e-14
+        assert np.linalg.eigvalsh(Tm).min() > 0
+        K = ops.hamiltonian(dims, h, np.zeros(n), periodic=periodic).toarray()
+        assert np.abs(Tm @ K - K @ Tm).max() <= 1e-12 * np.abs(K).max()

@@ -215,3 +215,26 @@ def config5_potential():
     """64^3 periodic grid, 32 seeded Gaussian wells (h = 1)."""
     dims = (64, 64, 64)
     return dims, gaussian_potential(dims, 32, SEED_BASE + 5)
+
+
+# Shift of the 64^3 differentiation workload: the 8 eigenvalues nearest it are
+# lambda_6 .. lambda_13 of H (about -1.4972 .. -1.3181; smallest gap inside the
+# block 4.8e-3; the 9th is 1.62 times farther than the 8th).  Written by
+# workloads/select_shift_ham64.py from a Lanczos solve of the oracle's operator.
+HAM64_SIGMA = -1.4076
+HAM64_K = 8
+# the 8 eigenvalues nearest HAM64_SIGMA from the same Lanczos solve (tol 1e-10)
+HAM64_LAMBDA_REF = (-1.4972095727, -1.4646666705, -1.3947918710, -1.3900142734, -1.3677701223, -1.3384194736,
+                    -1.3285495681, -1.3180617417)
+
+
+def config5():
+    """Differentiation workload on the 64^3 Hamiltonian: potential, shift,
+    block size, eigenvalue weights w ~ U(0.5, 1.5) and a density mask
+    m ~ Bernoulli(1/2) for the loss sum_k w_k lambda_k + sum_k |m (.) v_k|^2."""
+    dims, V = config5_potential()
+    n = int(np.prod(dims))
+    w = 0.5 + (uniform_block(HAM64_K, 1, SEED_BASE + 51).ravel() + 0.5)
+    mask = (uniform_block(n, 1, SEED_BASE + 52).ravel() >= 0.0).astype(np.float64)
+    return {"dims": dims, "h": 1.0, "V": V, "sigma": HAM64_SIGMA, "k": HAM64_K, "w": w, "mask": mask,
+            "seed": SEED_BASE + 5}
