@@ -159,11 +159,12 @@ def _rooflines(prof, w, peaks, sm_max_mhz, mixed):
     CUDA-event time; returns the entries sorted by total time.  In the mixed
     form the FP64 phase runs the Gram, the update and the V-cycle in
     double-word arithmetic on FP32 pipes: a double-word multiply-add costs 13
-    FP32 instructions, so its compute roof is the FP32 rate x 2 / 13 in
-    FP64-equivalent flops."""
+    FP32 instructions (lane operations) for 2 FP64-equivalent flops, so its
+    compute roof is (FP32 lane operations per second) x 2 / 13 = the FP32
+    flop rate / 13."""
     out = []
     fp32_peak = _fp32_simt_peak_tflops(sm_max_mhz or 2070.0)
-    dw_peak = fp32_peak * 2.0 / 13.0
+    dw_peak = fp32_peak / 13.0
     if mixed:
         f64_rows = [("gram", "k_gram_dw (double-word multi-Gram)", "alu", dw_peak, "TFLOP/s", 1e-12),
                     ("update", "k_update_dw (double-word update)", "alu", dw_peak, "TFLOP/s", 1e-12),
@@ -304,7 +305,7 @@ def run_ours(args, world, rank, local):
                                    "per launch (%d launches in the timed steps)" % prof["gram"]["calls"])
         dom["peak_src"] = ("measured (MEASURED_PEAKS.json hbm_gbs)" if dom["unit"] == "GB/s" else
                            "nominal FP64 rate of the profiling recipe" if "FP64" in dom["kernel"] else
-                           "FP32 lanes x clock x 2 / 13 (double-word multiply-add)" if "double-word" in dom["kernel"]
+                           "FP32 lanes x clock / 13 x 2 flops (double-word multiply-add = 13 FP32 instructions)" if "double-word" in dom["kernel"]
                            else "FP32 lanes x clock")
 
     out = {
@@ -469,22 +470,25 @@ def run_grad(args, world, rank, local):
         e2e.append(time.perf_counter() - t0)
     e2e_s = _max_over_ranks(statistics.mean(e2e), world)
 
-    # rooflines of the phases the library times; the TPA application is FP64
-    # dense per-axis transforms: 2 (forward, inverse) x 2 flops x (nx + ny + nz)
-    # per element (grid point x column)
+    # rooflines of the phases the library times; the TPA application is dense
+    # per-axis transforms in double-word arithmetic: 2 (forward, inverse) x 2
+    # flops x (nx + ny + nz) per element (grid point x column)
     fp64 = FP64_PEAK_TFLOPS
+    dw_peak = _fp32_simt_peak_tflops(clocks.get("sm_max_mhz") or 2070.0) / 13.0
     per_elem = 4.0 * sum(dims)
     roofs = []
-    for ph, kernel, per in (("preconditioner", "k_axis (TPA transforms, FP64)", per_elem * 1e-12),
-                            ("gram", "k_gram (FP64 multi-Gram)", 1e-12),
-                            ("update", "k_update (FP64)", 1e-12)):
+    for ph, kernel, per, peak, src in (
+            ("preconditioner", "k_axis (TPA transforms, double-word)", per_elem * 1e-12, dw_peak,
+             "FP32 lanes x clock / 13 x 2 flops (double-word multiply-add = 13 FP32 instructions)"),
+            ("gram", "k_gram (FP64 multi-Gram)", 1e-12, fp64, "nominal FP64 rate of the profiling recipe"),
+            ("update", "k_update (FP64)", 1e-12, fp64, "nominal FP64 rate of the profiling recipe")):
         d = prof.get(ph)
         if not d or d["ms"] <= 0 or d["work"] <= 0:
             continue
         a = d["work"] * per / (d["ms"] / 1e3)
-        roofs.append({"phase": ph, "kernel": kernel, "bound": "alu", "achieved": a, "peak": fp64, "unit": "TFLOP/s",
-                      "frac": a / fp64, "total_ms": d["ms"], "calls": d["calls"], "traffic": None,
-                      "peak_src": "nominal FP64 rate of the profiling recipe"})
+        roofs.append({"phase": ph, "kernel": kernel, "bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s",
+                      "frac": a / peak, "total_ms": d["ms"], "calls": d["calls"], "traffic": None,
+                      "peak_src": src})
     roofs.sort(key=lambda r: -r["total_ms"])
     out = {
         "metric": GRAD_METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,

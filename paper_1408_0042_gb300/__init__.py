@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
                 ("s_vectors", ctypes.c_int), ("soft_lock", ctypes.c_int),
                 ("v_init", ctypes.c_void_p), ("ld_init", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("history", ctypes.c_void_p), ("history_cap", ctypes.c_int), ("guard", ctypes.c_int),
-                ("switch_tol", ctypes.c_double)]
+                ("switch_tol", ctypes.c_double), ("extraction", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -452,10 +452,13 @@ def profile_read(reset: bool = False) -> dict:
 
 def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float = 1e-8, maxit: int = 1000,
           v_init=None, seed: int = 20140801, history: bool = False, precision: int = PRECISION_F64,
-          stream=None, raise_on_notconv: bool = False, guard: int = 1, switch_tol: float = 1e-5):
+          stream=None, raise_on_notconv: bool = False, guard: int = 1, switch_tol: float = 1e-5,
+          extraction: str = "tharm", s_vectors: bool = True):
     """k eigenpairs of A v = lambda v nearest sigma with k + guard block
-    columns.  Returns (eigvals (numpy, k), eigvecs (torch n x k float64,
-    CUDA), info dict)."""
+    columns.  extraction "tharm" (T-harmonic, default) or "harm" (harmonic:
+    T = I in the Petrov-Galerkin condition); s_vectors False drops the S block
+    (trial space [V W P]).  Returns (eigvals (numpy, k), eigvecs (torch n x k
+    float64, CUDA), info dict)."""
     import torch
     lib = load_library()
     n = A.n
@@ -467,6 +470,10 @@ def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float =
     opt.seed = seed
     opt.guard = guard
     opt.switch_tol = switch_tol
+    if extraction not in ("tharm", "harm"):
+        raise ValueError("extraction must be 'tharm' or 'harm'")
+    opt.extraction = 0 if extraction == "tharm" else 1
+    opt.s_vectors = 1 if s_vectors else 0
     if v_init is not None:
         _check_block(v_init, n, "v_init")
         if v_init.shape[1] < kp:

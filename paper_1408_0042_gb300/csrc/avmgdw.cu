@@ -278,14 +278,14 @@ __global__ void k_to_dw(int64_t n, int nc, const double* __restrict__ x, int64_t
     const int64_t total = n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = e / nc;
-        y[e] = dw_from_double(x[row * ldx + (e - row * nc)]);
+        y[e] = dw_split_trunc(x[row * ldx + (e - row * nc)]);
     }
 }
 __global__ void k_from_dw(int64_t n, int nc, const dw* __restrict__ x, double* __restrict__ y, int64_t ldy) {
     const int64_t total = n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = e / nc;
-        y[row * ldy + (e - row * nc)] = dw_to_double(x[e]);
+        y[row * ldy + (e - row * nc)] = dw_to_double_fast(x[e]);
     }
 }
 

@@ -58,9 +58,10 @@ __global__ void __launch_bounds__(kThreads) k_residual(int64_t n, int kp, const 
 }
 
 // fixed-order sum of per-CTA partials: out[j] = sum_b partial[b * width + j]
+// (one thread per output; launch with sum_blocks(width) CTAs of 128)
 __global__ void k_sum_partials(int nblocks, int width, const double* __restrict__ partial,
                                double* __restrict__ out) {
-    for (int j = threadIdx.x; j < width; j += blockDim.x) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < width; j += gridDim.x * blockDim.x) {
         double t = 0.0;
         for (int b = 0; b < nblocks; ++b) t += partial[(int64_t)b * width + j];
         out[j] = t;
@@ -278,7 +279,7 @@ cudaError_t residual_norms(int64_t n, int kp, const double* V, int64_t ldv, cons
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sum_partials<<<1, 128, 0, s>>>(blocks, 2 * kp, partial, out);
+    k_sum_partials<<<(2 * kp + 127) / 128, 128, 0, s>>>(blocks, 2 * kp, partial, out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -295,7 +296,7 @@ cudaError_t multi_gram(int64_t n, int nb, const Blk<const double>* Z, const Blk<
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sum_partials<<<1, 256, 0, s>>>(blocks, 3 * m * m, partial, out);
+    k_sum_partials<<<(3 * m * m + 127) / 128, 128, 0, s>>>(blocks, 3 * m * m, partial, out);
     count_launches(1);
     return cudaGetLastError();
 }

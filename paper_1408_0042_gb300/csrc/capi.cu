@@ -265,7 +265,6 @@ void plhr_prec_destroy(plhr_prec* T) {
     for (int a = 0; a < 3; ++a) {
         if (T->sp.d_S[a]) cudaFree(T->sp.d_S[a]);
         if (T->sp.d_St[a]) cudaFree(T->sp.d_St[a]);
-        if (T->sp.d_mu[a]) cudaFree(T->sp.d_mu[a]);
         if (T->H.d_basis[a]) cudaFree(T->H.d_basis[a]);
         if (T->H.d_mu[a]) cudaFree(T->H.d_mu[a]);
         if (T->H.f_basis[a]) cudaFree(T->H.f_basis[a]);
@@ -274,6 +273,7 @@ void plhr_prec_destroy(plhr_prec* T) {
         if (T->H.w_mu[a]) cudaFree(T->H.w_mu[a]);
     }
     if (T->diag) cudaFree(T->diag);
+    if (T->sp.d_K) cudaFree(T->sp.d_K);
     if (T->work) cudaFree(T->work);
     if (T->work32) cudaFree(T->work32);
     delete T;

@@ -37,16 +37,6 @@ FamD fam_d(const Blk<const double>* b, int nb) {
     return F;
 }
 
-// acc += a * b (a, b double-word): exact product of the high parts, FP32
-// cross terms, TwoSum on the high part of the accumulator
-__device__ __forceinline__ void dw_fma_acc(float& hi, float& lo, const dw& a, const dw& b) {
-    const float ph = __fmul_rn(a.hi, b.hi);
-    const float pl = __fmaf_rn(a.hi, b.hi, -ph);
-    const float cr = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
-    const dw s = dw_two_sum(hi, ph);
-    hi = s.hi;
-    lo = __fadd_rn(lo, __fadd_rn(s.lo, __fadd_rn(pl, cr)));
-}
 
 // Stage rows row0 .. of z = Z, u = AZ - sigma Z, q = Q (q = u when q_from_u)
 // as double-word [row][mp] tiles; U is formed by one FP64 FMA before the split
@@ -67,9 +57,9 @@ __device__ void stage_dw(dw* sz, dw* su, dw* sq, int mp, int64_t n, int64_t row0
             if (row < n) {
                 const double zd = Z.p[b][row * Z.ld[b] + c];
                 const double ud = fma(-sigma, zd, AZ.p[b][row * AZ.ld[b] + c]);
-                z = dw_from_double_fast(zd);
-                u = dw_from_double_fast(ud);
-                q = q_from_u ? u : dw_from_double_fast(Q.p[b][row * Q.ld[b] + c]);
+                z = dw_split_trunc(zd);
+                u = dw_split_trunc(ud);
+                q = q_from_u ? u : dw_split_trunc(Q.p[b][row * Q.ld[b] + c]);
             }
             sz[r * mp + col] = z;
             su[r * mp + col] = u;
@@ -168,7 +158,7 @@ __global__ void __launch_bounds__(256) k_update_dw(int64_t n, int m, int kp, int
             const int nc = F.nc[b];
             for (int t = threadIdx.x; t < nrows * nc; t += blockDim.x) {
                 const int r = t / nc, c = t - r * nc;
-                zr[r * m + F.off[b] + c] = dw_from_double_fast(F.p[b][(row0 + r) * F.ld[b] + c]);
+                zr[r * m + F.off[b] + c] = dw_split_trunc(F.p[b][(row0 + r) * F.ld[b] + c]);
             }
         }
         __syncthreads();
@@ -180,8 +170,8 @@ __global__ void __launch_bounds__(256) k_update_dw(int64_t n, int m, int kp, int
             float vh = ph, vl = pl;
             for (int i = 0; i < kp; ++i) dw_fma_acc(vh, vl, z[i], cv[i * kp + j]);
             const int64_t row = row0 + r;
-            Pout[row * ldpo + j] = (double)ph + (double)pl;
-            Vout[row * ldvo + j] = (double)vh + (double)vl;
+            Pout[row * ldpo + j] = dw_to_double_fast(dw{ph, pl});
+            Vout[row * ldvo + j] = dw_to_double_fast(dw{vh, vl});
         }
     }
 }

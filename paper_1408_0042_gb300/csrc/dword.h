@@ -22,7 +22,7 @@
 
 namespace plhr {
 
-struct dw {
+struct __align__(8) dw {   // 8-byte aligned: one 64-bit load or store per value
     float hi, lo;
 };
 
@@ -127,12 +127,43 @@ __device__ __forceinline__ dw dw_from_double(double d) {
 __device__ __forceinline__ double dw_to_double(dw a) { return (double)a.hi + (double)a.lo; }
 
 // The same split without FP64 instructions (GB300 issues FP64 at 1/64 of the
-// FP32 rate): hi is x truncated to 24 significant bits, assembled from the
-// sign, exponent and top mantissa bits of the IEEE-754 encoding; lo is the
-// remaining 29-bit mantissa converted to FP32 (rounded) and scaled by the
-// power of two 2^(e - 52).  x = hi + lo to ~2^-48 relative; |lo| < ulp(hi).
-// Zero, values below 2^-74 or above 2^127, Inf and NaN take the FP64 route.
+// FP32 rate), by integer operations on the IEEE-754 encodings: hi is x
+// rounded to 24 significant bits (round half up on the magnitude: the 29
+// discarded mantissa bits decide, and an increment of the encoding carries
+// into the exponent), lo is the remainder x - hi, an integer below 2^28 times
+// 2^(e - 52) converted to FP32 (rounded) with its sign.  x = hi + lo to ~2^-48
+// relative and |lo| <= ulp(hi) / 2, as from the FP64 route.  Zero, values
+// below 2^-74 or from 2^127 up, Inf and NaN take the FP64 route.
 __device__ __forceinline__ dw dw_from_double_fast(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+    if (e < -74 || e > 126) return dw_from_double(x);
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const unsigned long long mant = b & 0xfffffffffffffull;
+    const unsigned m29 = (unsigned)(mant & 0x1fffffffu);
+    const unsigned up = m29 >> 28;
+    const float hi = __uint_as_float((sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29)) + up);
+    const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);
+    const float mag = __fmul_rn(__uint2float_rn(up ? 0x20000000u - m29 : m29), scale);
+    return {hi, __uint_as_float(__float_as_uint(mag) ^ (up ? sign ^ 0x80000000u : sign))};
+}
+
+// acc += a * b (a, b double-word): exact product of the high parts, FP32
+// cross terms, TwoSum on the high part of the accumulator
+__device__ __forceinline__ void dw_fma_acc(float& hi, float& lo, const dw& a, const dw& b) {
+    const float ph = __fmul_rn(a.hi, b.hi);
+    const float pl = __fmaf_rn(a.hi, b.hi, -ph);
+    const float cr = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
+    const dw s = dw_two_sum(hi, ph);
+    hi = s.hi;
+    lo = __fadd_rn(lo, __fadd_rn(s.lo, __fadd_rn(pl, cr)));
+}
+
+// Truncating form of the same split: hi is x with the 29 low mantissa bits
+// cleared, lo the remainder (same sign as x, |lo| < ulp(hi)); x = hi + lo to
+// ~2^-48 relative.  Used where only the pair's sum matters (the double-word
+// Gram, update and V-cycle), never where hi serves as the FP32 value of x.
+__device__ __forceinline__ dw dw_split_trunc(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7ffu) - 1023;
     if (e < -74 || e > 127) return dw_from_double(x);
@@ -143,5 +174,20 @@ __device__ __forceinline__ dw dw_from_double_fast(double x) {
     const float lo = __fmul_rn(__uint2float_rn((unsigned)(mant & 0x1fffffffu)), scale);
     return {hi, __uint_as_float(__float_as_uint(lo) ^ sign)};
 }
+
+// FP32 -> FP64 widening by re-biasing the exponent of the encoding (exact for
+// normal numbers and zero); subnormal, Inf and NaN inputs take the conversion
+// instruction
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if (e == 0u) return (u & 0x7fffffu) ? (double)f : __longlong_as_double((long long)sign);
+    if (e == 0xffu) return (double)f;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+// hi + lo with one FP64 addition (the widenings are integer operations)
+__device__ __forceinline__ double dw_to_double_fast(dw a) { return f32_to_f64_bits(a.hi) + f32_to_f64_bits(a.lo); }
 
 }  // namespace plhr

@@ -319,7 +319,7 @@ __global__ void k_widen(int64_t n, int nc, const float* __restrict__ X, int64_t 
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / nc;
         const int c = (int)(e - r * nc);
-        Y[r * ldy + c] = (double)X[r * ldx + c];
+        Y[r * ldy + c] = f32_to_f64_bits(X[r * ldx + c]);
     }
 }
 

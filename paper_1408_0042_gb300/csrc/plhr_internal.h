@@ -147,9 +147,10 @@ struct SpecPrec {
     int d = 3;
     int64_t nx = 1, ny = 1, nz = 1;
     double energy = 1.0;
-    double* d_S[3] = {nullptr, nullptr, nullptr};    // N_a x N_a, [point][mode]
-    double* d_St[3] = {nullptr, nullptr, nullptr};   // transposes
-    double* d_mu[3] = {nullptr, nullptr, nullptr};   // kinetic energy per 1D mode
+    // double-word (hi, lo) FP32 pairs
+    float* d_S[3] = {nullptr, nullptr, nullptr};     // N_a x N_a, [point][mode]
+    float* d_St[3] = {nullptr, nullptr, nullptr};    // transposes
+    float* d_K = nullptr;                            // factor K(mu / energy) per 3D mode (n pairs)
     int64_t n() const { return nx * ny * nz; }
 };
 cudaError_t spectral_apply(const SpecPrec& P, int nc, const double* r, int64_t ldr, double* w, double* work,

@@ -75,6 +75,7 @@ extern "C" void plhr_options_default(plhr_options* o) {
     o->seed = 20140801ull;
     o->guard = 1;
     o->switch_tol = 1e-5;
+    o->extraction = 0;
 }
 
 extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sigma, int k, plhr_prec* T, double tol,
@@ -94,8 +95,12 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         return PLHR_EINVAL;
     }
     if (!opt.real_arithmetic || (opt.precision != PLHR_PRECISION_F64 && opt.precision != PLHR_PRECISION_MIXED) ||
-        !opt.s_vectors) {
-        set_error("plhr_solve: this build supports real arithmetic, FP64 or mixed precision, with s-vectors");
+        (opt.extraction != 0 && opt.extraction != 1)) {
+        set_error("plhr_solve: this build supports real arithmetic, FP64 or mixed precision, extraction 0 or 1");
+        return PLHR_EINVAL;
+    }
+    if ((!opt.s_vectors || opt.extraction != 0) && opt.precision != PLHR_PRECISION_F64) {
+        set_error("plhr_solve: harmonic extraction and s_vectors = 0 run in PLHR_PRECISION_F64");
         return PLHR_EINVAL;
     }
     const int64_t n = A->g.n();
@@ -175,7 +180,12 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     // FP64 phase of the mixed form: V-cycle, Gram and update in double-word
     // arithmetic on the FP64 blocks (FP64-class accuracy on the FP32 pipes)
     const bool dwf = opt.precision == PLHR_PRECISION_MIXED;
+    // thq: T-harmonic images Q = T(A - sigma B)Z are formed (T given and the
+    // T-harmonic extraction); sv: the trial space holds the S block
+    const bool thq = T && opt.extraction == 0;
+    const bool sv = opt.s_vectors != 0;
     int mixed_its = 0;
+    int restarts = 0;     // restarts of dependent columns at acceptance
     double best_worst = INFINITY;   // FP32 form: smallest worst residual so far and when
     int best_it = 0;
     struct FloatBuf {
@@ -267,7 +277,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     // AV, X3 := AV - sigma V, QV = T(AV - sigma V) (with T = I, Q = AZ - sigma Z is
     // formed inside the Gram pass and no Q block is stored)
     PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
-    if (T) {
+    if (thq) {
         if (mx) PLHR_TRY(applyT32(kp, (const double*)X3, kp, QV32));
         else PLHR_TRY(applyT(kp, X3, kp, QV));
     }
@@ -294,6 +304,56 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         return PLHR_OK;
     };
 
+    // Columns of V numerically dependent on the columns nearer sigma: Cholesky
+    // of the normalised Gram G = D V^T V D (host copy, kp x kp) in the order
+    // ord, skipping the columns already marked; a column whose squared
+    // distance to the span of the kept ones is below thresh is marked.  An
+    // iteration can let two columns drift into one direction of a degenerate
+    // eigenspace; the slot they waste leaves a member of another cluster out.
+    auto mark_dependent = [&](const double* G, const int* ord, double thresh, std::vector<char>& mark) {
+        std::vector<double> L(kp * kp, 0.0);
+        std::vector<int> kept;
+        bool any = false;
+        for (int q2 = 0; q2 < kp; ++q2) {
+            const int j = ord[q2];
+            if (mark[j]) continue;
+            double rest = 1.0;
+            for (size_t p = 0; p < kept.size(); ++p) {
+                const int i = kept[p];
+                double c = G[j * kp + i] / std::sqrt(G[j * kp + j] * G[i * kp + i]);
+                for (size_t r = 0; r < p; ++r) c -= L[j * kp + r] * L[i * kp + r];
+                L[j * kp + p] = c / L[i * kp + p];
+                rest -= L[j * kp + p] * L[j * kp + p];
+            }
+            if (!(rest > thresh)) {
+                mark[j] = 1;
+                any = true;
+                continue;
+            }
+            L[j * kp + kept.size()] = std::sqrt(rest);
+            kept.push_back(j);
+        }
+        return any;
+    };
+    // the marked columns of V restart from seeded random vectors (FP64 forms);
+    // A V, the images and the Rayleigh quotients are recomputed
+    auto restart_columns = [&](const std::vector<char>& mark, uint64_t salt) -> plhr_status {
+        PLHR_TRY_CUDA(seeded_block(n, kp, opt.seed ^ salt, Rc, kp, s));
+        for (int j = 0; j < kp; ++j)
+            if (mark[j])
+                PLHR_TRY_CUDA(cudaMemcpy2DAsync(V + j, sizeof(double) * kp, Rc + j, sizeof(double) * kp,
+                                                sizeof(double), n, cudaMemcpyDeviceToDevice, s));
+        PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
+        if (thq) PLHR_TRY(applyT(kp, X3, kp, QV));
+        std::vector<int> zeros(64, 0), neg(64, -1);
+        PLHR_TRY_CUDA(cudaMemcpyAsync(tags, zeros.data(), sizeof(int) * 64, cudaMemcpyHostToDevice, s));
+        PLHR_TRY_CUDA(cudaMemcpyAsync(partner, neg.data(), sizeof(int) * 64, cudaMemcpyHostToDevice, s));
+        PLHR_TRY_CUDA(column_dots(n, kp, V, kp, AV, kp, rpart, dots, s));
+        PLHR_TRY_CUDA(dense_rq(kp, dots, tags, partner, lam, scale, s));
+        PLHR_TRY_CUDA(cudaStreamSynchronize(s));   // the host vectors above
+        return PLHR_OK;
+    };
+
     // end of the FP32 form: P to FP64, then A V, A P, T(A V - sigma V) and
     // T(A P - sigma P) explicitly in FP64
     // ord: host column order by distance to sigma (the first k are kept)
@@ -301,14 +361,26 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         // guard columns (beyond the k nearest sigma) restart from fresh seeded
         // random vectors: the FP32 form can lose a weak direction (a member of a
         // degenerate cluster whose component sat below its rounding level), and
-        // random columns contain every eigendirection for the FP64 phase to find
-        if (kp > k) {
+        // random columns contain every eigendirection for the FP64 phase to
+        // find; so do columns dependent on the ones nearer sigma
+        std::vector<char> restart(kp, 0);
+        for (int q2 = k; q2 < kp; ++q2) restart[ord[q2]] = 1;
+        {
+            Blk<const double> vb[1] = {{V, kp, kp}};
+            PLHR_TRY_CUDA(multi_gram(n, 1, vb, vb, vb, 0.0, colscale, gpart, grams, s));
+            std::vector<double> G(kp * kp);
+            PLHR_TRY_CUDA(cudaMemcpyAsync(G.data(), grams, sizeof(double) * kp * kp, cudaMemcpyDeviceToHost, s));
+            PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+            mark_dependent(G.data(), ord, 1e-4, restart);
+        }
+        bool any = false;
+        for (int j2 = 0; j2 < kp; ++j2) any = any || restart[j2];
+        if (any) {
             PLHR_TRY_CUDA(seeded_block(n, kp, opt.seed ^ 0x5bd1e995ull, Rc, kp, s));
-            for (int q2 = k; q2 < kp; ++q2) {
-                const int j = ord[q2];
-                PLHR_TRY_CUDA(cudaMemcpy2DAsync(V + j, sizeof(double) * kp, Rc + j, sizeof(double) * kp,
-                                                sizeof(double), n, cudaMemcpyDeviceToDevice, s));
-            }
+            for (int j2 = 0; j2 < kp; ++j2)
+                if (restart[j2])
+                    PLHR_TRY_CUDA(cudaMemcpy2DAsync(V + j2, sizeof(double) * kp, Rc + j2, sizeof(double) * kp,
+                                                    sizeof(double), n, cudaMemcpyDeviceToDevice, s));
         }
         if (np) PLHR_TRY_CUDA(widen_block(n, kp, P32, kp, P, kp, s));
         PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
@@ -318,7 +390,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             if (T) PLHR_TRY(applyT(kp, X3, kp, QP));
         }
         mx = false;
-        if (kp > k) {
+        if (any) {
             // Rayleigh quotients and scales of the new columns (every column
             // real: the pairing of the last extraction no longer applies)
             std::vector<int> zeros(64, 0), neg(64, -1);
@@ -377,6 +449,19 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
             PLHR_TRY_CUDA(multi_gram(n, 1, zb, ab, qb, 0.0, colscale, gpart, grams, s));
             // grams: [V^T V | (AV)^T V | V^T V] (kp x kp blocks)
+            if (!mx && kp > k && restarts < 8) {
+                // a column dependent on the ones nearer sigma holds a slot that a
+                // missing eigenvector needs: restart it instead of accepting
+                std::vector<double> G(kp * kp);
+                PLHR_TRY_CUDA(cudaMemcpyAsync(G.data(), grams, sizeof(double) * kp * kp, cudaMemcpyDeviceToHost, s));
+                PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+                std::vector<char> mark(kp, 0);
+                if (mark_dependent(G.data(), h_order, 1e-8, mark)) {
+                    ++restarts;
+                    PLHR_TRY(restart_columns(mark, 0x2545f4914f6cdd1dull * (uint64_t)(restarts + 1)));
+                    continue;
+                }
+            }
             PLHR_TRY_CUDA(dense_rr(kp, grams + kp * kp, grams, sigma, scale, Crr, theta, dstat + 6, s));
             PLHR_TRY_CUDA(block_times_small(n, V, kp, kp, Crr, kp, Rc, kp, s));   // all Ritz vectors
             PLHR_TRY_CUDA(lap_axpby(g, kp, Rc, kp, AW, kp, 1.0, 0.0, s));
@@ -405,7 +490,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             // carry on from the rotated block (same span): V <- V C, A V explicit
             PLHR_TRY_CUDA(cudaMemcpyAsync(V, Rc, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
             PLHR_TRY_CUDA(cudaMemcpyAsync(AV, AW, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
-            if (!mx && T) PLHR_TRY_CUDA(block_times_small(n, QV, kp, kp, Crr, kp, QV, kp, s));
+            if (!mx && thq) PLHR_TRY_CUDA(block_times_small(n, QV, kp, kp, Crr, kp, QV, kp, s));
             PLHR_TRY_CUDA(cudaMemcpyAsync(lam, theta, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
             {
                 std::vector<double> ones(kp, 1.0);
@@ -519,31 +604,56 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             continue;
         }
         PLHR_TRY(applyT(na, Ract, ldra, W));
-        // -------------------------------------------- S = T(AW - BW Lambda), Q_W = T(AW - sigma BW)
-        double* X2in = T ? X2 : SQ;
-        {
-            PhaseScope ps(PH_STENCIL, s, (double)n * na);
-            PLHR_TRY_CUDA(lap_apply_shifts(g, na, W, na, AW, na, X2in, T ? 2 * na : na, lam_act,
-                                           T ? X2in + na : nullptr, 2 * na, sigma, s));
-        }
         const double* S = SQ;
-        const int64_t lds = T ? 2 * na : na;
-        if (T) PLHR_TRY(applyT(2 * na, X2, 2 * na, SQ));
+        int64_t lds = na;
         const double* QW = SQ + na;
-        // -------------------------------------------- A S, Q_S = T(AS - sigma BS)
-        {
-            PhaseScope ps(PH_STENCIL, s, (double)n * na);
-            PLHR_TRY_CUDA(lap_apply_shifts(g, na, S, lds, AS, na, nullptr, 0, nullptr, T ? X3 : nullptr, na, sigma, s));
+        int64_t ldqw = 2 * na;
+        if (sv) {
+            // ---------------------------------------- S = T(AW - BW Lambda), Q_W = T(AW - sigma BW)
+            {
+                PhaseScope ps(PH_STENCIL, s, (double)n * na);
+                if (thq)
+                    PLHR_TRY_CUDA(lap_apply_shifts(g, na, W, na, AW, na, X2, 2 * na, lam_act, X2 + na, 2 * na, sigma, s));
+                else
+                    PLHR_TRY_CUDA(lap_apply_shifts(g, na, W, na, AW, na, T ? X2 : SQ, na, lam_act, nullptr, 0, sigma, s));
+            }
+            if (thq) {
+                PLHR_TRY(applyT(2 * na, X2, 2 * na, SQ));
+                lds = 2 * na;
+            } else if (T) {
+                PLHR_TRY(applyT(na, X2, na, SQ));
+            }
+            // ---------------------------------------- A S, Q_S = T(AS - sigma BS)
+            {
+                PhaseScope ps(PH_STENCIL, s, (double)n * na);
+                PLHR_TRY_CUDA(lap_apply_shifts(g, na, S, lds, AS, na, nullptr, 0, nullptr, thq ? X3 : nullptr, na, sigma,
+                                               s));
+            }
+            if (thq) PLHR_TRY(applyT(na, X3, na, QS));
+        } else {
+            // ---------------------------------------- trial space [V W P]: A W and Q_W only
+            {
+                PhaseScope ps(PH_STENCIL, s, (double)n * na);
+                PLHR_TRY_CUDA(lap_apply_shifts(g, na, W, na, AW, na, nullptr, 0, nullptr, thq ? X2 : nullptr, na, sigma,
+                                               s));
+            }
+            if (thq) PLHR_TRY(applyT(na, X2, na, SQ));
+            QW = SQ;
+            ldqw = na;
         }
-        if (T) PLHR_TRY(applyT(na, X3, na, QS));
 
-        // -------------------------------------------- Grams over Z = [V W S P], AZ, Q (steps 6-7)
-        const int nb = np ? 4 : 3;
-        const int m = kp + 2 * na + np;
+        // -------------------------------------------- Grams over Z = [V W S P] (or [V W P]), AZ, Q (steps 6-7)
+        const int nb = (sv ? 3 : 2) + (np ? 1 : 0);
+        const int m = kp + (sv ? 2 : 1) * na + np;
         last_m = m;
         Blk<const double> zb[4] = {{V, kp, kp}, {W, na, na}, {S, lds, na}, {P, kp, np}};
         Blk<const double> ab[4] = {{AV, kp, kp}, {AW, na, na}, {AS, na, na}, {AP, kp, np}};
-        Blk<const double> qb[4] = {{QV, kp, kp}, {QW, 2 * na, na}, {QS, na, na}, {QP, kp, np}};
+        Blk<const double> qb[4] = {{QV, kp, kp}, {QW, ldqw, na}, {QS, na, na}, {QP, kp, np}};
+        if (!sv) {   // drop the S family: [V W P]
+            zb[2] = zb[3];
+            ab[2] = ab[3];
+            qb[2] = qb[3];
+        }
         PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
         DenseArgs da;
         da.m = m; da.kp = kp; da.nv = kp;
@@ -554,9 +664,9 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             {
                 PhaseScope ps(PH_GRAM, s, gram_flops(n, m));
                 if (dwf)
-                    PLHR_TRY_CUDA(multi_gram_dw(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams, s));
+                    PLHR_TRY_CUDA(multi_gram_dw(n, nb, zb, ab, thq ? qb : nullptr, sigma, colscale, gpart, grams, s));
                 else
-                    PLHR_TRY_CUDA(multi_gram(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams, s));
+                    PLHR_TRY_CUDA(multi_gram(n, nb, zb, ab, thq ? qb : nullptr, sigma, colscale, gpart, grams, s));
             }
             // ---------------------------------------- projected T-harmonic problem, selection (steps 7-10)
             {
@@ -565,7 +675,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             }
             PLHR_TRY_CUDA(cudaMemcpyAsync(hs->dense, dstat + 3, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
             PLHR_TRY_CUDA(cudaStreamSynchronize(s));
-            if (hs->dense[0] == kDenseOK || !T || pass == 1) break;
+            if (hs->dense[0] == kDenseOK || !thq || pass == 1) break;
             // recovery: the carried images T(A - sigma B)V, T(A - sigma B)P have
             // drifted; recompute them explicitly and project again
             PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
@@ -583,13 +693,13 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         }
         // -------------------------------------------- P, V (steps 11-12), images, RQs (13-14)
         {
-            PhaseScope ps(PH_UPDATE, s, (T ? 4.0 : 2.0) * n * m * kp);
+            PhaseScope ps(PH_UPDATE, s, (thq ? 4.0 : 2.0) * n * m * kp);
             if (dwf) {
                 PLHR_TRY_CUDA(block_update_dw(n, nb, zb, kp, Cp, Cvv, V, kp, P, kp, s));
-                if (T) PLHR_TRY_CUDA(block_update_dw(n, nb, qb, kp, Cp, Cvv, QV, kp, QP, kp, s));
+                if (thq) PLHR_TRY_CUDA(block_update_dw(n, nb, qb, kp, Cp, Cvv, QV, kp, QP, kp, s));
             } else {
                 PLHR_TRY_CUDA(block_update(n, nb, zb, kp, Cp, Cvv, V, kp, P, kp, nullptr, 0, nullptr, nullptr, s));
-                if (T) PLHR_TRY_CUDA(block_update(n, nb, qb, kp, Cp, Cvv, QV, kp, QP, kp, nullptr, 0, nullptr, nullptr, s));
+                if (thq) PLHR_TRY_CUDA(block_update(n, nb, qb, kp, Cp, Cvv, QV, kp, QP, kp, nullptr, 0, nullptr, nullptr, s));
             }
         }
         np = kp;

@@ -8,12 +8,19 @@
 // fixed reference energy.  T is symmetric positive definite and commutes with
 // -1/2 Lap_h.
 //
-// Application: three forward passes (one per axis, each a dense N_a x N_a
-// product along that axis with the matrix in shared memory), the factor
-// fused into the last of them, and three inverse passes.
+// Application: the FP64 block is split once into double-word values (hi + lo
+// FP32 pairs, ~48-bit significands); three forward passes (one per axis, each
+// a dense N_a x N_a product along that axis with the double-word matrix in
+// shared memory, double-word multiply-adds on the FP32 pipes), the factor
+// (a precomputed per-mode table) fused into the last of them, and three
+// inverse passes, the last one writing FP64.  GB300 issues FP64 at 1/64 of
+// the FP32 rate, so a double-word multiply-add (13 FP32 instructions) costs
+// about a fifth of an FP64 one.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "dword.h"
 #include "plhr_internal.h"
 
 namespace plhr {
@@ -30,21 +37,30 @@ struct AxisPass {
     int nc;
 };
 
-__device__ __forceinline__ double tpa(double x) {
+double tpa(double x) {
     const double num = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
     const double x2 = x * x;
     return num / (num + 16.0 * x2 * x2);
 }
 
+// x (double-word, dense [point][nc]) = r (FP64, leading dimension ldr)
+__global__ void __launch_bounds__(kT) k_split(int64_t total, int nc, const double* __restrict__ r, int64_t ldr,
+                                              dw* __restrict__ x) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pt = e / nc;
+        x[e] = dw_from_double_fast(r[pt * ldr + (e - pt * nc)]);
+    }
+}
+
 // out[.., q, ..] = sum_j M[j][q] in[.., j, ..] along one axis (M = S for the
-// forward transform, S^T for the inverse); with scale: times K(mu / E) of the
-// mode (qx, qy, qz) of the element (used on the last forward pass)
-template <bool SCALE>
-__global__ void __launch_bounds__(kT) k_axis(AxisPass a, const double* __restrict__ M, const double* __restrict__ in,
-                                             int64_t ldi, double* __restrict__ out, int64_t ldo,
-                                             const double* __restrict__ mux, const double* __restrict__ muy,
-                                             const double* __restrict__ muz, double inv_e) {
-    extern __shared__ double sm[];
+// forward transform, S^T for the inverse; in dense [point][nc]); with SCALE
+// times the factor K of the element's mode (last forward pass); OUT64: FP64
+// output with leading dimension ldo, else double-word dense
+template <bool SCALE, bool OUT64>
+__global__ void __launch_bounds__(kT) k_axis(AxisPass a, const dw* __restrict__ M, const dw* __restrict__ in,
+                                             void* __restrict__ out, int64_t ldo, const dw* __restrict__ K) {
+    extern __shared__ __align__(8) unsigned char smraw[];
+    dw* sm = reinterpret_cast<dw*>(smraw);
     const int N = a.N;
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) sm[i] = M[i];
     __syncthreads();
@@ -55,13 +71,12 @@ __global__ void __launch_bounds__(kT) k_axis(AxisPass a, const double* __restric
         const int64_t ix = pt % a.nx, t = pt / a.nx, iy = t % a.ny, iz = t / a.ny;
         const int q = (int)(a.axis == 0 ? ix : (a.axis == 1 ? iy : iz));
         const int64_t base = pt - (int64_t)q * a.stride;
-        double s = 0.0;
-        for (int j = 0; j < N; ++j) s = fma(sm[j * N + q], in[(base + j * a.stride) * ldi + c], s);
-        if (SCALE) {
-            double mu = mux[ix] + muy[iy] + (muz ? muz[iz] : 0.0);
-            s *= tpa(mu * inv_e);
-        }
-        out[pt * ldo + c] = s;
+        float hi = 0.0f, lo = 0.0f;
+        for (int j = 0; j < N; ++j) dw_fma_acc(hi, lo, sm[j * N + q], in[(base + j * a.stride) * a.nc + c]);
+        dw v = dw_fast_two_sum(hi, lo);
+        if (SCALE) v = dw_mul(v, K[pt]);
+        if (OUT64) static_cast<double*>(out)[pt * ldo + c] = dw_to_double_fast(v);
+        else static_cast<dw*>(out)[pt * a.nc + c] = v;
     }
 }
 
@@ -108,35 +123,42 @@ cudaError_t spectral_apply(const SpecPrec& P, int nc, const double* r, int64_t l
                            cudaStream_t s) {
     if (nc <= 0) return cudaSuccess;
     const int64_t n = P.n();
-    double* t0 = work;
-    double* t1 = work + n * nc;
+    dw* t0 = reinterpret_cast<dw*>(work);
+    dw* t1 = t0 + n * nc;
     const int64_t Ns[3] = {P.nx, P.ny, P.nz};
     const int64_t strides[3] = {1, P.nx, P.nx * P.ny};
-    const int d = P.d;
     const int64_t total = n * nc;
-    auto pass = [&](int axis, bool inverse, bool scale, const double* in, int64_t ldi, double* out) {
+    const dw* K = reinterpret_cast<const dw*>(P.d_K);
+    auto pass = [&](int axis, bool inverse, bool scale, const dw* in, void* out, bool out64) {
         AxisPass a{P.nx, P.ny, P.nz, axis, (int)Ns[axis], strides[axis], nc};
-        const size_t shm = sizeof(double) * Ns[axis] * Ns[axis];
-        const double* M = inverse ? P.d_St[axis] : P.d_S[axis];
+        const size_t shm = sizeof(dw) * Ns[axis] * Ns[axis];
+        const dw* M = reinterpret_cast<const dw*>(inverse ? P.d_St[axis] : P.d_S[axis]);
         if (scale)
-            k_axis<true><<<nblk(total), kT, shm, s>>>(a, M, in, ldi, out, nc, P.d_mu[0], P.d_mu[1],
-                                                      d == 3 ? P.d_mu[2] : nullptr, 1.0 / P.energy);
+            k_axis<true, false><<<nblk(total), kT, shm, s>>>(a, M, in, out, 0, K);
+        else if (out64)
+            k_axis<false, true><<<nblk(total), kT, shm, s>>>(a, M, in, out, nc, nullptr);
         else
-            k_axis<false><<<nblk(total), kT, shm, s>>>(a, M, in, ldi, out, nc, nullptr, nullptr, nullptr, 0.0);
+            k_axis<false, false><<<nblk(total), kT, shm, s>>>(a, M, in, out, 0, nullptr);
         count_launches(1);
         return cudaGetLastError();
     };
-    cudaError_t e;
-    // forward: x, y (, z); the factor on the last forward pass
-    if ((e = pass(0, false, false, r, ldr, t0)) != cudaSuccess) return e;
-    if ((e = pass(1, false, d == 2, t0, nc, t1)) != cudaSuccess) return e;
-    const double* f = t1;
-    if (d == 3) {
-        if ((e = pass(2, false, true, t1, nc, t0)) != cudaSuccess) return e;
-        if ((e = pass(2, true, false, t0, nc, t1)) != cudaSuccess) return e;
+    k_split<<<nblk(total), kT, 0, s>>>(total, nc, r, ldr, t0);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // forward x, y (, z) with the factor on the last forward pass; inverse in
+    // reverse order; the inverse x pass writes the FP64 result (dense, ld nc)
+    if ((e = pass(0, false, false, t0, t1, false)) != cudaSuccess) return e;
+    if (P.d == 3) {
+        if ((e = pass(1, false, false, t1, t0, false)) != cudaSuccess) return e;
+        if ((e = pass(2, false, true, t0, t1, false)) != cudaSuccess) return e;
+        if ((e = pass(2, true, false, t1, t0, false)) != cudaSuccess) return e;
+        if ((e = pass(1, true, false, t0, t1, false)) != cudaSuccess) return e;
+    } else {
+        if ((e = pass(1, false, true, t1, t0, false)) != cudaSuccess) return e;
+        if ((e = pass(1, true, false, t0, t1, false)) != cudaSuccess) return e;
     }
-    if ((e = pass(1, true, false, f, nc, t0)) != cudaSuccess) return e;
-    return pass(0, true, false, t0, nc, w);
+    return pass(0, true, false, t1, w, true);
 }
 
 }  // namespace plhr
@@ -181,37 +203,57 @@ extern "C" plhr_status plhr_prec_tpa(plhr_prec** out, const plhr_op* A, double s
     P.d = g.d;
     P.nx = Ns[0]; P.ny = Ns[1]; P.nz = Ns[2];
     P.energy = energy;
+    // double-word (hi, lo) pairs of FP64 values
+    auto pairs = [](const std::vector<double>& v) {
+        std::vector<float> w(2 * v.size());
+        for (size_t i = 0; i < v.size(); ++i) {
+            w[2 * i] = (float)v[i];
+            w[2 * i + 1] = (float)(v[i] - (double)w[2 * i]);
+        }
+        return w;
+    };
+    auto upload = [&](float** dst, const std::vector<float>& src) {
+        return cudaMalloc(dst, sizeof(float) * src.size()) == cudaSuccess &&
+               cudaMemcpy(*dst, src.data(), sizeof(float) * src.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    std::vector<double> mus[3];
+    for (int a = 0; a < 3; ++a) mus[a].assign(1, 0.0);
     for (int a = 0; a < g.d; ++a) {
         const int64_t N = Ns[a];
-        std::vector<double> S, mu;
-        axis_basis(N, g.periodic != 0, S, mu);
-        for (auto& v : mu) v *= g.inv_h2();     // scale / h^2: the kinetic operator's eigenvalues
+        std::vector<double> S;
+        axis_basis(N, g.periodic != 0, S, mus[a]);
+        for (auto& v : mus[a]) v *= g.inv_h2();     // scale / h^2: the kinetic operator's eigenvalues
         std::vector<double> St(N * N);
         for (int64_t p = 0; p < N; ++p)
             for (int64_t m = 0; m < N; ++m) St[m * N + p] = S[p * N + m];
-        if (cudaMalloc(&P.d_S[a], sizeof(double) * N * N) != cudaSuccess ||
-            cudaMalloc(&P.d_St[a], sizeof(double) * N * N) != cudaSuccess ||
-            cudaMalloc(&P.d_mu[a], sizeof(double) * N) != cudaSuccess) {
-            set_error("plhr_prec_tpa: cudaMalloc failed");
+        if (!upload(&P.d_S[a], pairs(S)) || !upload(&P.d_St[a], pairs(St))) {
+            set_error("plhr_prec_tpa: device allocation or upload failed");
             plhr_prec_destroy(T);
             return PLHR_ENOMEM;
         }
-        if (cudaMemcpy(P.d_S[a], S.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(P.d_St[a], St.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(P.d_mu[a], mu.data(), sizeof(double) * N, cudaMemcpyHostToDevice) != cudaSuccess) {
-            set_error("plhr_prec_tpa: upload failed");
-            plhr_prec_destroy(T);
-            return PLHR_ECUDA;
-        }
-        const int shm = (int)(sizeof(double) * N * N);
-        if (shm > 48 * 1024) {
-            if (cudaFuncSetAttribute(k_axis<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm) != cudaSuccess ||
-                cudaFuncSetAttribute(k_axis<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm) != cudaSuccess) {
-                set_error("plhr_prec_tpa: shared-memory attribute failed");
-                plhr_prec_destroy(T);
-                return PLHR_ECUDA;
-            }
-        }
+    }
+    // the factor per 3D mode, x fastest
+    std::vector<double> Kf(P.n());
+    for (int64_t iz = 0; iz < P.nz; ++iz)
+        for (int64_t iy = 0; iy < P.ny; ++iy)
+            for (int64_t ix = 0; ix < P.nx; ++ix)
+                Kf[(iz * P.ny + iy) * P.nx + ix] =
+                    tpa((mus[0][ix] + mus[1][iy] + (g.d == 3 ? mus[2][iz] : 0.0)) / energy);
+    if (!upload(&P.d_K, pairs(Kf))) {
+        set_error("plhr_prec_tpa: device allocation or upload failed");
+        plhr_prec_destroy(T);
+        return PLHR_ENOMEM;
+    }
+    int maxN = 0;
+    for (int a = 0; a < g.d; ++a) maxN = std::max<int>(maxN, (int)Ns[a]);
+    const int shm = (int)(sizeof(float) * 2 * maxN * maxN);
+    if (shm > 48 * 1024 &&
+        (cudaFuncSetAttribute(k_axis<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm) != cudaSuccess ||
+         cudaFuncSetAttribute(k_axis<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm) != cudaSuccess ||
+         cudaFuncSetAttribute(k_axis<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm) != cudaSuccess)) {
+        set_error("plhr_prec_tpa: shared-memory attribute failed");
+        plhr_prec_destroy(T);
+        return PLHR_ECUDA;
     }
     *out = T;
     return PLHR_OK;

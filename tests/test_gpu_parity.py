@@ -203,3 +203,42 @@ def test_config2_full(plhr):
     res = _independent_residuals(w, lam, Vn)
     assert np.all(res <= w.tol * 1.0001), res
     assert np.abs(Vn.T @ Vn - np.eye(w.k)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("variant", [{"extraction": "harm"}, {"s_vectors": False},
+                                     {"extraction": "harm", "s_vectors": False}])
+def test_ablation_variants_track_oracle(plhr, variant):
+    """The ablations of Section 5.1 (harmonic instead of T-harmonic extraction;
+    no S block) follow the oracle's iteration with the same options; the
+    harmonic variant converges to eigenpairs of the closed form (the variants
+    without S stall, as the oracle's pin shows)."""
+    w = wl.lap3d_small(16, levels=3, k=4, gap_index=40)
+    A = plhr.Operator.laplacian(w.dims, w.h)
+    T = plhr.AVMG(A, w.sigma, levels=w.mg_levels, nu=w.mg_nu,
+                  transfer=1 if w.extra.get("transfer") == "linear" else 0,
+                  coarse=1 if w.extra.get("coarse") == "fine_spectrum" else 0)
+    v0 = torch.from_numpy(w.v0()).cuda()
+    stalls = variant.get("s_vectors", True) is False
+    maxit = 12 if stalls else 1500
+    lam, V, info = plhr.solve(A, w.sigma, w.k, T=T, tol=w.tol, maxit=maxit, v_init=v0, history=True, **variant)
+    ref = oplhr.solve_workload(w, maxit=8, **variant)     # the first iterations, for tracking
+    for a, b in list(zip(info["history"], ref.history))[:6]:
+        assert np.allclose(a["lam"], b["lam"][: w.k], rtol=1e-9), (a["it"], a["lam"], b["lam"])
+    if stalls:
+        return
+    assert info["converged"]
+    # every returned pair is an eigenpair of the closed form (the harmonic
+    # extraction is the less robust one: with one guard column it may settle
+    # on a farther eigenvalue of a degenerate cluster's neighbourhood)
+    cf = wl.lap_closed_form(w.dims, w.h)
+    for x in lam:
+        assert np.min(np.abs(cf - x)) <= 1e-10 * abs(x)
+    res = _independent_residuals(w, lam, V.cpu().numpy())
+    assert np.all(res <= w.tol * 1.0001), res
+
+
+def test_ablation_variants_rejected_in_mixed_form(plhr):
+    A = plhr.Operator.laplacian((16, 16), 1.0 / 17)
+    for kw in ({"extraction": "harm"}, {"s_vectors": False}):
+        with pytest.raises(plhr.PlhrError):
+            plhr.solve(A, 500.0, 2, precision=plhr.PRECISION_MIXED, **kw)

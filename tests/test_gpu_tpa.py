@@ -1,6 +1,8 @@
 """GPU parity of the Teter-Payne-Allan preconditioner (Section 5.3) against
 the oracle's FFT form, and its use in block PLHR and in the preconditioned
-eigenvector adjoint on Hamiltonians."""
+eigenvector adjoint on Hamiltonians.  The GPU transforms run in double-word
+arithmetic (~2^-48 per operation over six passes of up to 64 terms), hence
+1e-12 relative for the apply."""
 import numpy as np
 import pytest
 
@@ -35,7 +37,7 @@ def test_tpa_apply_matches_oracle_hamiltonian(plhr, dims, periodic, nc, energy):
     X = wl.uniform_block(n, nc, 62)
     Y = T.apply(torch.from_numpy(X).cuda()).cpu().numpy()
     ref = osp.TPA(dims, 0.8, energy, periodic=periodic)(X)
-    assert np.abs(Y - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert np.abs(Y - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("dims", [(6, 5, 4), (10, 8)])
@@ -48,7 +50,7 @@ def test_tpa_apply_matches_oracle_dirichlet_laplacian(plhr, dims):
     X = wl.uniform_block(n, 3, 63)
     Y = T.apply(torch.from_numpy(X).cuda()).cpu().numpy()
     ref = osp.TPA(dims, h, 400.0, periodic=False, scale=1.0)(X)
-    assert np.abs(Y - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert np.abs(Y - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
 def test_tpa_default_energy_and_leading_dimension(plhr):
@@ -64,7 +66,7 @@ def test_tpa_default_energy_and_leading_dimension(plhr):
     out = torch.zeros(512, 9, dtype=torch.float64, device="cuda")
     T.apply(X[:, :4], out=out[:, 2:6])            # strided input and output
     ref = osp.TPA(p["dims"], 1.0, T.energy)(X[:, :4].cpu().numpy())
-    assert np.abs(out[:, 2:6].cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert np.abs(out[:, 2:6].cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
     assert float(out[:, :2].abs().max()) == 0.0 and float(out[:, 6:].abs().max()) == 0.0
 
 

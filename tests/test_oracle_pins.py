@@ -262,6 +262,42 @@ def test_bplhr_3d_avmg_matches_closed_form():
     assert np.all(r.residuals <= w.tol)
 
 
+def test_bplhr_without_s_vectors_stalls():
+    """Section 5.1: without the S block the iteration is much less robust; on
+    the 8^3 case the full method converges while the [V W P] variant is still
+    far from tolerance after three times as many iterations."""
+    w = wl.lap3d_small(8, levels=2, k=4, gap_index=30)
+    full = plhr.solve_workload(w, maxit=500)
+    assert full.converged
+    r = plhr.solve_workload(w, maxit=3 * len(full.history), s_vectors=False)
+    assert not r.converged
+    assert np.max(r.history[-1]["rel"][: w.k]) > 1e3 * w.tol
+
+
+@pytest.mark.parametrize("variant", [{"extraction": "harm"}])
+def test_bplhr_ablation_variants_match_closed_form(variant):
+    """The harmonic extraction of Section 5.1 converges to the closed-form
+    eigenvalues with orthonormal vectors."""
+    w = wl.lap3d_small(8, levels=2, k=4, gap_index=30)
+    r = plhr.solve_workload(w, maxit=1500, **variant)
+    assert r.converged
+    lam = fd_closed_form(w.dims, w.h)
+    ref = lam[np.lexsort((lam, np.abs(lam - w.sigma)))][: w.k]
+    assert np.allclose(np.sort(r.eigvals), np.sort(ref), rtol=1e-10)
+    assert np.all(r.residuals <= w.tol)
+    assert np.abs(r.eigvecs.T @ r.eigvecs - np.eye(w.k)).max() <= 1e-12
+
+
+def test_harmonic_extraction_equals_tharmonic_for_identity_T():
+    """With T = I the T-harmonic test space is the harmonic one (Section 3.1):
+    the two extractions give the same iteration."""
+    w = wl.lap2d_small(16, k=4, gap_index=20)
+    h1 = plhr.solve_workload(w, maxit=8, extraction="tharm").history
+    h2 = plhr.solve_workload(w, maxit=8, extraction="harm").history
+    for a, b in zip(h1, h2):
+        assert np.allclose(a["lam"], b["lam"], rtol=1e-12)
+
+
 def test_bplhr_generalized_fe_with_perturbed_exact_preconditioner():
     """Section 5.1 setting in small: Q1 FE pencil (B != I), T = |A - sB|^{-1} + E
     with a small SPD perturbation E; eigenpairs vs dense eigh(A, B)."""
