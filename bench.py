@@ -60,6 +60,9 @@ FP64_PEAK_TFLOPS = 1.25
 # 64^3 case (n = 262,144, m = 64): 446.1 MB, i.e. bytes per (row x trial column);
 # the traffic grows in proportion to n m (profiles/k_gram_lap3d_64cube.md).
 GRAM_DRAM_BYTES_PER_ROW_COL = 446.1e6 / (262144 * 64)
+# the same for the double-word Gram k_gram_dw (m = 64 launch on the 64^3
+# case: 402.8 MB read + 3.2 MB written; profiles/mixed_form_kernels_lap3d_64cube.md)
+GRAM_DW_DRAM_BYTES_PER_ROW_COL = 405.94e6 / (262144 * 64)
 
 
 class ClockSampler:
@@ -298,11 +301,15 @@ def run_ours(args, world, rank, local):
     dom = dict(roofs[0]) if roofs else None
     if dom is not None:
         dom["traffic"] = None
-        if dom["phase"] == "gram" and args.precision == "f64":
-            m_avg = kp + 2 * kp + kp
-            dom["traffic"] = GRAM_DRAM_BYTES_PER_ROW_COL * n * m_avg
-            dom["traffic_note"] = ("ncu dram bytes of one k_gram launch on the 64^3 case scaled by n m, "
-                                   "per launch (%d launches in the timed steps)" % prof["gram"]["calls"])
+        if dom["phase"] == "gram":
+            m_full = 4 * kp
+            per = GRAM_DRAM_BYTES_PER_ROW_COL if args.precision == "f64" else GRAM_DW_DRAM_BYTES_PER_ROW_COL
+            dom["traffic"] = per * n * m_full
+            dom["traffic_note"] = ("ncu dram__bytes_read + write of one %s launch with m = 64 on the 64^3 case, "
+                                   "scaled by n m to a 128^3, m = 64 launch (algorithmic bytes 3 n m x 8 = %.3g); "
+                                   "%d launches in the timed steps" % (
+                                       "k_gram" if args.precision == "f64" else "k_gram_dw", 24.0 * n * m_full,
+                                       prof["gram"]["calls"]))
         dom["peak_src"] = ("measured (MEASURED_PEAKS.json hbm_gbs)" if dom["unit"] == "GB/s" else
                            "nominal FP64 rate of the profiling recipe" if "FP64" in dom["kernel"] else
                            "FP32 lanes x clock / 13 x 2 flops (double-word multiply-add = 13 FP32 instructions)" if "double-word" in dom["kernel"]

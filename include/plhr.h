@@ -137,8 +137,9 @@ plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma,
  * a periodic grid, sine modes on a Dirichlet grid), mu their eigenvalues.  T
  * is symmetric positive definite and the same for every column.  energy <= 0
  * selects sigma - min(potential) when positive, else the mean of mu.  Any
- * stencil or Hamiltonian operator whose axis sizes are at most 144; the
- * potential is read once here.  Usable by plhr_solve (PLHR_PRECISION_F64),
+ * stencil or Hamiltonian operator whose axis sizes are at most 144 (an
+ * application takes 8 (N^2 + N ncols) <= 200 KB for every axis size N, else
+ * PLHR_ECUDA with an invalid-value error); the potential is read once here.  Usable by plhr_solve (PLHR_PRECISION_F64),
  * plhr_prec_apply and plhr_eigvec_adjoint. */
 plhr_status plhr_prec_tpa(plhr_prec** out, const plhr_op* A, double sigma, double energy);
 /* The reference energy a TPA preconditioner uses (0 for other kinds). */

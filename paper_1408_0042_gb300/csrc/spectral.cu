@@ -52,32 +52,86 @@ __global__ void __launch_bounds__(kT) k_split(int64_t total, int nc, const doubl
     }
 }
 
+// first point of line l along the axis (lines of axis x: (y, z) rows; of
+// axis y: (x, z) with x fastest; of axis z: (x, y) with x fastest, so that
+// consecutive lines are neighbours in memory)
+__device__ __forceinline__ int64_t line_base(const AxisPass& a, int64_t l) {
+    if (a.axis == 0) return l * a.nx;
+    if (a.axis == 1) return (l / a.nx) * a.nx * a.ny + l % a.nx;
+    return l;
+}
+
+constexpr int kQ = 4;   // outputs along the axis per thread (register block)
+
 // out[.., q, ..] = sum_j M[j][q] in[.., j, ..] along one axis (M = S for the
-// forward transform, S^T for the inverse; in dense [point][nc]); with SCALE
-// times the factor K of the element's mode (last forward pass); OUT64: FP64
-// output with leading dimension ldo, else double-word dense
+// forward transform, S^T for the inverse; in dense [point][nc]), for tiles of
+// TL lines: the CTA stages the tile's N x TL x nc inputs in shared memory
+// once, and each thread forms kQ outputs of one (line, column) from them.
+// SCALE: times the factor K of the output's mode (last forward pass); OUT64:
+// FP64 output with leading dimension ldo, else double-word dense
 template <bool SCALE, bool OUT64>
-__global__ void __launch_bounds__(kT) k_axis(AxisPass a, const dw* __restrict__ M, const dw* __restrict__ in,
-                                             void* __restrict__ out, int64_t ldo, const dw* __restrict__ K) {
-    extern __shared__ __align__(8) unsigned char smraw[];
-    dw* sm = reinterpret_cast<dw*>(smraw);
-    const int N = a.N;
+__global__ void __launch_bounds__(kT) k_axis(AxisPass a, int TL, const dw* __restrict__ M,
+                                             const dw* __restrict__ in, void* __restrict__ out, int64_t ldo,
+                                             const dw* __restrict__ K) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = a.N, nc = a.nc;
+    dw* sm = reinterpret_cast<dw*>(smraw);   // [N][N]
+    dw* tile = sm + N * N;                   // [N][TL][nc]
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) sm[i] = M[i];
-    __syncthreads();
-    const int64_t total = a.nx * a.ny * a.nz * a.nc;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t pt = e / a.nc;
-        const int c = (int)(e - pt * a.nc);
-        const int64_t ix = pt % a.nx, t = pt / a.nx, iy = t % a.ny, iz = t / a.ny;
-        const int q = (int)(a.axis == 0 ? ix : (a.axis == 1 ? iy : iz));
-        const int64_t base = pt - (int64_t)q * a.stride;
-        float hi = 0.0f, lo = 0.0f;
-        for (int j = 0; j < N; ++j) dw_fma_acc(hi, lo, sm[j * N + q], in[(base + j * a.stride) * a.nc + c]);
-        dw v = dw_fast_two_sum(hi, lo);
-        if (SCALE) v = dw_mul(v, K[pt]);
-        if (OUT64) static_cast<double*>(out)[pt * ldo + c] = dw_to_double_fast(v);
-        else static_cast<dw*>(out)[pt * a.nc + c] = v;
+    const int64_t L = a.nx * a.ny * a.nz / N;
+    const int nqg = (N + kQ - 1) / kQ;
+    for (int64_t l0 = (int64_t)blockIdx.x * TL; l0 < L; l0 += (int64_t)gridDim.x * TL) {
+        const int nl = (int)(L - l0 < TL ? L - l0 : TL);
+        __syncthreads();   // the previous tile is consumed (and M is staged)
+        const int tot = N * nl * nc;
+        for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+            const int c = t % nc, r = t / nc, o = r % nl, j = r / nl;
+            tile[(j * TL + o) * nc + c] = in[(line_base(a, l0 + o) + (int64_t)j * a.stride) * nc + c];
+        }
+        __syncthreads();
+        const int items = nqg * nl * nc;
+        for (int t = threadIdx.x; t < items; t += blockDim.x) {
+            const int c = t % nc, r = t / nc, o = r % nl, qg = r / nl;
+            const int q0 = qg * kQ;
+            float hi[kQ], lo[kQ];
+#pragma unroll
+            for (int u = 0; u < kQ; ++u) { hi[u] = 0.0f; lo[u] = 0.0f; }
+            if (q0 + kQ <= N) {
+                for (int j = 0; j < N; ++j) {
+                    const dw x = tile[(j * TL + o) * nc + c];
+                    const dw* mr = sm + j * N + q0;
+#pragma unroll
+                    for (int u = 0; u < kQ; ++u) dw_fma_acc(hi[u], lo[u], mr[u], x);
+                }
+            } else {
+                for (int j = 0; j < N; ++j) {
+                    const dw x = tile[(j * TL + o) * nc + c];
+#pragma unroll
+                    for (int u = 0; u < kQ; ++u)
+                        if (q0 + u < N) dw_fma_acc(hi[u], lo[u], sm[j * N + q0 + u], x);
+                }
+            }
+            const int64_t base = line_base(a, l0 + o);
+#pragma unroll
+            for (int u = 0; u < kQ; ++u) {
+                if (q0 + u >= N) break;
+                const int64_t pt = base + (int64_t)(q0 + u) * a.stride;
+                dw v = dw_fast_two_sum(hi[u], lo[u]);
+                if (SCALE) v = dw_mul(v, K[pt]);
+                if (OUT64) static_cast<double*>(out)[pt * ldo + c] = dw_to_double_fast(v);
+                else static_cast<dw*>(out)[pt * nc + c] = v;
+            }
+        }
     }
+}
+
+// shared memory of one k_axis launch and its tile height (lines per CTA)
+constexpr int kAxisShm = 200 * 1024;
+int tile_lines(int N, int nc) {
+    const int64_t room = (int64_t)kAxisShm - (int64_t)sizeof(dw) * N * N;
+    int64_t tl = room / ((int64_t)sizeof(dw) * N * nc);
+    if (tl > 8) tl = 8;
+    return (int)(tl < 1 ? 1 : tl);
 }
 
 int nblk(int64_t total) { return grid_size_for(total, kT, sm_count() * 8); }
@@ -131,14 +185,20 @@ cudaError_t spectral_apply(const SpecPrec& P, int nc, const double* r, int64_t l
     const dw* K = reinterpret_cast<const dw*>(P.d_K);
     auto pass = [&](int axis, bool inverse, bool scale, const dw* in, void* out, bool out64) {
         AxisPass a{P.nx, P.ny, P.nz, axis, (int)Ns[axis], strides[axis], nc};
-        const size_t shm = sizeof(dw) * Ns[axis] * Ns[axis];
+        const int N = (int)Ns[axis];
+        // one line of nc columns and the matrix must fit the shared memory
+        if ((int64_t)sizeof(dw) * ((int64_t)N * N + (int64_t)N * nc) > kAxisShm) return cudaErrorInvalidValue;
+        const int TL = tile_lines(N, nc);
+        const size_t shm = sizeof(dw) * ((size_t)N * N + (size_t)N * TL * nc);
+        const int64_t lines = n / N;
+        const int blocks = (int)std::min<int64_t>((lines + TL - 1) / TL, (int64_t)sm_count() * 16);
         const dw* M = reinterpret_cast<const dw*>(inverse ? P.d_St[axis] : P.d_S[axis]);
         if (scale)
-            k_axis<true, false><<<nblk(total), kT, shm, s>>>(a, M, in, out, 0, K);
+            k_axis<true, false><<<blocks, kT, shm, s>>>(a, TL, M, in, out, 0, K);
         else if (out64)
-            k_axis<false, true><<<nblk(total), kT, shm, s>>>(a, M, in, out, nc, nullptr);
+            k_axis<false, true><<<blocks, kT, shm, s>>>(a, TL, M, in, out, nc, nullptr);
         else
-            k_axis<false, false><<<nblk(total), kT, shm, s>>>(a, M, in, out, 0, nullptr);
+            k_axis<false, false><<<blocks, kT, shm, s>>>(a, TL, M, in, out, 0, nullptr);
         count_launches(1);
         return cudaGetLastError();
     };
@@ -244,13 +304,10 @@ extern "C" plhr_status plhr_prec_tpa(plhr_prec** out, const plhr_op* A, double s
         plhr_prec_destroy(T);
         return PLHR_ENOMEM;
     }
-    int maxN = 0;
-    for (int a = 0; a < g.d; ++a) maxN = std::max<int>(maxN, (int)Ns[a]);
-    const int shm = (int)(sizeof(float) * 2 * maxN * maxN);
-    if (shm > 48 * 1024 &&
-        (cudaFuncSetAttribute(k_axis<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm) != cudaSuccess ||
-         cudaFuncSetAttribute(k_axis<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm) != cudaSuccess ||
-         cudaFuncSetAttribute(k_axis<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm) != cudaSuccess)) {
+    const int shm = kAxisShm;   // the launches size their tiles to fit
+    if (cudaFuncSetAttribute(k_axis<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_axis<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_axis<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm) != cudaSuccess) {
         set_error("plhr_prec_tpa: shared-memory attribute failed");
         plhr_prec_destroy(T);
         return PLHR_ECUDA;
