@@ -262,7 +262,11 @@ plhr_status plhr_eigvec_adjoint(const plhr_op* A, plhr_prec* T, int k, const dou
  *   A        stencil (plhr_op_stencil), Hamiltonian (plhr_op_hamiltonian) or
  *            CSR (plhr_op_csr); PLHR_PRECISION_MIXED takes the Dirichlet
  *            Laplacian with AV-MG or T = NULL only.
- *   B        NULL = identity.
+ *   B        NULL = identity; else a symmetric positive definite operator of
+ *            A's size (stencil, Hamiltonian or CSR), PLHR_PRECISION_F64 only:
+ *            the B images of V, W, S, P are formed explicitly, the Grams are
+ *            Z^T B Z, U^T Q and Q^T B Z with U = A Z - sigma B Z, and the
+ *            returned vectors are B-orthonormal.
  *   T        NULL = identity (no preconditioning); AV-MG, TPA, diagonal or
  *            callback, symmetric positive definite.
  *   tol      relative residual ||A v - lambda B v|| / (max(|lambda|, 1) ||B v||).

@@ -453,9 +453,10 @@ def profile_read(reset: bool = False) -> dict:
 def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float = 1e-8, maxit: int = 1000,
           v_init=None, seed: int = 20140801, history: bool = False, precision: int = PRECISION_F64,
           stream=None, raise_on_notconv: bool = False, guard: int = 1, switch_tol: float = 1e-5,
-          extraction: str = "tharm", s_vectors: bool = True):
+          extraction: str = "tharm", s_vectors: bool = True, B: Operator | None = None):
     """k eigenpairs of A v = lambda v nearest sigma with k + guard block
-    columns.  extraction "tharm" (T-harmonic, default) or "harm" (harmonic:
+    columns (B: the generalized problem A v = lambda B v, FP64 form).
+    extraction "tharm" (T-harmonic, default) or "harm" (harmonic:
     T = I in the Petrov-Galerkin condition); s_vectors False drops the S block
     (trial space [V W P]).  Returns (eigvals (numpy, k), eigvecs (torch n x k
     float64, CUDA), info dict)."""
@@ -489,7 +490,7 @@ def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float =
     vals = np.zeros(k, dtype=np.float64)
     vecs = torch.empty((n, k), dtype=torch.float64, device="cuda")
     info = Info()
-    st = lib.plhr_solve(A._h, None, sigma, k, T._h if T is not None else None, tol, ctypes.byref(opt),
+    st = lib.plhr_solve(A._h, B._h if B is not None else None, sigma, k, T._h if T is not None else None, tol, ctypes.byref(opt),
                         vals.ctypes.data, ctypes.c_void_p(vecs.data_ptr()), k, ctypes.byref(info),
                         _stream_ptr(stream))
     if st not in (PLHR_OK, PLHR_ENOTCONV) or (raise_on_notconv and st == PLHR_ENOTCONV):

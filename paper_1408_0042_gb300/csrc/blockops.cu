@@ -94,14 +94,17 @@ __device__ __forceinline__ void stage_rows(double* dst, int m, int64_t row0, int
 }
 
 // Gram tile bookkeeping: 4x4 register tiles over three m x m outputs.
-//   g = 0: Z^T Z (upper tiles only), g = 1: U^T Q, g = 2: Q^T Z
+//   g = 0: Z^T BZ (upper tiles only), g = 1: U^T Q, g = 2: Q^T BZ, with
+//   U = AZ - sigma BZ; without a BZ family (B = I) BZ is Z
 __global__ void __launch_bounds__(kGramThreads) k_gram(int64_t n, int m, int nb, FamPtrs Z, FamPtrs AZ, FamPtrs Q,
-                                                       int q_from_u, double sigma, const double* __restrict__ csc,
+                                                       FamPtrs BZ, int has_b, int q_from_u, double sigma,
+                                                       const double* __restrict__ csc,
                                                        double* __restrict__ partial) {
     extern __shared__ double sh[];
     double* sz = sh;                         // [rows][m]
     double* su = sz + kGramRows * m;         // [rows][m]
     double* sq = su + kGramRows * m;         // [rows][m]
+    double* sb = has_b ? sq + kGramRows * m : sz;   // [rows][m], B Z
     const int T = (m + 3) / 4;
     const int nt0 = T * (T + 1) / 2, nt1 = T * T;
     const int ntiles = nt0 + 2 * nt1;
@@ -132,25 +135,32 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(int64_t n, int m, int nb,
         stage_rows(sz, m, row0, nrows, Z, nb);
         stage_rows(su, m, row0, nrows, AZ, nb);
         if (!q_from_u) stage_rows(sq, m, row0, nrows, Q, nb);
+        if (has_b) stage_rows(sb, m, row0, nrows, BZ, nb);
         __syncthreads();
-        // u = (az - sigma z) * scale, z, q scaled by the column scales
+        // u = (az - sigma bz) * scale, z, bz, q scaled by the column scales
         // (q = u when T = I)
         for (int t = threadIdx.x; t < nrows * m; t += blockDim.x) {
             int c = t % m;
             double s = csc[c];
             double z = sz[t] * s;
             sz[t] = z;
-            double u = su[t] * s - sigma * z;
+            double bz = z;
+            if (has_b) {
+                bz = sb[t] * s;
+                sb[t] = bz;
+            }
+            double u = su[t] * s - sigma * bz;
             su[t] = u;
             sq[t] = q_from_u ? u : sq[t] * s;
         }
         for (int t = nrows * m + threadIdx.x; t < kGramRows * m; t += blockDim.x) {
             sz[t] = 0.0; su[t] = 0.0; sq[t] = 0.0;
+            if (has_b) sb[t] = 0.0;
         }
         __syncthreads();
         for (int q = 0; q < my; ++q) {
             const double* A = tg[q] == 0 ? sz : (tg[q] == 1 ? su : sq);
-            const double* B = tg[q] == 0 ? sz : (tg[q] == 1 ? sq : sz);
+            const double* B = tg[q] == 0 ? sb : (tg[q] == 1 ? sq : sb);
             int i0 = ti[q] * 4, j0 = tj[q] * 4;
             for (int r = 0; r < kGramRows; ++r) {
                 double a[4], b[4];
@@ -287,12 +297,19 @@ cudaError_t residual_norms(int64_t n, int kp, const double* V, int64_t ldv, cons
 cudaError_t multi_gram(int64_t n, int nb, const Blk<const double>* Z, const Blk<const double>* AZ,
                        const Blk<const double>* Q, double sigma, const double* colscale, double* partial,
                        double* out, cudaStream_t s) {
-    FamPtrs FZ = fam_of(Z, nb), FA = fam_of(AZ, nb), FQ = fam_of(Q ? Q : AZ, nb);
+    return multi_gram_b(n, nb, Z, AZ, Q, nullptr, sigma, colscale, partial, out, s);
+}
+
+cudaError_t multi_gram_b(int64_t n, int nb, const Blk<const double>* Z, const Blk<const double>* AZ,
+                         const Blk<const double>* Q, const Blk<const double>* BZ, double sigma,
+                         const double* colscale, double* partial, double* out, cudaStream_t s) {
+    FamPtrs FZ = fam_of(Z, nb), FA = fam_of(AZ, nb), FQ = fam_of(Q ? Q : AZ, nb), FB = fam_of(BZ ? BZ : Z, nb);
     int m = 0;
     for (int i = 0; i < nb; ++i) m += Z[i].nc;
     int blocks = reduce_blocks();
-    size_t shm = sizeof(double) * 3 * kGramRows * m;
-    k_gram<<<blocks, kGramThreads, shm, s>>>(n, m, nb, FZ, FA, FQ, Q ? 0 : 1, sigma, colscale, partial);
+    size_t shm = sizeof(double) * (BZ ? 4 : 3) * kGramRows * m;
+    k_gram<<<blocks, kGramThreads, shm, s>>>(n, m, nb, FZ, FA, FQ, FB, BZ ? 1 : 0, Q ? 0 : 1, sigma, colscale,
+                                             partial);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -403,6 +420,34 @@ cudaError_t gather_columns(int64_t n, const double* X, int64_t ldx, const int* i
                            cudaStream_t s) {
     if (n == 0 || nc == 0) return cudaSuccess;
     k_gather<<<grid_size_for(n * nc, 256, sm_count() * 16), 256, 0, s>>>(n, X, ldx, idx, nc, Y, ldy);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void __launch_bounds__(256) k_shift_combine(int64_t n, int nc, const double* __restrict__ AX, int64_t ldax,
+                                                       const double* __restrict__ BX, int64_t ldbx,
+                                                       const double* __restrict__ lam, double* __restrict__ o1,
+                                                       int64_t ld1, double sig, double* __restrict__ o2,
+                                                       int64_t ld2) {
+    const int64_t total = n * nc;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / nc;
+        const int c = (int)(e - i * nc);
+        const double a = AX[i * ldax + c], b = BX[i * ldbx + c];
+        if (o1) o1[i * ld1 + c] = a - lam[c] * b;
+        if (o2) o2[i * ld2 + c] = a - sig * b;
+    }
+}
+}  // namespace
+
+cudaError_t shift_combine(int64_t n, int nc, const double* AX, int64_t ldax, const double* BX, int64_t ldbx,
+                          const double* lam, double* o1, int64_t ld1, double sig, double* o2, int64_t ld2,
+                          cudaStream_t s) {
+    const int64_t total = n * nc;
+    if (total == 0) return cudaSuccess;
+    k_shift_combine<<<grid_size_for(total, 256, sm_count() * 16), 256, 0, s>>>(n, nc, AX, ldax, BX, ldbx, lam, o1,
+                                                                                ld1, sig, o2, ld2);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -23,6 +23,18 @@ cudaError_t multi_gram(int64_t n, int nb, const Blk<const double>* Z, const Blk<
                        const Blk<const double>* Q, double sigma, const double* colscale, double* partial,
                        double* out, cudaStream_t s);
 
+// The same with a B Z family (generalized problem): out = [Z^T BZ | U^T Q |
+// Q^T BZ], U = AZ - sigma BZ; BZ == nullptr is B = I (multi_gram).  The
+// partial buffer is the same.
+cudaError_t multi_gram_b(int64_t n, int nb, const Blk<const double>* Z, const Blk<const double>* AZ,
+                         const Blk<const double>* Q, const Blk<const double>* BZ, double sigma,
+                         const double* colscale, double* partial, double* out, cudaStream_t s);
+
+// o1 = AX - BX diag(lam) and o2 = AX - sig BX (each optional), n x nc
+cudaError_t shift_combine(int64_t n, int nc, const double* AX, int64_t ldax, const double* BX, int64_t ldbx,
+                          const double* lam, double* o1, int64_t ld1, double sig, double* o2, int64_t ld2,
+                          cudaStream_t s);
+
 // Family F = [F_0 .. F_{nb-1}] (m columns): Pout = F C_P, Vout = F_0 C_VV + F C_P
 // (in place allowed: Vout may be F_0, Pout may be F_{nb-1}).  When dotV is
 // given, out[0:kp] = sum Vout .* dotV, out[kp:2kp] = sum dotV .^ 2.

@@ -90,8 +90,8 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         set_error("plhr_solve: invalid argument");
         return PLHR_EINVAL;
     }
-    if (B != nullptr) {
-        set_error("plhr_solve: only B = identity is supported by this build");
+    if (B != nullptr && (B->g.n() != A->g.n() || opt.precision != PLHR_PRECISION_F64)) {
+        set_error("plhr_solve: B must have the size of A, and B != I runs in PLHR_PRECISION_F64");
         return PLHR_EINVAL;
     }
     if (!opt.real_arithmetic || (opt.precision != PLHR_PRECISION_F64 && opt.precision != PLHR_PRECISION_MIXED) ||
@@ -135,12 +135,14 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
 
     // ---------------------------------------------------------------- workspace
     const int64_t nk = n * kp;
+    const bool hasB = B != nullptr;
     const int64_t big_doubles = 6 * nk /*V AV QV P AP QP*/ + nk /*R*/ + nk /*Rc*/ + nk /*W*/ + nk /*AW*/ +
-                                2 * nk /*SQ*/ + 2 * nk /*X2*/ + nk /*AS*/ + nk /*X3*/ + nk /*QS*/;
+                                2 * nk /*SQ*/ + 2 * nk /*X2*/ + nk /*AS*/ + nk /*X3*/ + nk /*QS*/ +
+                                (hasB ? 4 * nk /*BV BW BS BP*/ : 0);
     const int m3 = 3 * mmax * mmax;
     const int64_t part_doubles = (int64_t)reduce_blocks() * m3 + (int64_t)residual_blocks(kp) * 2 * kp + 64;
     const int64_t small_doubles = m3 /*grams*/ + (int64_t)dense_work_doubles() + mmax * kp /*Cp*/ + kp * kp /*Cvv*/ +
-                                  8 * 64 /*vectors*/ + kp * kp /*Crr*/ + 2 * 64 /*xi*/;
+                                  9 * 64 /*vectors*/ + kp * kp /*Crr*/ + 2 * 64 /*xi*/;
     DevBuf big, part, small;
     if (cudaMallocAsync(&big.p, sizeof(double) * big_doubles, s) != cudaSuccess ||
         cudaMallocAsync(&part.p, sizeof(double) * part_doubles, s) != cudaSuccess ||
@@ -174,6 +176,9 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     double *V = take(nk), *AV = take(nk), *QV = take(nk), *P = take(nk), *AP = take(nk), *QP = take(nk);
     double *R = take(nk), *Rc = take(nk), *W = take(nk), *AW = take(nk), *SQ = take(2 * nk), *X2 = take(2 * nk);
     double *AS = take(nk), *X3 = take(nk), *QS = take(nk);
+    // B images of V, W, S, P (generalized problem A v = lambda B v)
+    double *BV = hasB ? take(nk) : nullptr, *BW = hasB ? take(nk) : nullptr, *BS = hasB ? take(nk) : nullptr,
+           *BP = hasB ? take(nk) : nullptr;
     // FP32 blocks of the mixed form: W, A W, [S | Q_W], its input, A S, A S - sigma S,
     // Q_S, P, A P, Q_P, Q_V
     bool mx = opt.precision == PLHR_PRECISION_MIXED;
@@ -228,6 +233,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     double* lam_act = q; q += 64;
     double* dots = q; q += 64;
     double* theta = q; q += 64;
+    double* dots2 = q; q += 64;
     double* Crr = q; q += kp * kp;
     double* xi = q; q += 128;
     int* active = ints;
@@ -268,6 +274,29 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         return PLHR_OK;
     };
 
+    // A X with the shifted outputs o1 = AX - BX diag(lam), o2 = AX - sigma BX
+    // (each optional); BX = B X is formed when B is given (FP64 forms)
+    auto prod = [&](int nc, const double* X, int64_t ldx, double* AX, int64_t ldax, double* BX, int64_t ldbx,
+                    double* o1, int64_t ld1, const double* lamv, double* o2, int64_t ld2) -> plhr_status {
+        if (!hasB) {
+            PLHR_TRY_CUDA(lap_apply_shifts(g, nc, X, ldx, AX, ldax, o1, ld1, lamv, o2, ld2, sigma, s));
+            return PLHR_OK;
+        }
+        PLHR_TRY_CUDA(lap_axpby(g, nc, X, ldx, AX, ldax, 1.0, 0.0, s));
+        PLHR_TRY_CUDA(lap_axpby(B->g, nc, X, ldx, BX, ldbx, 1.0, 0.0, s));
+        if (o1 || o2) PLHR_TRY_CUDA(shift_combine(n, nc, AX, ldax, BX, ldbx, lamv, o1, ld1, sigma, o2, ld2, s));
+        return PLHR_OK;
+    };
+    // dots = [v.Av (kp) | v.Bv (kp)] for the Rayleigh quotients and scales
+    auto rq_dots = [&]() -> plhr_status {
+        PLHR_TRY_CUDA(column_dots(n, kp, V, kp, AV, kp, rpart, dots, s));   // v.Av, v.v
+        if (hasB) {
+            PLHR_TRY_CUDA(column_dots(n, kp, V, kp, BV, kp, rpart, dots2, s));
+            PLHR_TRY_CUDA(cudaMemcpyAsync(dots + kp, dots2, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
+        }
+        return PLHR_OK;
+    };
+
     // ---------------------------------------------------------------- start (Alg. 3 steps 1-2)
     if (opt.v_init)
         PLHR_TRY_CUDA(cudaMemcpy2DAsync(V, sizeof(double) * kp, opt.v_init, sizeof(double) * opt.ld_init,
@@ -276,12 +305,12 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         PLHR_TRY_CUDA(seeded_block(n, kp, opt.seed, V, kp, s));
     // AV, X3 := AV - sigma V, QV = T(AV - sigma V) (with T = I, Q = AZ - sigma Z is
     // formed inside the Gram pass and no Q block is stored)
-    PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
+    PLHR_TRY(prod(kp, V, kp, AV, kp, BV, kp, nullptr, 0, nullptr, X3, kp));
     if (thq) {
         if (mx) PLHR_TRY(applyT32(kp, (const double*)X3, kp, QV32));
         else PLHR_TRY(applyT(kp, X3, kp, QV));
     }
-    PLHR_TRY_CUDA(column_dots(n, kp, V, kp, AV, kp, rpart, dots, s));   // v.Av, v.v
+    PLHR_TRY(rq_dots());
     {
         std::vector<int> zeros(64, 0), neg(64, -1);
         PLHR_TRY_CUDA(cudaMemcpyAsync(tags, zeros.data(), sizeof(int) * 64, cudaMemcpyHostToDevice, s));
@@ -296,11 +325,13 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     auto refresh_images = [&]() -> plhr_status {
         PhaseScope ps(PH_STENCIL, s, (double)n * (np ? 2 * kp : kp));
         PLHR_TRY_CUDA(lap_axpby(g, kp, V, kp, AV, kp, 1.0, 0.0, s));
+        if (hasB) PLHR_TRY_CUDA(lap_axpby(B->g, kp, V, kp, BV, kp, 1.0, 0.0, s));
         if (np) {
             if (mx) PLHR_TRY_CUDA(lap32_apply_shifts(g, kp, P32, kp, AP32, kp, nullptr, 0, nullptr, nullptr, 0, 0.0, s));
             else PLHR_TRY_CUDA(lap_axpby(g, kp, P, kp, AP, kp, 1.0, 0.0, s));
+            if (hasB) PLHR_TRY_CUDA(lap_axpby(B->g, kp, P, kp, BP, kp, 1.0, 0.0, s));
         }
-        PLHR_TRY_CUDA(column_dots(n, kp, V, kp, AV, kp, rpart, dots, s));
+        PLHR_TRY(rq_dots());
         return PLHR_OK;
     };
 
@@ -343,12 +374,12 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             if (mark[j])
                 PLHR_TRY_CUDA(cudaMemcpy2DAsync(V + j, sizeof(double) * kp, Rc + j, sizeof(double) * kp,
                                                 sizeof(double), n, cudaMemcpyDeviceToDevice, s));
-        PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
+        PLHR_TRY(prod(kp, V, kp, AV, kp, BV, kp, nullptr, 0, nullptr, X3, kp));
         if (thq) PLHR_TRY(applyT(kp, X3, kp, QV));
         std::vector<int> zeros(64, 0), neg(64, -1);
         PLHR_TRY_CUDA(cudaMemcpyAsync(tags, zeros.data(), sizeof(int) * 64, cudaMemcpyHostToDevice, s));
         PLHR_TRY_CUDA(cudaMemcpyAsync(partner, neg.data(), sizeof(int) * 64, cudaMemcpyHostToDevice, s));
-        PLHR_TRY_CUDA(column_dots(n, kp, V, kp, AV, kp, rpart, dots, s));
+        PLHR_TRY(rq_dots());
         PLHR_TRY_CUDA(dense_rq(kp, dots, tags, partner, lam, scale, s));
         PLHR_TRY_CUDA(cudaStreamSynchronize(s));   // the host vectors above
         return PLHR_OK;
@@ -413,7 +444,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         // -------------------------------------------- residual, convergence (step 4 input)
         {
             PhaseScope ps(PH_OTHER, s, (double)n * kp);
-            PLHR_TRY_CUDA(residual_norms(n, kp, V, kp, AV, kp, lam, scale, R, kp, rpart, sums, s));
+            PLHR_TRY_CUDA(residual_norms(n, kp, hasB ? BV : V, kp, AV, kp, lam, scale, R, kp, rpart, sums, s));
         }
         StatusArgs sa;
         sa.kp = kp; sa.k = k; sa.sigma = sigma; sa.tol = tol;
@@ -445,10 +476,12 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             // final standard Rayleigh-Ritz (Alg. 3 step 16) and acceptance on the
             // returned vectors: explicit A V, B V
             PLHR_TRY_CUDA(lap_axpby(g, kp, V, kp, AW, kp, 1.0, 0.0, s));
-            Blk<const double> zb[1] = {{V, kp, kp}}, ab[1] = {{AW, kp, kp}}, qb[1] = {{V, kp, kp}};
+            if (hasB) PLHR_TRY_CUDA(lap_axpby(B->g, kp, V, kp, X3, kp, 1.0, 0.0, s));
+            Blk<const double> zb[1] = {{V, kp, kp}}, ab[1] = {{AW, kp, kp}}, qb[1] = {{V, kp, kp}},
+                              bzb[1] = {{X3, kp, kp}};
             PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
-            PLHR_TRY_CUDA(multi_gram(n, 1, zb, ab, qb, 0.0, colscale, gpart, grams, s));
-            // grams: [V^T V | (AV)^T V | V^T V] (kp x kp blocks)
+            PLHR_TRY_CUDA(multi_gram_b(n, 1, zb, ab, qb, hasB ? bzb : nullptr, 0.0, colscale, gpart, grams, s));
+            // grams: [V^T B V | (AV)^T V | V^T B V] (kp x kp blocks)
             if (!mx && kp > k && restarts < 8) {
                 // a column dependent on the ones nearer sigma holds a slot that a
                 // missing eigenvector needs: restart it instead of accepting
@@ -465,11 +498,12 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             PLHR_TRY_CUDA(dense_rr(kp, grams + kp * kp, grams, sigma, scale, Crr, theta, dstat + 6, s));
             PLHR_TRY_CUDA(block_times_small(n, V, kp, kp, Crr, kp, Rc, kp, s));   // all Ritz vectors
             PLHR_TRY_CUDA(lap_axpby(g, kp, Rc, kp, AW, kp, 1.0, 0.0, s));
+            if (hasB) PLHR_TRY_CUDA(lap_axpby(B->g, kp, Rc, kp, X3, kp, 1.0, 0.0, s));
             {
                 std::vector<double> ones(kp, 1.0);
                 PLHR_TRY_CUDA(cudaMemcpyAsync(dots, ones.data(), sizeof(double) * kp, cudaMemcpyHostToDevice, s));
             }
-            PLHR_TRY_CUDA(residual_norms(n, kp, Rc, kp, AW, kp, theta, dots, R, kp, rpart, sums, s));
+            PLHR_TRY_CUDA(residual_norms(n, kp, hasB ? X3 : Rc, kp, AW, kp, theta, dots, R, kp, rpart, sums, s));
             sa.lam = theta;
             PLHR_TRY_CUDA(dense_status(sa, s));
             PLHR_TRY_CUDA(cudaMemcpyAsync(hs, dstat, sizeof(int) * 7, cudaMemcpyDeviceToHost, s));
@@ -490,6 +524,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             // carry on from the rotated block (same span): V <- V C, A V explicit
             PLHR_TRY_CUDA(cudaMemcpyAsync(V, Rc, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
             PLHR_TRY_CUDA(cudaMemcpyAsync(AV, AW, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
+            if (hasB) PLHR_TRY_CUDA(cudaMemcpyAsync(BV, X3, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
             if (!mx && thq) PLHR_TRY_CUDA(block_times_small(n, QV, kp, kp, Crr, kp, QV, kp, s));
             PLHR_TRY_CUDA(cudaMemcpyAsync(lam, theta, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
             {
@@ -613,9 +648,9 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             {
                 PhaseScope ps(PH_STENCIL, s, (double)n * na);
                 if (thq)
-                    PLHR_TRY_CUDA(lap_apply_shifts(g, na, W, na, AW, na, X2, 2 * na, lam_act, X2 + na, 2 * na, sigma, s));
+                    PLHR_TRY(prod(na, W, na, AW, na, BW, na, X2, 2 * na, lam_act, X2 + na, 2 * na));
                 else
-                    PLHR_TRY_CUDA(lap_apply_shifts(g, na, W, na, AW, na, T ? X2 : SQ, na, lam_act, nullptr, 0, sigma, s));
+                    PLHR_TRY(prod(na, W, na, AW, na, BW, na, T ? X2 : SQ, na, lam_act, nullptr, 0));
             }
             if (thq) {
                 PLHR_TRY(applyT(2 * na, X2, 2 * na, SQ));
@@ -626,16 +661,14 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             // ---------------------------------------- A S, Q_S = T(AS - sigma BS)
             {
                 PhaseScope ps(PH_STENCIL, s, (double)n * na);
-                PLHR_TRY_CUDA(lap_apply_shifts(g, na, S, lds, AS, na, nullptr, 0, nullptr, thq ? X3 : nullptr, na, sigma,
-                                               s));
+                PLHR_TRY(prod(na, S, lds, AS, na, BS, na, nullptr, 0, nullptr, thq ? X3 : nullptr, na));
             }
             if (thq) PLHR_TRY(applyT(na, X3, na, QS));
         } else {
             // ---------------------------------------- trial space [V W P]: A W and Q_W only
             {
                 PhaseScope ps(PH_STENCIL, s, (double)n * na);
-                PLHR_TRY_CUDA(lap_apply_shifts(g, na, W, na, AW, na, nullptr, 0, nullptr, thq ? X2 : nullptr, na, sigma,
-                                               s));
+                PLHR_TRY(prod(na, W, na, AW, na, BW, na, nullptr, 0, nullptr, thq ? X2 : nullptr, na));
             }
             if (thq) PLHR_TRY(applyT(na, X2, na, SQ));
             QW = SQ;
@@ -649,10 +682,12 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         Blk<const double> zb[4] = {{V, kp, kp}, {W, na, na}, {S, lds, na}, {P, kp, np}};
         Blk<const double> ab[4] = {{AV, kp, kp}, {AW, na, na}, {AS, na, na}, {AP, kp, np}};
         Blk<const double> qb[4] = {{QV, kp, kp}, {QW, ldqw, na}, {QS, na, na}, {QP, kp, np}};
+        Blk<const double> bzb[4] = {{BV, kp, kp}, {BW, na, na}, {BS, na, na}, {BP, kp, np}};
         if (!sv) {   // drop the S family: [V W P]
             zb[2] = zb[3];
             ab[2] = ab[3];
             qb[2] = qb[3];
+            bzb[2] = bzb[3];
         }
         PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
         DenseArgs da;
@@ -666,7 +701,8 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
                 if (dwf)
                     PLHR_TRY_CUDA(multi_gram_dw(n, nb, zb, ab, thq ? qb : nullptr, sigma, colscale, gpart, grams, s));
                 else
-                    PLHR_TRY_CUDA(multi_gram(n, nb, zb, ab, thq ? qb : nullptr, sigma, colscale, gpart, grams, s));
+                    PLHR_TRY_CUDA(multi_gram_b(n, nb, zb, ab, thq ? qb : nullptr, hasB ? bzb : nullptr, sigma, colscale,
+                                               gpart, grams, s));
             }
             // ---------------------------------------- projected T-harmonic problem, selection (steps 7-10)
             {
@@ -678,10 +714,10 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             if (hs->dense[0] == kDenseOK || !thq || pass == 1) break;
             // recovery: the carried images T(A - sigma B)V, T(A - sigma B)P have
             // drifted; recompute them explicitly and project again
-            PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
+            PLHR_TRY(prod(kp, V, kp, AV, kp, BV, kp, nullptr, 0, nullptr, X3, kp));
             PLHR_TRY(applyT(kp, X3, kp, QV));
             if (np) {
-                PLHR_TRY_CUDA(lap_apply_shifts(g, kp, P, kp, AP, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
+                PLHR_TRY(prod(kp, P, kp, AP, kp, BP, kp, nullptr, 0, nullptr, X3, kp));
                 PLHR_TRY(applyT(kp, X3, kp, QP));
             }
         }
@@ -711,15 +747,18 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         if (result == PLHR_ENOTCONV) {
             // final Rayleigh-Ritz on the current block
             PLHR_TRY_CUDA(lap_axpby(g, kp, V, kp, AW, kp, 1.0, 0.0, s));
-            Blk<const double> zb[1] = {{V, kp, kp}}, ab[1] = {{AW, kp, kp}}, qb[1] = {{V, kp, kp}};
+            if (hasB) PLHR_TRY_CUDA(lap_axpby(B->g, kp, V, kp, X3, kp, 1.0, 0.0, s));
+            Blk<const double> zb[1] = {{V, kp, kp}}, ab[1] = {{AW, kp, kp}}, qb[1] = {{V, kp, kp}},
+                              bzb[1] = {{X3, kp, kp}};
             PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
-            PLHR_TRY_CUDA(multi_gram(n, 1, zb, ab, qb, 0.0, colscale, gpart, grams, s));
+            PLHR_TRY_CUDA(multi_gram_b(n, 1, zb, ab, qb, hasB ? bzb : nullptr, 0.0, colscale, gpart, grams, s));
             PLHR_TRY_CUDA(dense_rr(kp, grams + kp * kp, grams, sigma, scale, Crr, theta, dstat + 6, s));
             PLHR_TRY_CUDA(block_times_small(n, V, kp, kp, Crr, kp, Rc, kp, s));
             PLHR_TRY_CUDA(lap_axpby(g, kp, Rc, kp, AW, kp, 1.0, 0.0, s));
+            if (hasB) PLHR_TRY_CUDA(lap_axpby(B->g, kp, Rc, kp, X3, kp, 1.0, 0.0, s));
             std::vector<double> ones(kp, 1.0);
             PLHR_TRY_CUDA(cudaMemcpyAsync(dots, ones.data(), sizeof(double) * kp, cudaMemcpyHostToDevice, s));
-            PLHR_TRY_CUDA(residual_norms(n, kp, Rc, kp, AW, kp, theta, dots, R, kp, rpart, sums, s));
+            PLHR_TRY_CUDA(residual_norms(n, kp, hasB ? X3 : Rc, kp, AW, kp, theta, dots, R, kp, rpart, sums, s));
             StatusArgs sa;
             sa.kp = kp; sa.k = k; sa.sigma = sigma; sa.tol = tol;
             sa.sums = sums; sa.lam = theta; sa.lam_act = lam_act; sa.active = active; sa.rel = rel; sa.order = order;

@@ -138,3 +138,86 @@ def test_diagonal_preconditioner_rejects_nonpositive(plhr):
         plhr.DiagPrec(np.array([1.0, np.nan]))
     with pytest.raises(plhr.PlhrError):
         plhr.TPA(plhr.Operator.csr(sp.identity(8, format="csr")), 0.5)
+
+
+# ---------------------------------------------------------------- generalized problem A v = lambda B v
+
+def _fe_pencil(elems):
+    A, Bm = oops.q1_fe_2d(elems)
+    import scipy.linalg as sl
+    lam, Y = sl.eigh(A.toarray(), Bm.toarray())
+    return A, Bm, lam, Y
+
+
+@pytest.mark.parametrize("prec", ["none", "diag"])
+def test_generalized_fe_matches_dense_and_is_b_orthonormal(plhr, prec):
+    """Q1 stiffness A and mass B (Section 5.1) as CSR operators: the k pairs
+    nearest sigma of A v = lambda B v against LAPACK's generalized eigh, with
+    B-orthonormal vectors and residuals recomputed on the CPU."""
+    A, Bm, lam, Y = _fe_pencil(20)
+    sigma = 0.5 * (lam[30] + lam[31])
+    k = 4
+    near = np.sort(np.argsort(np.abs(lam - sigma))[:k])
+    opA, opB = plhr.Operator.csr(A), plhr.Operator.csr(Bm)
+    T = None
+    if prec == "diag":
+        T = plhr.DiagPrec(1.0 / np.abs(A.diagonal() - sigma * Bm.diagonal()))
+    ev, vecs, info = plhr.solve(opA, sigma, k, T=T, B=opB, tol=1e-10, maxit=8000, guard=2)
+    assert info["converged"], info
+    assert np.allclose(np.sort(ev), lam[near], rtol=1e-10)
+    V = vecs.cpu().numpy()
+    assert np.abs(V.T @ (Bm @ V) - np.eye(k)).max() <= 1e-11
+    R = A @ V - (Bm @ V) * ev[None, :]
+    rel = np.linalg.norm(R, axis=0) / (np.maximum(np.abs(ev), 1.0) * np.linalg.norm(Bm @ V, axis=0))
+    assert np.all(rel <= 1e-10 * 1.0001), rel
+
+
+def test_generalized_tracks_oracle(plhr):
+    """Per-iteration Ritz values of the generalized T-harmonic iteration equal
+    the oracle's (Algorithm 3 with B) for the first iterations, on the same
+    start block, with the exact shifted-inverse preconditioner of the oracle's
+    pin perturbed to stay generic."""
+    from oracle import plhr as oplhr
+    A, Bm, lam, Y = _fe_pencil(12)
+    Ad, Bd = A.toarray(), Bm.toarray()
+    n = Ad.shape[0]
+    sigma = 0.5 * (lam[15] + lam[16])
+    k, guard = 3, 1
+    # T = |A - sigma B|^{-1} (symmetric, from the eigendecomposition of A - sigma B) + 0.1 I / ||...||
+    w, Q = np.linalg.eigh(Ad - sigma * Bd)
+    Tm = (Q / np.abs(w)[None, :]) @ Q.T
+    Tm = Tm + 0.05 * np.abs(Tm).max() * np.eye(n)
+    Tt = torch.from_numpy(Tm).cuda()
+
+    def fn(R, Wout):
+        Wout.copy_(Tt @ R)
+
+    Tc = plhr.CallbackPrec(n, fn)
+    V0 = wl.uniform_block(n, k + guard, 81)
+    ev, vecs, info = plhr.solve(plhr.Operator.csr(A), sigma, k, T=Tc, B=plhr.Operator.csr(Bm), tol=1e-10,
+                                maxit=300, guard=guard, v_init=torch.from_numpy(V0).cuda(), history=True)
+    ref = oplhr.bplhr(A, Bm, lambda Xb: Tm @ Xb, sigma, k, V0, tol=1e-10, maxit=8)
+    for a, b in list(zip(info["history"], ref.history))[:6]:
+        assert np.allclose(a["lam"], b["lam"][:k], rtol=1e-9), (a["it"], a["lam"], b["lam"])
+
+
+def test_generalized_fe_50x50_reproduces_printed_eigenvalues(plhr):
+    """The paper's Section 5.1 FE problem (50 x 50 elements, n = 2401): the
+    eigenvalues nearest the shifts 497 and 980 are the printed lambda_31 and
+    lambda_66 (tests/golden/fe_q1_50x50.json, 4 decimals)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fe_q1_50x50.json")) as f:
+        gold = json.load(f)
+    A, Bm = oops.q1_fe_2d(gold["elements_per_side"])
+    opA, opB = plhr.Operator.csr(A), plhr.Operator.csr(Bm)
+    for shift, key in ((497.0, "31"), (980.0, "66")):
+        ev, vecs, info = plhr.solve(opA, shift, 1, B=opB, tol=1e-10, maxit=20000, guard=3)
+        assert info["converged"], info
+        assert abs(ev[0] - gold["eigenvalues_1based"][key]) <= 0.5e-4 * 1.0001, (key, ev[0])
+
+
+def test_generalized_rejected_in_mixed_form(plhr):
+    A, Bm = oops.q1_fe_2d(8)
+    with pytest.raises(plhr.PlhrError):
+        plhr.solve(plhr.Operator.csr(A), 100.0, 2, B=plhr.Operator.csr(Bm), precision=plhr.PRECISION_MIXED)
