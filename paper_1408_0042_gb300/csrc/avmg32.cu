@@ -10,6 +10,7 @@
 // (blockIdx.y = y, blockIdx.z = z), so a warp reads 128 contiguous bytes and no
 // 64-bit index division is needed.  The two pre-smoothing sweeps from w = 0 on
 // an L_l level are fused: w = 2 omega r - omega^2 L r.
+#include "dword.h"
 #include "plhr_internal.h"
 
 namespace plhr {
@@ -488,7 +489,7 @@ __global__ void k_narrow_rhs(int64_t n, int nc, const double* __restrict__ r, in
     const int64_t total = n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = e / nc;
-        r32[e] = (float)r[row * ldr + (e - row * nc)];
+        r32[e] = f64_to_f32_rn(r[row * ldr + (e - row * nc)]);
     }
 }
 

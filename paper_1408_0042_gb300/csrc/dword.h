@@ -128,11 +128,11 @@ __device__ __forceinline__ double dw_to_double(dw a) { return (double)a.hi + (do
 
 // The same split without FP64 instructions (GB300 issues FP64 at 1/64 of the
 // FP32 rate), by integer operations on the IEEE-754 encodings: hi is x
-// rounded to 24 significant bits (round half up on the magnitude: the 29
-// discarded mantissa bits decide, and an increment of the encoding carries
-// into the exponent), lo is the remainder x - hi, an integer below 2^28 times
-// 2^(e - 52) converted to FP32 (rounded) with its sign.  x = hi + lo to ~2^-48
-// relative and |lo| <= ulp(hi) / 2, as from the FP64 route.  Zero, values
+// rounded to 24 significant bits (to nearest, ties to even: the 29 discarded
+// mantissa bits decide, and an increment of the encoding carries into the
+// exponent), lo is the remainder x - hi, an integer of at most 2^28 times
+// 2^(e - 52) converted to FP32 (rounded) with its sign.  The pair is the one
+// the FP64 route gives, bit for bit, in the fast range.  Zero, values
 // below 2^-74 or from 2^127 up, Inf and NaN take the FP64 route.
 __device__ __forceinline__ dw dw_from_double_fast(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -141,7 +141,8 @@ __device__ __forceinline__ dw dw_from_double_fast(double x) {
     const unsigned sign = (unsigned)(b >> 63) << 31;
     const unsigned long long mant = b & 0xfffffffffffffull;
     const unsigned m29 = (unsigned)(mant & 0x1fffffffu);
-    const unsigned up = m29 >> 28;
+    // round to nearest, ties to even (the FP64 route's conversion)
+    const unsigned up = (m29 > 0x10000000u) | ((m29 == 0x10000000u) & (unsigned)(mant >> 29) & 1u);
     const float hi = __uint_as_float((sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29)) + up);
     const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);
     const float mag = __fmul_rn(__uint2float_rn(up ? 0x20000000u - m29 : m29), scale);
@@ -157,6 +158,19 @@ __device__ __forceinline__ void dw_fma_acc(float& hi, float& lo, const dw& a, co
     const dw s = dw_two_sum(hi, ph);
     hi = s.hi;
     lo = __fadd_rn(lo, __fadd_rn(s.lo, __fadd_rn(pl, cr)));
+}
+
+// FP64 -> FP32 rounding (to nearest, ties to even: the conversion
+// instruction's result) by integer operations on the encodings, for normal
+// FP32 results; other inputs take the conversion instruction
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+    if (e < -126 || e > 126) return __double2float_rn(x);
+    const unsigned long long mant = b & 0xfffffffffffffull;
+    const unsigned m29 = (unsigned)(mant & 0x1fffffffu);
+    const unsigned up = (m29 > 0x10000000u) | ((m29 == 0x10000000u) & (unsigned)(mant >> 29) & 1u);
+    return __uint_as_float(((unsigned)(b >> 63) << 31 | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29)) + up);
 }
 
 // Truncating form of the same split: hi is x with the 29 low mantissa bits

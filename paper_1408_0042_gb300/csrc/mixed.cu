@@ -45,7 +45,7 @@ __device__ __forceinline__ double ldv(const FamMx& F, int b, int64_t row, int c)
                     : (double)static_cast<const float*>(F.p[b])[row * F.ld[b] + c];
 }
 __device__ __forceinline__ float ldf(const FamMx& F, int b, int64_t row, int c) {
-    return F.f64[b] ? (float)static_cast<const double*>(F.p[b])[row * F.ld[b] + c]
+    return F.f64[b] ? f64_to_f32_rn(static_cast<const double*>(F.p[b])[row * F.ld[b] + c])
                     : static_cast<const float*>(F.p[b])[row * F.ld[b] + c];
 }
 
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int
                 const int r = t / nc, c = t - r * nc;
                 const int64_t row = row0 + r;
                 if (b == 0 && v64) {
-                    const dw v = dw_from_double(ldv(F, 0, row, c));
+                    const dw v = dw_from_double_fast(ldv(F, 0, row, c));
                     zw[r * kp + c] = v;
                     zf[r * m + c] = v.hi;
                 } else {
@@ -245,18 +245,18 @@ __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int
             for (int i = 0; i < kp; ++i) pv = fmaf(z[i], cpf[i * kp + j], pv);
             const int64_t row = row0 + r;
             const float p = pv + prest;
-            if (po64) static_cast<double*>(Pout)[row * ldpo + j] = (double)p;
+            if (po64) static_cast<double*>(Pout)[row * ldpo + j] = f32_to_f64_bits(p);
             else static_cast<float*>(Pout)[row * ldpo + j] = p;
             if (v64) {
                 const dw* zr = zw + r * kp;
                 dw v = dw_make(prest);
                 for (int i = 0; i < kp; ++i) v = dw_add(v, dw_mul(zr[i], csw[i * kp + j]));
-                static_cast<double*>(Vout)[row * ldvo + j] = dw_to_double(v);
+                static_cast<double*>(Vout)[row * ldvo + j] = dw_to_double_fast(v);
             } else {
                 float v = 0.0f;
                 for (int i = 0; i < kp; ++i) v = fmaf(z[i], csf[i * kp + j], v);
                 v += prest;
-                if (vo64) static_cast<double*>(Vout)[row * ldvo + j] = (double)v;
+                if (vo64) static_cast<double*>(Vout)[row * ldvo + j] = f32_to_f64_bits(v);
                 else static_cast<float*>(Vout)[row * ldvo + j] = v;
             }
         }
@@ -272,8 +272,8 @@ __global__ void k_prepare_v(int64_t n, int kp, const double* __restrict__ V, con
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const double v = V[e];
         const double u = fma(-sigma, v, AV[e]);
-        V32[e] = (float)v;
-        U32[e] = (float)u;
+        V32[e] = f64_to_f32_rn(v);
+        U32[e] = f64_to_f32_rn(u);
         if (X3) X3[e] = u;
     }
 }
@@ -330,7 +330,7 @@ __global__ void k_narrow(int64_t n, int nc, const double* __restrict__ X, int64_
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / nc;
         const int c = (int)(e - r * nc);
-        Y[r * ldy + c] = (float)X[r * ldx + c];
+        Y[r * ldy + c] = f64_to_f32_rn(X[r * ldx + c]);
     }
 }
 
