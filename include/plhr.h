@@ -139,8 +139,12 @@ plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma,
  * selects sigma - min(potential) when positive, else the mean of mu.  Any
  * stencil or Hamiltonian operator whose axis sizes are at most 144 (an
  * application takes 8 (N^2 + N ncols) <= 200 KB for every axis size N, else
- * PLHR_ECUDA with an invalid-value error); the potential is read once here.  Usable by plhr_solve (PLHR_PRECISION_F64),
- * plhr_prec_apply and plhr_eigvec_adjoint. */
+ * PLHR_ECUDA with an invalid-value error); the potential is read once here.
+ * The transforms run in double-word arithmetic (~1e-12 relative rounding per
+ * application): PLHR with this T reaches relative residuals near 1e-11, below
+ * which the T-harmonic iteration stalls (use T = NULL for tighter
+ * tolerances).  Usable by plhr_solve (PLHR_PRECISION_F64), plhr_prec_apply
+ * and plhr_eigvec_adjoint. */
 plhr_status plhr_prec_tpa(plhr_prec** out, const plhr_op* A, double sigma, double energy);
 /* The reference energy a TPA preconditioner uses (0 for other kinds). */
 double plhr_prec_tpa_energy(const plhr_prec* T);
