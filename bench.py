@@ -61,8 +61,8 @@ FP64_PEAK_TFLOPS = 1.25
 # the traffic grows in proportion to n m (profiles/k_gram_lap3d_64cube.md).
 GRAM_DRAM_BYTES_PER_ROW_COL = 446.1e6 / (262144 * 64)
 # the same for the double-word Gram k_gram_dw (m = 64 launch on the 64^3
-# case: 402.8 MB read + 3.2 MB written; profiles/mixed_form_kernels_lap3d_64cube.md)
-GRAM_DW_DRAM_BYTES_PER_ROW_COL = 405.94e6 / (262144 * 64)
+# case: 402.8 MB read + 3.8 MB written; profiles/mixed_form_kernels_lap3d_64cube.md)
+GRAM_DW_DRAM_BYTES_PER_ROW_COL = 406.60e6 / (262144 * 64)
 
 
 class ClockSampler:

@@ -6,6 +6,42 @@
 namespace plhr {
 
 int reduce_blocks();
+
+// Asynchronous global -> shared copies of one 8- or 4-byte element (both
+// addresses aligned to the size); wait_all waits for this thread's copies, a
+// barrier after it makes every thread's copies visible.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// The 4x4 register tiles of the three m x m Gram outputs (T = ceil(m / 4)
+// tiles per side), numbered compactly: t < T(T+1)/2 are the upper tiles
+// ti <= tj of output 0 in row order, then the T^2 tiles of output 1 and of
+// output 2 in row order.  Returns false for t past the last tile.  Numbering
+// only the tiles that exist keeps the idle lanes of a warp at the end of the
+// list, so fewer warps issue when m < 64.
+__device__ __forceinline__ bool gram_tile(int t, int T, int& g, int& ti, int& tj) {
+    const int nt0 = T * (T + 1) / 2, nt1 = T * T;
+    g = 0; ti = 0; tj = 0;
+    if (t < nt0) {
+        int r = 0, rem = t;
+        while (rem >= T - r) { rem -= T - r; ++r; }
+        ti = r; tj = r + rem;
+        return true;
+    }
+    if (t >= nt0 + 2 * nt1) return false;
+    const int u = t - nt0;
+    g = 1 + u / nt1;
+    ti = (u % nt1) / T; tj = u % T;
+    return true;
+}
 int residual_blocks(int kp);
 int gram_max_m();
 

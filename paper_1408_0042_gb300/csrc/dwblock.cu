@@ -38,11 +38,11 @@ FamD fam_d(const Blk<const double>* b, int nb) {
 }
 
 
-// Stage rows row0 .. of z = Z, u = AZ - sigma Z, q = Q (q = u when q_from_u)
-// as double-word [row][mp] tiles; U is formed by one FP64 FMA before the split
-// (the column scales are applied to the finished Grams)
-__device__ void stage_dw(dw* sz, dw* su, dw* sq, int mp, int64_t n, int64_t row0, const FamD& Z, const FamD& AZ,
-                         const FamD& Q, int nb, int q_from_u, double sigma) {
+// Start the copies of rows row0 .. row0 + kDwRows - 1 (those below n) of the
+// Z, AZ and (unless q_from_u) Q families into the FP64 row buffers rz, ra, rq
+// ([row][mp], column off[b] + c for column c of block b)
+__device__ void fetch_dw(double* rz, double* ra, double* rq, int mp, int64_t n, int64_t row0, const FamD& Z,
+                         const FamD& AZ, const FamD& Q, int nb, int q_from_u) {
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         if (b >= nb) break;
@@ -52,24 +52,43 @@ __device__ void stage_dw(dw* sz, dw* su, dw* sq, int mp, int64_t n, int64_t row0
         for (int t = threadIdx.x; t < tot; t += blockDim.x) {
             const int r = t / nc, c = t - r * nc;
             const int64_t row = row0 + r;
-            const int col = Z.off[b] + c;
-            dw z = dw_make(0.0f), u = z, q = z;
-            if (row < n) {
-                const double zd = Z.p[b][row * Z.ld[b] + c];
-                const double ud = fma(-sigma, zd, AZ.p[b][row * AZ.ld[b] + c]);
-                z = dw_split_trunc(zd);
-                u = dw_split_trunc(ud);
-                q = q_from_u ? u : dw_split_trunc(Q.p[b][row * Q.ld[b] + c]);
-            }
-            sz[r * mp + col] = z;
-            su[r * mp + col] = u;
-            sq[r * mp + col] = q;
+            if (row >= n) continue;
+            const int at = r * mp + Z.off[b] + c;
+            cp_async8(rz + at, Z.p[b] + row * Z.ld[b] + c);
+            cp_async8(ra + at, AZ.p[b] + row * AZ.ld[b] + c);
+            if (!q_from_u) cp_async8(rq + at, Q.p[b] + row * Q.ld[b] + c);
         }
     }
 }
 
-// 768 threads: thread t owns output g = t / 256 (0: Z^T Z, written for ti <= tj
-// and mirrored; 1: U^T Q; 2: Q^T Z) and its 4x4 tile (ti, tj).  mp <= 64.
+// Stage the fetched rows as double-word [row][mp] tiles of z = Z, u = AZ -
+// sigma Z, q = Q (q = u when q_from_u); U is formed by one FP64 FMA before the
+// split, rows at or past n are zero (the column scales are applied to the
+// finished Grams)
+__device__ void stage_dw(dw* sz, dw* su, dw* sq, const double* rz, const double* ra, const double* rq, int m,
+                         int mp, int64_t n, int64_t row0, int q_from_u, double sigma) {
+    const int tot = kDwRows * m;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        const int r = t / m, col = t - r * m;
+        const int at = r * mp + col;
+        dw z = dw_make(0.0f), u = z, q = z;
+        if (row0 + r < n) {
+            const double zd = rz[at];
+            const double ud = fma(-sigma, zd, ra[at]);
+            z = dw_split_trunc(zd);
+            u = dw_split_trunc(ud);
+            q = q_from_u ? u : dw_split_trunc(rq[at]);
+        }
+        sz[at] = z;
+        su[at] = u;
+        sq[at] = q;
+    }
+}
+
+// 768 threads: thread t owns tile t of gram_tile (output g = 0: Z^T Z,
+// written for ti <= tj and mirrored; 1: U^T Q; 2: Q^T Z); at most 648 tiles
+// (mp <= 64), every thread fetches and stages.  The rows of the next chunk
+// are copied asynchronously while the current one is multiplied.
 __global__ void __launch_bounds__(kDwThreads, 1) k_gram_dw(int64_t n, int m, int mp, int nb, FamD Z, FamD AZ, FamD Q,
                                                            int q_from_u, double sigma,
                                                            double* __restrict__ partial) {
@@ -77,9 +96,12 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_gram_dw(int64_t n, int m, int
     dw* sz = reinterpret_cast<dw*>(raw);
     dw* su = sz + kDwRows * mp;
     dw* sq = su + kDwRows * mp;
+    double* rz = reinterpret_cast<double*>(sq + kDwRows * mp);
+    double* ra = rz + kDwRows * mp;
+    double* rq = ra + kDwRows * mp;
     const int T = mp / 4;
-    const int g = threadIdx.x >> 8, ti = (threadIdx.x >> 4) & 15, tj = threadIdx.x & 15;
-    const bool act = ti < T && tj < T && (g != 0 || ti <= tj);
+    int g, ti, tj;
+    const bool act = gram_tile(threadIdx.x, T, g, ti, tj);
     const dw* A = g == 0 ? sz : (g == 1 ? su : sq);
     const dw* B = g == 1 ? sq : sz;
     float hi[16], lo[16];
@@ -89,24 +111,32 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_gram_dw(int64_t n, int m, int
         if (t % mp >= m) { sz[t] = dw_make(0.0f); su[t] = dw_make(0.0f); sq[t] = dw_make(0.0f); }
     }
     const int64_t nchunks = (n + kDwRows - 1) / kDwRows;
+    if ((int64_t)blockIdx.x < nchunks) fetch_dw(rz, ra, rq, mp, n, (int64_t)blockIdx.x * kDwRows, Z, AZ, Q, nb, q_from_u);
+    cp_async_commit();
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        __syncthreads();
-        stage_dw(sz, su, sq, mp, n, ch * kDwRows, Z, AZ, Q, nb, q_from_u, sigma);
-        __syncthreads();
-        if (!act) continue;
+        cp_async_wait_all();
+        __syncthreads();          // rows of chunk ch landed; the previous chunk's products are done
+        stage_dw(sz, su, sq, rz, ra, rq, m, mp, n, ch * kDwRows, q_from_u, sigma);
+        __syncthreads();          // tiles staged; the row buffers are free
+        if (ch + gridDim.x < nchunks)
+            fetch_dw(rz, ra, rq, mp, n, (ch + gridDim.x) * kDwRows, Z, AZ, Q, nb, q_from_u);
+        cp_async_commit();
+        if (act) {
 #pragma unroll 2
-        for (int r = 0; r < kDwRows; ++r) {
-            const float4* ap = reinterpret_cast<const float4*>(A + r * mp + 4 * ti);
-            const float4* bp = reinterpret_cast<const float4*>(B + r * mp + 4 * tj);
-            const float4 a01 = ap[0], a23 = ap[1], b01 = bp[0], b23 = bp[1];
-            const dw av[4] = {{a01.x, a01.y}, {a01.z, a01.w}, {a23.x, a23.y}, {a23.z, a23.w}};
-            const dw bv[4] = {{b01.x, b01.y}, {b01.z, b01.w}, {b23.x, b23.y}, {b23.z, b23.w}};
+            for (int r = 0; r < kDwRows; ++r) {
+                const float4* ap = reinterpret_cast<const float4*>(A + r * mp + 4 * ti);
+                const float4* bp = reinterpret_cast<const float4*>(B + r * mp + 4 * tj);
+                const float4 a01 = ap[0], a23 = ap[1], b01 = bp[0], b23 = bp[1];
+                const dw av[4] = {{a01.x, a01.y}, {a01.z, a01.w}, {a23.x, a23.y}, {a23.z, a23.w}};
+                const dw bv[4] = {{b01.x, b01.y}, {b01.z, b01.w}, {b23.x, b23.y}, {b23.z, b23.w}};
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+                for (int x = 0; x < 4; ++x)
 #pragma unroll
-                for (int y = 0; y < 4; ++y) dw_fma_acc(hi[x * 4 + y], lo[x * 4 + y], av[x], bv[y]);
+                    for (int y = 0; y < 4; ++y) dw_fma_acc(hi[x * 4 + y], lo[x * 4 + y], av[x], bv[y]);
+            }
         }
     }
+    cp_async_wait_all();
     if (!act) return;
     double* out = partial + (int64_t)blockIdx.x * 3 * m * m + (int64_t)g * m * m;
     for (int x = 0; x < 4; ++x)
@@ -187,11 +217,11 @@ cudaError_t multi_gram_dw(int64_t n, int nb, const Blk<const double>* Z, const B
     const int mp = (m + 3) / 4 * 4;
     if (mp > 64) return cudaErrorInvalidValue;
     const int blocks = sm_count();
-    const size_t shm = sizeof(dw) * 3 * kDwRows * mp;
+    const size_t shm = (sizeof(dw) + sizeof(double)) * 3 * kDwRows * mp;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_gram_dw, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(dw) * 3 * kDwRows * 64));
+                                             (int)((sizeof(dw) + sizeof(double)) * 3 * kDwRows * 64));
         if (e != cudaSuccess) return e;
         attr = true;
     }

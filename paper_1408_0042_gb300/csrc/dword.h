@@ -125,6 +125,10 @@ __device__ __forceinline__ dw dw_from_double(double d) {
     return {hi, lo};
 }
 __device__ __forceinline__ double dw_to_double(dw a) { return (double)a.hi + (double)a.lo; }
+// The same as a call: the rare-input branch of the integer splits below calls
+// it, so the compiler keeps that branch instead of evaluating the FP64 route
+// for every element
+static __device__ __noinline__ dw dw_from_double_call(double d) { return dw_from_double(d); }
 
 // The same split without FP64 instructions (GB300 issues FP64 at 1/64 of the
 // FP32 rate), by integer operations on the IEEE-754 encodings: hi is x
@@ -137,7 +141,7 @@ __device__ __forceinline__ double dw_to_double(dw a) { return (double)a.hi + (do
 __device__ __forceinline__ dw dw_from_double_fast(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7ffu) - 1023;
-    if (e < -74 || e > 126) return dw_from_double(x);
+    if (e < -74 || e > 126) return dw_from_double_call(x);
     const unsigned sign = (unsigned)(b >> 63) << 31;
     const unsigned long long mant = b & 0xfffffffffffffull;
     const unsigned m29 = (unsigned)(mant & 0x1fffffffu);
@@ -180,7 +184,7 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
 __device__ __forceinline__ dw dw_split_trunc(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7ffu) - 1023;
-    if (e < -74 || e > 127) return dw_from_double(x);
+    if (e < -74 || e > 127) return dw_from_double_call(x);
     const unsigned sign = (unsigned)(b >> 63) << 31;
     const unsigned long long mant = b & 0xfffffffffffffull;
     const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29));

@@ -7,6 +7,7 @@
 // 32-row sum into a per-thread double-FP32 (hi, lo) accumulator with TwoSum,
 // so the accumulation error does not grow with n.  The per-CTA partials are
 // summed in FP64 in a fixed order (deterministic).
+#include "blockops.h"
 #include "dword.h"
 #include "mixed.h"
 
@@ -49,13 +50,50 @@ __device__ __forceinline__ float ldf(const FamMx& F, int b, int64_t row, int c) 
                     : static_cast<const float*>(F.p[b])[row * F.ld[b] + c];
 }
 
-// Stage rows row0 .. row0 + kMxRows - 1 of z = Z s, u = (AZ - sigma Z) s (u =
-// AZ s for a block flagged is_u, which already holds AZ - sigma Z) and q = Q s
-// (q = u when Q is absent) into [row][mp] FP32 tiles; FP64 blocks are combined
-// in FP64 and rounded once.
-__device__ void stage_mx(float* sz, float* su, float* sq, int mp, int64_t n, int64_t row0, const FamMx& Z,
-                         const FamMx& AZ, const FamMx& Q, int nb, int has_q, double sigma,
-                         const double* __restrict__ csc, const float* __restrict__ cscf, float sigf) {
+// Start the copies of rows row0 .. row0 + kMxRows - 1 (those below n) of the
+// Z, AZ and (with has_q) Q families into the row buffers rz, ra, rq: one
+// 8-byte slot per element ([row][mp], column off[b] + c), an FP32 element in
+// the slot's first 4 bytes
+__device__ __forceinline__ void fetch_el(double* dst, const FamMx& F, int b, int64_t row, int c) {
+    if (F.f64[b]) cp_async8(dst, static_cast<const double*>(F.p[b]) + row * F.ld[b] + c);
+    else cp_async4(dst, static_cast<const float*>(F.p[b]) + row * F.ld[b] + c);
+}
+__device__ void fetch_mx(double* rz, double* ra, double* rq, int mp, int64_t n, int64_t row0, const FamMx& Z,
+                         const FamMx& AZ, const FamMx& Q, int nb, int has_q) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        if (b >= nb) break;
+        const int nc = Z.nc[b];
+        if (nc == 0) continue;
+        const int tot = kMxRows * nc;
+        for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+            const int r = t / nc, c = t - r * nc;
+            const int64_t row = row0 + r;
+            if (row >= n) continue;
+            const int at = r * mp + Z.off[b] + c;
+            fetch_el(rz + at, Z, b, row, c);
+            fetch_el(ra + at, AZ, b, row, c);
+            if (has_q) fetch_el(rq + at, Q, b, row, c);
+        }
+    }
+}
+
+// a fetched element as FP64 / rounded to FP32
+__device__ __forceinline__ double rdv(const FamMx& F, int b, const double* slot) {
+    return F.f64[b] ? *slot : (double)*reinterpret_cast<const float*>(slot);
+}
+__device__ __forceinline__ float rdf(const FamMx& F, int b, const double* slot) {
+    return F.f64[b] ? f64_to_f32_rn(*slot) : *reinterpret_cast<const float*>(slot);
+}
+
+// Stage the fetched rows of z = Z s, u = (AZ - sigma Z) s (u = AZ s for a
+// block flagged is_u, which already holds AZ - sigma Z) and q = Q s (q = u
+// when Q is absent) as [row][mp] FP32 tiles; FP64 blocks are combined in FP64
+// and rounded once; rows at or past n are zero.
+__device__ void stage_mx(float* sz, float* su, float* sq, const double* rz, const double* ra, const double* rq,
+                         int mp, int64_t n, int64_t row0, const FamMx& Z, const FamMx& AZ, const FamMx& Q, int nb,
+                         int has_q, double sigma, const double* __restrict__ csc,
+                         const float* __restrict__ cscf, float sigf) {
     // static block indices: the family descriptors stay in registers / the
     // parameter space instead of a local copy
 #pragma unroll
@@ -70,24 +108,25 @@ __device__ void stage_mx(float* sz, float* su, float* sq, int mp, int64_t n, int
             const int r = t / nc, c = t - r * nc;
             const int64_t row = row0 + r;
             const int col = Z.off[b] + c;
+            const int at = r * mp + col;
             float z = 0.0f, u = 0.0f, q = 0.0f;
             if (row < n) {
                 const float sf = cscf[col];
                 if (wide) {
                     const double s = csc[col];
-                    const double zd = ldv(Z, b, row, c) * s;
-                    const double ud = isu ? ldv(AZ, b, row, c) * s : ldv(AZ, b, row, c) * s - sigma * zd;
+                    const double zd = rdv(Z, b, rz + at) * s;
+                    const double ud = isu ? rdv(AZ, b, ra + at) * s : rdv(AZ, b, ra + at) * s - sigma * zd;
                     z = (float)zd;
                     u = (float)ud;
                 } else {
-                    z = ldf(Z, b, row, c) * sf;
-                    u = isu ? ldf(AZ, b, row, c) * sf : ldf(AZ, b, row, c) * sf - sigf * z;
+                    z = rdf(Z, b, rz + at) * sf;
+                    u = isu ? rdf(AZ, b, ra + at) * sf : rdf(AZ, b, ra + at) * sf - sigf * z;
                 }
-                q = has_q ? ldf(Q, b, row, c) * sf : u;
+                q = has_q ? rdf(Q, b, rq + at) * sf : u;
             }
-            sz[r * mp + col] = z;
-            su[r * mp + col] = u;
-            sq[r * mp + col] = q;
+            sz[at] = z;
+            su[at] = u;
+            sq[at] = q;
         }
     }
 }
@@ -123,25 +162,28 @@ __device__ __forceinline__ void put_tile(double* G, int m, int i0, int j0, const
         }
 }
 
-// 768 threads: thread t owns output g = t / 256 (0: Z^T Z, written for
-// ti <= tj and mirrored; 1: U^T Q; 2: Q^T Z) and its 4x4 tile (ti, tj) =
-// ((t % 256) / 16, t % 16).  One tile per thread keeps ~70 registers, so 24
-// warps per SM hide the latency of the staging loads.  mp <= 64.
+// 768 threads: thread t owns tile t of gram_tile (output g = 0: Z^T Z,
+// written for ti <= tj and mirrored; 1: U^T Q; 2: Q^T Z); at most 648 tiles
+// (mp <= 64).  One tile per thread keeps ~70 registers, and all 24 warps
+// stage, which hides the latency of the staging loads.
 constexpr int kGramMxThreads = 768;
 __global__ void __launch_bounds__(kGramMxThreads, 1) k_gram_mx(int64_t n, int m, int mp, int nb, FamMx Z, FamMx AZ,
                                                                FamMx Q, int has_q, double sigma,
                                                                const double* __restrict__ csc,
                                                                double* __restrict__ partial) {
-    extern __shared__ __align__(16) float shm[];
-    float* sz = shm;
+    extern __shared__ __align__(16) double shmd[];
+    double* rz = shmd;                      // [rows][mp] fetched rows (8-byte slots)
+    double* ra = rz + kMxRows * mp;
+    double* rq = ra + kMxRows * mp;
+    float* sz = reinterpret_cast<float*>(rq + kMxRows * mp);
     float* su = sz + kMxRows * mp;
     float* sq = su + kMxRows * mp;
     float* cscf = sq + kMxRows * mp;        // [mp] FP32 column scales
     for (int t = threadIdx.x; t < m; t += blockDim.x) cscf[t] = (float)csc[t];
     const float sigf = (float)sigma;
     const int T = mp / 4;
-    const int g = threadIdx.x >> 8, ti = (threadIdx.x >> 4) & 15, tj = threadIdx.x & 15;
-    const bool act = ti < T && tj < T && (g != 0 || ti <= tj);
+    int g, ti, tj;
+    const bool act = gram_tile(threadIdx.x, T, g, ti, tj);
     // operands of this output: A^T B with A, B in {z, u, q}
     const float* A = g == 0 ? sz : (g == 1 ? su : sq);
     const float* B = g == 1 ? sq : sz;
@@ -153,10 +195,15 @@ __global__ void __launch_bounds__(kGramMxThreads, 1) k_gram_mx(int64_t n, int m,
         if (t % mp >= m) { sz[t] = 0.0f; su[t] = 0.0f; sq[t] = 0.0f; }
     }
     const int64_t nchunks = (n + kMxRows - 1) / kMxRows;
+    if ((int64_t)blockIdx.x < nchunks) fetch_mx(rz, ra, rq, mp, n, (int64_t)blockIdx.x * kMxRows, Z, AZ, Q, nb, has_q);
+    cp_async_commit();
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        __syncthreads();
-        stage_mx(sz, su, sq, mp, n, ch * kMxRows, Z, AZ, Q, nb, has_q, sigma, csc, cscf, sigf);
-        __syncthreads();
+        cp_async_wait_all();
+        __syncthreads();          // rows of chunk ch landed; the previous chunk's products are done
+        stage_mx(sz, su, sq, rz, ra, rq, mp, n, ch * kMxRows, Z, AZ, Q, nb, has_q, sigma, csc, cscf, sigf);
+        __syncthreads();          // tiles staged; the row buffers are free
+        if (ch + gridDim.x < nchunks) fetch_mx(rz, ra, rq, mp, n, (ch + gridDim.x) * kMxRows, Z, AZ, Q, nb, has_q);
+        cp_async_commit();
         if (act) {
             float acc[16];
 #pragma unroll
@@ -174,6 +221,7 @@ __global__ void __launch_bounds__(kGramMxThreads, 1) k_gram_mx(int64_t n, int m,
             }
         }
     }
+    cp_async_wait_all();
     if (!act) return;
     double* out = partial + (int64_t)blockIdx.x * 3 * m * m + (int64_t)g * m * m;
     put_tile(out, m, 4 * ti, 4 * tj, hi, lo, g == 0);
@@ -346,12 +394,13 @@ cudaError_t multi_gram_mx(int64_t n, int nb, const BlkMx* Z, const BlkMx* AZ, co
     const int mp = (m + 3) / 4 * 4;
     if (mp > 64) return cudaErrorInvalidValue;
     const int blocks = gram_mx_blocks();
-    const size_t shm = sizeof(float) * (3 * kMxRows * mp + mp);
+    const size_t shm = sizeof(double) * 3 * kMxRows * mp + sizeof(float) * (3 * kMxRows * mp + mp);
     // above the 48 KB default at mp = 64: raise the kernel's limit to the largest size
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_gram_mx, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(float) * (3 * kMxRows * 64 + 64)));
+                                             (int)(sizeof(double) * 3 * kMxRows * 64 +
+                                                   sizeof(float) * (3 * kMxRows * 64 + 64)));
         if (e != cudaSuccess) return e;
         attr = true;
     }
