@@ -318,7 +318,7 @@ plhr_status plhr_tharm_extract(int m, int kp, int nv, const double* Gzz, const d
  * allocation after start-up, or code running from a host callback where an
  * allocation could block.  The paper has no counterpart: this is a property
  * of the library, not of the method.
- *   - Scratch comes from a 256 KiB array built into the library (enough for
+ *   - Scratch comes from a 263 KiB array built into the library (enough for
  *     the largest supported m = 64); every GPU that loads the library keeps it
  *     until the process exits.  m > 64 is rejected with PLHR_EINVAL.
  *   - The call performs no cudaMalloc, cudaFree or other allocation.  Its first

@@ -117,11 +117,22 @@ __device__ int bchol_drop(double* A, int n, int* keep, double tol) {
     return nk;
 }
 
-// X <- R^{-T} X R^{-1} for upper triangular R (both n x n, stride LDS)
-__device__ void bcongruence(const double* R, double* X, int n) {
-    const int tid = threadIdx.x;
-    if (tid < n) {
-        const int c = tid;
+// Column (row) index of this thread in the one-column-per-thread FP64 loops:
+// 16 lanes of each of the four warps, one warp per SM sub-partition, so that
+// all four FP64 pipes work (a warp instruction occupies the pipe for the same
+// time whatever its active lanes).  Lanes 16..31 take the same index of a
+// second matrix (spread_second).  Every index is handled by one thread, in
+// the same order as with one thread per index.
+static_assert(NT == 128 && MAXM <= 64, "four warps of 16 lanes cover the columns");
+__device__ __forceinline__ int spread_index() { return (threadIdx.x >> 5) * 16 + (threadIdx.x & 15); }
+__device__ __forceinline__ bool spread_second() { return (threadIdx.x & 16) != 0; }
+
+// X1 <- R^{-T} X1 R^{-1} and X2 <- R^{-T} X2 R^{-1} (X2 optional) for upper
+// triangular R (all n x n, stride LDS)
+__device__ void bcongruence2(const double* R, double* X1, double* X2, int n) {
+    const int c = spread_index();
+    double* X = spread_second() ? X2 : X1;
+    if (X != nullptr && c < n) {
         for (int i = 0; i < n; ++i) {
             double s = X[i * LDS + c];
             for (int l = 0; l < i; ++l) s -= R[l * LDS + i] * X[l * LDS + c];
@@ -129,8 +140,8 @@ __device__ void bcongruence(const double* R, double* X, int n) {
         }
     }
     bsync();
-    if (tid < n) {
-        const int r = tid;
+    if (X != nullptr && c < n) {
+        const int r = c;
         for (int j = 0; j < n; ++j) {
             double s = X[r * LDS + j];
             for (int l = 0; l < j; ++l) s -= X[r * LDS + l] * R[l * LDS + j];
@@ -189,8 +200,10 @@ __device__ void bhessenberg(double* H, double* Vh, double* beta, int n, double* 
         bsync();
         if (!skip) {
             const double* v = Vh + k * LDS;
+            const int own = spread_second() ? n : spread_index();
             // H <- (I - b v v^T) H : one column per thread
-            for (int c = tid; c < n; c += NT) {
+            if (own < n) {
+                const int c = own;
                 double s = 0.0;
                 for (int i = k + 1; i < n; ++i) s += v[i] * H[i * LDS + c];
                 s *= b;
@@ -198,7 +211,8 @@ __device__ void bhessenberg(double* H, double* Vh, double* beta, int n, double* 
             }
             bsync();
             // H <- H (I - b v v^T) : one row per thread
-            for (int r = tid; r < n; r += NT) {
+            if (own < n) {
+                const int r = own;
                 double s = 0.0;
                 for (int i = k + 1; i < n; ++i) s += H[r * LDS + i] * v[i];
                 s *= b;
@@ -420,7 +434,7 @@ __device__ __noinline__ bool francis_eigenvalues(double* Hd, int n, long long* s
 // Inverse iteration on the Hessenberg H0 for the eigenvalue lam: two solves of
 // (H0 - lam I) x = b (Gaussian elimination with adjacent-row pivoting, which
 // keeps the Hessenberg structure), starting from b = 1.  U (packed upper
-// triangle, complex) lives in per-warp scratch.  x is returned normalised to
+// triangle, complex) lives in the caller's shared memory.  x is returned normalised to
 // max |x_i| = 1.
 __device__ void inverse_iteration(const double* H0, int n, cplx lam, cplx* x, cplx* U, cplx* cur, cplx* nxt,
                                   double tiny) {
@@ -516,11 +530,11 @@ struct Smem {
 // words of the shared-memory state saved to global memory between the launches
 constexpr int kStateWords = (int)(sizeof(Smem) / sizeof(int));
 static_assert(sizeof(Smem) % sizeof(int) == 0, "state copy granularity");
-// Yre, Yim, Yp (MAXM^2 each) and one packed complex LU factor (MAXM (MAXM+1) / 2)
-// per selected unit (at most MAXKP)
+// Yre, Yim, Yp (MAXM^2 each), then the saved state; a selected unit (at most
+// MAXKP) keeps its packed complex LU factor (MAXM (MAXM+1) / 2) in shared memory
 constexpr int MAXKP = 16;
 constexpr size_t kLuComplex = (size_t)MAXM * (MAXM + 1) / 2;
-constexpr size_t kWorkMainDoubles = 3 * (size_t)MAXM * MAXM + 2 * MAXKP * kLuComplex;
+constexpr size_t kWorkMainDoubles = 3 * (size_t)MAXM * MAXM;
 constexpr size_t kDenseWorkDoubles = kWorkMainDoubles + (sizeof(Smem) + sizeof(double) - 1) / sizeof(double);
 
 __device__ __forceinline__ Smem* state_of(const DenseArgs& a) {
@@ -542,8 +556,7 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
     int* gst = reinterpret_cast<int*>(state_of(a));
     int* sst = reinterpret_cast<int*>(&S);
     int nk = 0, nvk = 0;
-    // global scratch: complex eigenvector coefficients per selected unit, Y',
-    // and per-warp packed LU factors of the inverse iteration
+    // global scratch: complex eigenvector coefficients per selected unit and Y'
     double* Yre = a.work;                          // [unit][MAXM]
     double* Yim = Yre + MAXM * MAXM;               // [unit][MAXM]
     double* Yp = Yim + MAXM * MAXM;                // [col][MAXM]
@@ -602,8 +615,7 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
         }
         bsync();
         // ---- 2. the pencil in the B-orthonormal basis, via tau = 1/xi
-        bcongruence(S.A, S.B, nk);
-        bcongruence(S.A, S.H, nk);
+        bcongruence2(S.A, S.B, S.H, nk);
         for (int i = tid; i < nk * nk; i += NT) {
             int r = i / nk, c = i % nk;
             if (c > r) {
@@ -625,8 +637,9 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
         return;
     }
     // C = L^{-1} G_R L^{-T}: L Y = G_R by columns, then C L^T = Y by rows
-    if (tid < nk) {
-        const int c = tid;
+    const int own = spread_second() ? nk : spread_index();
+    if (own < nk) {
+        const int c = own;
         for (int i = 0; i < nk; ++i) {
             double sv = S.H[i * LDS + c];
             for (int l = 0; l < i; ++l) sv -= S.B[i * LDS + l] * S.H[l * LDS + c];
@@ -634,8 +647,8 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
         }
     }
     bsync();
-    if (tid < nk) {
-        const int r = tid;
+    if (own < nk) {
+        const int r = own;
         for (int j = 0; j < nk; ++j) {
             double sv = S.H[r * LDS + j];
             for (int l = 0; l < j; ++l) sv -= S.H[r * LDS + l] * S.B[j * LDS + l];
@@ -837,17 +850,23 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
     // upper triangular with the V columns first, so
     //   P_new = Z-hat[:, rest] Y'_rest = Z diag(colscale t) R^{-1} [0; Y'_rest]
     //   V_new - P_new = Z-hat[:, V] Y'_V = Z_V diag(colscale t) R_VV^{-1} Y'_V
-    if (tid < kp) {
-        const int j = tid;
-        for (int i = nk - 1; i >= 0; --i) {
-            double sv = (i >= nvk) ? Yp[j * MAXM + i] : 0.0;
-            for (int l = i + 1; l < nk; ++l) sv -= S.A[i * LDS + l] * Wr[j * MAXM + l];
-            Wr[j * MAXM + i] = sv / S.A[i * LDS + i];
-        }
-        for (int i = nvk - 1; i >= 0; --i) {
-            double sv = Yp[j * MAXM + i];
-            for (int l = i + 1; l < nvk; ++l) sv -= S.A[i * LDS + l] * Wv[j * MAXM + l];
-            Wv[j * MAXM + i] = sv / S.A[i * LDS + i];
+    // column j = 4 warp + (lane & 3): lanes 0..3 solve for Wr, lanes 4..7 for
+    // Wv, so the 2 kp solves run on all four sub-partitions
+    static_assert(MAXKP <= 16, "four warps of four columns");
+    {
+        const int j = warp * 4 + (lane & 3);
+        if (lane < 4 && j < kp) {
+            for (int i = nk - 1; i >= 0; --i) {
+                double sv = (i >= nvk) ? Yp[j * MAXM + i] : 0.0;
+                for (int l = i + 1; l < nk; ++l) sv -= S.A[i * LDS + l] * Wr[j * MAXM + l];
+                Wr[j * MAXM + i] = sv / S.A[i * LDS + i];
+            }
+        } else if (lane >= 4 && lane < 8 && j < kp) {
+            for (int i = nvk - 1; i >= 0; --i) {
+                double sv = Yp[j * MAXM + i];
+                for (int l = i + 1; l < nvk; ++l) sv -= S.A[i * LDS + l] * Wv[j * MAXM + l];
+                Wv[j * MAXM + i] = sv / S.A[i * LDS + i];
+            }
         }
     }
     for (int i = tid; i < m * kp; i += NT) a.Cp[i] = 0.0;
@@ -874,8 +893,19 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
 // saved Hessenberg form H0, back to C's basis with the Householder reflectors,
 // then y = L^{-T} z in the orthonormal basis, into Yre[u], Yim[u].  The units
 // run as separate CTAs on separate SMs (the FP64 work of one unit is serial).
+// shared memory of k_eigvec: H0, the Cholesky factor L of G_L and the
+// Householder vectors (MAXM x LDS each), the reflector coefficients, the
+// packed LU factor of the inverse iteration and the result y (re, im)
+constexpr size_t kEigvecShmDoubles = 3 * (size_t)MAXM * LDS + MAXM + 2 * kLuComplex + 2 * MAXM;
+
 __global__ void __launch_bounds__(32) k_eigvec(DenseArgs a) {
-    extern __shared__ __align__(16) double sh0[];   // H0, MAXM x LDS
+    extern __shared__ __align__(16) double sh0[];
+    double* sL = sh0 + MAXM * LDS;
+    double* sV = sL + MAXM * LDS;
+    double* sbeta = sV + MAXM * LDS;
+    cplx* U = reinterpret_cast<cplx*>(sbeta + MAXM);
+    double* syr = reinterpret_cast<double*>(U + kLuComplex);
+    double* syi = syr + MAXM;
     const Smem* G = state_of(a);
     if (G->ints[6]) return;
     const int u = blockIdx.x;
@@ -887,21 +917,23 @@ __global__ void __launch_bounds__(32) k_eigvec(DenseArgs a) {
     for (int i = lane; i < nk * LDS; i += 32) {
         const double v = G->H0[i];
         sh0[i] = v;
+        sL[i] = G->B[i];
+        sV[i] = G->Vh[i];
         if (i % LDS < nk) hn = fmax(hn, fabs(v));
     }
+    for (int i = lane; i < nk; i += 32) sbeta[i] = G->beta[i];
     hn = warp_max(hn);
     const double tiny = DBL_EPSILON * (hn > 0.0 ? hn : 1.0);
     __syncwarp();
     const int e = G->order[u];
     cplx lam = {G->eig_re[e], G->eig_im[e]};
     if (G->nclose[u] > 0) lam = cscale(lam, 1.0 + 1e-10 * G->nclose[u]);
-    cplx* U = reinterpret_cast<cplx*>(a.work + 3 * (size_t)MAXM * MAXM) + (size_t)u * kLuComplex;
     inverse_iteration(sh0, nk, lam, x, U, cur, nxt, tiny);
     // z = Q x with Q = H_0 H_1 ... (reflectors applied last-first)
     for (int k = nk - 3; k >= 0; --k) {
-        const double b = G->beta[k];
+        const double b = sbeta[k];
         if (b == 0.0) continue;
-        const double* v = G->Vh + k * LDS;
+        const double* v = sV + k * LDS;
         double sr = 0.0, si = 0.0;
         for (int i = k + 1 + lane; i < nk; i += 32) { sr += v[i] * x[i].re; si += v[i] * x[i].im; }
         sr = warp_sum(sr) * b;
@@ -911,22 +943,25 @@ __global__ void __launch_bounds__(32) k_eigvec(DenseArgs a) {
         __syncwarp();
     }
     // y = L^{-T} z  (back substitution with the lower factor L)
-    double* yr = a.work + (size_t)u * MAXM;
-    double* yi = a.work + (size_t)MAXM * MAXM + (size_t)u * MAXM;
     for (int i = nk - 1; i >= 0; --i) {
         double sr = 0.0, si = 0.0;
         for (int l = i + 1 + lane; l < nk; l += 32) {
-            sr += G->B[l * LDS + i] * yr[l];
-            si += G->B[l * LDS + i] * yi[l];
+            sr += sL[l * LDS + i] * syr[l];
+            si += sL[l * LDS + i] * syi[l];
         }
         sr = warp_sum(sr);
         si = warp_sum(si);
         if (lane == 0) {
-            yr[i] = (x[i].re - sr) / G->B[i * LDS + i];
-            yi[i] = (x[i].im - si) / G->B[i * LDS + i];
+            syr[i] = (x[i].re - sr) / sL[i * LDS + i];
+            syi[i] = (x[i].im - si) / sL[i * LDS + i];
         }
-        __threadfence_block();
         __syncwarp();
+    }
+    double* yr = a.work + (size_t)u * MAXM;
+    double* yi = a.work + (size_t)MAXM * MAXM + (size_t)u * MAXM;
+    for (int i = lane; i < nk; i += 32) {
+        yr[i] = syr[i];
+        yi[i] = syi[i];
     }
 }
 
@@ -951,10 +986,10 @@ __global__ void __launch_bounds__(32) k_francis(DenseArgs a) {
 
 size_t dense_smem_bytes() { return sizeof(Smem); }
 
-// Yre, Yim, Yp (3 MAXM^2), one packed complex LU factor per selected unit, and
-// the shared-memory state passed between the launches.
+// Yre, Yim, Yp (3 MAXM^2) and the shared-memory state passed between the
+// launches.
 size_t dense_work_doubles() { return kDenseWorkDoubles; }
-static_assert(kWorkMainDoubles >= 3 * (size_t)MAXM * MAXM + 2 * MAXKP * kLuComplex, "dense scratch layout");
+static_assert(kWorkMainDoubles >= 3 * (size_t)MAXM * MAXM, "dense scratch layout");
 
 cudaError_t dense_extract(const DenseArgs& a, cudaStream_t s) {
     size_t shm = sizeof(Smem);
@@ -963,12 +998,13 @@ cudaError_t dense_extract(const DenseArgs& a, cudaStream_t s) {
     const size_t shf = sizeof(double) * MAXM * LDS;
     e = cudaFuncSetAttribute(k_francis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_eigvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf);
+    const size_t she = sizeof(double) * kEigvecShmDoubles;
+    e = cudaFuncSetAttribute(k_eigvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)she);
     if (e != cudaSuccess) return e;
     k_extract<<<1, NT, shm, s>>>(a, 0);
     k_francis<<<1, 32, shf, s>>>(a);
     k_extract<<<1, NT, shm, s>>>(a, 1);
-    k_eigvec<<<a.kp, 32, shf, s>>>(a);
+    k_eigvec<<<a.kp, 32, she, s>>>(a);
     k_extract<<<1, NT, shm, s>>>(a, 2);
     count_launches(5);
     return cudaGetLastError();
@@ -1205,8 +1241,8 @@ extern "C" plhr_status plhr_tharm_extract(int m, int kp, int nv, const double* G
 namespace {
 
 // Scratch of the projected eigensolve for the largest supported basis
-// (m = 64): 8 * 64 * 64 doubles = 256 KiB.  Every GPU that loads the library
-// holds this array until the process exits.
+// (m = 64): three 64 x 64 arrays and the saved state, about 263 KiB.  Every
+// GPU that loads the library holds this array until the process exits.
 constexpr size_t kNoAllocScratchDoubles = plhr::kDenseWorkDoubles;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
