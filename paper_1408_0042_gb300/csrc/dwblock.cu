@@ -166,7 +166,11 @@ __global__ void k_sum_wide_dw(int nblocks, int m, const double* __restrict__ csc
 // Pout = F C_P, Vout = F_0 C_VV + F C_P in double-word arithmetic on FP64
 // blocks (in place allowed: every output row depends only on the same input
 // row and a chunk is staged before any of its rows is written)
-constexpr int kDwUpRows = 16;
+constexpr int kDwUpRows = 32;
+// Thread t owns column j = t % kp of rows r = t / kp and r + kDwUpRows / 2 of
+// each chunk (kp <= 16, so 16 kp <= 256 threads): the two rows share the
+// coefficient loads and give each thread two independent sums.  Every output
+// is summed over i in the same order as with one output per thread.
 __global__ void __launch_bounds__(256) k_update_dw(int64_t n, int m, int kp, int nb, FamD F,
                                                    const double* __restrict__ Cp, const double* __restrict__ Cvv,
                                                    double* __restrict__ Vout, int64_t ldvo, double* __restrict__ Pout,
@@ -177,6 +181,9 @@ __global__ void __launch_bounds__(256) k_update_dw(int64_t n, int m, int kp, int
     dw* zr = cv + kp * kp;                    // [rows][m]
     for (int t = threadIdx.x; t < m * kp; t += blockDim.x) cp[t] = dw_from_double(Cp[t]);
     for (int t = threadIdx.x; t < kp * kp; t += blockDim.x) cv[t] = dw_from_double(Cvv[t]);
+    constexpr int kHalf = kDwUpRows / 2;
+    const int r0 = threadIdx.x / kp, j = threadIdx.x - r0 * kp;
+    const bool own = r0 < kHalf;
     const int64_t nchunks = (n + kDwUpRows - 1) / kDwUpRows;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const int64_t row0 = ch * kDwUpRows;
@@ -192,16 +199,28 @@ __global__ void __launch_bounds__(256) k_update_dw(int64_t n, int m, int kp, int
             }
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < nrows * kp; t += blockDim.x) {
-            const int r = t / kp, j = t - r * kp;
-            const dw* z = zr + r * m;
-            float ph = 0.0f, pl = 0.0f;
-            for (int i = 0; i < m; ++i) dw_fma_acc(ph, pl, z[i], cp[i * kp + j]);
-            float vh = ph, vl = pl;
-            for (int i = 0; i < kp; ++i) dw_fma_acc(vh, vl, z[i], cv[i * kp + j]);
-            const int64_t row = row0 + r;
-            Pout[row * ldpo + j] = dw_to_double_fast(dw{ph, pl});
-            Vout[row * ldvo + j] = dw_to_double_fast(dw{vh, vl});
+        if (!own || r0 >= nrows) continue;
+        const bool two = r0 + kHalf < nrows;
+        const dw* z0 = zr + r0 * m;
+        const dw* z1 = zr + (two ? r0 + kHalf : r0) * m;
+        float ph0 = 0.0f, pl0 = 0.0f, ph1 = 0.0f, pl1 = 0.0f;
+        for (int i = 0; i < m; ++i) {
+            const dw c = cp[i * kp + j];
+            dw_fma_acc(ph0, pl0, z0[i], c);
+            dw_fma_acc(ph1, pl1, z1[i], c);
+        }
+        float vh0 = ph0, vl0 = pl0, vh1 = ph1, vl1 = pl1;
+        for (int i = 0; i < kp; ++i) {
+            const dw c = cv[i * kp + j];
+            dw_fma_acc(vh0, vl0, z0[i], c);
+            dw_fma_acc(vh1, vl1, z1[i], c);
+        }
+        const int64_t row = row0 + r0;
+        Pout[row * ldpo + j] = dw_to_double_fast(dw{ph0, pl0});
+        Vout[row * ldvo + j] = dw_to_double_fast(dw{vh0, vl0});
+        if (two) {
+            Pout[(row + kHalf) * ldpo + j] = dw_to_double_fast(dw{ph1, pl1});
+            Vout[(row + kHalf) * ldvo + j] = dw_to_double_fast(dw{vh1, vl1});
         }
     }
 }

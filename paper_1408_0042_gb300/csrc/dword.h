@@ -125,12 +125,10 @@ __device__ __forceinline__ dw dw_from_double(double d) {
     return {hi, lo};
 }
 __device__ __forceinline__ double dw_to_double(dw a) { return (double)a.hi + (double)a.lo; }
-// The FP64 routes as calls: the rare-input branches of the integer
-// conversions below call them, so the compiler keeps those branches instead of
-// evaluating the FP64 instructions for every element
+// The same as a call: the rare-input branch of the integer splits below calls
+// it, so the compiler keeps that branch instead of evaluating the FP64 route
+// for every element
 static __device__ __noinline__ dw dw_from_double_call(double d) { return dw_from_double(d); }
-static __device__ __noinline__ float f64_to_f32_call(double d) { return __double2float_rn(d); }
-static __device__ __noinline__ double f32_to_f64_call(float f) { return (double)f; }
 
 // The same split without FP64 instructions (GB300 issues FP64 at 1/64 of the
 // FP32 rate), by integer operations on the IEEE-754 encodings: hi is x
@@ -138,12 +136,11 @@ static __device__ __noinline__ double f32_to_f64_call(float f) { return (double)
 // mantissa bits decide, and an increment of the encoding carries into the
 // exponent), lo is the remainder x - hi, an integer of at most 2^28 times
 // 2^(e - 52) converted to FP32 (rounded) with its sign.  The pair is the one
-// the FP64 route gives, bit for bit, in the fast range and for zero (+-0,
-// +0).  Values below 2^-74 or from 2^127 up, Inf and NaN take the FP64 route.
+// the FP64 route gives, bit for bit, in the fast range.  Zero, values
+// below 2^-74 or from 2^127 up, Inf and NaN take the FP64 route.
 __device__ __forceinline__ dw dw_from_double_fast(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7ffu) - 1023;
-    if ((b << 1) == 0ull) return {__uint_as_float((unsigned)(b >> 63) << 31), 0.0f};
     if (e < -74 || e > 126) return dw_from_double_call(x);
     const unsigned sign = (unsigned)(b >> 63) << 31;
     const unsigned long long mant = b & 0xfffffffffffffull;
@@ -168,13 +165,12 @@ __device__ __forceinline__ void dw_fma_acc(float& hi, float& lo, const dw& a, co
 }
 
 // FP64 -> FP32 rounding (to nearest, ties to even: the conversion
-// instruction's result) by integer operations on the encodings, for zero and
-// normal FP32 results; other inputs take the conversion instruction
+// instruction's result) by integer operations on the encodings, for normal
+// FP32 results; other inputs take the conversion instruction
 __device__ __forceinline__ float f64_to_f32_rn(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7ffu) - 1023;
-    if ((b << 1) == 0ull) return __uint_as_float((unsigned)(b >> 63) << 31);
-    if (e < -126 || e > 126) return f64_to_f32_call(x);
+    if (e < -126 || e > 126) return __double2float_rn(x);
     const unsigned long long mant = b & 0xfffffffffffffull;
     const unsigned m29 = (unsigned)(mant & 0x1fffffffu);
     const unsigned up = (m29 > 0x10000000u) | ((m29 == 0x10000000u) & (unsigned)(mant >> 29) & 1u);
@@ -188,7 +184,6 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
 __device__ __forceinline__ dw dw_split_trunc(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7ffu) - 1023;
-    if ((b << 1) == 0ull) return {__uint_as_float((unsigned)(b >> 63) << 31), 0.0f};
     if (e < -74 || e > 127) return dw_from_double_call(x);
     const unsigned sign = (unsigned)(b >> 63) << 31;
     const unsigned long long mant = b & 0xfffffffffffffull;
@@ -205,8 +200,8 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned e = (u >> 23) & 0xffu;
     const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-    if (e == 0u) return (u & 0x7fffffu) ? f32_to_f64_call(f) : __longlong_as_double((long long)sign);
-    if (e == 0xffu) return f32_to_f64_call(f);
+    if (e == 0u) return (u & 0x7fffffu) ? (double)f : __longlong_as_double((long long)sign);
+    if (e == 0xffu) return (double)f;
     return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
                                             ((unsigned long long)(u & 0x7fffffu) << 29)));
 }
