@@ -263,6 +263,12 @@ __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int
         csw[t] = dw_from_double(v);
         csf[t] = (float)v;
     }
+    // thread t owns column j = t % kp of rows t / kp and t / kp + kUpRows / 2
+    // (kp <= 16): two independent sums sharing the coefficient loads, each
+    // summed in the same order as with one output per thread
+    constexpr int kHalfUp = kUpRows / 2;
+    const int r0 = threadIdx.x / kp, j = threadIdx.x - r0 * kp;
+    const bool own = r0 < kHalfUp;
     const int64_t nchunks = (n + kUpRows - 1) / kUpRows;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const int64_t row0 = ch * kUpRows;
@@ -285,27 +291,58 @@ __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int
             }
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < nrows * kp; t += blockDim.x) {
-            const int r = t / kp, j = t - r * kp;
-            const float* z = zf + r * m;
-            float prest = 0.0f, pv = 0.0f;
-            for (int i = kp; i < m; ++i) prest = fmaf(z[i], cpf[i * kp + j], prest);
-            for (int i = 0; i < kp; ++i) pv = fmaf(z[i], cpf[i * kp + j], pv);
-            const int64_t row = row0 + r;
-            const float p = pv + prest;
-            if (po64) static_cast<double*>(Pout)[row * ldpo + j] = f32_to_f64_bits(p);
-            else static_cast<float*>(Pout)[row * ldpo + j] = p;
-            if (v64) {
-                const dw* zr = zw + r * kp;
-                dw v = dw_make(prest);
-                for (int i = 0; i < kp; ++i) v = dw_add(v, dw_mul(zr[i], csw[i * kp + j]));
-                static_cast<double*>(Vout)[row * ldvo + j] = dw_to_double_fast(v);
+        if (!own || r0 >= nrows) continue;
+        // rows ra = r0 and rb = r0 + kUpRows / 2 (rb = ra, not stored, past nrows)
+        const bool two = r0 + kHalfUp < nrows;
+        const int ra = r0, rb = two ? r0 + kHalfUp : r0;
+        const float* za = zf + ra * m;
+        const float* zb = zf + rb * m;
+        float resta = 0.0f, restb = 0.0f, pva = 0.0f, pvb = 0.0f;
+        for (int i = kp; i < m; ++i) {
+            const float c = cpf[i * kp + j];
+            resta = fmaf(za[i], c, resta);
+            restb = fmaf(zb[i], c, restb);
+        }
+        for (int i = 0; i < kp; ++i) {
+            const float c = cpf[i * kp + j];
+            pva = fmaf(za[i], c, pva);
+            pvb = fmaf(zb[i], c, pvb);
+        }
+        const int64_t rowa = row0 + ra, rowb = row0 + rb;
+        const float pa = pva + resta, pb = pvb + restb;
+        if (po64) {
+            static_cast<double*>(Pout)[rowa * ldpo + j] = f32_to_f64_bits(pa);
+            if (two) static_cast<double*>(Pout)[rowb * ldpo + j] = f32_to_f64_bits(pb);
+        } else {
+            static_cast<float*>(Pout)[rowa * ldpo + j] = pa;
+            if (two) static_cast<float*>(Pout)[rowb * ldpo + j] = pb;
+        }
+        if (v64) {
+            const dw* zra = zw + ra * kp;
+            const dw* zrb = zw + rb * kp;
+            dw va = dw_make(resta), vb = dw_make(restb);
+            for (int i = 0; i < kp; ++i) {
+                const dw c = csw[i * kp + j];
+                va = dw_add(va, dw_mul(zra[i], c));
+                vb = dw_add(vb, dw_mul(zrb[i], c));
+            }
+            static_cast<double*>(Vout)[rowa * ldvo + j] = dw_to_double_fast(va);
+            if (two) static_cast<double*>(Vout)[rowb * ldvo + j] = dw_to_double_fast(vb);
+        } else {
+            float va = 0.0f, vb = 0.0f;
+            for (int i = 0; i < kp; ++i) {
+                const float c = csf[i * kp + j];
+                va = fmaf(za[i], c, va);
+                vb = fmaf(zb[i], c, vb);
+            }
+            va += resta;
+            vb += restb;
+            if (vo64) {
+                static_cast<double*>(Vout)[rowa * ldvo + j] = f32_to_f64_bits(va);
+                if (two) static_cast<double*>(Vout)[rowb * ldvo + j] = f32_to_f64_bits(vb);
             } else {
-                float v = 0.0f;
-                for (int i = 0; i < kp; ++i) v = fmaf(z[i], csf[i * kp + j], v);
-                v += prest;
-                if (vo64) static_cast<double*>(Vout)[row * ldvo + j] = f32_to_f64_bits(v);
-                else static_cast<float*>(Vout)[row * ldvo + j] = v;
+                static_cast<float*>(Vout)[rowa * ldvo + j] = va;
+                if (two) static_cast<float*>(Vout)[rowb * ldvo + j] = vb;
             }
         }
     }
