@@ -1,7 +1,8 @@
 // Double-word forms of the multi-Gram and the coefficient update on FP64
 // blocks, for the FP64 phase of the mixed-precision solve.  The inputs are
-// rounded once to double-word values (hi + lo FP32 pairs, ~48-bit
-// significands); products are formed with the FMA exact product of the high
+// split once into double-word values (hi = the leading 24 bits, lo = the
+// rest rounded to FP32: ~48-bit significands, dw_split_trunc); products are
+// formed with the FMA exact product of the high
 // parts plus the FP32 cross terms, and sums are accumulated with TwoSum on the
 // high part, so every result carries ~2^-46 relative error of the sum of
 // |terms| - FP64-class accuracy for the projected problem at a fraction of the
