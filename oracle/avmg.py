@@ -32,6 +32,13 @@ parameters to its reference [Ve.Kn:13]; the readings taken here are:
   numbers m (so |L_0 - sigma I|^{-1} resonates where the fine operator does);
 * the garbled "|L_l - I_l|^{-1}" of the algorithm's output line is read as
   |L_l - sigma I_l|^{-1}.
+
+Pins (tests/test_oracle_pins.py): one level is exactly |L - sigma I|^{-1} on
+the analytic modes; the spectrum of p_2; the transfer identities; a two-grid
+cycle equals its closed algebraic form; the cycle is symmetric positive
+definite.  Parity unpinned with respect to the paper's own multigrid: the
+parameter readings above replace a reference that is not available, so no
+printed number of the paper checks them.
 """
 from __future__ import annotations
 
