@@ -15,6 +15,12 @@ written with the slowest axis first.
   Kronecker sum with the 1D second difference closed periodically
   (u[-1] = u[N-1], u[N] = u[0]) or with Dirichlet ends, times 1/2, plus the
   potential on the diagonal.
+* Bloch Hamiltonian H_kappa = -1/2 Lap_kappa + diag(V) on a periodic grid
+  (the complex Hermitian Hamiltonians of Section 5.3 at a crystal momentum
+  kappa): the periodic second difference with the phase e^{+-i kappa_d h} on
+  every link along axis d, (2u[j] - e^{i kappa h} u[j+1] - e^{-i kappa h}
+  u[j-1]) / h^2, so that a plane wave e^{i theta j} has the eigenvalue
+  (2 - 2 cos(theta + kappa h)) / h^2; kappa = 0 is the real periodic case.
 * Bilinear (Q1) finite elements (Section 5.1: "standard bilinear finite
   elements", stiffness A and mass B): on a tensor mesh the Q1 element matrices
   factor into 1D linear-element matrices, so A = K (x) M + M (x) K and
@@ -68,6 +74,29 @@ def hamiltonian(dims, h: float, V, periodic: bool = True) -> sp.csr_matrix:
     one_d = second_difference_periodic_1d if periodic else second_difference_1d
     lap = kron_sum([one_d(N, h) for N in reversed(dims)])
     return (0.5 * lap + sp.diags(np.asarray(V, dtype=np.float64).ravel(), 0)).tocsr()
+
+
+def second_difference_bloch_1d(N: int, h: float, kappa: float) -> sp.csr_matrix:
+    """(2u[j] - e^{i kappa h} u[j+1] - e^{-i kappa h} u[j-1]) / h^2 on N points
+    of a periodic line (Hermitian; the phase sits on every link)."""
+    ph = np.exp(1j * kappa * h)
+    D = sp.lil_matrix((N, N), dtype=np.complex128)
+    for j in range(N):
+        D[j, j] += 2.0
+        D[j, (j + 1) % N] -= ph
+        D[j, (j - 1) % N] -= np.conj(ph)
+    return (D.tocsr() / h**2).tocsr()
+
+
+def bloch_hamiltonian(dims, h: float, V, kappa) -> sp.csr_matrix:
+    """H = -1/2 Lap_kappa + diag(V) on the periodic grid dims = (nx, ny[, nz])
+    at crystal momentum kappa = (kappa_x, kappa_y[, kappa_z]); V flattened x
+    fastest; complex Hermitian."""
+    kap = [float(k) for k in kappa]
+    assert len(kap) == len(dims)
+    mats = [second_difference_bloch_1d(N, h, k) for N, k in zip(reversed(dims), reversed(kap))]
+    lap = kron_sum(mats)
+    return (0.5 * lap + sp.diags(np.asarray(V, dtype=np.float64).ravel().astype(np.complex128), 0)).tocsr()
 
 
 def q1_1d(N: int, h: float):

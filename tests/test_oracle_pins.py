@@ -520,3 +520,82 @@ def test_tpa_symmetric_positive_definite_and_commutes_with_kinetic_operator():
         assert np.linalg.eigvalsh(Tm).min() > 0
         K = ops.hamiltonian(dims, h, np.zeros(n), periodic=periodic).toarray()
         assert np.abs(Tm @ K - K @ Tm).max() <= 1e-12 * np.abs(K).max()
+
+
+# ---------------------------------------------------------------- Bloch Hamiltonian (complex Hermitian)
+
+def test_bloch_free_particle_closed_form():
+    """V = 0, h = 1: a plane wave with mode numbers m_d has the eigenvalue
+    sum_d (1 - cos(2 pi m_d / N_d + kappa_d)) of -1/2 Lap_kappa."""
+    dims, kappa = (5, 4, 3), (0.3, -0.5, 0.9)
+    H = operators.bloch_hamiltonian(dims, 1.0, np.zeros(60), kappa).toarray()
+    lam = np.linalg.eigvalsh(H)
+    ms = [np.arange(N) for N in dims]
+    cf = sum(np.meshgrid(*[1.0 - np.cos(2 * np.pi * m / N + k) for m, N, k in zip(ms, dims, kappa)],
+                         indexing="ij"))
+    assert np.allclose(lam, np.sort(cf.ravel()), atol=1e-12)
+
+
+def test_bloch_hermitian_and_real_at_zero_momentum():
+    p = wl.bloch_small(5, 2)
+    H = operators.bloch_hamiltonian(p["dims"], 1.0, p["V"], p["kappa"]).toarray()
+    assert np.abs(H - H.conj().T).max() == 0.0
+    assert np.abs(H.imag).max() > 0.0
+    H0 = operators.bloch_hamiltonian(p["dims"], 1.0, p["V"], (0.0, 0.0, 0.0)).toarray()
+    R = operators.hamiltonian(p["dims"], 1.0, p["V"], periodic=True).toarray()
+    assert np.abs(H0 - R).max() <= 1e-15
+
+
+def test_bloch_spectrum_periodic_in_momentum_and_time_reversal():
+    """A shift of kappa_d by 2 pi / N_d is the gauge transform u_x ->
+    e^{2 pi i x_d / N_d} u_x (unitary), and H(-kappa) = conj(H(kappa)): the
+    spectrum is the same in all three, with the wells present."""
+    p = wl.bloch_small(6, 3)
+    dims, V, kap = p["dims"], p["V"], np.array(p["kappa"])
+    lam = np.linalg.eigvalsh(operators.bloch_hamiltonian(dims, 1.0, V, kap).toarray())
+    for d in range(3):
+        k2 = kap.copy()
+        k2[d] += 2 * np.pi / dims[d]
+        lam2 = np.linalg.eigvalsh(operators.bloch_hamiltonian(dims, 1.0, V, k2).toarray())
+        assert np.allclose(lam2, lam, atol=1e-12)
+    lam3 = np.linalg.eigvalsh(operators.bloch_hamiltonian(dims, 1.0, V, -kap).toarray())
+    assert np.allclose(lam3, lam, atol=1e-12)
+    # and a generic momentum change does move the spectrum
+    lam4 = np.linalg.eigvalsh(operators.bloch_hamiltonian(dims, 1.0, V, kap + 0.2).toarray())
+    assert np.abs(lam4 - lam).max() > 1e-3
+
+
+def test_bloch_workload_recipe():
+    p = wl.bloch_small(6, 3)
+    assert len(p["kappa"]) == 3 and all(abs(k) < np.pi / 6 for k in p["kappa"])
+    assert p["V"].min() < -0.5 and p["V"].max() <= 0.0
+    q = wl.bloch_small(6, 3)
+    assert q["kappa"] == p["kappa"] and np.array_equal(q["V"], p["V"])
+
+
+def test_bloch_hamiltonian_algorithm2_matches_dense():
+    """Alg. 2 (complex arithmetic, T = I) on a 6^3 Bloch Hamiltonian with
+    three wells: the k nearest eigenvalues of a clean gap and orthonormal
+    eigenvectors with small residuals."""
+    p = wl.bloch_small(6, 3)
+    H = operators.bloch_hamiltonian(p["dims"], 1.0, p["V"], p["kappa"])
+    w = np.linalg.eigvalsh(H.toarray())
+    k = 3
+    # a shift between two levels near index 12 with the k nearest well separated
+    best = None
+    for i in range(6, 20):
+        sig = 0.5 * (w[i] + w[i + 1])
+        d = np.sort(np.abs(w - sig))
+        score = d[k] - d[k - 1]
+        if best is None or score > best[0]:
+            best = (score, sig)
+    sigma = best[1]
+    V0 = wl.start_block(H.shape[0], k + 1, 33, complex_=True)
+    r = plhr.bplhr(H, None, None, sigma, k, V0, tol=1e-10, maxit=5000, real=False)
+    assert r.converged
+    ref = w[np.lexsort((w, np.abs(w - sigma)))][:k]
+    assert np.allclose(np.sort(r.eigvals), np.sort(ref), rtol=1e-10, atol=1e-12)
+    X = r.eigvecs
+    assert np.abs(X.conj().T @ X - np.eye(k)).max() <= 1e-12
+    R = H @ X - X * np.asarray(r.eigvals)[None, :]
+    assert np.linalg.norm(R, axis=0).max() <= 1e-8 * max(1.0, np.abs(r.eigvals).max())

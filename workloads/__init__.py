@@ -211,6 +211,26 @@ def hamiltonian_small(N: int = 10, nwells: int = 6, k: int = 4, seed: int = SEED
     return {"dims": dims, "h": 1.0, "V": gaussian_potential(dims, nwells, seed), "k": k, "seed": seed}
 
 
+def bloch_small(N: int = 6, nwells: int = 3, seed: int = SEED_BASE + 3, dim: int = 3):
+    """Complex Hermitian test problem of the Bloch-Hamiltonian workload at a
+    size a dense eigensolver finishes quickly: a seeded Gaussian-well
+    potential on an N^dim periodic grid (h = 1) and a crystal momentum kappa
+    uniform in the supercell zone [-pi/N, pi/N)^dim (drawn after the wells)."""
+    dims = (N,) * dim
+    V = gaussian_potential(dims, nwells, seed)
+    u = uniform_block(dim, 1, seed, start=nwells * (dim + 2)).ravel()     # [-0.5, 0.5)
+    kappa = tuple(2.0 * np.pi / N * float(x) for x in u)
+    return {"dims": dims, "h": 1.0, "V": V, "kappa": kappa, "seed": seed}
+
+
+def config3_problem():
+    """96^3 periodic Bloch Hamiltonian: 64 seeded Gaussian wells (depth
+    U(-4, -1), width U(0.5, 1.5) grid units, centres uniform) and kappa uniform
+    in [-pi/96, pi/96)^3 (h = 1).  The shift is the midpoint of the 31st and
+    32nd eigenvalues of the assembled operator, k = 16."""
+    return bloch_small(96, 64, SEED_BASE + 3, 3)
+
+
 def config5_potential():
     """64^3 periodic grid, 32 seeded Gaussian wells (h = 1)."""
     dims = (64, 64, 64)
