@@ -26,6 +26,12 @@ written with the slowest axis first.
   factor into 1D linear-element matrices, so A = K (x) M + M (x) K and
   B = M (x) M with K = tridiag(-1, 2, -1)/h and M = tridiag(1, 4, 1) h/6 on
   the interior nodes.
+* Trilinear (Q1) finite elements in 3D with a coefficient c per element
+  (the generalized pencil of the survey's config 4): assembled element by
+  element from the 8 x 8 element matrices c_e (k (x) m (x) m + m (x) k (x) m
+  + m (x) m (x) k) and m (x) m (x) m of the 1D linear element (k = [[1, -1],
+  [-1, 1]] / h, m = [[2, 1], [1, 2]] h / 6), then restricted to the interior
+  nodes (homogeneous Dirichlet).
 """
 from __future__ import annotations
 
@@ -116,6 +122,38 @@ def q1_fe_2d(elems: int):
     A = (sp.kron(K, M) + sp.kron(M, K)).tocsr()
     B = sp.kron(M, M).tocsr()
     return A, B
+
+
+def q1_fe_3d(elems: int, coeff=None):
+    """Stiffness A (of -div(c grad)) and mass B of trilinear elements on the
+    unit cube with `elems` elements per side, homogeneous Dirichlet; coeff is
+    None (c = 1) or an array of elems^3 element values, x fastest.  Assembled
+    element by element (interior nodes, x fastest)."""
+    E = int(elems)
+    h = 1.0 / E
+    k1 = np.array([[1.0, -1.0], [-1.0, 1.0]]) / h
+    m1 = np.array([[2.0, 1.0], [1.0, 2.0]]) * (h / 6.0)
+    # local node (a, b, c) -> a + 2 b + 4 c: Kronecker products slowest axis first
+    Ke = np.kron(m1, np.kron(m1, k1)) + np.kron(m1, np.kron(k1, m1)) + np.kron(k1, np.kron(m1, m1))
+    Me = np.kron(m1, np.kron(m1, m1))
+    c = np.ones(E**3) if coeff is None else np.asarray(coeff, dtype=np.float64).ravel()
+    assert c.size == E**3
+    ex, ey, ez = np.meshgrid(np.arange(E), np.arange(E), np.arange(E), indexing="ij")
+    ex, ey, ez = ex.ravel(), ey.ravel(), ez.ravel()
+    elem = (ez * E + ey) * E + ex
+    nn = E + 1
+    local = np.array([[a, b, cc] for cc in (0, 1) for b in (0, 1) for a in (0, 1)])   # a fastest
+    gnode = np.stack([((ez + cc) * nn + (ey + b)) * nn + (ex + a) for a, b, cc in local], axis=1)
+    rows = np.repeat(gnode, 8, axis=1).ravel()
+    cols = np.tile(gnode, (1, 8)).ravel()
+    A = sp.coo_matrix(((c[elem][:, None] * Ke.ravel()[None, :]).ravel(), (rows, cols)),
+                      shape=(nn**3, nn**3)).tocsr()
+    B = sp.coo_matrix((np.tile(Me.ravel(), E**3), (rows, cols)), shape=(nn**3, nn**3)).tocsr()
+    g = np.arange(nn)
+    inner = (g > 0) & (g < E)
+    mask = (inner[None, None, :] & inner[None, :, None] & inner[:, None, None]).ravel()   # [z][y][x]
+    idx = np.nonzero(mask)[0]
+    return A[idx][:, idx].tocsr(), B[idx][:, idx].tocsr()
 
 
 def model_operator(workload):

@@ -599,3 +599,83 @@ def test_bloch_hamiltonian_algorithm2_matches_dense():
     assert np.abs(X.conj().T @ X - np.eye(k)).max() <= 1e-12
     R = H @ X - X * np.asarray(r.eigvals)[None, :]
     assert np.linalg.norm(R, axis=0).max() <= 1e-8 * max(1.0, np.abs(r.eigvals).max())
+
+
+# ---------------------------------------------------------------- 3D trilinear elements with a coefficient
+
+def _q1_mu(E):
+    h = 1.0 / E
+    t = np.arange(1, E) * np.pi * h
+    return 6.0 / h**2 * (1 - np.cos(t)) / (2 + np.cos(t))
+
+
+def test_q1_3d_element_assembly_matches_tensor_closed_form():
+    """c = 1: the pencil's eigenvalues are mu_i + mu_j + mu_l with the 1D
+    linear-element values mu = (6/h^2)(1 - cos t)/(2 + cos t)."""
+    E = 6
+    A, B = operators.q1_fe_3d(E)
+    ev = sla.eigh(A.toarray(), B.toarray(), eigvals_only=True)
+    mu = _q1_mu(E)
+    cf = np.sort((mu[:, None, None] + mu[None, :, None] + mu[None, None, :]).ravel())
+    assert np.allclose(ev, cf, rtol=1e-12)
+
+
+def test_q1_3d_element_assembly_equals_kronecker_form():
+    E = 5
+    A, B = operators.q1_fe_3d(E)
+    K, M = operators.q1_1d(E - 1, 1.0 / E)
+    Ak = sp_kron3(K, M, M) + sp_kron3(M, K, M) + sp_kron3(M, M, K)
+    Bk = sp_kron3(M, M, M)
+    assert np.abs((A - Ak).toarray()).max() <= 1e-13 * np.abs(Ak.toarray()).max()
+    assert np.abs((B - Bk).toarray()).max() <= 1e-15
+
+
+def sp_kron3(a, b, c):
+    import scipy.sparse as sps
+    return sps.kron(a, sps.kron(b, c)).tocsr()
+
+
+def test_q1_3d_coefficient_scaling_and_courant_fischer():
+    """A(c) is linear in c, so c = 10 scales A by 10; for c in {1, 10} per
+    cube A(c) - A(1) and A(10) - A(c) are positive semidefinite, so every
+    eigenvalue of (A(c), B) lies between those of c = 1 and c = 10."""
+    E = 8
+    A1, B = operators.q1_fe_3d(E)
+    A10, _ = operators.q1_fe_3d(E, np.full(E**3, 10.0))
+    assert np.abs((A10 - 10.0 * A1).toarray()).max() <= 1e-12 * np.abs(A10.toarray()).max()
+    c = wl.q1_coefficient(E, 4, 11)
+    assert set(np.unique(c)) == {1.0, 10.0}
+    Ac, _ = operators.q1_fe_3d(E, c)
+    l1 = sla.eigh(A1.toarray(), B.toarray(), eigvals_only=True)
+    lc = sla.eigh(Ac.toarray(), B.toarray(), eigvals_only=True)
+    l10 = 10.0 * l1
+    tol = 1e-9 * l10.max()
+    assert np.all(lc >= l1 - tol) and np.all(lc <= l10 + tol)
+    assert np.abs(lc - l1).max() > 1.0 and np.abs(l10 - lc).max() > 1.0
+
+
+def test_q1_3d_generalized_algorithm3_matches_dense():
+    """Alg. 3 with B on the 8^3-element pencil with a seeded {1, 10}
+    coefficient, T = A^{-1} (the stiffness inverse, symmetric positive
+    definite): the k pairs nearest sigma against LAPACK's generalized eigh,
+    B-orthonormal."""
+    E = 8
+    A, B = operators.q1_fe_3d(E, wl.q1_coefficient(E, 4, 11))
+    w = sla.eigh(A.toarray(), B.toarray(), eigvals_only=True)
+    k = 3
+    best = None
+    for i in range(20, 40):
+        sig = 0.5 * (w[i] + w[i + 1])
+        d = np.sort(np.abs(w - sig))
+        score = (d[k] - d[k - 1]) / d[k]
+        if best is None or score > best[0]:
+            best = (score, sig)
+    sigma = best[1]
+    cho = sla.cho_factor(A.toarray())
+    V0 = wl.start_block(A.shape[0], k + 1, 41)
+    r = plhr.bplhr(A, B, lambda X: sla.cho_solve(cho, X), sigma, k, V0, tol=1e-9, maxit=3000)
+    assert r.converged
+    ref = w[np.lexsort((w, np.abs(w - sigma)))][:k]
+    assert np.allclose(np.sort(r.eigvals), np.sort(ref), rtol=1e-9)
+    X = r.eigvecs
+    assert np.abs(X.T @ (B @ X) - np.eye(k)).max() <= 1e-10

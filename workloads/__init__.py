@@ -231,6 +231,25 @@ def config3_problem():
     return bloch_small(96, 64, SEED_BASE + 3, 3)
 
 
+def q1_coefficient(elems: int, block: int, seed: int) -> np.ndarray:
+    """Element coefficients c in {1, 10} (x fastest): constant on cubes of
+    block^3 elements, each cube 10 with probability 1/2 (one SplitMix64 draw
+    per cube, cubes in x-fastest order)."""
+    nb = elems // block
+    assert nb * block == elems
+    u = uniform_block(nb**3, 1, seed).ravel()
+    cb = np.where(u >= 0.0, 10.0, 1.0).reshape(nb, nb, nb)         # [z][y][x] cubes
+    e = np.arange(elems) // block
+    return cb[e[:, None, None], e[None, :, None], e[None, None, :]].ravel()
+
+
+def config4_problem():
+    """64^3 trilinear elements on the unit cube (interior 63^3 nodes),
+    coefficient c in {1, 10} on 8^3-element cubes; k = 8 pairs near spectral
+    index 300 of the pencil (stiffness, mass)."""
+    return {"elems": 64, "coeff": q1_coefficient(64, 8, SEED_BASE + 4), "k": 8}
+
+
 def config5_potential():
     """64^3 periodic grid, 32 seeded Gaussian wells (h = 1)."""
     dims = (64, 64, 64)
