@@ -238,12 +238,12 @@ cudaError_t multi_gram_dw(int64_t n, int nb, const Blk<const double>* Z, const B
     if (mp > 64) return cudaErrorInvalidValue;
     const int blocks = sm_count();
     const size_t shm = (sizeof(dw) + sizeof(double)) * 3 * kDwRows * mp;
-    static bool attr = false;
-    if (!attr) {
+    // above the 48 KB default: raise the limit on the current device (every
+    // call, so that each device a process uses gets it)
+    {
         cudaError_t e = cudaFuncSetAttribute(k_gram_dw, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)((sizeof(dw) + sizeof(double)) * 3 * kDwRows * 64));
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     k_gram_dw<<<blocks, kDwThreads, shm, s>>>(n, m, mp, nb, FZ, FA, FQ, Q ? 0 : 1, sigma, partial);
     count_launches(1);

@@ -432,14 +432,13 @@ cudaError_t multi_gram_mx(int64_t n, int nb, const BlkMx* Z, const BlkMx* AZ, co
     if (mp > 64) return cudaErrorInvalidValue;
     const int blocks = gram_mx_blocks();
     const size_t shm = sizeof(double) * 3 * kMxRows * mp + sizeof(float) * (3 * kMxRows * mp + mp);
-    // above the 48 KB default at mp = 64: raise the kernel's limit to the largest size
-    static bool attr = false;
-    if (!attr) {
+    // above the 48 KB default: raise the kernel's limit to the largest size on
+    // the current device (every call, so that each device a process uses gets it)
+    {
         cudaError_t e = cudaFuncSetAttribute(k_gram_mx, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(sizeof(double) * 3 * kMxRows * 64 +
                                                    sizeof(float) * (3 * kMxRows * 64 + 64)));
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     k_gram_mx<<<blocks, kGramMxThreads, shm, s>>>(n, m, mp, nb, FZ, FA, FQ, Q ? 1 : 0, sigma, colscale, partial);
     count_launches(1);
