@@ -1,10 +1,11 @@
-"""Host logic of the N > 1 bench path on CPU: two gloo ranks.
+"""Host logic of bench.py on CPU: the N > 1 path on two gloo ranks, and the
+clock record.
 
 Block PLHR on one problem does not shard here (one GPU per box), so N ranks
 run N replicas and the reported time is the maximum over the ranks, taken
 between barriers.  These tests run that reduction and the barrier as two
-processes over gloo, and check that the reference arm does no work on ranks
-other than 0."""
+processes over gloo, check that the reference arm does no work on ranks
+other than 0, and parse nvidia-smi samples into the clock summary."""
 import os
 import socket
 import sys
@@ -74,3 +75,17 @@ def test_reference_arm_returns_without_work_on_other_ranks():
 
     # rank 1 of 2 prints nothing and runs no oracle
     assert bench.run_reference(Args(), 2, 1, 1) is None
+
+
+def test_clock_summary_parses_samples_and_throttle_reasons():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.lines = ["0, 2070, 2070, 950.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 1001.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line", "0, [N/A], 2070, 0, 0x0, a, b, c, d"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+    assert bench.ClockSampler(0).summary()["sm_mhz"] is None
