@@ -216,7 +216,7 @@ def run_ours(args, world, rank, local):
     import workloads as wl
 
     torch.cuda.set_device(local)
-    w = wl.config2()
+    w = wl.lap3d_128cube_k10()
     profile_case = args.profile_grid > 0
     if profile_case:
         # reduced grid with the same structure, a fixed number of iterations:
@@ -360,7 +360,7 @@ def _oracle_iteration_seconds(samples=1):
     import workloads as wl
     from oracle import avmg, operators, plhr
 
-    w = wl.config2()
+    w = wl.lap3d_128cube_k10()
     A, _ = operators.model_operator(w)
     T = avmg.AVMG(w.dims, w.h, w.sigma, w.mg_levels, w.mg_nu, transfer="linear", coarse="fine_spectrum")
     marks = []
@@ -397,7 +397,7 @@ def run_grad(args, world, rank, local):
     import workloads as wl
 
     torch.cuda.set_device(local)
-    c = wl.config5()
+    c = wl.ham64_k8_grad()
     dims, sigma, k = c["dims"], c["sigma"], c["k"]
     n = int(np.prod(dims))
     guard, tol, adj_tol = 2, 1e-10, 1e-10
@@ -538,7 +538,7 @@ def grad_cpu_baseline(gpu_iterations):
     import workloads as wl
     from oracle import operators, plhr, spectral
 
-    c = wl.config5()
+    c = wl.ham64_k8_grad()
     H = operators.hamiltonian(c["dims"], 1.0, c["V"])
     T = spectral.TPA(c["dims"], 1.0, spectral.default_energy(c["sigma"], c["V"], c["dims"], 1.0))
     n = H.shape[0]
@@ -566,7 +566,7 @@ def run_reference(args, world, rank, local):
     if rank != 0:
         return
     import workloads as wl
-    w = wl.config2()
+    w = wl.lap3d_128cube_k10()
     iters = F64_ITERATIONS_TO_TOL
     for _ in range(args.warmup):
         _oracle_iteration_seconds(samples=1)

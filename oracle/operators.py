@@ -27,7 +27,7 @@ written with the slowest axis first.
   B = M (x) M with K = tridiag(-1, 2, -1)/h and M = tridiag(1, 4, 1) h/6 on
   the interior nodes.
 * Trilinear (Q1) finite elements in 3D with a coefficient c per element
-  (the generalized pencil of the survey's config 4): assembled element by
+  (the generalized pencil of -div(c grad u) = lambda u): assembled element by
   element from the 8 x 8 element matrices c_e (k (x) m (x) m + m (x) k (x) m
   + m (x) m (x) k) and m (x) m (x) m of the 1D linear element (k = [[1, -1],
   [-1, 1]] / h, m = [[2, 1], [1, 2]] h / 6), then restricted to the interior

@@ -248,7 +248,7 @@ def test_dense_reference_gradient_12cube(plhr):
     assert np.abs(g - ref).max() <= 1e-8 * np.abs(ref).max(), np.abs(g - ref).max()
 
 
-def test_config5_gradient_matches_finite_differences_at_64_points(plhr):
+def test_ham64_gradient_matches_finite_differences_at_64_points(plhr):
     """The 64^3 differentiation workload: dL/dV of
     L = sum_k w_k lambda_k + sum_k |m (.) v_k|^2 (k = 8) against central
     differences of L at 64 seeded grid points, each perturbed solve
@@ -256,7 +256,7 @@ def test_config5_gradient_matches_finite_differences_at_64_points(plhr):
     largest gradient entry.  The solves run to relative residual 1e-12 without
     preconditioner: the double-word TPA transforms carry ~1e-12 relative
     rounding, and the T-harmonic iteration with them stalls near 1e-11."""
-    c = wl.config5()
+    c = wl.ham64_k8_grad()
     dims, sigma, k = c["dims"], c["sigma"], c["k"]
     guard = 2
     V = c["V"]

@@ -109,10 +109,10 @@ def test_mixed_switch_tol_zero_stays_fp32_until_forced(plhr):
 
 
 @pytest.mark.slow
-def test_config2_mixed_full(plhr):
+def test_lap3d_128cube_mixed_full(plhr):
     """128^3 Laplacian, k = 10, 4-level AV-MG, mixed precision: the same
     closed-form eigenvalues and residual bound as the FP64 form."""
-    w = wl.config2()
+    w = wl.lap3d_128cube_k10()
     A = plhr.Operator.laplacian(w.dims, w.h)
     T = plhr.AVMG(A, w.sigma, levels=w.mg_levels, nu=w.mg_nu, transfer=1, coarse=1)
     v0 = torch.from_numpy(w.v0()).cuda()

@@ -116,8 +116,8 @@ def test_solve_tracks_oracle_and_closed_form(plhr, case):
     assert np.sqrt(max(0.0, 1.0 - s.min() ** 2)) <= 1e-7
 
 
-def test_config1_full(plhr):
-    w = wl.config1()
+def test_lap2d_32x32_full(plhr):
+    w = wl.lap2d_32x32_k4()
     A = plhr.Operator.laplacian(w.dims, w.h)
     v0 = torch.from_numpy(w.v0()).cuda()
     lam, V, info = plhr.solve(A, w.sigma, w.k, T=None, tol=w.tol, maxit=w.maxit, v_init=v0, guard=w.guard)
@@ -187,10 +187,10 @@ def test_tharm_extract_matches_lapack(plhr, seed):
             assert abs(nrm[j] - 1.0) <= 1e-9
 
 
-def test_config2_full(plhr):
+def test_lap3d_128cube_full(plhr):
     """128^3 Laplacian, k = 10 nearest sigma, 4-level AV-MG: eigenvalues equal
     the closed-form ones, residuals (recomputed on the CPU) meet tol."""
-    w = wl.config2()
+    w = wl.lap3d_128cube_k10()
     A = plhr.Operator.laplacian(w.dims, w.h)
     T = plhr.AVMG(A, w.sigma, levels=w.mg_levels, nu=w.mg_nu, transfer=1, coarse=1)
     v0 = torch.from_numpy(w.v0()).cuda()

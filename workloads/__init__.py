@@ -106,7 +106,7 @@ def _mid_gap(dims, h, lo_index: int) -> float:
     return 0.5 * (lam[lo_index] + lam[lo_index + 1])
 
 
-def config1() -> Workload:
+def lap2d_32x32_k4() -> Workload:
     """2D 5-point Laplacian, 32x32 Dirichlet interior grid, h = 1/33, B = I,
     sigma midway between the 100th and 101st eigenvalues, k = 4, T = I."""
     dims, h = (32, 32), 1.0 / 33.0
@@ -119,7 +119,7 @@ def config1() -> Workload:
 # the eigenvalues 1064.0220711725 (mode (6,6,6)) and 1073.1201516674 (modes
 # (3,6,8) and permutations); 471 eigenvalues lie below it and the 10 nearest
 # form complete multiplets (3 + 1 + 6), the 11th is 12.18 away.
-def config2() -> Workload:
+def lap3d_128cube_k10() -> Workload:
     dims, h = (128, 128, 128), 1.0 / 129.0
     sigma = 0.5 * (_lap3_mode((6, 6, 6), h) + _lap3_mode((3, 6, 8), h))
     return Workload(name="lap3d_128cube_k10", kind="lap3d", dims=dims, h=h,
@@ -175,7 +175,7 @@ def _clean_shift(lam: np.ndarray, target: int, k: int) -> float:
     return float(best[1])
 
 
-CONFIGS = {"config1": config1, "config2": config2}
+WORKLOADS = {"lap2d_32x32_k4": lap2d_32x32_k4, "lap3d_128cube_k10": lap3d_128cube_k10}
 
 
 def gaussian_potential(dims, nwells: int, seed: int, depth=(-4.0, -1.0), width=(0.5, 1.5)) -> np.ndarray:
@@ -223,7 +223,7 @@ def bloch_small(N: int = 6, nwells: int = 3, seed: int = SEED_BASE + 3, dim: int
     return {"dims": dims, "h": 1.0, "V": V, "kappa": kappa, "seed": seed}
 
 
-def config3_problem():
+def bloch_96cube():
     """96^3 periodic Bloch Hamiltonian: 64 seeded Gaussian wells (depth
     U(-4, -1), width U(0.5, 1.5) grid units, centres uniform) and kappa uniform
     in [-pi/96, pi/96)^3 (h = 1).  The shift is the midpoint of the 31st and
@@ -243,14 +243,14 @@ def q1_coefficient(elems: int, block: int, seed: int) -> np.ndarray:
     return cb[e[:, None, None], e[None, :, None], e[None, None, :]].ravel()
 
 
-def config4_problem():
+def q1_fe_64cube():
     """64^3 trilinear elements on the unit cube (interior 63^3 nodes),
     coefficient c in {1, 10} on 8^3-element cubes; k = 8 pairs near spectral
     index 300 of the pencil (stiffness, mass)."""
     return {"elems": 64, "coeff": q1_coefficient(64, 8, SEED_BASE + 4), "k": 8}
 
 
-def config5_potential():
+def ham64_potential():
     """64^3 periodic grid, 32 seeded Gaussian wells (h = 1)."""
     dims = (64, 64, 64)
     return dims, gaussian_potential(dims, 32, SEED_BASE + 5)
@@ -267,11 +267,11 @@ HAM64_LAMBDA_REF = (-1.4972095727, -1.4646666705, -1.3947918710, -1.3900142734, 
                     -1.3285495681, -1.3180617417)
 
 
-def config5():
+def ham64_k8_grad():
     """Differentiation workload on the 64^3 Hamiltonian: potential, shift,
     block size, eigenvalue weights w ~ U(0.5, 1.5) and a density mask
     m ~ Bernoulli(1/2) for the loss sum_k w_k lambda_k + sum_k |m (.) v_k|^2."""
-    dims, V = config5_potential()
+    dims, V = ham64_potential()
     n = int(np.prod(dims))
     w = 0.5 + (uniform_block(HAM64_K, 1, SEED_BASE + 51).ravel() + 0.5)
     mask = (uniform_block(n, 1, SEED_BASE + 52).ravel() >= 0.0).astype(np.float64)

@@ -22,7 +22,7 @@ from oracle import operators as ops  # noqa: E402
 
 
 def main(k=8, count=80):
-    dims, V = wl.config5_potential()
+    dims, V = wl.ham64_potential()
     lam = np.sort(sla.eigsh(ops.hamiltonian(dims, 1.0, V), k=count, which="SA", tol=1e-10)[0])
     best = None
     for i in range(1, count - k - 1):
