@@ -27,7 +27,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // output 2 in row order.  Returns false for t past the last tile.  Numbering
 // only the tiles that exist keeps the idle lanes of a warp at the end of the
 // list, so fewer warps issue when m < 64.
-__device__ __forceinline__ bool gram_tile(int t, int T, int& g, int& ti, int& tj) {
+__host__ __device__ __forceinline__ bool gram_tile(int t, int T, int& g, int& ti, int& tj) {
     const int nt0 = T * (T + 1) / 2, nt1 = T * T;
     g = 0; ti = 0; tj = 0;
     if (t < nt0) {
