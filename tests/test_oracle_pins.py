@@ -679,3 +679,37 @@ def test_q1_3d_generalized_algorithm3_matches_dense():
     assert np.allclose(np.sort(r.eigvals), np.sort(ref), rtol=1e-9)
     X = r.eigvecs
     assert np.abs(X.T @ (B @ X) - np.eye(k)).max() <= 1e-10
+
+
+# ---------------------------------------------------------------- precision of T
+
+def _round_to_bf16(x):
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16          # to nearest, ties to even
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _best_residual_with_rounded_T(rounding, maxit):
+    w = wl.lap3d_small(16, levels=3, k=4, gap_index=40)
+    A, _ = operators.model_operator(w)
+    T0 = avmg.AVMG(w.dims, w.h, w.sigma, w.mg_levels, w.mg_nu)
+    hist = []
+    try:
+        plhr.bplhr(A, None, lambda R: rounding(T0(R)), w.sigma, w.k, w.v0(), tol=1e-10, maxit=maxit,
+                   callback=lambda rec: hist.append(np.sort(rec["rel"])[w.k - 1]))
+    except np.linalg.LinAlgError:          # G_L no longer positive definite: the iteration stops
+        pass
+    return min(hist)
+
+
+def test_rounded_preconditioner_limits_the_attainable_residual():
+    """T-harmonic PLHR assumes one fixed symmetric positive definite T.  With
+    the V-cycle's output rounded to FP32 the k-th relative residual of the
+    16^3 AV-MG case gets to ~1e-7 and no further; rounded to BF16 it stays
+    above 1e-3 (the reason the preconditioner is not stored in BF16).  In
+    FP64 it converges."""
+    assert _best_residual_with_rounded_T(lambda x: x, 80) <= 1e-10
+    r32 = _best_residual_with_rounded_T(lambda x: x.astype(np.float32).astype(np.float64), 80)
+    assert 1e-9 < r32 < 1e-5
+    assert _best_residual_with_rounded_T(_round_to_bf16, 80) > 1e-3
