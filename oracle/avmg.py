@@ -33,10 +33,14 @@ parameters to its reference [Ve.Kn:13]; the readings taken here are:
 * the garbled "|L_l - I_l|^{-1}" of the algorithm's output line is read as
   |L_l - sigma I_l|^{-1}.
 
-Pins (tests/test_oracle_pins.py): one level is exactly |L - sigma I|^{-1} on
-the analytic modes; the spectrum of p_2; the transfer identities; a two-grid
-cycle equals its closed algebraic form; the cycle is symmetric positive
-definite.  Parity unpinned with respect to the paper's own multigrid: the
+Pins (tests/test_oracle_pins.py, tests/test_oracle_pins_transfer_pairs.py):
+one level is exactly |L - sigma I|^{-1} on the analytic modes; the spectrum of
+p_2; the transfer identities of both transfers (the trilinear weights against
+a brute-force construction from the cell centres, reproduction of linear
+fields, R 1 = 1 away from the walls); the fine-spectrum coarsest operator's
+eigenpairs against LAPACK on independently built matrices; a two-grid cycle
+equals its closed algebraic form for both option pairs; the cycle is
+symmetric positive definite for both option pairs.  Parity unpinned with respect to the paper's own multigrid: the
 parameter readings above replace a reference that is not available, so no
 printed number of the paper checks them.
 """

@@ -349,6 +349,7 @@ def bplhr(A, B, T, sigma, k, V0, tol=1e-8, maxit=1000, real=None, s_vectors=True
             Yp, tags, _ = select_real(xi, Y, kp)
         else:
             Yp, tags, _ = select_complex(xi, Y, kp)
+        rec["tags"] = [t[0] for t in tags]
         nv = sizes[0]
         Yv, Yr = Yp[:nv], Yp[nv:]
         P = Zh[:, nv:] @ Yr
