@@ -46,22 +46,52 @@ typedef enum {
 } plhr_status;
 
 /* ------------------------------------------------------------------ operators
- * A model operator given by a stencil on a tensor grid with homogeneous
- * Dirichlet boundary conditions.  LAP5_2D / LAP7_3D are the negative
- * finite-difference Laplacians of Section 5.2 ("standard 5-point FD
- * discretization"; the 7-point 3D analogue):
- *     (L u)_i = scale * sum_axes (2 u_i - u_{i-e} - u_{i+e}) / h^2,
- * values outside the grid taken as zero. */
+ * A model operator given by a stencil on a tensor grid.
+ *   LAP5_2D / LAP7_3D: the negative finite-difference Laplacians of Section
+ *     5.2 ("standard 5-point FD discretization"; the 7-point 3D analogue):
+ *         (L u)_i = scale * sum_axes (2 u_i - u_{i-e} - u_{i+e}) / h^2,
+ *     values outside the grid zero (bc = DIRICHLET) or wrapped around
+ *     (bc = PERIODIC).
+ *   HAM7_BLOCH: the Bloch Hamiltonian H = -1/2 Lap_kappa + diag(V) of the
+ *     complex Hermitian problems of Section 5.3 on a periodic 3D grid at
+ *     crystal momentum kappa = bloch_k: the link from point j to j + e_d
+ *     carries the phase e^{i kappa_d h},
+ *         (H u)_j = 1/2 sum_d (2 u_j - e^{i kappa_d h} u_{j+e_d}
+ *                   - e^{-i kappa_d h} u_{j-e_d}) / h^2 + V_j u_j
+ *     (indices wrap; a plane wave e^{i theta j} has the kinetic eigenvalue
+ *     (1 - cos(theta + kappa h)) / h^2 per axis); field = V (device, n
+ *     doubles, caller-owned, kept alive while the operator is used); scale
+ *     and bc ignored.  Complex blocks: plhr_op_apply_c128; real blocks only
+ *     when kappa = 0.
+ *   Q1_STIFF27 / Q1_MASS27: the trilinear (Q1) finite-element stiffness of
+ *     -div(c grad u) and the mass matrix (Section 5.1's bilinear elements in
+ *     3D) on the unit cube with E = dims[a] + 1 elements per axis, h = 1/E,
+ *     homogeneous Dirichlet (the unknowns are the dims[0] x dims[1] x dims[2]
+ *     interior nodes, x fastest; dims need not be equal, h is taken from the
+ *     descriptor); 27-point stencils assembled from the element matrices
+ *     c_e (k (x) m (x) m + m (x) k (x) m + m (x) m (x) k) and m (x) m (x) m of
+ *     the 1D linear element (k = [[1, -1], [-1, 1]] / h, m = [[2, 1], [1, 2]]
+ *     h / 6).  field (STIFF only) = the element coefficients c_e (device,
+ *     (dims[0]+1)(dims[1]+1)(dims[2]+1) positive doubles, x fastest,
+ *     caller-owned) or NULL for c = 1; scale multiplies the matrix. */
 typedef enum {
     PLHR_STENCIL_LAP5_2D = 1,
-    PLHR_STENCIL_LAP7_3D = 2
+    PLHR_STENCIL_LAP7_3D = 2,
+    PLHR_STENCIL_HAM7_BLOCH = 3,
+    PLHR_STENCIL_Q1_STIFF27 = 4,
+    PLHR_STENCIL_Q1_MASS27 = 5
 } plhr_stencil_kind;
 
+typedef enum { PLHR_BC_DIRICHLET = 0, PLHR_BC_PERIODIC = 1 } plhr_bc;
+
 typedef struct {
-    int kind;          /* plhr_stencil_kind */
-    int64_t dims[3];   /* grid points per axis (x, y, z); dims[2] = 1 for 2D */
-    double h;          /* mesh width, > 0 */
-    double scale;      /* multiplier of the stencil, > 0 (1 for -Laplacian) */
+    int kind;            /* plhr_stencil_kind */
+    int64_t dims[3];     /* grid points (interior nodes) per axis (x, y, z); dims[2] = 1 for 2D */
+    double h;            /* mesh width, > 0 */
+    double scale;        /* multiplier of the stencil, > 0 (1 for -Laplacian) */
+    int bc;              /* plhr_bc (LAP kinds) */
+    double bloch_k[3];   /* HAM7_BLOCH: crystal momentum kappa */
+    const double* field; /* HAM7_BLOCH: potential V; Q1_STIFF27: element coefficients or NULL */
 } plhr_stencil_desc;
 
 typedef struct plhr_op plhr_op;
@@ -93,9 +123,21 @@ plhr_status plhr_op_csr(plhr_op** out, int64_t n, const int64_t* rowptr, const i
 int64_t plhr_op_size(const plhr_op* op);
 void plhr_op_destroy(plhr_op* op);
 
-/* Y = op X for an n x ncols block (ncols >= 0).  X and Y must not overlap. */
+/* Y = op X for an n x ncols block (ncols >= 0).  X and Y must not overlap.
+ * PLHR_EINVAL for a Bloch operator with kappa != 0 (complex). */
 plhr_status plhr_op_apply(const plhr_op* op, int ncols, const double* X, int64_t ldx,
                           double* Y, int64_t ldy, void* stream);
+/* Y = op X for complex blocks: element (i, j) is the pair (re, im) of doubles
+ * at X[2 (i * ldx + j)], X[2 (i * ldx + j) + 1] (complex128 row-major, ld in
+ * complex elements).  Any stencil operator (a real one acts on the real and
+ * imaginary parts alike); not CSR. */
+plhr_status plhr_op_apply_c128(const plhr_op* op, int ncols, const double* X, int64_t ldx,
+                               double* Y, int64_t ldy, void* stream);
+/* AX = A X and BX = B X in one pass over X, for the Q1 pair (A Q1_STIFF27,
+ * B Q1_MASS27 on the same mesh); any other pair of operators of equal size is
+ * applied one after the other.  Blocks as for plhr_op_apply. */
+plhr_status plhr_op_apply_pair(const plhr_op* A, const plhr_op* B, int ncols, const double* X, int64_t ldx,
+                               double* AX, int64_t ldax, double* BX, int64_t ldbx, void* stream);
 
 /* ------------------------------------------------------------- preconditioner
  * T ~ |L - sigma I|^{-1}: the absolute-value multigrid V-cycle of Appendix A,
@@ -214,6 +256,10 @@ typedef struct {
                                   (T = I in the Petrov-Galerkin condition, Section 5.1's
                                   comparison).  extraction 1 and s_vectors 0 (the trial space
                                   [V W P] of the ablation in Section 5.1) run in PLHR_PRECISION_F64 */
+    int tensor_cores;          /* PLHR_PRECISION_MIXED: 1 (default) forms the Grams of the FP32
+                                  phase on the tensor cores (split-BF16 slices, FP32 accumulation,
+                                  PLHR_GRAM_F32_TC of plhr_gram); 0 on the FP32 pipes
+                                  (PLHR_GRAM_F32) */
 } plhr_options;
 
 typedef struct {
@@ -334,6 +380,36 @@ plhr_status plhr_tharm_extract_noalloc(int m, int kp, int nv, const double* Gzz,
                                        const double* Gqz, const double* colscale, double* Cp, double* Cvv,
                                        int* tags, int* partner, double* xi, int* status, void* stream);
 
+/* ------------------------------------------------------- projected Grams (device)
+ * The Gram pass of the solver on caller blocks, in one of its arithmetic
+ * forms: with the trial basis Z = [Z_0 .. Z_{nb-1}] (nb <= 4 blocks of
+ * ncols[b] columns, m = sum ncols in 1..64), its image AZ (same block shapes)
+ * and, when Q is non-NULL, its T-harmonic image Q (Q NULL: Q = U), all columns
+ * scaled by colscale (device, m doubles, D = diag(colscale)),
+ *     out[0 .. m^2)        = (Z D)^T (Z D)
+ *     out[m^2 .. 2 m^2)    = (U D)^T (Q D),   U = AZ - sigma Z
+ *     out[2 m^2 .. 3 m^2)  = (Q D)^T (Z D)
+ * (row-major m x m, device, FP64): the Grams of Eq. THarm_evp for B = I
+ * (G_L = U^T T U = U^T Q, G_R = (T U)^T Z), Algorithm 2 steps 6-7.  Block b
+ * has n rows, element (i, j) at Z[b][i * ldz[b] + j] (host arrays of device
+ * pointers and leading dimensions).  Forms:
+ *   PLHR_GRAM_F64     FP64 blocks, FP64 products and sums;
+ *   PLHR_GRAM_F32     FP32 blocks, FP32 products on the FP32 pipes, sums
+ *                     folded into double-FP32 every 32 rows;
+ *   PLHR_GRAM_DW      FP64 blocks, double-word (hi + lo FP32) arithmetic;
+ *   PLHR_GRAM_F32_TC  FP32 blocks on the tensor cores (tcgen05): each value
+ *                     split into three BF16 slices, the six slice products of
+ *                     order <= 2 accumulated in FP32 in tensor memory, folded
+ *                     into double-FP32 every 128 rows (the form the
+ *                     mixed-precision solve uses).
+ * Allocates a partial-sum buffer (max(2 x SMs, 152) x 3 m^2 doubles) on the
+ * stream, synchronises the stream before returning.  PLHR_EINVAL for bad
+ * arguments, PLHR_ECUDA on a CUDA error or a timed-out tensor-core wait. */
+enum { PLHR_GRAM_F64 = 0, PLHR_GRAM_F32 = 1, PLHR_GRAM_DW = 2, PLHR_GRAM_F32_TC = 3 };
+plhr_status plhr_gram(int form, int64_t n, int nb, const int* ncols, const void* const* Z, const int64_t* ldz,
+                      const void* const* AZ, const int64_t* ldaz, const void* const* Q, const int64_t* ldq,
+                      double sigma, const double* colscale, double* out, void* stream);
+
 /* ---------------------------------------------------------------- utilities */
 const char* plhr_status_string(plhr_status s);
 /* Number of CUDA kernels the library has launched in this process. */
@@ -356,6 +432,17 @@ void plhr_profile_read(double* ms, long long* calls, int reset);
  * U^T Q, Q^T Z for an n x m trial basis); update phases: flops 2 n m k' per
  * updated family; dense: 0. */
 void plhr_profile_work(double* work);
+/* bytes[9]: algorithmic HBM bytes accumulated per phase since the last reset
+ * of plhr_profile_read, counting every operand block read once and every
+ * result block written once per call (the unit of the roofline of these
+ * bandwidth-bound passes): stencil products (1 + outputs) x element size per
+ * grid point x column; AV-MG V-cycles 14.25 passes per smoothing level (the
+ * fused first two sweeps 2, residual 3, restriction 1 1/8, prolongation with
+ * correction 2 1/8, two post-sweeps 6) summed over the levels above the
+ * coarsest; Grams the Z, AZ (, BZ) and Q families once (3 n m elements);
+ * updates the m input columns once and the V and P outputs once per updated
+ * family; residual pass V, AV read and R written; dense: 0. */
+void plhr_profile_bytes(double* bytes);
 /* Text of the last error recorded on the calling thread ("" if none). */
 const char* plhr_last_error(void);
 

@@ -23,13 +23,16 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libplhr.so")
 
 PLHR_OK, PLHR_ENOTCONV, PLHR_EINVAL, PLHR_EBREAKDOWN, PLHR_ENAN, PLHR_ENOMEM, PLHR_ECUDA = range(7)
-LAP5_2D, LAP7_3D = 1, 2
+LAP5_2D, LAP7_3D, HAM7_BLOCH, Q1_STIFF27, Q1_MASS27 = 1, 2, 3, 4, 5
+BC_DIRICHLET, BC_PERIODIC = 0, 1
 PRECISION_F64, PRECISION_MIXED = 0, 1
+GRAM_F64, GRAM_F32, GRAM_DW, GRAM_F32_TC = 0, 1, 2, 3
 
 
 class StencilDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("dims", ctypes.c_int64 * 3), ("h", ctypes.c_double),
-                ("scale", ctypes.c_double)]
+                ("scale", ctypes.c_double), ("bc", ctypes.c_int), ("bloch_k", ctypes.c_double * 3),
+                ("field", ctypes.c_void_p)]
 
 
 class MGOpts(ctypes.Structure):
@@ -42,7 +45,7 @@ class Options(ctypes.Structure):
                 ("s_vectors", ctypes.c_int), ("soft_lock", ctypes.c_int),
                 ("v_init", ctypes.c_void_p), ("ld_init", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("history", ctypes.c_void_p), ("history_cap", ctypes.c_int), ("guard", ctypes.c_int),
-                ("switch_tol", ctypes.c_double), ("extraction", ctypes.c_int)]
+                ("switch_tol", ctypes.c_double), ("extraction", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -76,6 +79,11 @@ _SIGS = {
     "plhr_op_destroy": (None, [ctypes.c_void_p]),
     "plhr_op_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "plhr_op_apply_c128": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "plhr_op_apply_pair": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_void_p]),
     "plhr_mg_opts_default": (None, [ctypes.POINTER(MGOpts)]),
     "plhr_prec_avmg": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_double,
                                       ctypes.POINTER(MGOpts)]),
@@ -83,6 +91,10 @@ _SIGS = {
     "plhr_prec_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "plhr_profile_work": (None, [ctypes.c_void_p]),
+    "plhr_profile_bytes": (None, [ctypes.c_void_p]),
+    "plhr_gram": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "plhr_prec_apply_dw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "plhr_prec_apply_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
@@ -160,22 +172,62 @@ class Operator:
         self.scale = scale
 
     @classmethod
-    def laplacian(cls, dims, h, scale=1.0):
+    def _stencil(cls, kind, dims, h, scale=1.0, bc=BC_DIRICHLET, bloch_k=(0.0, 0.0, 0.0), field=None):
         lib = load_library()
         d = StencilDesc()
-        if len(dims) == 2:
-            d.kind = LAP5_2D
-            d.dims[:] = [dims[0], dims[1], 1]
-        elif len(dims) == 3:
-            d.kind = LAP7_3D
-            d.dims[:] = list(dims)
-        else:
-            raise ValueError("dims must have 2 or 3 entries")
+        d.kind = kind
+        d.dims[:] = list(dims) + [1] * (3 - len(dims))
         d.h = h
         d.scale = scale
+        d.bc = bc
+        d.bloch_k[:] = [float(v) for v in bloch_k]
+        d.field = field.data_ptr() if field is not None else None
         out = ctypes.c_void_p()
         _check(lib.plhr_op_stencil(ctypes.byref(out), ctypes.byref(d)), "plhr_op_stencil")
-        return cls(out, dims, h, scale)
+        op = cls(out, tuple(dims), h, scale)
+        op._field = field
+        return op
+
+    @classmethod
+    def laplacian(cls, dims, h, scale=1.0, periodic=False):
+        """Negative FD Laplacian (5-point 2D, 7-point 3D), Dirichlet or periodic."""
+        if len(dims) not in (2, 3):
+            raise ValueError("dims must have 2 or 3 entries")
+        return cls._stencil(LAP5_2D if len(dims) == 2 else LAP7_3D, dims, h, scale,
+                            BC_PERIODIC if periodic else BC_DIRICHLET)
+
+    @staticmethod
+    def _device_field(v, count, name):
+        import torch
+        if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == torch.float64):
+            raise ValueError("%s must be a float64 CUDA tensor" % name)
+        v = v.contiguous().reshape(-1)
+        if v.numel() != count:
+            raise ValueError("%s has %d values, %d expected" % (name, v.numel(), count))
+        return v
+
+    @classmethod
+    def q1_stiffness(cls, elems, coeff=None, scale=1.0):
+        """Trilinear FE stiffness of -div(c grad u) on the unit cube with elems =
+        (Ex, Ey, Ez) elements per axis (an int: the same on every axis), h =
+        1/Ex, interior nodes x fastest; coeff: float64 CUDA tensor of the element
+        coefficients (x fastest) or None (c = 1)."""
+        E = (elems,) * 3 if isinstance(elems, int) else tuple(elems)
+        f = None if coeff is None else cls._device_field(coeff, int(np.prod(E)), "coeff")
+        return cls._stencil(Q1_STIFF27, tuple(e - 1 for e in E), 1.0 / E[0], scale, field=f)
+
+    @classmethod
+    def q1_mass(cls, elems, scale=1.0):
+        """Trilinear FE mass matrix on the mesh of q1_stiffness(elems)."""
+        E = (elems,) * 3 if isinstance(elems, int) else tuple(elems)
+        return cls._stencil(Q1_MASS27, tuple(e - 1 for e in E), 1.0 / E[0], scale)
+
+    @classmethod
+    def bloch(cls, dims, h, potential, kappa):
+        """Bloch Hamiltonian -1/2 Lap_kappa + diag(V) on a periodic 3D grid
+        (complex for kappa != 0: apply_c128)."""
+        f = cls._device_field(potential, int(np.prod(dims)), "potential")
+        return cls._stencil(HAM7_BLOCH, dims, h, 0.5, BC_PERIODIC, kappa, f)
 
     @classmethod
     def csr(cls, A):
@@ -227,6 +279,31 @@ class Operator:
                                             ctypes.c_void_p(out.data_ptr()), out.stride(0), _stream_ptr(stream)),
                "plhr_op_apply")
         return out
+
+    def apply_c128(self, X, out=None, stream=None):
+        """Y = op X for a complex128 CUDA block (n x ncols, row-major)."""
+        import torch
+        if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.complex128 and X.dim() == 2
+                and X.shape[0] == self.n and X.stride(1) == 1):
+            raise ValueError("X must be a row-major complex128 CUDA block with n rows")
+        if out is None:
+            out = torch.empty_like(X)
+        _check(load_library().plhr_op_apply_c128(self._h, X.shape[1], ctypes.c_void_p(X.data_ptr()), X.stride(0),
+                                                 ctypes.c_void_p(out.data_ptr()), out.stride(0),
+                                                 _stream_ptr(stream)), "plhr_op_apply_c128")
+        return out
+
+    def apply_pair(self, B, X, stream=None):
+        """(A X, B X) in one pass for the Q1 stiffness/mass pair of a mesh."""
+        import torch
+        _check_block(X, self.n, "X")
+        AX = torch.empty_like(X)
+        BX = torch.empty_like(X)
+        _check(load_library().plhr_op_apply_pair(self._h, B._h, X.shape[1], ctypes.c_void_p(X.data_ptr()),
+                                                 X.stride(0), ctypes.c_void_p(AX.data_ptr()), AX.stride(0),
+                                                 ctypes.c_void_p(BX.data_ptr()), BX.stride(0), _stream_ptr(stream)),
+               "plhr_op_apply_pair")
+        return AX, BX
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -444,16 +521,51 @@ def profile_read(reset: bool = False) -> dict:
     ms = (ctypes.c_double * len(PHASES))()
     calls = (ctypes.c_longlong * len(PHASES))()
     work = (ctypes.c_double * len(PHASES))()
+    nbytes = (ctypes.c_double * len(PHASES))()
     lib = load_library()
     lib.plhr_profile_work(work)
+    lib.plhr_profile_bytes(nbytes)
     lib.plhr_profile_read(ms, calls, 1 if reset else 0)
-    return {name: {"ms": ms[i], "calls": calls[i], "work": work[i]} for i, name in enumerate(PHASES)}
+    return {name: {"ms": ms[i], "calls": calls[i], "work": work[i], "bytes": nbytes[i]}
+            for i, name in enumerate(PHASES)}
+
+
+def gram(form, Z, AZ, Q=None, sigma=0.0, colscale=None, stream=None):
+    """The three projected Grams [Z^T Z, U^T Q, Q^T Z] (U = AZ - sigma Z,
+    columns scaled by colscale) in one of the library's arithmetic forms
+    (GRAM_F64 / GRAM_DW on float64 blocks, GRAM_F32 / GRAM_F32_TC on float32
+    blocks).  Z, AZ, Q: a CUDA tensor (n x m) or a list of up to 4 column
+    blocks.  Returns a (3, m, m) float64 CUDA tensor."""
+    import torch
+    lib = load_library()
+    zs = list(Z) if isinstance(Z, (list, tuple)) else [Z]
+    az = list(AZ) if isinstance(AZ, (list, tuple)) else [AZ]
+    qs = None if Q is None else (list(Q) if isinstance(Q, (list, tuple)) else [Q])
+    nb = len(zs)
+    dt = torch.float64 if form in (GRAM_F64, GRAM_DW) else torch.float32
+    n = zs[0].shape[0]
+    for X in zs + az + (qs or []):
+        if not X.is_cuda or X.dtype != dt or X.dim() != 2 or X.shape[0] != n or X.stride(1) != 1:
+            raise ValueError("gram blocks must be row-major %s CUDA tensors with n rows" % dt)
+    m = sum(X.shape[1] for X in zs)
+    dev = zs[0].device
+    if colscale is None:
+        colscale = torch.ones(m, dtype=torch.float64, device=dev)
+    out = torch.empty((3, m, m), dtype=torch.float64, device=dev)
+    ncols = (ctypes.c_int * nb)(*[X.shape[1] for X in zs])
+    P = lambda L: (ctypes.c_void_p * nb)(*[X.data_ptr() for X in L])
+    LD = lambda L: (ctypes.c_int64 * nb)(*[X.stride(0) for X in L])
+    _check(lib.plhr_gram(form, n, nb, ncols, P(zs), LD(zs), P(az), LD(az), P(qs) if qs else None,
+                         LD(qs) if qs else None, sigma, ctypes.c_void_p(colscale.data_ptr()),
+                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "plhr_gram")
+    return out
 
 
 def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float = 1e-8, maxit: int = 1000,
           v_init=None, seed: int = 20140801, history: bool = False, precision: int = PRECISION_F64,
           stream=None, raise_on_notconv: bool = False, guard: int = 1, switch_tol: float = 1e-5,
-          extraction: str = "tharm", s_vectors: bool = True, B: Operator | None = None):
+          extraction: str = "tharm", s_vectors: bool = True, B: Operator | None = None,
+          tensor_cores: bool = True):
     """k eigenpairs of A v = lambda v nearest sigma with k + guard block
     columns (B: the generalized problem A v = lambda B v, FP64 form).
     extraction "tharm" (T-harmonic, default) or "harm" (harmonic:
@@ -475,6 +587,7 @@ def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float =
         raise ValueError("extraction must be 'tharm' or 'harm'")
     opt.extraction = 0 if extraction == "tharm" else 1
     opt.s_vectors = 1 if s_vectors else 0
+    opt.tensor_cores = 1 if tensor_cores else 0
     if v_init is not None:
         _check_block(v_init, n, "v_init")
         if v_init.shape[1] < kp:

@@ -59,26 +59,60 @@ const char* plhr_status_string(plhr_status s) {
 plhr_status plhr_op_stencil(plhr_op** out, const plhr_stencil_desc* d) {
     clear_error();
     if (!out || !d) { set_error("plhr_op_stencil: null argument"); return PLHR_EINVAL; }
-    if (d->kind != PLHR_STENCIL_LAP5_2D && d->kind != PLHR_STENCIL_LAP7_3D) {
-        set_error("plhr_op_stencil: unknown kind %d", d->kind);
+    const int kind = d->kind;
+    if (kind < PLHR_STENCIL_LAP5_2D || kind > PLHR_STENCIL_Q1_MASS27) {
+        set_error("plhr_op_stencil: unknown kind %d", kind);
         return PLHR_EINVAL;
     }
-    if (d->dims[0] < 1 || d->dims[1] < 1 || d->dims[2] < 1 || !(d->h > 0) || !(d->scale > 0)) {
-        set_error("plhr_op_stencil: bad dims/h/scale");
+    if (d->dims[0] < 1 || d->dims[1] < 1 || d->dims[2] < 1 || !(d->h > 0) || !std::isfinite(d->h)) {
+        set_error("plhr_op_stencil: bad dims/h");
         return PLHR_EINVAL;
     }
-    if (d->kind == PLHR_STENCIL_LAP5_2D && d->dims[2] != 1) {
+    if (kind != PLHR_STENCIL_HAM7_BLOCH && !(d->scale > 0 && std::isfinite(d->scale))) {
+        set_error("plhr_op_stencil: scale must be positive and finite");
+        return PLHR_EINVAL;
+    }
+    if (kind == PLHR_STENCIL_LAP5_2D && d->dims[2] != 1) {
         set_error("plhr_op_stencil: 2D stencil needs dims[2] == 1");
         return PLHR_EINVAL;
     }
+    if ((kind == PLHR_STENCIL_LAP5_2D || kind == PLHR_STENCIL_LAP7_3D) && d->bc != PLHR_BC_DIRICHLET &&
+        d->bc != PLHR_BC_PERIODIC) {
+        set_error("plhr_op_stencil: unknown boundary condition %d", d->bc);
+        return PLHR_EINVAL;
+    }
+    if (kind == PLHR_STENCIL_HAM7_BLOCH) {
+        if (!d->field) { set_error("plhr_op_stencil: HAM7_BLOCH needs the potential (field)"); return PLHR_EINVAL; }
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(d->bloch_k[a])) { set_error("plhr_op_stencil: bloch_k not finite"); return PLHR_EINVAL; }
+    }
     plhr_op* op = new plhr_op;
-    op->kind = d->kind;
-    op->g.d = d->kind == PLHR_STENCIL_LAP7_3D ? 3 : 2;
+    op->kind = kind;
+    op->g.d = kind == PLHR_STENCIL_LAP5_2D ? 2 : 3;
     op->g.nx = d->dims[0];
     op->g.ny = d->dims[1];
     op->g.nz = d->dims[2];
     op->g.h = d->h;
     op->g.scale = d->scale;
+    switch (kind) {
+        case PLHR_STENCIL_LAP5_2D:
+        case PLHR_STENCIL_LAP7_3D:
+            op->g.periodic = d->bc == PLHR_BC_PERIODIC;
+            break;
+        case PLHR_STENCIL_HAM7_BLOCH:
+            op->g.scale = 0.5;
+            op->g.periodic = 1;
+            op->g.pot = d->field;
+            for (int a = 0; a < 3; ++a) op->g.kappa[a] = d->bloch_k[a];
+            break;
+        case PLHR_STENCIL_Q1_STIFF27:
+            op->g.q1 = 1;
+            op->g.cell = d->field;
+            break;
+        case PLHR_STENCIL_Q1_MASS27:
+            op->g.q1 = 2;
+            break;
+    }
     *out = op;
     return PLHR_OK;
 }
@@ -128,8 +162,58 @@ plhr_status plhr_op_apply(const plhr_op* op, int ncols, const double* X, int64_t
         set_error("plhr_op_apply: invalid argument");
         return PLHR_EINVAL;
     }
+    if (op->g.complex_op()) {
+        set_error("plhr_op_apply: a Bloch operator with kappa != 0 is complex (use plhr_op_apply_c128)");
+        return PLHR_EINVAL;
+    }
     if (ncols == 0) return PLHR_OK;
     PLHR_TRY_CUDA(lap_axpby(op->g, ncols, X, ldx, Y, ldy, 1.0, 0.0, (cudaStream_t)stream));
+    return PLHR_OK;
+}
+
+plhr_status plhr_op_apply_c128(const plhr_op* op, int ncols, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                               void* stream) {
+    clear_error();
+    if (!op || ncols < 0 || (ncols > 0 && (!X || !Y)) || ldx < ncols || ldy < ncols) {
+        set_error("plhr_op_apply_c128: invalid argument");
+        return PLHR_EINVAL;
+    }
+    if (op->g.csr) {
+        set_error("plhr_op_apply_c128: stencil operators only");
+        return PLHR_EINVAL;
+    }
+    if (ncols == 0) return PLHR_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (op->g.complex_op()) {
+        PLHR_TRY_CUDA(bloch_apply(op->g, ncols, X, ldx, Y, ldy, s));
+    } else {
+        // a real operator acts on the real and imaginary parts alike: the
+        // interleaved block is a real block of 2 ncols columns
+        PLHR_TRY_CUDA(lap_axpby(op->g, 2 * ncols, X, 2 * ldx, Y, 2 * ldy, 1.0, 0.0, s));
+    }
+    return PLHR_OK;
+}
+
+plhr_status plhr_op_apply_pair(const plhr_op* A, const plhr_op* B, int ncols, const double* X, int64_t ldx,
+                               double* AX, int64_t ldax, double* BX, int64_t ldbx, void* stream) {
+    clear_error();
+    if (!A || !B || ncols < 0 || (ncols > 0 && (!X || !AX || !BX)) || ldx < ncols || ldax < ncols ||
+        ldbx < ncols || A->g.n() != B->g.n()) {
+        set_error("plhr_op_apply_pair: invalid argument");
+        return PLHR_EINVAL;
+    }
+    if (A->g.complex_op() || B->g.complex_op()) {
+        set_error("plhr_op_apply_pair: real operators only");
+        return PLHR_EINVAL;
+    }
+    if (ncols == 0) return PLHR_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (q1_same_mesh(A->g, B->g)) {
+        PLHR_TRY_CUDA(q1_pair(A->g, B->g, ncols, X, ldx, AX, ldax, BX, ldbx, s));
+    } else {
+        PLHR_TRY_CUDA(lap_axpby(A->g, ncols, X, ldx, AX, ldax, 1.0, 0.0, s));
+        PLHR_TRY_CUDA(lap_axpby(B->g, ncols, X, ldx, BX, ldbx, 1.0, 0.0, s));
+    }
     return PLHR_OK;
 }
 

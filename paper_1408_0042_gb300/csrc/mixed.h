@@ -23,6 +23,15 @@ int gram_mx_blocks();
 cudaError_t multi_gram_mx(int64_t n, int nb, const BlkMx* Z, const BlkMx* AZ, const BlkMx* Q, double sigma,
                           const double* colscale, double* partial, double* out, cudaStream_t s);
 
+// The same three Grams on the tensor cores (gram_tc.cu): FP32 families only,
+// each value split into three BF16 slices, FP32 accumulation in tensor
+// memory folded into double-FP32 every 128 rows.  partial: gram_tc_blocks()
+// * 3 m^2 doubles; *err (device) is set to 1 when a completion wait times
+// out (the outputs are then invalid).  m <= 64.
+int gram_tc_blocks();
+cudaError_t multi_gram_tc(int64_t n, int nb, const BlkMx* Z, const BlkMx* AZ, const BlkMx* Q, double sigma,
+                          const double* colscale, double* partial, double* out, int* err, cudaStream_t s);
+
 // Pout = F C_P, Vout = F_0 C_VV + F C_P (types by the flags; in place allowed).
 cudaError_t block_update_mx(int64_t n, int nb, const BlkMx* F, int kp, const double* Cp, const double* Cvv,
                             void* Vout, int vo64, int64_t ldvo, void* Pout, int po64, int64_t ldpo, cudaStream_t s);

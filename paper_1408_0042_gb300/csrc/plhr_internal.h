@@ -56,9 +56,14 @@ struct Grid {
     int periodic = 0;     // 1: periodic wrap instead of zero Dirichlet values
     const double* pot = nullptr;   // optional diagonal term (device, n values): A = scale L + diag(pot)
     const CsrData* csr = nullptr;  // general sparse operator instead of the stencil
+    int q1 = 0;                    // 1: Q1 stiffness, 2: Q1 mass (27-point finite-element stencils)
+    const double* cell = nullptr;  // Q1 stiffness: element coefficients ((nx+1)(ny+1)(nz+1)) or null (1)
+    double kappa[3] = {0.0, 0.0, 0.0};   // Bloch phases e^{i kappa_d h} on the links (periodic Hamiltonian)
     int64_t n() const { return nx * ny * nz; }
     double inv_h2() const { return scale / (h * h); }
-    bool plain() const { return !periodic && pot == nullptr && csr == nullptr; }   // the Dirichlet Laplacian
+    bool complex_op() const { return kappa[0] != 0.0 || kappa[1] != 0.0 || kappa[2] != 0.0; }
+    // the Dirichlet finite-difference Laplacian
+    bool plain() const { return !periodic && pot == nullptr && csr == nullptr && q1 == 0 && !complex_op(); }
 };
 
 // A block of row-major vectors: element (i, j) at p[i * ld + j].
@@ -85,8 +90,9 @@ void count_launches(int n);
 enum Phase { PH_STENCIL = 0, PH_VCYCLE = 1, PH_GRAM = 2, PH_UPDATE = 3, PH_DENSE = 4, PH_OTHER = 5,
              PH_VCYCLE32 = 6, PH_GRAM32 = 7, PH_UPDATE32 = 8, PH_COUNT = 9 };
 struct PhaseScope {
-    // work: algorithmic work of the call, in the phase's unit (see plhr_profile_work)
-    PhaseScope(int phase, cudaStream_t s, double work = 0.0);
+    // work: algorithmic work of the call, in the phase's unit (see plhr_profile_work);
+    // bytes: algorithmic HBM bytes of the call (each operand read or written once)
+    PhaseScope(int phase, cudaStream_t s, double work = 0.0, double bytes = 0.0);
     ~PhaseScope();
     int phase;
     cudaStream_t s;
@@ -110,6 +116,20 @@ cudaError_t csr_axpby(const CsrData& A, int nc, const double* x, int64_t ldx, do
 cudaError_t csr_apply_shifts(const CsrData& A, int nc, const double* x, int64_t ldx, double* ax, int64_t ldax,
                              double* o1, int64_t ld1, const double* lam, double* o2, int64_t ld2, double sig,
                              cudaStream_t s);
+
+// Q1 finite-element stencils (q1.cu): a single operator (stiffness or mass by
+// g.q1) as y = alpha op x + beta x or with the shifted outputs; both
+// operators of a mesh in one pass (ax = A x, bx = B x)
+cudaError_t q1_axpby(const Grid& g, int nc, const double* x, int64_t ldx, double* y, int64_t ldy, double alpha,
+                     double beta, cudaStream_t s);
+cudaError_t q1_apply_shifts(const Grid& g, int nc, const double* x, int64_t ldx, double* ax, int64_t ldax,
+                            double* o1, int64_t ld1, const double* lam, double* o2, int64_t ld2, double sig,
+                            cudaStream_t s);
+cudaError_t q1_pair(const Grid& A, const Grid& B, int nc, const double* x, int64_t ldx, double* ax, int64_t ldax,
+                    double* bx, int64_t ldbx, cudaStream_t s);
+bool q1_same_mesh(const Grid& A, const Grid& B);
+// Bloch Hamiltonian on complex128 blocks (ld in complex elements)
+cudaError_t bloch_apply(const Grid& g, int nc, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t s);
 
 // ---------------------------------------------------------------- multigrid
 struct MGLevel {

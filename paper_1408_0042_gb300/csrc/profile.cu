@@ -18,15 +18,17 @@ std::vector<Pending> g_pending;
 double g_ms[PH_COUNT] = {0};
 long long g_calls[PH_COUNT] = {0};
 double g_work[PH_COUNT] = {0};
+double g_bytes[PH_COUNT] = {0};
 }  // namespace
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-PhaseScope::PhaseScope(int ph, cudaStream_t st, double work) : phase(ph), s(st) {
+PhaseScope::PhaseScope(int ph, cudaStream_t st, double work, double bytes) : phase(ph), s(st) {
     if (!g_prof_on.load()) return;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         g_work[ph] += work;
+        g_bytes[ph] += bytes;
     }
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) { a = b = nullptr; return; }
     cudaEventRecord(a, s);
@@ -70,7 +72,7 @@ void plhr_profile_read(double* ms, long long* calls, int reset) {
     for (int i = 0; i < plhr::PH_COUNT; ++i) {
         if (ms) ms[i] = plhr::g_ms[i];
         if (calls) calls[i] = plhr::g_calls[i];
-        if (reset) { plhr::g_ms[i] = 0.0; plhr::g_calls[i] = 0; plhr::g_work[i] = 0.0; }
+        if (reset) { plhr::g_ms[i] = 0.0; plhr::g_calls[i] = 0; plhr::g_work[i] = 0.0; plhr::g_bytes[i] = 0.0; }
     }
 }
 
@@ -79,6 +81,13 @@ void plhr_profile_work(double* work) {
     std::lock_guard<std::mutex> lk(plhr::g_mu);
     for (int i = 0; i < plhr::PH_COUNT; ++i)
         if (work) work[i] = plhr::g_work[i];
+}
+
+void plhr_profile_bytes(double* bytes) {
+    plhr::profile_flush();
+    std::lock_guard<std::mutex> lk(plhr::g_mu);
+    for (int i = 0; i < plhr::PH_COUNT; ++i)
+        if (bytes) bytes[i] = plhr::g_bytes[i];
 }
 
 }  // extern "C"

@@ -58,6 +58,18 @@ struct HostStatus {
 // triangle), U^T Q and Q^T Z
 double gram_flops(int64_t n, int m) { return 2.0 * (double)n * (m * (m + 1) / 2.0 + 2.0 * m * m); }
 
+// Algorithmic HBM bytes of one preconditioner application on nc columns of
+// eb-byte elements: for AV-MG 14.25 passes per level above the coarsest (the
+// fused first two sweeps 2, residual 3, restriction 1 1/8, prolongation with
+// correction 2 1/8, two post-sweeps 6); any other T reads r and writes w.
+double prec_bytes(const plhr_prec* T, int64_t n, int nc, int eb) {
+    if (T->kind != PREC_AVMG) return 2.0 * (double)n * nc * eb;
+    double el = 0.0;
+    for (size_t l = 1; l < T->H.lev.size(); ++l) el += (double)T->H.lev[l].g.n();
+    if (T->H.lev.size() <= 1) el = (double)n;
+    return 14.25 * el * nc * eb;
+}
+
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -76,6 +88,7 @@ extern "C" void plhr_options_default(plhr_options* o) {
     o->guard = 1;
     o->switch_tol = 1e-5;
     o->extraction = 0;
+    o->tensor_cores = 1;
 }
 
 extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sigma, int k, plhr_prec* T, double tol,
@@ -88,6 +101,10 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     if (opt_in) opt = *opt_in;
     if (!A || !eigvals || !eigvecs || k < 1 || ldv < k || !(tol > 0) || !std::isfinite(sigma) || opt.maxit < 0) {
         set_error("plhr_solve: invalid argument");
+        return PLHR_EINVAL;
+    }
+    if (A->g.complex_op() || (B && B->g.complex_op())) {
+        set_error("plhr_solve: complex operators (Bloch kappa != 0) are not supported by the real solver");
         return PLHR_EINVAL;
     }
     if (B != nullptr && (B->g.n() != A->g.n() || opt.precision != PLHR_PRECISION_F64)) {
@@ -240,7 +257,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     int* order = ints + 64;
     int* tags = ints + 128;
     int* partner = ints + 192;
-    int* dstat = ints + 256;   // [conv, nact, nan, dense0, dense1, dense2, rr_ok]
+    int* dstat = ints + 256;   // [conv, nact, nan, dense0, dense1, dense2, rr_ok, tensor-core wait timeout]
     if (T) PLHR_TRY(prec_reserve(T, 2 * kp, 0));
 
     // colscale = 1 everywhere (the V part is overwritten every iteration)
@@ -258,7 +275,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
                                             cudaMemcpyDeviceToDevice, s));
             return PLHR_OK;
         }
-        PhaseScope ps(PH_VCYCLE, s, (double)n * nc);
+        PhaseScope ps(PH_VCYCLE, s, (double)n * nc, prec_bytes(T, n, nc, 8));
         if (dwf)   // FP64 phase of the mixed form: double-word V-cycle
             PLHR_TRY_CUDA(mg_vcycle_dw(T->H, nc, r, ldr, w, nc, T->work, s));
         else
@@ -269,7 +286,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     auto applyT32 = [&](int nc, const auto* r, int64_t ldr, float* w) -> plhr_status {
         // w (ld nc, FP32) = T r in the FP32 V-cycle
         if (nc == 0) return PLHR_OK;
-        PhaseScope ps(PH_VCYCLE32, s, (double)n * nc);
+        PhaseScope ps(PH_VCYCLE32, s, (double)n * nc, prec_bytes(T, n, nc, 4));
         PLHR_TRY_CUDA(mg_vcycle_f32(T->H, nc, r, ldr, w, T->work32, s));
         return PLHR_OK;
     };
@@ -282,10 +299,19 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             PLHR_TRY_CUDA(lap_apply_shifts(g, nc, X, ldx, AX, ldax, o1, ld1, lamv, o2, ld2, sigma, s));
             return PLHR_OK;
         }
-        PLHR_TRY_CUDA(lap_axpby(g, nc, X, ldx, AX, ldax, 1.0, 0.0, s));
-        PLHR_TRY_CUDA(lap_axpby(B->g, nc, X, ldx, BX, ldbx, 1.0, 0.0, s));
+        if (q1_same_mesh(g, B->g)) {   // both finite-element operators in one pass
+            PLHR_TRY_CUDA(q1_pair(g, B->g, nc, X, ldx, AX, ldax, BX, ldbx, s));
+        } else {
+            PLHR_TRY_CUDA(lap_axpby(g, nc, X, ldx, AX, ldax, 1.0, 0.0, s));
+            PLHR_TRY_CUDA(lap_axpby(B->g, nc, X, ldx, BX, ldbx, 1.0, 0.0, s));
+        }
         if (o1 || o2) PLHR_TRY_CUDA(shift_combine(n, nc, AX, ldax, BX, ldbx, lamv, o1, ld1, sigma, o2, ld2, s));
         return PLHR_OK;
+    };
+    // algorithmic bytes of prod on nc columns with `outs` shifted outputs
+    auto prod_bytes = [&](int nc, int outs) -> double {
+        const double passes = hasB ? 4.0 + (outs ? 2.0 + outs : 0.0) : 2.0 + outs;
+        return 8.0 * (double)n * nc * passes;
     };
     // dots = [v.Av (kp) | v.Bv (kp)] for the Rayleigh quotients and scales
     auto rq_dots = [&]() -> plhr_status {
@@ -315,6 +341,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         std::vector<int> zeros(64, 0), neg(64, -1);
         PLHR_TRY_CUDA(cudaMemcpyAsync(tags, zeros.data(), sizeof(int) * 64, cudaMemcpyHostToDevice, s));
         PLHR_TRY_CUDA(cudaMemcpyAsync(partner, neg.data(), sizeof(int) * 64, cudaMemcpyHostToDevice, s));
+        PLHR_TRY_CUDA(cudaMemsetAsync(dstat + 7, 0, sizeof(int), s));
         PLHR_TRY_CUDA(cudaStreamSynchronize(s));
     }
     PLHR_TRY_CUDA(dense_rq(kp, dots, tags, partner, lam, scale, s));
@@ -323,13 +350,15 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     // images of V and P under A: explicit stencil products after every update
     // (no recursion, so no drift), dots for the Rayleigh quotients of V
     auto refresh_images = [&]() -> plhr_status {
-        PhaseScope ps(PH_STENCIL, s, (double)n * (np ? 2 * kp : kp));
-        PLHR_TRY_CUDA(lap_axpby(g, kp, V, kp, AV, kp, 1.0, 0.0, s));
-        if (hasB) PLHR_TRY_CUDA(lap_axpby(B->g, kp, V, kp, BV, kp, 1.0, 0.0, s));
+        // V (and B V) and P: read the block, write its image
+        PhaseScope ps(PH_STENCIL, s, (double)n * (np ? 2 * kp : kp),
+                      (double)n * kp * 2.0 * (8.0 * (hasB ? 2 : 1) + (np ? (mx ? 4.0 : 8.0 * (hasB ? 2 : 1)) : 0.0)));
+        if (hasB) PLHR_TRY(prod(kp, V, kp, AV, kp, BV, kp, nullptr, 0, nullptr, nullptr, 0));
+        else PLHR_TRY_CUDA(lap_axpby(g, kp, V, kp, AV, kp, 1.0, 0.0, s));
         if (np) {
             if (mx) PLHR_TRY_CUDA(lap32_apply_shifts(g, kp, P32, kp, AP32, kp, nullptr, 0, nullptr, nullptr, 0, 0.0, s));
+            else if (hasB) PLHR_TRY(prod(kp, P, kp, AP, kp, BP, kp, nullptr, 0, nullptr, nullptr, 0));
             else PLHR_TRY_CUDA(lap_axpby(g, kp, P, kp, AP, kp, 1.0, 0.0, s));
-            if (hasB) PLHR_TRY_CUDA(lap_axpby(B->g, kp, P, kp, BP, kp, 1.0, 0.0, s));
         }
         PLHR_TRY(rq_dots());
         return PLHR_OK;
@@ -443,7 +472,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     for (it = 0; it <= opt.maxit; ++it) {
         // -------------------------------------------- residual, convergence (step 4 input)
         {
-            PhaseScope ps(PH_OTHER, s, (double)n * kp);
+            PhaseScope ps(PH_OTHER, s, (double)n * kp, 24.0 * (double)n * kp);
             PLHR_TRY_CUDA(residual_norms(n, kp, hasB ? BV : V, kp, AV, kp, lam, scale, R, kp, rpart, sums, s));
         }
         StatusArgs sa;
@@ -570,7 +599,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             else PLHR_TRY_CUDA(narrow_block(n, na, Ract, ldra, W32, na, s));
             float* X2in = T ? X2_32 : SQ32;
             {
-                PhaseScope ps(PH_STENCIL, s, (double)n * na);
+                PhaseScope ps(PH_STENCIL, s, (double)n * na, 4.0 * n * na * (T ? 4 : 3));
                 PLHR_TRY_CUDA(lap32_apply_shifts(g, na, W32, na, AW32, na, X2in, T ? 2 * na : na, lam_act,
                                                  T ? X2in + na : nullptr, 2 * na, sigma, s));
             }
@@ -579,7 +608,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             if (T) PLHR_TRY(applyT32(2 * na, (const float*)X2_32, 2 * na, SQ32));
             const float* QW32 = SQ32 + na;
             {
-                PhaseScope ps(PH_STENCIL, s, (double)n * na);
+                PhaseScope ps(PH_STENCIL, s, (double)n * na, 4.0 * n * na * (T ? 3 : 2));
                 PLHR_TRY_CUDA(lap32_apply_shifts(g, na, S32, lds, AS32, na, nullptr, 0, nullptr, T ? X3_32 : nullptr,
                                                  na, sigma, s));
             }
@@ -612,15 +641,25 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             da.colscale = colscale; da.work = dwork; da.Cp = Cp; da.Cvv = Cvv; da.tags = tags;
             da.tag_partner = partner; da.xi = xi; da.out_int = dstat + 3; da.clk = nullptr;
             {
-                PhaseScope ps(PH_GRAM32, s, gram_flops(n, m));
-                PLHR_TRY_CUDA(multi_gram_mx(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams, s));
+                PhaseScope ps(PH_GRAM32, s, gram_flops(n, m), 4.0 * n * m * (T ? 3 : 2));
+                if (opt.tensor_cores)
+                    PLHR_TRY_CUDA(multi_gram_tc(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams,
+                                                dstat + 7, s));
+                else
+                    PLHR_TRY_CUDA(multi_gram_mx(n, nb, zb, ab, T ? qb : nullptr, sigma, colscale, gpart, grams, s));
             }
             {
                 PhaseScope ps(PH_DENSE, s);
                 PLHR_TRY_CUDA(dense_extract(da, s));
             }
             PLHR_TRY_CUDA(cudaMemcpyAsync(hs->dense, dstat + 3, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+            PLHR_TRY_CUDA(cudaMemcpyAsync(&hs->pad, dstat + 7, sizeof(int), cudaMemcpyDeviceToHost, s));
             PLHR_TRY_CUDA(cudaStreamSynchronize(s));
+            if (hs->pad) {
+                set_error("plhr_solve: a tensor-core completion wait of the Gram timed out at iteration %d", it);
+                result = PLHR_ECUDA;
+                break;
+            }
             if (hs->dense[0] != kDenseOK) {
                 // the images are already explicit: leave the FP32 form and redo the
                 // step in FP64 (the next pass of the loop, from the same V)
@@ -630,7 +669,8 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             }
             last_kept = hs->dense[1];
             {
-                PhaseScope ps(PH_UPDATE32, s, 2.0 * n * m * kp);
+                // read V (FP64) and W, S, P (FP32); write V (FP64) and P (FP32)
+                PhaseScope ps(PH_UPDATE32, s, 2.0 * n * m * kp, (double)n * (8.0 * kp + 4.0 * (m - kp) + 12.0 * kp));
                 PLHR_TRY_CUDA(block_update_mx(n, nb, ub, kp, Cp, Cvv, V, 1, kp, P32, 0, kp, s));
             }
             np = kp;
@@ -646,7 +686,8 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         if (sv) {
             // ---------------------------------------- S = T(AW - BW Lambda), Q_W = T(AW - sigma BW)
             {
-                PhaseScope ps(PH_STENCIL, s, (double)n * na);
+                // read W, write A W (B W) and the shifted outputs
+                PhaseScope ps(PH_STENCIL, s, (double)n * na, prod_bytes(na, thq ? 2 : 1));
                 if (thq)
                     PLHR_TRY(prod(na, W, na, AW, na, BW, na, X2, 2 * na, lam_act, X2 + na, 2 * na));
                 else
@@ -660,14 +701,14 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             }
             // ---------------------------------------- A S, Q_S = T(AS - sigma BS)
             {
-                PhaseScope ps(PH_STENCIL, s, (double)n * na);
+                PhaseScope ps(PH_STENCIL, s, (double)n * na, prod_bytes(na, thq ? 1 : 0));
                 PLHR_TRY(prod(na, S, lds, AS, na, BS, na, nullptr, 0, nullptr, thq ? X3 : nullptr, na));
             }
             if (thq) PLHR_TRY(applyT(na, X3, na, QS));
         } else {
             // ---------------------------------------- trial space [V W P]: A W and Q_W only
             {
-                PhaseScope ps(PH_STENCIL, s, (double)n * na);
+                PhaseScope ps(PH_STENCIL, s, (double)n * na, prod_bytes(na, thq ? 1 : 0));
                 PLHR_TRY(prod(na, W, na, AW, na, BW, na, nullptr, 0, nullptr, thq ? X2 : nullptr, na));
             }
             if (thq) PLHR_TRY(applyT(na, X2, na, SQ));
@@ -697,7 +738,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         da.xi = xi; da.out_int = dstat + 3; da.clk = nullptr;
         for (int pass = 0; pass < 2; ++pass) {
             {
-                PhaseScope ps(PH_GRAM, s, gram_flops(n, m));
+                PhaseScope ps(PH_GRAM, s, gram_flops(n, m), 8.0 * n * m * ((thq ? 3 : 2) + (hasB ? 1 : 0)));
                 if (dwf)
                     PLHR_TRY_CUDA(multi_gram_dw(n, nb, zb, ab, thq ? qb : nullptr, sigma, colscale, gpart, grams, s));
                 else
@@ -729,7 +770,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         }
         // -------------------------------------------- P, V (steps 11-12), images, RQs (13-14)
         {
-            PhaseScope ps(PH_UPDATE, s, (thq ? 4.0 : 2.0) * n * m * kp);
+            PhaseScope ps(PH_UPDATE, s, (thq ? 4.0 : 2.0) * n * m * kp, (thq ? 2.0 : 1.0) * 8.0 * n * (m + 2.0 * kp));
             if (dwf) {
                 PLHR_TRY_CUDA(block_update_dw(n, nb, zb, kp, Cp, Cvv, V, kp, P, kp, s));
                 if (thq) PLHR_TRY_CUDA(block_update_dw(n, nb, qb, kp, Cp, Cvv, QV, kp, QP, kp, s));

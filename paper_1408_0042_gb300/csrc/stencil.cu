@@ -97,6 +97,7 @@ Geo geo_of(const Grid& g) {
 cudaError_t lap_axpby(const Grid& g, int nc, const double* x, int64_t ldx, double* y, int64_t ldy,
                       double alpha, double beta, cudaStream_t s) {
     if (g.csr) return csr_axpby(*g.csr, nc, x, ldx, y, ldy, alpha, beta, s);
+    if (g.q1) return q1_axpby(g, nc, x, ldx, y, ldy, alpha, beta, s);
     int64_t total = g.n() * nc;
     if (total == 0) return cudaSuccess;
     int blocks = grid_size_for(total, 256, sm_count() * 16);
@@ -113,6 +114,7 @@ cudaError_t lap_apply_shifts(const Grid& g, int nc, const double* x, int64_t ldx
                              int64_t ldax, double* o1, int64_t ld1, const double* lam, double* o2,
                              int64_t ld2, double sig, cudaStream_t s) {
     if (g.csr) return csr_apply_shifts(*g.csr, nc, x, ldx, ax, ldax, o1, ld1, lam, o2, ld2, sig, s);
+    if (g.q1) return q1_apply_shifts(g, nc, x, ldx, ax, ldax, o1, ld1, lam, o2, ld2, sig, s);
     int64_t total = g.n() * nc;
     if (total == 0) return cudaSuccess;
     int blocks = grid_size_for(total, 256, sm_count() * 16);

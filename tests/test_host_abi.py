@@ -80,13 +80,56 @@ def test_stencil_descriptors_and_sizes(p):
     (7, (4, 4, 4), 0.1, 1.0, "unknown kind"),
     (2, (0, 4, 4), 0.1, 1.0, "bad dims"),
     (2, (4, 4, 4), 0.0, 1.0, "bad dims"),
-    (2, (4, 4, 4), 0.1, -1.0, "bad dims"),
+    (2, (4, 4, 4), 0.1, -1.0, "scale must be positive"),
+    (6, (4, 4, 4), 0.1, 1.0, "unknown kind"),
     (1, (4, 4, 2), 0.1, 1.0, "dims[2] == 1"),
 ])
 def test_stencil_rejects_bad_descriptors(p, kind, dims, h, scale, msg):
     st, op = _stencil(p, kind, dims, h, scale)
     assert st == p.PLHR_EINVAL and not op.value
     assert msg in _err(p)
+
+
+def test_new_stencil_kinds_descriptors(p):
+    """Q1 stiffness / mass (interior nodes per axis), the Bloch Hamiltonian
+    (needs its potential), periodic Laplacian, and the argument checks of
+    the complex and paired products (no device work is enqueued)."""
+    lib = p.load_library()
+    for kind in (p.Q1_STIFF27, p.Q1_MASS27):
+        st, op = _stencil(p, kind, (7, 5, 6), h=1.0 / 8)
+        assert st == p.PLHR_OK and lib.plhr_op_size(op) == 210
+        lib.plhr_op_destroy(op)
+    st, op = _stencil(p, p.HAM7_BLOCH, (6, 6, 6), h=1.0)
+    assert st == p.PLHR_EINVAL and "potential" in _err(p)
+    d = p.StencilDesc()
+    d.kind = p.LAP7_3D
+    d.dims[:] = [4, 4, 4]
+    d.h, d.scale, d.bc = 0.1, 1.0, 5
+    op = ctypes.c_void_p()
+    assert lib.plhr_op_stencil(ctypes.byref(op), ctypes.byref(d)) == p.PLHR_EINVAL
+    assert "boundary condition" in _err(p)
+    d.bc = p.BC_PERIODIC
+    assert lib.plhr_op_stencil(ctypes.byref(op), ctypes.byref(d)) == p.PLHR_OK
+    # a Bloch operator with kappa != 0 is complex: the real product refuses it
+    buf = (ctypes.c_double * 512)()
+    ptr = ctypes.cast(buf, ctypes.c_void_p)
+    db = p.StencilDesc()
+    db.kind = p.HAM7_BLOCH
+    db.dims[:] = [4, 4, 4]
+    db.h, db.scale = 1.0, 1.0
+    db.bloch_k[:] = [0.1, 0.0, 0.0]
+    db.field = ptr.value
+    ob = ctypes.c_void_p()
+    assert lib.plhr_op_stencil(ctypes.byref(ob), ctypes.byref(db)) == p.PLHR_OK
+    assert lib.plhr_op_apply(ob, 1, ptr, 1, ptr, 1, None) == p.PLHR_EINVAL
+    assert "complex" in _err(p)
+    assert lib.plhr_op_apply_c128(ob, 2, ptr, 1, ptr, 2, None) == p.PLHR_EINVAL      # ldx < ncols
+    assert lib.plhr_op_apply_c128(ob, 0, None, 0, None, 0, None) == p.PLHR_OK
+    st, q = _stencil(p, p.Q1_MASS27, (3, 3, 3), h=0.25)
+    assert lib.plhr_op_apply_pair(op, q, 1, ptr, 1, ptr, 1, ptr, 1, None) == p.PLHR_EINVAL   # sizes differ
+    assert lib.plhr_op_apply_pair(ob, op, 1, ptr, 1, ptr, 1, ptr, 1, None) == p.PLHR_EINVAL  # complex
+    for o in (op, ob, q):
+        lib.plhr_op_destroy(o)
 
 
 def test_stencil_rejects_null_arguments(p):
