@@ -160,6 +160,14 @@ typedef struct {
                           rediscretised with h_0 = 2^(levels-1) h; 1 = L_0 with the
                           cell-centred sine modes as eigenvectors and the fine grid's
                           eigenvalues of the same modes */
+    int indefinite;    /* 1: INV-MG of Appendix A, Algorithm 5 instead: the same cycle for
+                          (L - sigma I) w = r (B_l = L_l - sigma I_l on every level,
+                          Richardson step 1 / max |Gershgorin bound of L_l - sigma I_l|,
+                          exact (L_0 - sigma I_0)^{-1} on the coarsest grid), an indefinite
+                          T ~ (L - sigma I)^{-1}: usable by plhr_prec_apply and by
+                          plhr_solve with the harmonic extraction (extraction = 1, FP64)
+                          only, the combination of Section 5.2's Table tab:laplace10;
+                          default 0 */
 } plhr_mg_opts;
 
 typedef struct plhr_prec plhr_prec;
@@ -255,7 +263,13 @@ typedef struct {
     int extraction;            /* 0: T-harmonic Rayleigh-Ritz (Section 3.1, default); 1: harmonic
                                   (T = I in the Petrov-Galerkin condition, Section 5.1's
                                   comparison).  extraction 1 and s_vectors 0 (the trial space
-                                  [V W P] of the ablation in Section 5.1) run in PLHR_PRECISION_F64 */
+                                  [V W P] of the ablation in Section 5.1) run in PLHR_PRECISION_F64;
+                                  2: the refinement of Section 3.3 (Eq. rRR): the single-vector
+                                  method (k = 1, guard = 0, FP64) whose new v minimises
+                                  ||(A - lam B) v||_T over span[v w s p], lam the current Rayleigh
+                                  quotient (the preconditioned locally minimal residual method; it
+                                  converges to the eigenpair its start vector is close to, not
+                                  necessarily the one nearest sigma; sigma is not used) */
     int tensor_cores;          /* PLHR_PRECISION_MIXED: 1 (default) forms the Grams of the FP32
                                   phase on the tensor cores (split-BF16 slices, FP32 accumulation,
                                   PLHR_GRAM_F32_TC of plhr_gram); 0 on the FP32 pipes

@@ -33,6 +33,14 @@ parameters to its reference [Ve.Kn:13]; the readings taken here are:
 * the garbled "|L_l - I_l|^{-1}" of the algorithm's output line is read as
   |L_l - sigma I_l|^{-1}.
 
+INV-MG (Appendix A, Algorithm 5, indefinite=True): the same V-cycle with
+B_l = L_l - sigma I_l on every level and the exact (L_0 - sigma I_0)^{-1} on
+the coarsest grid (an indefinite T ~ (L - sigma I)^{-1}); the smoother is
+Richardson with 1/beta_l, beta_l = max(|a_l|, |b_l|) over the Gershgorin
+interval [a_l, b_l] of L_l - sigma I_l (the paper takes the smoothers and
+transfers of Algorithm 4).  The algorithm's recursion into "AV-MG" and its
+"(L_l - I_l)^{-1}" are read as INV-MG and (L_l - sigma I_l)^{-1}.
+
 Pins (tests/test_oracle_pins.py, tests/test_oracle_pins_transfer_pairs.py):
 one level is exactly |L - sigma I|^{-1} on the analytic modes; the spectrum of
 p_2; the transfer identities of both transfers (the trilinear weights against
@@ -99,7 +107,7 @@ def restriction(dims, transfer: str = "constant") -> sp.csr_matrix:
 
 
 class Level:
-    def __init__(self, dims, h, sigma):
+    def __init__(self, dims, h, sigma, indefinite=False):
         self.dims = tuple(dims)
         self.h = h
         self.d = len(dims)
@@ -110,7 +118,12 @@ class Level:
         b = 4.0 * self.d / h**2 - sigma
         self.use_poly = not (math.sqrt(max(sigma, 0.0)) * h < DELTA)
         self.sigma = sigma
-        if self.use_poly:
+        self.indefinite = indefinite
+        if indefinite:
+            self.use_poly = False
+            self.c = None
+            self.beta = max(abs(a), abs(b))
+        elif self.use_poly:
             self.c = 0.5 * max(abs(a), abs(b))
             self.beta = (max(a * a, b * b) + self.c**2) / (2.0 * self.c)
         else:
@@ -118,7 +131,9 @@ class Level:
             self.beta = 4.0 * self.d / h**2
 
     def apply_B(self, x):
-        """B_l x: the Laplacian, or p_2(L_l - sigma I) x."""
+        """B_l x: the Laplacian, or p_2(L_l - sigma I) x (INV-MG: L_l - sigma I)."""
+        if self.indefinite:
+            return self.L @ x - self.sigma * x
         if not self.use_poly:
             return self.L @ x
         y = self.L @ x - self.sigma * x
@@ -146,9 +161,11 @@ class AVMG:
     """V-cycle T r of Algorithm 4 with `levels` grids (levels = 1: exact
     |L - sigma I|^{-1} on the given grid)."""
 
-    def __init__(self, dims, h, sigma, levels, nu=2, transfer="constant", coarse="rediscretised"):
+    def __init__(self, dims, h, sigma, levels, nu=2, transfer="constant", coarse="rediscretised",
+                 indefinite=False):
         if levels < 1:
             raise ValueError("levels >= 1")
+        self.indefinite = indefinite
         self.transfer = transfer
         self.coarse = coarse
         self.sigma = sigma
@@ -162,7 +179,7 @@ class AVMG:
                 dl = [N // 2 for N in dl]
                 hl = 2.0 * hl
         for dims_l, h_l in reversed(grids):
-            self.levels.append(Level(dims_l, h_l, sigma))
+            self.levels.append(Level(dims_l, h_l, sigma, indefinite))
         self.R = [None] + [restriction(self.levels[l].dims, transfer) for l in range(1, levels)]
         # coarsest: |L_0 - sigma I|^{-1} from a dense symmetric eigendecomposition
         if coarse == "rediscretised":
@@ -173,7 +190,7 @@ class AVMG:
             raise ValueError("unknown coarse operator %r" % coarse)
         lam, Q = np.linalg.eigh(L0 - sigma * np.eye(L0.shape[0]))
         self.coarse_eigs = lam
-        self.coarse_inv = (Q / np.abs(lam)[None, :]) @ Q.T
+        self.coarse_inv = (Q / (lam if indefinite else np.abs(lam))[None, :]) @ Q.T
 
     @property
     def n(self):

@@ -31,6 +31,11 @@ The iteration follows the paper's steps in order:
       B-normalise V (Alg. 3 steps 13-14).
 3. Standard Rayleigh-Ritz with respect to V (step 12 / 16).
 
+plmr() is the single-vector method with the refinement extraction of Eq. rRR
+(Section 3.3); bplhr with one column (k = 1, V0 of one column) is Algorithm 1
+(in real arithmetic a conjugate pair at the selection keeps its real part,
+Algorithm 3 with k' = k).
+
 Readings where the paper is silent (each also listed in the design notes):
 * convergence: relative residual ||Av - lam Bv|| / (max(|lam|, 1) ||Bv||) of
   the k pairs nearest sigma (ties broken by the smaller eigenvalue);
@@ -366,6 +371,87 @@ def bplhr(A, B, T, sigma, k, V0, tol=1e-8, maxit=1000, real=None, s_vectors=True
     theta, V, res, _, _ = final_rayleigh_ritz(A, B, V, sigma, k)
     return Result(eigvals=theta, eigvecs=V, residuals=res, converged=converged,
                   iterations=it, history=history)
+
+
+def refined_coefficients(Zh, AZh, BZh, lam_t, T):
+    """Eq. rRR on the basis Zh (images AZh, BZh; BZh = Zh for B = I): the
+    coefficient vector y of v = Zh y minimising ||(A - lam_t B) v||_T / ||v||_B,
+    i.e. the eigenvector of X* T X y = theta^2 Zh* B Zh y, X = (A - lam_t B) Zh,
+    for the smallest theta^2."""
+    X = AZh - lam_t * BZh
+    TX = _tmul(T, X)
+    G = _adj(X) @ TX
+    G = 0.5 * (G + _adj(G))
+    Gz = _adj(Zh) @ BZh
+    theta2, Y = sla.eigh(G, 0.5 * (Gz + _adj(Gz)))
+    return Y[:, [0]]                       # smallest theta^2 (eigh sorts ascending)
+
+
+def plmr(A, B, T, v0, tol=1e-8, maxit=1000, callback=None):
+    """Preconditioned locally minimal residual method (Section 3.3, "Possible
+    variations"): the single-vector trial space of Algorithm 1,
+    Z = [v, w, s, p] with w = T(Av - lam Bv) and s = T(Aw - lam Bw), and the
+    refinement extraction of Eq. rRR in place of the T-harmonic one: the new
+    v minimises ||(A - lam~ B) v||_T over the unit B-norm vectors of span(Z),
+    lam~ the current Rayleigh quotient, i.e. v = Z y with y the eigenvector of
+        Z*(A - lam~ B) T (A - lam~ B) Z y = theta^2 Z*BZ y
+    for the smallest theta^2; p = the w, s, p part of Z y (as in Algorithm 1
+    steps 6-7).  Z is B-orthonormalised blockwise first (as in bplhr).  Real
+    or complex v0 (n x 1 or n).  Returns a Result with the final eigenpair
+    (no final Rayleigh-Ritz: the block has one column)."""
+    v = np.array(v0, dtype=np.complex128 if np.iscomplexobj(v0) else np.float64, copy=True).reshape(-1, 1)
+    Av, Bv = A @ v, _bmul(B, v)
+    nb = np.sqrt(_cdot(v, Bv))
+    v, Av, Bv = v / nb, Av / nb, Bv / nb
+    lam = _cdot(v, Av)
+    P = AP = BP = None
+    history = []
+    converged = False
+    it = 0
+    for it in range(maxit + 1):
+        R = Av - Bv * lam[None, :]
+        rel = relative_residuals(R, lam, Bv)
+        rec = {"it": it, "lam": lam.copy(), "rel": rel.copy()}
+        history.append(rec)
+        if callback is not None:
+            callback(rec)
+        if rel[0] <= tol:
+            converged = True
+            break
+        if it == maxit:
+            break
+        W = _tmul(T, R)
+        AW, BW = A @ W, _bmul(B, W)
+        S = _tmul(T, AW - BW * lam[None, :])
+        AS, BS = A @ S, _bmul(B, S)
+        # blockwise B-orthonormal basis of [v w s p] with the A and B images
+        # (the T images are formed below for the fixed lam~)
+        blocks = [(v, Av, Bv, Bv), (W, AW, BW, BW), (S, AS, BS, BS)]
+        if P is not None:
+            blocks.append((P, AP, BP, BP))
+        basis, sizes = [], []
+        for blk in blocks:
+            ob = orthonormalize_block(blk, basis)
+            sizes.append(ob[0].shape[1])
+            if ob[0].shape[1] > 0:
+                basis.append(ob)
+        Zh = np.hstack([b_[0] for b_ in basis])
+        AZh = np.hstack([b_[1] for b_ in basis])
+        BZh = np.hstack([b_[2] for b_ in basis])
+        y = refined_coefficients(Zh, AZh, BZh, lam[0], T)
+        nv = sizes[0]
+        P = Zh[:, nv:] @ y[nv:]
+        AP, BP = AZh[:, nv:] @ y[nv:], BZh[:, nv:] @ y[nv:]
+        v = Zh[:, :nv] @ y[:nv] + P
+        Av = AZh[:, :nv] @ y[:nv] + AP
+        Bv = BZh[:, :nv] @ y[:nv] + BP
+        nb = np.sqrt(_cdot(v, Bv))
+        v, Av, Bv, P, AP, BP = v / nb, Av / nb, Bv / nb, P / nb, AP / nb, BP / nb
+        lam = _cdot(v, Av)
+    # explicit products for the reported residual
+    AVx, BVx = A @ v, _bmul(B, v)
+    res = relative_residuals(AVx - BVx * lam[None, :], lam, BVx)
+    return Result(eigvals=lam, eigvecs=v, residuals=res, converged=converged, iterations=it, history=history)
 
 
 def final_rayleigh_ritz(A, B, V, sigma, k):

@@ -37,7 +37,7 @@ class StencilDesc(ctypes.Structure):
 
 class MGOpts(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("nu", ctypes.c_int), ("delta", ctypes.c_double),
-                ("transfer", ctypes.c_int), ("coarse", ctypes.c_int)]
+                ("transfer", ctypes.c_int), ("coarse", ctypes.c_int), ("indefinite", ctypes.c_int)]
 
 
 class Options(ctypes.Structure):
@@ -312,14 +312,16 @@ class Operator:
 
 
 class AVMG:
-    """Absolute-value multigrid preconditioner T ~ |L - sigma I|^{-1} (Alg. 4)."""
+    """Absolute-value multigrid preconditioner T ~ |L - sigma I|^{-1} (Alg. 4);
+    indefinite=True gives INV-MG (Alg. 5), T ~ (L - sigma I)^{-1}."""
 
     def __init__(self, A: Operator, sigma: float, levels: int = 1, nu: int = 2,
-                 delta: float = 2 * math.pi / 10, transfer: int = 0, coarse: int = 0):
+                 delta: float = 2 * math.pi / 10, transfer: int = 0, coarse: int = 0, indefinite: bool = False):
         lib = load_library()
         o = MGOpts()
         lib.plhr_mg_opts_default(ctypes.byref(o))
         o.levels, o.nu, o.delta, o.transfer, o.coarse = levels, nu, delta, transfer, coarse
+        o.indefinite = 1 if indefinite else 0
         out = ctypes.c_void_p()
         _check(lib.plhr_prec_avmg(ctypes.byref(out), A._h, sigma, ctypes.byref(o)), "plhr_prec_avmg")
         self._h = out
@@ -570,7 +572,9 @@ def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float =
     columns (B: the generalized problem A v = lambda B v, FP64 form).
     extraction "tharm" (T-harmonic, default) or "harm" (harmonic:
     T = I in the Petrov-Galerkin condition); s_vectors False drops the S block
-    (trial space [V W P]).  Returns (eigvals (numpy, k), eigvecs (torch n x k
+    (trial space [V W P]); extraction "refined" is the single-vector
+    method with the refinement of Eq. rRR (k = 1, guard = 0).  Returns
+    (eigvals (numpy, k), eigvecs (torch n x k
     float64, CUDA), info dict)."""
     import torch
     lib = load_library()
@@ -583,9 +587,9 @@ def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float =
     opt.seed = seed
     opt.guard = guard
     opt.switch_tol = switch_tol
-    if extraction not in ("tharm", "harm"):
-        raise ValueError("extraction must be 'tharm' or 'harm'")
-    opt.extraction = 0 if extraction == "tharm" else 1
+    if extraction not in ("tharm", "harm", "refined"):
+        raise ValueError("extraction must be 'tharm', 'harm' or 'refined'")
+    opt.extraction = {"tharm": 0, "harm": 1, "refined": 2}[extraction]
     opt.s_vectors = 1 if s_vectors else 0
     opt.tensor_cores = 1 if tensor_cores else 0
     if v_init is not None:

@@ -13,6 +13,10 @@
 // weights 3/4, 1/4 to the two nearest coarse cells).  The coarsest solve
 // applies |L_0 - sigma I|^{-1} = S diag(1 / |mu - sigma|) S^T with a separable
 // orthonormal basis S = Sx (x) Sy (x) Sz and per-axis eigenvalues mu.
+//
+// INV-MG (Appendix A, Algorithm 5; H.indefinite): the same cycle with
+// B_l = L_l - sigma I_l on every level (the shift enters the sweeps and the
+// residual) and the signed coarsest solve S diag(1 / (mu - sigma)) S^T.
 #include "plhr_internal.h"
 
 namespace plhr {
@@ -51,11 +55,11 @@ __device__ __forceinline__ double lap_pt(const double* __restrict__ xp, int64_t 
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (total);        \
          e += (int64_t)gridDim.x * blockDim.x)
 
-// w_out = w_in + om * (r - ih2 * L w_in)          (w_in may be null: w_out = om r)
+// w_out = w_in + om * (r - (ih2 * L - shift) w_in)    (w_in may be null: w_out = om r)
 template <bool D3>
-__global__ void __launch_bounds__(kT) k_rich_lap(G3 g, int nc, double ih2, double om, const double* __restrict__ win,
-                                                 const double* __restrict__ r, int64_t ldr,
-                                                 double* __restrict__ wout, int64_t total) {
+__global__ void __launch_bounds__(kT) k_rich_lap(G3 g, int nc, double ih2, double shift, double om,
+                                                 const double* __restrict__ win, const double* __restrict__ r,
+                                                 int64_t ldr, double* __restrict__ wout, int64_t total) {
     GRID_LOOP(total) {
         int64_t row = e / nc;
         int c = (int)(e - row * nc);
@@ -65,7 +69,7 @@ __global__ void __launch_bounds__(kT) k_rich_lap(G3 g, int nc, double ih2, doubl
             int64_t ix, iy, iz;
             unflat(row, g, ix, iy, iz);
             const double* wp = win + row * nc + c;
-            v = wp[0] + om * (rv - ih2 * lap_pt<D3>(wp, nc, ix, iy, iz, g));
+            v = wp[0] + om * (rv - (ih2 * lap_pt<D3>(wp, nc, ix, iy, iz, g) - shift * wp[0]));
         } else {
             v = om * rv;
         }
@@ -108,9 +112,9 @@ __global__ void __launch_bounds__(kT) k_poly_step(G3 g, int nc, double ih2, doub
     }
 }
 
-// res = r - ih2 * L w
+// res = r - (ih2 * L - shift) w
 template <bool D3>
-__global__ void __launch_bounds__(kT) k_resid_lap(G3 g, int nc, double ih2, const double* __restrict__ w,
+__global__ void __launch_bounds__(kT) k_resid_lap(G3 g, int nc, double ih2, double shift, const double* __restrict__ w,
                                                   const double* __restrict__ r, int64_t ldr,
                                                   double* __restrict__ out, int64_t total) {
     GRID_LOOP(total) {
@@ -118,7 +122,8 @@ __global__ void __launch_bounds__(kT) k_resid_lap(G3 g, int nc, double ih2, cons
         int c = (int)(e - row * nc);
         int64_t ix, iy, iz;
         unflat(row, g, ix, iy, iz);
-        out[row * nc + c] = r[row * ldr + c] - ih2 * lap_pt<D3>(w + row * nc + c, nc, ix, iy, iz, g);
+        out[row * nc + c] = r[row * ldr + c] - (ih2 * lap_pt<D3>(w + row * nc + c, nc, ix, iy, iz, g) -
+                                                shift * w[row * nc + c]);
     }
 }
 
@@ -204,18 +209,22 @@ __global__ void __launch_bounds__(kT) k_restrict(G3 gf, G3 gc, int nc, int lin, 
 }
 
 // Coarsest solve, one CTA per column: out = S diag(1/|mu_i + mu_j + mu_k - sig|) S^T in
+// (signed: 1 / (mu - sig)); the two work vectors of the column live in shared
+// memory, or in global scratch (gwork, 2 n0 doubles per column) when the
+// coarsest grid is too large for it
 // (S[point][mode] per axis, orthonormal).
 __global__ void __launch_bounds__(kT) k_coarse_sep(int d, int64_t nx, int64_t ny, int64_t nz, int nc,
                                                    const double* __restrict__ Sx, const double* __restrict__ Sy,
                                                    const double* __restrict__ Sz, const double* __restrict__ mx,
                                                    const double* __restrict__ my, const double* __restrict__ mz,
-                                                   double sig, const double* __restrict__ in, int64_t ldi,
-                                                   double* __restrict__ out, int64_t ldo) {
+                                                   double sig, int signed_inv, const double* __restrict__ in,
+                                                   int64_t ldi, double* __restrict__ out, int64_t ldo,
+                                                   double* __restrict__ gwork) {
     extern __shared__ double sh[];
     const int64_t n0 = nx * ny * nz;
-    double* a = sh;
-    double* b = sh + n0;
     const int c = blockIdx.x;
+    double* a = gwork ? gwork + (int64_t)c * 2 * n0 : sh;
+    double* b = a + n0;
     for (int64_t i = threadIdx.x; i < n0; i += blockDim.x) a[i] = in[i * ldi + c];
     __syncthreads();
     // forward: coefficient(mode) = sum_point S[point][mode] x[point], axis by axis
@@ -250,7 +259,7 @@ __global__ void __launch_bounds__(kT) k_coarse_sep(int d, int64_t nx, int64_t ny
     for (int64_t i = threadIdx.x; i < n0; i += blockDim.x) {
         int64_t ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
         double mu = mx[ix] + my[iy] + (d == 3 ? mz[iz] : 0.0);
-        b[i] = b[i] / fabs(mu - sig);
+        b[i] = b[i] / (signed_inv ? mu - sig : fabs(mu - sig));
     }
     __syncthreads();
     // inverse: x[point] = sum_mode S[point][mode] coef[mode]
@@ -286,6 +295,7 @@ G3 g3(const Grid& g) { return G3{g.nx, g.ny, g.nz}; }
 int nblk(int64_t total) { return grid_size_for(total, kT, sm_count() * 16); }
 
 struct LevelBufs {
+    double* cw;    // coarsest level only: global scratch of a large coarsest solve
     double* w0;    // ping
     double* w1;    // pong
     double* tmp;   // residual / polynomial intermediate
@@ -299,9 +309,10 @@ cudaError_t rich_sweep(const MGLevel& L, double sigma, int nc, const double* win
     int64_t total = g.n() * nc;
     G3 G = g3(g);
     bool d3 = g.d == 3;
+    const double shift = L.shifted ? sigma : 0.0;
     if (!L.poly || win == nullptr) {
-        if (d3) k_rich_lap<true><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), L.omega, L.poly ? nullptr : win, r, ldr, wout, total);
-        else k_rich_lap<false><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), L.omega, L.poly ? nullptr : win, r, ldr, wout, total);
+        if (d3) k_rich_lap<true><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), shift, L.omega, L.poly ? nullptr : win, r, ldr, wout, total);
+        else k_rich_lap<false><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), shift, L.omega, L.poly ? nullptr : win, r, ldr, wout, total);
         count_launches(1);
         return cudaGetLastError();
     }
@@ -321,8 +332,9 @@ cudaError_t level_residual(const MGLevel& L, double sigma, int nc, const double*
     G3 G = g3(g);
     bool d3 = g.d == 3;
     if (!L.poly) {
-        if (d3) k_resid_lap<true><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), w, r, ldr, out, total);
-        else k_resid_lap<false><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), w, r, ldr, out, total);
+        const double shift = L.shifted ? sigma : 0.0;
+        if (d3) k_resid_lap<true><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), shift, w, r, ldr, out, total);
+        else k_resid_lap<false><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), shift, w, r, ldr, out, total);
         count_launches(1);
         return cudaGetLastError();
     }
@@ -335,18 +347,23 @@ cudaError_t level_residual(const MGLevel& L, double sigma, int nc, const double*
     return cudaGetLastError();
 }
 
+// largest coarsest grid whose two work vectors are staged in shared memory
+constexpr int64_t kCoarseShmPoints = kMaxSmemCoarse;
+
 cudaError_t coarse_solve(const MGHierarchy& H, int nc, const double* in, int64_t ldi, double* out, int64_t ldo,
-                         cudaStream_t s) {
+                         double* gwork, cudaStream_t s) {
     const Grid& g = H.lev[0].g;
     int64_t n0 = g.n();
-    size_t shm = sizeof(double) * 2 * n0;
+    const bool global = n0 > kCoarseShmPoints;
+    size_t shm = global ? 0 : sizeof(double) * 2 * n0;
     if (shm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_coarse_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;
     }
     k_coarse_sep<<<nc, kT, shm, s>>>(g.d, g.nx, g.ny, g.nz, nc, H.d_basis[0], H.d_basis[1],
                                      g.d == 3 ? H.d_basis[2] : H.d_basis[1], H.d_mu[0], H.d_mu[1],
-                                     g.d == 3 ? H.d_mu[2] : H.d_mu[1], H.sigma, in, ldi, out, ldo);
+                                     g.d == 3 ? H.d_mu[2] : H.d_mu[1], H.sigma, H.indefinite, in, ldi, out, ldo,
+                                     global ? gwork : nullptr);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -355,7 +372,7 @@ cudaError_t coarse_solve(const MGHierarchy& H, int nc, const double* in, int64_t
 // the result is written to out with leading dimension nc.
 cudaError_t vcycle(const MGHierarchy& H, int l, int nc, const double* r, int64_t ldr, double* out,
                    std::vector<LevelBufs>& B, cudaStream_t s) {
-    if (l == 0) return coarse_solve(H, nc, r, ldr, out, nc, s);
+    if (l == 0) return coarse_solve(H, nc, r, ldr, out, nc, B[0].cw, s);
     const MGLevel& L = H.lev[l];
     const MGLevel& Lc = H.lev[l - 1];
     LevelBufs& b = B[l];
@@ -404,7 +421,7 @@ int64_t mg_workspace_doubles(const MGHierarchy& H, int nc) {
         tot += 3 * H.lev[l].g.n() * nc;            // w0, w1, tmp
         tot += 2 * H.lev[l - 1].g.n() * nc;        // rc, wc
     }
-    if (H.lev.size() == 1) tot += 0;
+    if (H.lev[0].g.n() > kCoarseShmPoints) tot += 2 * H.lev[0].g.n() * nc;   // large coarsest solve
     return tot;
 }
 
@@ -414,6 +431,7 @@ cudaError_t mg_vcycle(const MGHierarchy& H, int nc, const double* r, int64_t ldr
     const int top = (int)H.lev.size() - 1;
     std::vector<LevelBufs> B(H.lev.size());
     double* p = work;
+    B[0].cw = nullptr;
     for (int l = 1; l <= top; ++l) {
         int64_t nf = H.lev[l].g.n() * nc, ncc = H.lev[l - 1].g.n() * nc;
         B[l].w0 = p; p += nf;
@@ -422,6 +440,7 @@ cudaError_t mg_vcycle(const MGHierarchy& H, int nc, const double* r, int64_t ldr
         B[l].rc = p; p += ncc;
         B[l].wc = p; p += ncc;
     }
+    if (H.lev[0].g.n() > kCoarseShmPoints) B[0].cw = p;
     // the kernels use leading dimension nc for level buffers; the caller's
     // output must be dense (ldw == nc) or is staged through the ping buffer
     if (ldw == nc) return vcycle(H, top, nc, r, ldr, w, B, s);

@@ -224,6 +224,7 @@ void plhr_mg_opts_default(plhr_mg_opts* o) {
     o->delta = 2.0 * M_PI / 10.0;
     o->transfer = 0;
     o->coarse = 0;
+    o->indefinite = 0;
 }
 
 plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma, const plhr_mg_opts* opts) {
@@ -233,7 +234,7 @@ plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma, cons
     if (opts) o = *opts;
     if (!out || !A) { set_error("plhr_prec_avmg: null argument"); return PLHR_EINVAL; }
     if (o.levels < 1 || o.nu < 1 || !(o.delta > 0) || (o.transfer != 0 && o.transfer != 1) ||
-        (o.coarse != 0 && o.coarse != 1) || !std::isfinite(sigma)) {
+        (o.coarse != 0 && o.coarse != 1) || (o.indefinite != 0 && o.indefinite != 1) || !std::isfinite(sigma)) {
         set_error("plhr_prec_avmg: bad options");
         return PLHR_EINVAL;
     }
@@ -253,6 +254,7 @@ plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma, cons
     H.dim = g.d;
     H.nu = o.nu;
     H.linear = o.transfer;
+    H.indefinite = o.indefinite;
     H.sigma = sigma;
     H.lev.resize(o.levels);
     for (int l = o.levels - 1, s = 0; l >= 0; --l, ++s) {
@@ -266,7 +268,13 @@ plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma, cons
         // Gershgorin interval of L_l - sigma I: [-sigma, 4 d scale / h_l^2 - sigma]
         double a = -sigma, b = 4.0 * g.d * L.g.inv_h2() - sigma;
         L.poly = !(std::sqrt(std::fmax(sigma, 0.0)) * L.g.h < o.delta);
-        if (L.poly) {
+        if (o.indefinite) {
+            // INV-MG: B_l = L_l - sigma I, Richardson step 1 / max(|a|, |b|)
+            L.poly = false;
+            L.shifted = true;
+            L.c = 0.0;
+            L.omega = 1.0 / std::fmax(std::fabs(a), std::fabs(b));
+        } else if (L.poly) {
             L.c = 0.5 * std::fmax(std::fabs(a), std::fabs(b));
             double beta = (std::fmax(a * a, b * b) + L.c * L.c) / (2.0 * L.c);
             L.omega = 1.0 / beta;
@@ -333,12 +341,10 @@ plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma, cons
         }
         H.n0[ax] = N;
     }
-    int64_t n0 = g0.n();
-    if (2 * n0 * (int64_t)sizeof(double) > 200 * 1024) {
-        set_error("plhr_prec_avmg: coarsest grid of %lld points exceeds the single-CTA solve", (long long)n0);
-        plhr_prec_destroy(T);
-        return PLHR_EINVAL;
-    }
+    // a coarsest grid above kMaxSmemCoarse points is solved with global
+    // scratch by the FP64 cycle; the FP32 and double-word cycles (the mixed
+    // form) stage it in shared memory and refuse larger grids
+    (void)g0;
     *out = T;
     return PLHR_OK;
 }
@@ -417,7 +423,7 @@ extern "C" plhr_status plhr_prec_apply_dw(plhr_prec* T, int ncols, const double*
         set_error("plhr_prec_apply_dw: invalid argument");
         return PLHR_EINVAL;
     }
-    if (T->kind != PREC_AVMG) {
+    if (T->kind != PREC_AVMG || T->H.indefinite || T->H.lev[0].g.n() > kMaxSmemCoarse) {
         set_error("plhr_prec_apply_dw: double-word form exists for AV-MG only");
         return PLHR_EINVAL;
     }
@@ -434,7 +440,7 @@ extern "C" plhr_status plhr_prec_apply_f32(plhr_prec* T, int ncols, const float*
         set_error("plhr_prec_apply_f32: invalid argument");
         return PLHR_EINVAL;
     }
-    if (T->kind != PREC_AVMG) {
+    if (T->kind != PREC_AVMG || T->H.indefinite || T->H.lev[0].g.n() > kMaxSmemCoarse) {
         set_error("plhr_prec_apply_f32: FP32 form exists for AV-MG only");
         return PLHR_EINVAL;
     }

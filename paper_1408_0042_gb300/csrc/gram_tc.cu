@@ -11,25 +11,33 @@
 // three BF16 slices x = x0 + x1 + x2 (+ about 2^-24 |x|), and a product
 // a b is formed from the six slice products of total order <= 2,
 //     a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0,
-// each exact in the tensor core's FP32 accumulation (8-bit x 8-bit
-// significands), so a product carries about the FP32 rounding of its inputs
-// (the dropped terms are below 2^-24 |a b|).  The FP32 accumulator in tensor
-// memory sums 128 grid points; every 128 points it is read back and folded
-// into a per-thread double-FP32 (hi, lo) sum with TwoSum, so the accumulation
-// error does not grow with n (as in the FP32-pipe Gram of the same form).
+// each exact (8-bit x 8-bit significands), so a product carries about the
+// FP32 rounding of its inputs (the dropped terms are below 2^-24 |a b|).
+// The sums are what the tensor core rounds (each MMA adds its products to
+// the FP32 accumulator with at most about one unit of the accumulator's last
+// place), so the leading products a0 b0 and the five corrections (2^-8 and
+// smaller) accumulate separately in tensor memory: the leading sum is read
+// back after every chunk of 32 points (two MMA additions, no more rounding
+// than the FP32 pipes' 32-row sums), the corrections after every 128 points;
+// both are folded into a per-thread double-FP32 (hi, lo) sum with TwoSum, so
+// the accumulation error does not grow with n.
 //
-// Tiles.  A chunk of 64 grid points is staged in shared memory as one
+// Tiles.  A chunk of 32 grid points is staged in shared memory as one
 // K-major operand panel of 192 rows (U columns 0..63, Z columns 64..127, Q
 // columns 128..191; padding columns and points past n are zero), per slice.
 // One 128 x 128 x 16 MMA with A = panel rows 0..127 ([U; Z]) and B = panel
 // rows 64..191 ([Z; Q]) yields
 //     D = [ U^T Z  U^T Q ]
 //         [ Z^T Z  Z^T Q ]
-// so all three Grams come from one accumulator (U^T Z is not needed).  Two
-// panels alternate so that the MMAs of one chunk run while the next chunk is
-// converted; two TMEM accumulators alternate so that one is read back while
-// the other accumulates.  One CTA of 512 threads per SM; thread 0 issues the
-// MMAs, all 16 warps stage, 12 warps read back.
+// so all three Grams come from one accumulator (U^T Z is not needed).
+//
+// Pipeline (one CTA of 512 threads per SM, chunks strided over the CTAs):
+// the raw FP32 rows of the next four chunks are in flight into a ring of
+// shared-memory row buffers (cp.async) while the current chunk is converted
+// and the tensor cores multiply the one before; two panels alternate between
+// conversion and MMA; two TMEM accumulators alternate by groups of four
+// chunks (128 points), one read back while the other accumulates.  Thread 0
+// issues the MMAs, 12 warps copy, all 16 convert, 12 read back.
 #include "blockops.h"
 #include "dword.h"
 #include "mixed.h"
@@ -38,7 +46,9 @@
 namespace plhr {
 namespace {
 
-constexpr int kTcK = 64;                                   // grid points per chunk
+constexpr int kTcK = 32;                                   // grid points per chunk
+constexpr int kGroup = 4;                                  // chunks per accumulator group (128 points)
+constexpr int kRawBufs = 5;                                // raw row buffers: chunks in flight
 constexpr int kTcThreads = 512;
 constexpr int kPanelRows = 192;                            // U | Z | Q
 constexpr int kCoreBytes = 128;                            // 8 rows x 16 bytes
@@ -47,13 +57,13 @@ constexpr uint32_t kSBO = kCoreBytes;                      // next 8-row group a
 constexpr int kSliceBytes = kPanelRows * kTcK * 2;         // one BF16 slice of a panel
 constexpr int kBufBytes = 3 * kSliceBytes;                 // three slices
 constexpr int kOperandBytes = 2 * kBufBytes;               // two panels
-// shared memory kept past the panels: the descriptors address the panels
-// only, but the allocation also covers the span the same descriptors would
-// reach with the two byte offsets exchanged
-constexpr int kGuardBytes = 48 * 1024;
+constexpr int kRawStride = 192;                            // raw row: Z (64) | AZ (64) | Q (64) floats
+constexpr int kRawBytes = kTcK * kRawStride * 4;           // one chunk of raw FP32 rows
 constexpr int kMetaBytes = 4096;
-constexpr int kSmemBytes = kOperandBytes + kGuardBytes + kMetaBytes;
-constexpr uint32_t kTmemCols = 256;                        // two 128-column FP32 accumulators
+constexpr int kSmemBytes = kOperandBytes + kRawBufs * kRawBytes + kMetaBytes;
+// tensor memory: leading-product accumulators for even / odd chunks (columns
+// 0, 128), correction accumulators for even / odd groups (256, 384)
+constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(128, 128);
 constexpr long long kWaitCycles = 4LL << 30;               // about 2 s at 2 GHz
 
@@ -67,6 +77,15 @@ struct ColTc {
     const float* a[64];
     const float* q[64];
     int64_t ldz[64], lda[64], ldq[64];
+    int is_u[64];
+};
+
+// The column table in shared memory: indexing the kernel-parameter copy with
+// a per-thread column serialises every access of a warp (one distinct
+// constant-bank address per lane), shared memory serves it in one pass.
+struct ColSh {
+    const float* p[3][64];    // Z, AZ, Q
+    int64_t ld[3][64];
     int is_u[64];
 };
 
@@ -84,11 +103,33 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// Convert the chunk of grid points row0 .. row0 + 63 into the panel at buf.
-// Task t: panel row mr (column j of U, Z or Q) and core-matrix column ki
-// (8 consecutive grid points): 8 values, three 16-byte slice stores.
-__device__ __forceinline__ void stage_tc(unsigned char* buf, int64_t n, int64_t row0, int m, const ColTc& C,
-                                         int has_q, float sigf, const float* cscf) {
+// Start the asynchronous copies of the raw rows row0 .. row0 + 31 (those
+// below n) of the Z, AZ and (with has_q) Q families into raw[row][192]:
+// element (r, j) of family f at raw[r * 192 + 64 f + j].  Thread t < 384
+// copies column j of family f for one half of the rows (consecutive threads
+// take consecutive columns, so a warp reads contiguous row segments); the
+// addresses advance by one row stride per copy.
+__device__ __forceinline__ void fetch_tc(float* raw, int64_t n, int64_t row0, int m, const ColSh& C, int has_q) {
+    const int t = threadIdx.x;
+    if (t >= 2 * kPanelRows) return;
+    const int half = t / kPanelRows, fj = t - half * kPanelRows;
+    const int f = fj >> 6, j = fj & 63;
+    if (j >= m || (f == 2 && !has_q)) return;
+    const int64_t r0 = row0 + half * (kTcK / 2);
+    const int cnt = (int)(n - r0 < kTcK / 2 ? n - r0 : kTcK / 2);
+    const int64_t ld = C.ld[f][j];
+    const float* src = C.p[f][j] + r0 * ld;
+    float* dst = raw + half * (kTcK / 2) * kRawStride + fj;
+#pragma unroll 4
+    for (int r = 0; r < cnt; ++r, src += ld, dst += kRawStride) cp_async4(dst, src);
+}
+
+// Convert the chunk of grid points row0 .. row0 + 31 (raw rows in shared
+// memory) into the panel at buf.  Task t: panel row mr (column j of U, Z or
+// Q) and core-matrix column ki (8 consecutive grid points): 8 values, three
+// 16-byte slice stores.
+__device__ __forceinline__ void stage_tc(unsigned char* buf, const float* raw, int64_t n, int64_t row0, int m,
+                                         const ColSh& C, int has_q, float sigf, const float* cscf) {
     for (int t = threadIdx.x; t < kPanelRows * (kTcK / 8); t += kTcThreads) {
         const int mr = t % kPanelRows, ki = t / kPanelRows;
         const int part = mr >> 6, j = mr & 63;
@@ -97,26 +138,18 @@ __device__ __forceinline__ void stage_tc(unsigned char* buf, int64_t n, int64_t 
         for (int r = 0; r < 8; ++r) x[r] = 0.0f;
         if (j < m) {
             const float sf = cscf[j];
-            const int64_t r0 = row0 + 8 * ki;
-            const bool needa = part == 0 || (part == 2 && !has_q);
             const bool isu = C.is_u[j] != 0;
+            const float* rr = raw + (8 * ki) * kRawStride;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const int64_t row = r0 + r;
-                if (row < n) {
-                    float v;
-                    if (part == 2 && has_q) {
-                        v = C.q[j][row * C.ldq[j]] * sf;
-                    } else {
-                        const float z = C.z[j][row * C.ldz[j]] * sf;
-                        if (needa) {
-                            const float a = C.a[j][row * C.lda[j]] * sf;
-                            v = isu ? a : a - sigf * z;
-                        } else {
-                            v = z;
-                        }
-                    }
-                    x[r] = v;
+            for (int r = 0; r < 8; ++r, rr += kRawStride) {
+                if (row0 + 8 * ki + r >= n) break;
+                if (part == 1) {
+                    x[r] = rr[j] * sf;
+                } else if (part == 2 && has_q) {
+                    x[r] = rr[128 + j] * sf;
+                } else {
+                    const float z = rr[j] * sf, a = rr[64 + j] * sf;
+                    x[r] = isu ? a : a - sigf * z;
                 }
             }
         }
@@ -137,15 +170,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int64_t n, int m, con
                                                            int has_q, float sigf, const double* __restrict__ csc,
                                                            double* __restrict__ partial, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* meta = smem + kOperandBytes + kGuardBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(meta);        // [0..1] panels, [2..3] accumulators
+    float* raw = reinterpret_cast<float*>(smem + kOperandBytes);
+    unsigned char* meta = smem + kOperandBytes + kRawBufs * kRawBytes;
+    // [0..1] panels, [2..3] correction accumulators, [4..5] leading accumulators
+    uint64_t* bars = reinterpret_cast<uint64_t*>(meta);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(meta + 64);
     float* cscf = reinterpret_cast<float*>(meta + 128);        // [64]
+    ColSh& cols = *reinterpret_cast<ColSh*>(meta + 512);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid < 64) cscf[tid] = tid < m ? (float)csc[tid] : 0.0f;
+    if (tid < 64) {
+        cscf[tid] = tid < m ? (float)csc[tid] : 0.0f;
+        cols.p[0][tid] = C.z[tid];
+        cols.p[1][tid] = C.a[tid];
+        cols.p[2][tid] = C.q[tid];
+        cols.ld[0][tid] = C.ldz[tid];
+        cols.ld[1][tid] = C.lda[tid];
+        cols.ld[2][tid] = C.ldq[tid];
+        cols.is_u[tid] = C.is_u[tid];
+    }
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) tc::mbar_init(&bars[i], 1);
+        for (int i = 0; i < 6; ++i) tc::mbar_init(&bars[i], 1);
         tc::mbar_init_fence();
     }
     if (warp == 0) {
@@ -167,17 +212,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int64_t n, int m, con
 
     const int64_t nchunks = (n + kTcK - 1) / kTcK;
     const int nloc = (int64_t)blockIdx.x < nchunks ? (int)((nchunks - 1 - blockIdx.x) / gridDim.x + 1) : 0;
-    const int ngroups = (nloc + 1) / 2;
+    const int ngroups = (nloc + kGroup - 1) / kGroup;
     bool ok = true;
-    int drained = 0, committed = 0;   // groups read back / whose accumulator commit was issued
+    int drained = 0, issued = 0;   // correction groups read back / chunks whose MMAs were issued
 
-    auto drain = [&](int g) -> bool {
-        const int a = g & 1;
-        const bool w = tc::mbar_wait(&bars[2 + a], (uint32_t)((g >> 1) & 1), kWaitCycles);
+    // read back the accumulator at TMEM column col0 once the barrier's phase
+    // with the given parity has completed, and fold it into (hi, lo)
+    auto drain_acc = [&](uint64_t* bar, uint32_t parity, uint32_t col0) -> bool {
+        const bool w = tc::mbar_wait(bar, parity, kWaitCycles);
         if (__syncthreads_or(!w)) return false;
         tc::fence_after_sync();
         if (useful) {
-            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * 128 + 32 * cq);
+            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + col0 + (uint32_t)(32 * cq);
             float v[16];
             tc::tmem_ld16(ta, v);
             tc::tmem_ld_wait();
@@ -189,24 +235,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int64_t n, int m, con
         tc::fence_before_sync();
         return true;
     };
+    // corrections of group g; leading products of chunk i
+    auto drain = [&](int g) -> bool {
+        return drain_acc(&bars[2 + (g & 1)], (uint32_t)((g >> 1) & 1), 256u + 128u * (uint32_t)(g & 1));
+    };
+    auto drain_main = [&](int i) -> bool {
+        return drain_acc(&bars[4 + (i & 1)], (uint32_t)((i >> 1) & 1), 128u * (uint32_t)(i & 1));
+    };
 
+    // prologue: the copies of the first kRawBufs - 1 chunks, one commit group each
+    for (int i = 0; i < kRawBufs - 1; ++i) {
+        if (i < nloc) fetch_tc(raw + i * (kRawBytes / 4), n, ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * kTcK,
+                               m, cols, has_q);
+        cp_async_commit();
+    }
     for (int i = 0; i < nloc; ++i) {
         const int64_t row0 = ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * kTcK;
         const int b = i & 1;
         unsigned char* buf = smem + b * kBufBytes;
-        if (i >= 2) {   // the MMAs that read this panel two chunks ago have completed
-            const bool w = tc::mbar_wait(&bars[b], (uint32_t)(((i >> 1) - 1) & 1), kWaitCycles);
-            if (__syncthreads_or(!w)) { ok = false; break; }
-        }
-        stage_tc(buf, n, row0, m, C, has_q, sigf, cscf);
+        // this thread's raw rows of chunk i (the groups complete in order and one
+        // is committed per chunk); the barrier below shows every thread's rows
+        cp_async_wait_group<kRawBufs - 2>();
+        bool w = true;
+        if (i >= 2)            // the MMAs that read this panel two chunks ago have completed
+            w = tc::mbar_wait(&bars[b], (uint32_t)(((i >> 1) - 1) & 1), kWaitCycles);
+        if (__syncthreads_or(!w)) { ok = false; break; }
+        stage_tc(buf, raw + (i % kRawBufs) * (kRawBytes / 4), n, row0, m, cols, has_q, sigf, cscf);
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
-        const int g = i >> 1, a = g & 1;
-        const bool group_end = (i & 1) || i == nloc - 1;
+        // the raw buffer of chunk i - 1 is free: start the copies of chunk i + kRawBufs - 1 into it
+        {
+            const int inext = i + kRawBufs - 1;
+            if (inext < nloc)
+                fetch_tc(raw + (inext % kRawBufs) * (kRawBytes / 4), n,
+                         ((int64_t)blockIdx.x + (int64_t)inext * gridDim.x) * kTcK, m, cols, has_q);
+            cp_async_commit();
+        }
+        const int g = i / kGroup, a = g & 1;
+        const bool group_start = i % kGroup == 0;
+        const bool group_end = (i + 1) % kGroup == 0 || i == nloc - 1;
         if (tid == 0) {
-            const uint32_t d = tmem + (uint32_t)(a * 128);
+            const uint32_t dmain = tmem + 128u * (uint32_t)(i & 1);
+            const uint32_t dcorr = tmem + 256u + 128u * (uint32_t)a;
             const uint32_t sb = tc::smem_u32(buf);
 #pragma unroll
             for (int s = 0; s < kTcK / 16; ++s) {
@@ -215,28 +287,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int64_t n, int m, con
                 for (int p = 0; p < 6; ++p) {
                     const uint64_t ad = tc::smem_desc(sb + slice_a(p) * kSliceBytes + kofs, kLBO, kSBO);
                     const uint64_t bd = tc::smem_desc(sb + slice_b(p) * kSliceBytes + kofs + 8 * kCoreBytes, kLBO, kSBO);
-                    tc::mma_bf16(d, ad, bd, kIdesc, ((i & 1) | s | p) ? 1u : 0u);
+                    if (p == 0) tc::mma_bf16(dmain, ad, bd, kIdesc, s ? 1u : 0u);
+                    else tc::mma_bf16(dcorr, ad, bd, kIdesc, (!group_start || s || p > 1) ? 1u : 0u);
                 }
             }
             tc::mma_commit(&bars[b]);
+            tc::mma_commit(&bars[4 + (i & 1)]);
             if (group_end) tc::mma_commit(&bars[2 + a]);
         }
-        if (group_end) ++committed;
-        if ((i & 1) && i >= 3) {
+        ++issued;
+        // the leading products of the previous chunk (their accumulator is next
+        // written by chunk i + 1)
+        if (i >= 1 && !drain_main(i - 1)) { ok = false; break; }
+        // after the last chunk of group g, the corrections of group g - 1 (their
+        // accumulator is next written by group g + 1)
+        if (group_end && g >= 1 && drained == g - 1) {
             if (!drain(drained)) { ok = false; break; }
             ++drained;
         }
     }
+    if (ok && nloc > 0 && !drain_main(nloc - 1)) ok = false;
     while (ok && drained < ngroups) {
         if (!drain(drained)) { ok = false; break; }
         ++drained;
     }
+    cp_async_wait_all();
     if (!ok) {
         if (tid == 0) atomicExch(err, 1);
-        // let the MMAs already issued finish (bounded) before the TMEM is freed
-        if (committed > 0) {
-            const int gl = committed - 1;
-            tc::mbar_wait(&bars[2 + (gl & 1)], (uint32_t)((gl >> 1) & 1), kWaitCycles);
+        // let the MMAs already issued finish (bounded) before the TMEM is freed:
+        // the last chunk's commit tracks every MMA issued before it
+        if (issued > 0) {
+            const int il = issued - 1;
+            tc::mbar_wait(&bars[4 + (il & 1)], (uint32_t)((il >> 1) & 1), kWaitCycles);
         }
     }
     tc::fence_before_sync();

@@ -135,6 +135,7 @@ cudaError_t bloch_apply(const Grid& g, int nc, const double* x, int64_t ldx, dou
 struct MGLevel {
     Grid g;
     bool poly = false;    // B_l = p_2(L_l - sigma I) instead of L_l
+    bool shifted = false; // B_l = L_l - sigma I (INV-MG)
     double c = 0.0;       // p_2 parameter
     double omega = 0.0;   // Richardson step 1 / beta_l
 };
@@ -143,6 +144,7 @@ struct MGHierarchy {
     int dim = 3;
     int nu = 2;
     int linear = 0;                    // 1: trilinear cell-centred transfers, 0: piecewise constant
+    int indefinite = 0;                // 1: INV-MG (Algorithm 5), T ~ (L - sigma I)^{-1}
     double sigma = 0.0;
     std::vector<MGLevel> lev;          // 0 = coarsest
     // coarsest solve: w = S3 diag(1/|mu_i + mu_j + mu_k - sigma|) S3^T r with
@@ -155,6 +157,11 @@ struct MGHierarchy {
     float* w_mu[3] = {nullptr, nullptr, nullptr};      // double-word V-cycle
     int64_t n0[3] = {1, 1, 1};
 };
+
+// Largest coarsest grid (points) of the FP32 and double-word V-cycles, whose
+// coarsest solve stages the grid in shared memory (the FP64 cycle takes any
+// size: above this it works in global scratch).
+constexpr int64_t kMaxSmemCoarse = 12288;
 
 cudaError_t mg_vcycle(const MGHierarchy& H, int nc, const double* r, int64_t ldr, double* w,
                       int64_t ldw, double* work, cudaStream_t s);

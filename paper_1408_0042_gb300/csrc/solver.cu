@@ -34,6 +34,9 @@
 
 namespace plhr {
 plhr_status prec_reserve(plhr_prec* T, int nc, int64_t extra_doubles);
+plhr_status plmr_solve(const plhr_op* A, const plhr_op* B, plhr_prec* T, double tol, const plhr_options& opt,
+                       double* eigvals, double* eigvecs, int64_t ldv, plhr_info* info, cudaStream_t s,
+                       double t_start);
 plhr_status prec_reserve32(plhr_prec* T, int nc, int64_t extra_floats);
 plhr_status prec_reserve_dw(plhr_prec* T, int nc);
 }
@@ -112,15 +115,36 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         return PLHR_EINVAL;
     }
     if (!opt.real_arithmetic || (opt.precision != PLHR_PRECISION_F64 && opt.precision != PLHR_PRECISION_MIXED) ||
-        (opt.extraction != 0 && opt.extraction != 1)) {
-        set_error("plhr_solve: this build supports real arithmetic, FP64 or mixed precision, extraction 0 or 1");
+        opt.extraction < 0 || opt.extraction > 2) {
+        set_error("plhr_solve: this build supports real arithmetic, FP64 or mixed precision, extraction 0, 1 or 2");
         return PLHR_EINVAL;
+    }
+    if (opt.extraction == 2) {
+        // the refinement extraction of Eq. rRR: the single-vector method of Section 3.3
+        if (k != 1 || opt.guard != 0 || opt.precision != PLHR_PRECISION_F64 ||
+            (T && T->kind == PREC_AVMG && T->H.indefinite) || (T && prec_size(T) != A->g.n()) ||
+            (opt.v_init && opt.ld_init < 1)) {
+            set_error("plhr_solve: extraction 2 (refinement, Eq. rRR) is the single-vector method: k = 1, "
+                      "guard = 0, PLHR_PRECISION_F64, a symmetric positive definite T of A's size");
+            return PLHR_EINVAL;
+        }
+        return plmr_solve(A, B, T, tol, opt, eigvals, eigvecs, ldv, info, (cudaStream_t)stream, t0);
     }
     if ((!opt.s_vectors || opt.extraction != 0) && opt.precision != PLHR_PRECISION_F64) {
         set_error("plhr_solve: harmonic extraction and s_vectors = 0 run in PLHR_PRECISION_F64");
         return PLHR_EINVAL;
     }
     const int64_t n = A->g.n();
+    if (T && T->kind == PREC_AVMG && T->H.indefinite && (opt.extraction == 0 || opt.precision != PLHR_PRECISION_F64)) {
+        set_error("plhr_solve: the INV-MG preconditioner is indefinite: it needs the harmonic extraction "
+                  "(extraction = 1) in PLHR_PRECISION_F64");
+        return PLHR_EINVAL;
+    }
+    if (opt.precision == PLHR_PRECISION_MIXED && T && T->kind == PREC_AVMG && T->H.lev[0].g.n() > kMaxSmemCoarse) {
+        set_error("plhr_solve: PLHR_PRECISION_MIXED needs a coarsest multigrid grid of at most %lld points",
+                  (long long)kMaxSmemCoarse);
+        return PLHR_EINVAL;
+    }
     if (opt.precision == PLHR_PRECISION_MIXED && (!A->g.plain() || (T && T->kind != PREC_AVMG))) {
         set_error("plhr_solve: the mixed-precision form supports the Dirichlet Laplacian with AV-MG or T = I only");
         return PLHR_EINVAL;

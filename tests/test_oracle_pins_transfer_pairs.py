@@ -306,3 +306,72 @@ def test_solver_with_pairs_mid_solve_matches_closed_form_and_dense():
     ref2 = ev[np.lexsort((ev, np.abs(ev - w.sigma)))][: w.k]
     assert np.allclose(np.sort(r.eigvals), np.sort(ref2), rtol=1e-10)
     assert np.abs(r.eigvecs.T @ r.eigvecs - np.eye(w.k)).max() <= 1e-12
+
+
+# ---------------------------------------------------------------- INV-MG (Algorithm 5)
+
+def test_inv_mg_single_level_is_exact_inverse():
+    """levels = 1: T = (L - sigma I)^{-1}, signed: on an analytic sine mode
+    T u = u / (lambda - sigma)."""
+    dims, h, sigma = (6, 5, 4), 1.0 / 7.0, 300.0
+    T = avmg.AVMG(dims, h, sigma, levels=1, indefinite=True)
+    signs = set()
+    for modes in [(1, 1, 1), (2, 3, 1), (6, 5, 4), (3, 2, 2)]:
+        vecs = [np.sin(np.arange(1, N + 1) * m * np.pi / (N + 1)) for N, m in zip(dims, modes)]
+        u = vecs[2]
+        for v in (vecs[1], vecs[0]):
+            u = np.kron(u, v)
+        lam = sum((2.0 - 2.0 * math.cos(m * math.pi / (N + 1))) / h**2 for N, m in zip(dims, modes))
+        assert np.allclose(T(u), u / (lam - sigma), rtol=1e-10, atol=1e-14)
+        signs.add(np.sign(lam - sigma))
+    assert signs == {-1.0, 1.0}
+
+
+@pytest.mark.parametrize("sigma", [60.0, 700.0])
+def test_inv_mg_two_level_algebraic_form(sigma):
+    """Two-grid Algorithm 5: T = S^{-1}(I - E^{2nu}) + E^nu P T_c R E^nu with
+    S = L - sigma I, E = I - S / beta, beta the Gershgorin bound of |S|, P and
+    R from the brute-force trilinear weights, T_c = (L_0 - sigma I)^{-1} from
+    the independent eigenpairs (fine-spectrum coarse operator)."""
+    dims, h, nu = (4, 4, 6), 1.0 / 7.0, 2
+    T = avmg.AVMG(dims, h, sigma, levels=2, nu=nu, transfer="linear", coarse="fine_spectrum", indefinite=True)
+    n = int(np.prod(dims))
+    Td = _dense(T, n)
+    S = operators.laplacian_dirichlet(dims, h).toarray() - sigma * np.eye(n)
+    beta = max(sigma, 12.0 / h**2 - sigma)
+    E = np.eye(n) - S / beta
+    En = np.linalg.matrix_power(E, nu)
+    R = _brute_restriction(dims)
+    P = 8.0 * R.T
+    cd = tuple(N // 2 for N in dims)
+    vecs, vals = [], []
+    for N0, N in zip(cd, dims):
+        _, Sv = np.linalg.eigh(_cell_centred_dirichlet_1d(N0))
+        vecs.append(Sv)
+        vals.append(np.linalg.eigvalsh(operators.second_difference_1d(N, h).toarray())[:N0])
+    S3, lam = vecs[-1], vals[-1]
+    for a in reversed(range(len(cd) - 1)):
+        S3 = np.kron(S3, vecs[a])
+        lam = (lam[:, None] + vals[a][None, :]).ravel()
+    Tc = S3 @ np.diag(1.0 / (lam - sigma)) @ S3.T
+    ref = np.linalg.solve(S, np.eye(n) - En @ En) + En @ P @ Tc @ R @ En
+    assert np.allclose(Td, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+    # symmetric; indefinite when sigma lies inside the spectrum of L (max 12/h^2 = 588)
+    assert np.abs(Td - Td.T).max() <= 1e-12 * np.abs(Td).max()
+    ev = np.linalg.eigvalsh(0.5 * (Td + Td.T))
+    if sigma < 12.0 / h**2:
+        assert ev.min() < 0 < ev.max()
+
+
+def test_bplhr_harmonic_with_inv_mg_matches_closed_form():
+    """The paper's "BPLHR, Indef., harm." combination (Table tab:laplace10):
+    harmonic extraction (T = I in the Petrov-Galerkin condition) with the
+    indefinite INV-MG T converges to the closed-form eigenvalues."""
+    w = wl.lap2d_small(32, k=4, gap_index=60)
+    A, _ = operators.model_operator(w)
+    T = avmg.AVMG(w.dims, w.h, w.sigma, 3, 2, transfer="linear", coarse="fine_spectrum", indefinite=True)
+    r = plhr.bplhr(A, None, T, w.sigma, w.k, w.v0(), tol=1e-9, maxit=1500, extraction="harm")
+    assert r.converged
+    lam = wl.lap_closed_form(w.dims, w.h)
+    ref = lam[np.lexsort((lam, np.abs(lam - w.sigma)))][: w.k]
+    assert np.allclose(np.sort(r.eigvals), np.sort(ref), rtol=1e-9)
