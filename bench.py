@@ -425,6 +425,156 @@ def cpu_baseline(iterations, which):
                                                                     os.cpu_count())}
 
 
+LAP2D_METRIC = "PLHR seconds to k interior pairs at rel. residual 1e-8 (FP64)"
+
+
+def run_lap2d(args, world, rank, local):
+    """The small 2D workload: 5-point Dirichlet Laplacian on 32 x 32 interior
+    points (n = 1024, h = 1/33), the 4 pairs nearest sigma = 1297.84 (the
+    midpoint of lambda_100 and lambda_101, closed form), T = I, FP64, tol 1e-8,
+    guard 2 (the double eigenvalue outside the wanted set).  A step is one
+    solve from the seeded start block.  Latency-bound at this size: every
+    iteration is a few dozen small launches and one host synchronisation."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1408_0042_gb300 as plhr
+    import workloads as wl
+
+    torch.cuda.set_device(local)
+    w = wl.lap2d_32x32_k4()
+    A = plhr.Operator.laplacian(w.dims, w.h)
+    v0_host = torch.from_numpy(w.v0()).pin_memory()
+    v0 = v0_host.cuda()
+    stream = torch.cuda.current_stream()
+
+    def one(vinit):
+        return plhr.solve(A, w.sigma, w.k, tol=w.tol, maxit=w.maxit, v_init=vinit, guard=w.guard,
+                          raise_on_notconv=True)
+
+    for _ in range(args.warmup):
+        one(v0)
+    torch.cuda.synchronize()
+    plhr.profile_read(reset=True)
+    plhr.profile_enable(True)
+    launches0 = plhr.kernel_launches()
+    times = []
+    with ClockSampler(_gpu_id(local)) as clk:
+        _barrier(world)
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lam, V, info = one(v0)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+        _barrier(world)
+    launches = plhr.kernel_launches() - launches0
+    plhr.profile_enable(False)
+    prof = plhr.profile_read(reset=True)
+    step_s = _max_over_ranks(statistics.mean(times), world)
+    cf = wl.lap_closed_form(w.dims, w.h)
+    want = np.sort(cf[np.lexsort((cf, np.abs(cf - w.sigma)))][: w.k])
+    eig_err = float(np.abs(np.sort(lam) - want).max() / np.abs(want).max())
+    e2e = []
+    vecs_host = torch.empty((w.n, w.k), dtype=torch.float64).pin_memory()
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lam2, V2, _ = one(v0_host.to("cuda", non_blocking=True))
+        vecs_host.copy_(V2, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e.append(e0.elapsed_time(e1) / 1e3)
+    e2e_s = _max_over_ranks(statistics.mean(e2e), world)
+    roofs = _rooflines(prof, _peaks(), clk.summary().get("sm_max_mhz"), False)
+    out = {
+        "metric": LAP2D_METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded start block)",
+        "config": {"workload": w.name, "operator": "5-point Dirichlet Laplacian 32 x 32, h = 1/33", "n": w.n,
+                   "k": w.k, "k_prime": w.kprime, "sigma": w.sigma, "tol": w.tol, "preconditioner": "none (T = I)",
+                   "l2": "the whole problem fits in L2 (latency-bound)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iterations": info["iterations"], "max_rel_residual": info["max_rel_residual"],
+        "max_rel_eig_err_vs_closed_form": eig_err, "us_per_iteration": step_s / max(1, info["iterations"]) * 1e6,
+        "phases_ms_per_step": {p: prof[p]["ms"] / max(1, args.steps) for p in prof},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": w.n * w.kprime * 8,
+                "d2h_bytes_per_step": w.n * w.k * 8},
+        "gpu_launches": launches, "roofline": roofs[0] if roofs else None, "rooflines": roofs[1:],
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import operators, plhr as oplhr
+        Ao, _ = operators.model_operator(w)
+        t0, c0 = time.perf_counter(), time.process_time()
+        r = oplhr.bplhr(Ao, None, None, w.sigma, w.k, w.v0(), tol=w.tol, maxit=w.maxit)
+        t1, c1 = time.perf_counter(), time.process_time()
+        out["cpu_baseline"] = {"value": t1 - t0, "unit": "s", "cores": round((c1 - c0) / max(t1 - t0, 1e-9), 1),
+                               "kind": "oracle",
+                               "sample": "the full oracle solve of the same workload (%d iterations); cores = CPU "
+                                         "time / wall time (%d host cores present)" % (r.iterations, os.cpu_count())}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_gram_case(args, world, rank, local):
+    """The projected-Gram pass on its own (rows A6 of the hot path): every
+    arithmetic form of plhr_gram on seeded random families shaped like one
+    m = 64 launch of the mixed form (Z, AZ, Q as four blocks of 16 columns; Q
+    a positive row scaling of U = AZ - sigma Z, so that U^T Q is symmetric as
+    in the solver), n = --gram-case rows; CUDA events around each call (which
+    also allocates its partial-sum buffer on the stream and reads back one
+    status word).  Reports ms per call and the algorithmic bytes 3 n m x
+    element size over that time."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1408_0042_gb300 as plhr
+
+    torch.cuda.set_device(local)
+    n, ncols, sigma = args.gram_case, [16, 16, 16, 16], 1068.5711114200
+    m = sum(ncols)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(20140801)
+    res = {}
+    peaks = _peaks()
+    for form in [int(f) for f in args.gram_forms.split(",")]:
+        dt = torch.float64 if form in (plhr.GRAM_F64, plhr.GRAM_DW) else torch.float32
+        Z = [torch.randn(n, c, dtype=dt, device="cuda", generator=gen) for c in ncols]
+        A = [sigma * torch.randn(n, c, dtype=dt, device="cuda", generator=gen) for c in ncols]
+        wts = 1e-3 * (0.5 + torch.rand(n, 1, dtype=dt, device="cuda", generator=gen))
+        Q = [(wts * (a - sigma * z)).contiguous() for z, a in zip(Z, A)]
+        cs = torch.ones(m, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            plhr.gram(form, Z, A, Q, sigma, cs)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plhr.gram(form, Z, A, Q, sigma, cs)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        gbs = 3.0 * n * m * (8 if dt == torch.float64 else 4) / (ms / 1e3) / 1e9
+        res[{0: "f64", 1: "f32_pipes", 2: "double_word", 3: "f32_tensor_cores"}[form]] = {
+            "ms_per_call": ms, "GB_per_s": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"]}
+        del Z, A, Q
+        torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps({"gram_case": {"n": n, "m": m, "steps": args.steps, "warmup": args.warmup,
+                                        "peak_hbm_gbs": peaks["hbm_gbs"], "forms": res}}), flush=True)
+
+
 GRAD_METRIC = ("seconds per forward + backward: k = 8 eigenpairs nearest sigma and dL/dV of "
                "sum_k w_k lambda_k + sum_k |m (.) v_k|^2, 64^3 Hamiltonian")
 
@@ -655,8 +805,14 @@ def main():
     ap.add_argument("--profile-grid", type=int, default=0,
                     help="profiling case: N^3 grid of the same problem, fixed iteration count")
     ap.add_argument("--profile-iters", type=int, default=3)
-    ap.add_argument("--workload", choices=["lap3d_128cube_k10", "ham64_k8_grad"], default="lap3d_128cube_k10",
-                    help="ham64_k8_grad: forward + backward of the 64^3 differentiation workload")
+    ap.add_argument("--workload", choices=["lap3d_128cube_k10", "ham64_k8_grad", "lap2d_32x32_k4"],
+                    default="lap3d_128cube_k10",
+                    help="ham64_k8_grad: forward + backward of the 64^3 differentiation workload; "
+                         "lap2d_32x32_k4: the 32 x 32 Laplacian, T = I, FP64")
+    ap.add_argument("--gram-case", type=int, default=0,
+                    help="time plhr_gram alone on random families of n = GRAM_CASE rows, m = 64")
+    ap.add_argument("--gram-forms", default="0,1,2,3",
+                    help="with --gram-case: forms to time (0 FP64, 1 FP32 pipes, 2 double-word, 3 tensor cores)")
     ap.add_argument("--adjoint-prec", choices=["none", "tpa"], default="none",
                     help="preconditioner of the adjoint MINRES in the ham64_k8_grad workload")
     args = ap.parse_args()
@@ -669,8 +825,12 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, world, rank, local)
+        elif args.gram_case > 0:
+            run_gram_case(args, world, rank, local)
         elif args.workload == "ham64_k8_grad":
             run_grad(args, world, rank, local)
+        elif args.workload == "lap2d_32x32_k4":
+            run_lap2d(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

@@ -384,7 +384,9 @@ plhr_status plhr_tharm_extract(int m, int kp, int nv, const double* Gzz, const d
  *   - The call performs no cudaMalloc, cudaFree or other allocation.  Its first
  *     call on a device looks up the array's device address for that device
  *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: do not call this entry point after cudaDeviceReset on that
+ *     device (the array then lives at a new address).
  *   - All calls share the one array, which keeps the last call's contents (the
  *     solver writes every scratch element it reads, so nothing needs clearing).
  *     Calls whose work overlaps on the GPU, e.g. on two streams at once, race
@@ -404,7 +406,11 @@ plhr_status plhr_tharm_extract_noalloc(int m, int kp, int nv, const double* Gzz,
  *     out[m^2 .. 2 m^2)    = (U D)^T (Q D),   U = AZ - sigma Z
  *     out[2 m^2 .. 3 m^2)  = (Q D)^T (Z D)
  * (row-major m x m, device, FP64): the Grams of Eq. THarm_evp for B = I
- * (G_L = U^T T U = U^T Q, G_R = (T U)^T Z), Algorithm 2 steps 6-7.  Block b
+ * (G_L = U^T T U = U^T Q, G_R = (T U)^T Z), Algorithm 2 steps 6-7.  The
+ * first two are symmetric for Q = T U with T symmetric (and for Q = U): the
+ * pass forms their upper triangles and mirrors them (for an input with a
+ * non-symmetric U^T Q the lower triangle is the mirror of the upper).  The
+ * tensor-core form computes the full U^T Q.  Block b
  * has n rows, element (i, j) at Z[b][i * ldz[b] + j] (host arrays of device
  * pointers and leading dimensions).  Forms:
  *   PLHR_GRAM_F64     FP64 blocks, FP64 products and sums;
@@ -442,8 +448,8 @@ void plhr_profile_read(double* ms, long long* calls, int reset);
 /* work[9]: algorithmic work accumulated per phase since the last reset of
  * plhr_profile_read: stencil products and residual pass: grid points x
  * columns; preconditioner phases: finest-level grid points x columns of the
- * V-cycles; Gram phases: flops 2 n (m(m+1)/2 + 2 m^2) (Z^T Z upper triangle,
- * U^T Q, Q^T Z for an n x m trial basis); update phases: flops 2 n m k' per
+ * V-cycles; Gram phases: flops 2 n (m(m+1) + m^2) (the upper triangles of
+ * Z^T Z and U^T Q, which are symmetric, and Q^T Z for an n x m trial basis); update phases: flops 2 n m k' per
  * updated family; dense: 0. */
 void plhr_profile_work(double* work);
 /* bytes[9]: algorithmic HBM bytes accumulated per phase since the last reset

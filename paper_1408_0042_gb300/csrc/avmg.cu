@@ -55,8 +55,9 @@ __device__ __forceinline__ double lap_pt(const double* __restrict__ xp, int64_t 
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (total);        \
          e += (int64_t)gridDim.x * blockDim.x)
 
-// w_out = w_in + om * (r - (ih2 * L - shift) w_in)    (w_in may be null: w_out = om r)
-template <bool D3>
+// w_out = w_in + om * (r - (ih2 * L - shift) w_in)    (w_in may be null: w_out = om r);
+// SHIFT = false is the AV-MG sweep (shift 0, the expression without the shift term)
+template <bool D3, bool SHIFT>
 __global__ void __launch_bounds__(kT) k_rich_lap(G3 g, int nc, double ih2, double shift, double om,
                                                  const double* __restrict__ win, const double* __restrict__ r,
                                                  int64_t ldr, double* __restrict__ wout, int64_t total) {
@@ -69,7 +70,8 @@ __global__ void __launch_bounds__(kT) k_rich_lap(G3 g, int nc, double ih2, doubl
             int64_t ix, iy, iz;
             unflat(row, g, ix, iy, iz);
             const double* wp = win + row * nc + c;
-            v = wp[0] + om * (rv - (ih2 * lap_pt<D3>(wp, nc, ix, iy, iz, g) - shift * wp[0]));
+            if (SHIFT) v = wp[0] + om * (rv - (ih2 * lap_pt<D3>(wp, nc, ix, iy, iz, g) - shift * wp[0]));
+            else v = wp[0] + om * (rv - ih2 * lap_pt<D3>(wp, nc, ix, iy, iz, g));
         } else {
             v = om * rv;
         }
@@ -112,8 +114,8 @@ __global__ void __launch_bounds__(kT) k_poly_step(G3 g, int nc, double ih2, doub
     }
 }
 
-// res = r - (ih2 * L - shift) w
-template <bool D3>
+// res = r - (ih2 * L - shift) w  (SHIFT = false: r - ih2 * L w)
+template <bool D3, bool SHIFT>
 __global__ void __launch_bounds__(kT) k_resid_lap(G3 g, int nc, double ih2, double shift, const double* __restrict__ w,
                                                   const double* __restrict__ r, int64_t ldr,
                                                   double* __restrict__ out, int64_t total) {
@@ -122,8 +124,11 @@ __global__ void __launch_bounds__(kT) k_resid_lap(G3 g, int nc, double ih2, doub
         int c = (int)(e - row * nc);
         int64_t ix, iy, iz;
         unflat(row, g, ix, iy, iz);
-        out[row * nc + c] = r[row * ldr + c] - (ih2 * lap_pt<D3>(w + row * nc + c, nc, ix, iy, iz, g) -
-                                                shift * w[row * nc + c]);
+        if (SHIFT)
+            out[row * nc + c] = r[row * ldr + c] - (ih2 * lap_pt<D3>(w + row * nc + c, nc, ix, iy, iz, g) -
+                                                    shift * w[row * nc + c]);
+        else
+            out[row * nc + c] = r[row * ldr + c] - ih2 * lap_pt<D3>(w + row * nc + c, nc, ix, iy, iz, g);
     }
 }
 
@@ -311,8 +316,14 @@ cudaError_t rich_sweep(const MGLevel& L, double sigma, int nc, const double* win
     bool d3 = g.d == 3;
     const double shift = L.shifted ? sigma : 0.0;
     if (!L.poly || win == nullptr) {
-        if (d3) k_rich_lap<true><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), shift, L.omega, L.poly ? nullptr : win, r, ldr, wout, total);
-        else k_rich_lap<false><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), shift, L.omega, L.poly ? nullptr : win, r, ldr, wout, total);
+        const double* wi = L.poly ? nullptr : win;
+        if (L.shifted) {
+            if (d3) k_rich_lap<true, true><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), shift, L.omega, wi, r, ldr, wout, total);
+            else k_rich_lap<false, true><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), shift, L.omega, wi, r, ldr, wout, total);
+        } else {
+            if (d3) k_rich_lap<true, false><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), 0.0, L.omega, wi, r, ldr, wout, total);
+            else k_rich_lap<false, false><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), 0.0, L.omega, wi, r, ldr, wout, total);
+        }
         count_launches(1);
         return cudaGetLastError();
     }
@@ -332,9 +343,13 @@ cudaError_t level_residual(const MGLevel& L, double sigma, int nc, const double*
     G3 G = g3(g);
     bool d3 = g.d == 3;
     if (!L.poly) {
-        const double shift = L.shifted ? sigma : 0.0;
-        if (d3) k_resid_lap<true><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), shift, w, r, ldr, out, total);
-        else k_resid_lap<false><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), shift, w, r, ldr, out, total);
+        if (L.shifted) {
+            if (d3) k_resid_lap<true, true><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), sigma, w, r, ldr, out, total);
+            else k_resid_lap<false, true><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), sigma, w, r, ldr, out, total);
+        } else {
+            if (d3) k_resid_lap<true, false><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), 0.0, w, r, ldr, out, total);
+            else k_resid_lap<false, false><<<nblk(total), kT, 0, s>>>(G, nc, g.inv_h2(), 0.0, w, r, ldr, out, total);
+        }
         count_launches(1);
         return cudaGetLastError();
     }

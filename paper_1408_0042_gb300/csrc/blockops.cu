@@ -94,8 +94,9 @@ __device__ __forceinline__ void stage_rows(double* dst, int m, int64_t row0, int
 }
 
 // Gram tile bookkeeping: 4x4 register tiles over three m x m outputs.
-//   g = 0: Z^T BZ (upper tiles only), g = 1: U^T Q, g = 2: Q^T BZ, with
-//   U = AZ - sigma BZ; without a BZ family (B = I) BZ is Z
+//   g = 0: Z^T BZ and g = 1: U^T Q (upper tiles only, mirrored: both are
+//   symmetric, U^T Q = U^T T U), g = 2: Q^T BZ, with U = AZ - sigma BZ;
+//   without a BZ family (B = I) BZ is Z
 __global__ void __launch_bounds__(kGramThreads) k_gram(int64_t n, int m, int nb, FamPtrs Z, FamPtrs AZ, FamPtrs Q,
                                                        FamPtrs BZ, int has_b, int q_from_u, double sigma,
                                                        const double* __restrict__ csc,
@@ -107,22 +108,20 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(int64_t n, int m, int nb,
     double* sb = has_b ? sq + kGramRows * m : sz;   // [rows][m], B Z
     const int T = (m + 3) / 4;
     const int nt0 = T * (T + 1) / 2, nt1 = T * T;
-    const int ntiles = nt0 + 2 * nt1;
+    const int ntiles = 2 * nt0 + nt1;
     constexpr int kMaxTilesPerThread = 4;
     double acc[kMaxTilesPerThread][16];
     int tg[kMaxTilesPerThread], ti[kMaxTilesPerThread], tj[kMaxTilesPerThread];
     int my = 0;
     for (int t = threadIdx.x; t < ntiles && my < kMaxTilesPerThread; t += blockDim.x, ++my) {
-        if (t < nt0) {
-            // upper triangle tile enumeration
-            int r = 0, rem = t;
+        if (t < 2 * nt0) {
+            // upper triangle tile enumeration (outputs 0 and 1)
+            const int g = t < nt0 ? 0 : 1;
+            int r = 0, rem = t - g * nt0;
             while (rem >= T - r) { rem -= T - r; ++r; }
-            tg[my] = 0; ti[my] = r; tj[my] = r + rem;
-        } else if (t < nt0 + nt1) {
-            int u = t - nt0;
-            tg[my] = 1; ti[my] = u / T; tj[my] = u % T;
+            tg[my] = g; ti[my] = r; tj[my] = r + rem;
         } else {
-            int u = t - nt0 - nt1;
+            int u = t - 2 * nt0;
             tg[my] = 2; ti[my] = u / T; tj[my] = u % T;
         }
 #pragma unroll
@@ -187,7 +186,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(int64_t n, int m, int nb,
                 int i = i0 + x, j = j0 + y;
                 if (i < m && j < m) {
                     G[i * m + j] = acc[q][x * 4 + y];
-                    if (tg[q] == 0) G[j * m + i] = acc[q][x * 4 + y];
+                    if (tg[q] <= 1) G[j * m + i] = acc[q][x * 4 + y];
                 }
             }
     }
@@ -319,7 +318,7 @@ cudaError_t multi_gram_b(int64_t n, int nb, const Blk<const double>* Z, const Bl
 }
 
 int gram_max_m() {
-    // 4 tiles per thread * 256 threads >= ntiles(m) = T(T+1)/2 + 2T^2, T = ceil(m/4)
+    // 4 tiles per thread * 256 threads >= ntiles(m) = T(T+1) + T^2, T = ceil(m/4)
     return 64;
 }
 

@@ -26,23 +26,26 @@ __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.w
 
 // The 4x4 register tiles of the three m x m Gram outputs (T = ceil(m / 4)
 // tiles per side), numbered compactly: t < T(T+1)/2 are the upper tiles
-// ti <= tj of output 0 in row order, then the T^2 tiles of output 1 and of
-// output 2 in row order.  Returns false for t past the last tile.  Numbering
-// only the tiles that exist keeps the idle lanes of a warp at the end of the
-// list, so fewer warps issue when m < 64.
+// ti <= tj of output 0 (Z^T Z) in row order, the next T(T+1)/2 the upper
+// tiles of output 1 (U^T Q, symmetric in exact arithmetic: U^T T U, or U^T U
+// without T, so its upper triangle is mirrored like output 0's), then the T^2
+// tiles of output 2 in row order.  Returns false for t past the last tile.
+// Numbering only the tiles that exist keeps the idle lanes of a warp at the
+// end of the list, so fewer warps issue when m < 64.
 __host__ __device__ __forceinline__ bool gram_tile(int t, int T, int& g, int& ti, int& tj) {
-    const int nt0 = T * (T + 1) / 2, nt1 = T * T;
+    const int nt0 = T * (T + 1) / 2, nt2 = T * T;
     g = 0; ti = 0; tj = 0;
-    if (t < nt0) {
-        int r = 0, rem = t;
+    if (t < 2 * nt0) {
+        g = t < nt0 ? 0 : 1;
+        int r = 0, rem = t - g * nt0;
         while (rem >= T - r) { rem -= T - r; ++r; }
         ti = r; tj = r + rem;
         return true;
     }
-    if (t >= nt0 + 2 * nt1) return false;
-    const int u = t - nt0;
-    g = 1 + u / nt1;
-    ti = (u % nt1) / T; tj = u % T;
+    if (t >= 2 * nt0 + nt2) return false;
+    const int u = t - 2 * nt0;
+    g = 2;
+    ti = u / T; tj = u % T;
     return true;
 }
 int residual_blocks(int kp);

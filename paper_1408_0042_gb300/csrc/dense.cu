@@ -431,81 +431,119 @@ __device__ __noinline__ bool francis_eigenvalues(double* Hd, int n, long long* s
 }
 
 // ---------------------------------------------------------------- eigenvectors (one warp each)
-// Inverse iteration on the Hessenberg H0 for the eigenvalue lam: two solves of
-// (H0 - lam I) x = b (Gaussian elimination with adjacent-row pivoting, which
-// keeps the Hessenberg structure), starting from b = 1.  U (packed upper
-// triangle, complex) lives in the caller's shared memory.  x is returned normalised to
-// max |x_i| = 1.
-__device__ void inverse_iteration(const double* H0, int n, cplx lam, cplx* x, cplx* U, cplx* cur, cplx* nxt,
-                                  double tiny) {
+// Complex double-word arithmetic for the per-unit eigenvector work: each
+// step of a triangular factorisation or solve is a short serial chain, and
+// on GB300 an FP64 warp instruction holds the FP64 pipe for 64 cycles, so
+// the chains run several times faster on the FP32 pipes in double-word form
+// (~48-bit significands, the accuracy of the QR iteration that supplies the
+// shifts).  The operands are scaled by a power of two to unit norm first so
+// that they stay inside FP32's exponent range.
+struct cdw {
+    dw re, im;
+};
+__device__ __forceinline__ cdw cdw_mul(cdw a, cdw b) {
+    return {dw_sub(dw_mul(a.re, b.re), dw_mul(a.im, b.im)), dw_add(dw_mul(a.re, b.im), dw_mul(a.im, b.re))};
+}
+__device__ __forceinline__ cdw cdw_sub(cdw a, cdw b) { return {dw_sub(a.re, b.re), dw_sub(a.im, b.im)}; }
+__device__ __forceinline__ float cdw_abs1(cdw a) { return fabsf(a.re.hi) + fabsf(a.im.hi); }
+// 1 / b, the denominator scaled by a power of two first (no under- or overflow)
+__device__ __forceinline__ cdw cdw_recip(cdw b) {
+    const float sc = pow2_inverse_of(fmaxf(fabsf(b.re.hi), fabsf(b.im.hi)));
+    const dw r = dw_mul_pow2(b.re, sc), i = dw_mul_pow2(b.im, sc);
+    const dw den = dw_add(dw_mul(r, r), dw_mul(i, i));
+    const dw inv = dw_div(dw_make(1.0f), den);
+    return {dw_mul_pow2(dw_mul(r, inv), sc), dw_mul_pow2(dw_neg(dw_mul(i, inv)), sc)};
+}
+
+// Inverse iteration on the Hessenberg H0 (FP64, scaled here by `down`, a power
+// of two) for the eigenvalue lam (same scale): (H0 - lam I) is factored once
+// by Gaussian elimination with adjacent-row pivoting (keeps the Hessenberg
+// structure; multipliers, swaps, the packed upper factor U and the
+// reciprocals of its pivots kept), then two solves starting from b = 1, each
+// normalised to max |x_i| = 1.  Column-oriented back substitution: one
+// reciprocal multiply on the critical path per step, the updates in parallel.
+
+__device__ void inverse_iteration_dw(const double* H0, int n, double down, cdw lam, cdw* x, cdw* U, cdw* mult,
+                                     cdw* rpiv, int* swp, cdw* cur, cdw* nxt, float tiny) {
     const int lane = threadIdx.x & 31;
-    for (int i = lane; i < n; i += 32) x[i] = {1.0, 0.0};
+    const cdw zero = {dw_make(0.0f), dw_make(0.0f)};
+    auto hs = [&](int r, int c) -> cdw {
+        dw v = dw_from_double(H0[r * LDS + c] * down);
+        cdw e = {v, dw_make(0.0f)};
+        if (r == c) e = cdw_sub(e, lam);
+        return e;
+    };
+    for (int j = lane; j < n; j += 32) cur[j] = hs(0, j);
+    wsync();
+    for (int k = 0; k < n - 1; ++k) {
+        for (int j = k + lane; j < n; j += 32) nxt[j] = (j >= k) ? hs(k + 1, j) : zero;
+        wsync();
+        const bool swap = cdw_abs1(nxt[k]) > cdw_abs1(cur[k]);
+        wsync();
+        if (swap) {
+            for (int j = k + lane; j < n; j += 32) { const cdw t2 = cur[j]; cur[j] = nxt[j]; nxt[j] = t2; }
+        }
+        wsync();
+        cdw piv = cur[k];
+        if (cdw_abs1(piv) < tiny) piv = {dw_make(tiny), dw_make(0.0f)};
+        const cdw rp = cdw_recip(piv);
+        const cdw f = cdw_mul(nxt[k], rp);
+        cdw* urow = U + (k * n - (k * (k - 1)) / 2);   // row k holds columns k..n-1
+        for (int j = k + lane; j < n; j += 32) {
+            urow[j - k] = (j == k) ? piv : cur[j];
+            if (j > k) nxt[j] = cdw_sub(nxt[j], cdw_mul(f, cur[j]));
+        }
+        if (lane == 0) { mult[k] = f; rpiv[k] = rp; swp[k] = swap ? 1 : 0; }
+        wsync();
+        for (int j = k + 1 + lane; j < n; j += 32) cur[j] = nxt[j];
+        wsync();
+    }
+    {
+        cdw piv = cur[n - 1];
+        if (cdw_abs1(piv) < tiny) piv = {dw_make(tiny), dw_make(0.0f)};
+        if (lane == 0) {
+            U[(n - 1) * n - ((n - 1) * (n - 2)) / 2] = piv;
+            rpiv[n - 1] = cdw_recip(piv);
+        }
+    }
+    for (int i = lane; i < n; i += 32) x[i] = {dw_make(1.0f), dw_make(0.0f)};
     wsync();
     for (int iter = 0; iter < 2; ++iter) {
-        // cur = row 0 of (H0 - lam I)
-        for (int j = lane; j < n; j += 32) cur[j] = {H0[j] - (j == 0 ? lam.re : 0.0), j == 0 ? -lam.im : 0.0};
-        cplx bcur = x[0];
-        wsync();
-        for (int k = 0; k < n - 1; ++k) {
-            // nxt = row k+1 (columns >= k)
-            for (int j = k + lane; j < n; j += 32)
-                nxt[j] = {H0[(k + 1) * LDS + j] - (j == k + 1 ? lam.re : 0.0), j == k + 1 ? -lam.im : 0.0};
-            cplx bnxt = x[k + 1];
-            wsync();
-            const bool swap = cabs1(nxt[k]) > cabs1(cur[k]);
-            wsync();
-            if (swap) {
-                for (int j = k + lane; j < n; j += 32) { cplx t2 = cur[j]; cur[j] = nxt[j]; nxt[j] = t2; }
-                cplx t2 = bcur; bcur = bnxt; bnxt = t2;
+        // forward: the recorded row swaps and eliminations applied to b = x
+        if (lane == 0) {
+            for (int k = 0; k < n - 1; ++k) {
+                if (swp[k]) { const cdw t2 = x[k]; x[k] = x[k + 1]; x[k + 1] = t2; }
+                x[k + 1] = cdw_sub(x[k + 1], cdw_mul(mult[k], x[k]));
             }
-            wsync();
-            cplx piv = cur[k];
-            if (cabs1(piv) < tiny) piv = {tiny, 0.0};
-            const cplx f = cdiv(nxt[k], piv);
-            // store U row k, eliminate
-            cplx* urow = U + (k * n - (k * (k - 1)) / 2);   // row k holds columns k..n-1
-            for (int j = k + lane; j < n; j += 32) {
-                urow[j - k] = (j == k) ? piv : cur[j];
-                if (j > k) nxt[j] = csub(nxt[j], cmul(f, cur[j]));
-            }
-            x[k] = bcur;   // all lanes hold the same value; x[k] is rhs after elimination
-            bnxt = csub(bnxt, cmul(f, bcur));
-            wsync();
-            for (int j = k + 1 + lane; j < n; j += 32) cur[j] = nxt[j];
-            bcur = bnxt;
-            wsync();
-        }
-        {
-            cplx piv = cur[n - 1];
-            if (cabs1(piv) < tiny) piv = {tiny, 0.0};
-            if (lane == 0) U[(n - 1) * n - ((n - 1) * (n - 2)) / 2] = piv;
-            x[n - 1] = bcur;
         }
         wsync();
-        // back substitution U x = b
+        // backward: x_i = b_i / U_ii, then b_j -= U_ji x_i for j < i
         for (int i = n - 1; i >= 0; --i) {
-            const cplx* urow = U + (i * n - (i * (i - 1)) / 2);
-            double sr = 0.0, si = 0.0;
-            for (int j = i + 1 + lane; j < n; j += 32) {
-                cplx p = cmul(urow[j - i], x[j]);
-                sr += p.re;
-                si += p.im;
-            }
-            sr = warp_sum(sr);
-            si = warp_sum(si);
-            cplx xi_ = cdiv(csub(x[i], cplx{sr, si}), urow[0]);
+            const cdw xi_ = cdw_mul(x[i], rpiv[i]);
             wsync();
+            for (int j = lane; j < i; j += 32) {
+                const cdw u = U[j * n - (j * (j - 1)) / 2 + (i - j)];
+                x[j] = cdw_sub(x[j], cdw_mul(u, xi_));
+            }
             if (lane == 0) x[i] = xi_;
             wsync();
         }
-        // normalise
-        double mx = 0.0;
-        for (int j = lane; j < n; j += 32) mx = fmax(mx, cabs1(x[j]));
-        mx = warp_max(mx);
-        if (!(mx > 0.0) || !isfinite(mx)) mx = 1.0;
-        for (int j = lane; j < n; j += 32) x[j] = cscale(x[j], 1.0 / mx);
+        // normalise to max |x_i| = 1 (scale by a power of two, then exactly)
+        float mx = 0.0f;
+        for (int j = lane; j < n; j += 32) mx = fmaxf(mx, cdw_abs1(x[j]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float sc = (mx > 0.0f && isfinite(mx)) ? pow2_inverse_of(mx) : 1.0f;
+        for (int j = lane; j < n; j += 32) x[j] = {dw_mul_pow2(x[j].re, sc), dw_mul_pow2(x[j].im, sc)};
         wsync();
     }
+}
+
+__device__ __forceinline__ dw warp_sum_dw(dw v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const dw t = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = dw_add(v, t);
+    }
+    return v;
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -766,7 +804,10 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
         for (int u = 0; u < nsel; ++u) {
             double* yr = Yre + u * MAXM;
             double* yi = Yim + u * MAXM;
-            if (S.nclose[u] > 0) {
+            // two passes of modified Gram-Schmidt against the earlier members
+            // of the cluster (the second restores the orthogonality the first
+            // loses when most of y lies in their span)
+            for (int pass = 0; pass < 2 && S.nclose[u] > 0; ++pass) {
                 const int e = S.order[u];
                 const double re = S.eig_re[e], im = S.eig_im[e];
                 const double mag = fmax(fabs(re) + fabs(im), 1e-300);
@@ -894,74 +935,97 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
 // then y = L^{-T} z in the orthonormal basis, into Yre[u], Yim[u].  The units
 // run as separate CTAs on separate SMs (the FP64 work of one unit is serial).
 // shared memory of k_eigvec: H0, the Cholesky factor L of G_L and the
-// Householder vectors (MAXM x LDS each), the reflector coefficients, the
-// packed LU factor of the inverse iteration and the result y (re, im)
-constexpr size_t kEigvecShmDoubles = 3 * (size_t)MAXM * LDS + MAXM + 2 * kLuComplex + 2 * MAXM;
+// Householder vectors (MAXM x LDS each), the reflector coefficients, then the
+// double-word working set: the packed LU factor of the inverse iteration,
+// its multipliers, pivot reciprocals and row swaps, the vector and two work
+// rows, and the result y (re, im)
+struct EigvecDw {
+    cdw U[kLuComplex];
+    cdw mult[MAXM], rpiv[MAXM], x[MAXM], cur[MAXM], nxt[MAXM];
+    dw yr[MAXM], yi[MAXM];
+    int swp[MAXM];
+};
+constexpr size_t kEigvecShmDoubles = 3 * (size_t)MAXM * LDS + MAXM + (sizeof(EigvecDw) + 7) / 8;
 
 __global__ void __launch_bounds__(32) k_eigvec(DenseArgs a) {
     extern __shared__ __align__(16) double sh0[];
     double* sL = sh0 + MAXM * LDS;
     double* sV = sL + MAXM * LDS;
     double* sbeta = sV + MAXM * LDS;
-    cplx* U = reinterpret_cast<cplx*>(sbeta + MAXM);
-    double* syr = reinterpret_cast<double*>(U + kLuComplex);
-    double* syi = syr + MAXM;
+    EigvecDw* E = reinterpret_cast<EigvecDw*>(sbeta + MAXM);
     const Smem* G = state_of(a);
     if (G->ints[6]) return;
     const int u = blockIdx.x;
     const int nsel = G->ints[3], nk = G->ints[0];
     if (u >= nsel) return;
     const int lane = threadIdx.x;
-    __shared__ cplx x[MAXM], cur[MAXM], nxt[MAXM];
-    double hn = 0.0;
+    double hn = 0.0, ln = 0.0;
     for (int i = lane; i < nk * LDS; i += 32) {
         const double v = G->H0[i];
         sh0[i] = v;
         sL[i] = G->B[i];
         sV[i] = G->Vh[i];
-        if (i % LDS < nk) hn = fmax(hn, fabs(v));
+        if (i % LDS < nk) {
+            hn = fmax(hn, fabs(v));
+            ln = fmax(ln, fabs(G->B[i]));
+        }
     }
     for (int i = lane; i < nk; i += 32) sbeta[i] = G->beta[i];
     hn = warp_max(hn);
-    const double tiny = DBL_EPSILON * (hn > 0.0 ? hn : 1.0);
+    ln = warp_max(ln);
     __syncwarp();
+    // H0 and lam scaled by a power of two to unit norm
+    const double down = ldexp(1.0, -(hn > 0.0 ? ilogb(hn) : 0));
     const int e = G->order[u];
-    cplx lam = {G->eig_re[e], G->eig_im[e]};
-    if (G->nclose[u] > 0) lam = cscale(lam, 1.0 + 1e-10 * G->nclose[u]);
-    inverse_iteration(sh0, nk, lam, x, U, cur, nxt, tiny);
+    double lre = G->eig_re[e], lim = G->eig_im[e];
+    if (G->nclose[u] > 0) { lre *= 1.0 + 1e-10 * G->nclose[u]; lim *= 1.0 + 1e-10 * G->nclose[u]; }
+    const cdw lam = {dw_from_double(lre * down), dw_from_double(lim * down)};
+    const float tiny = 0x1p-46f;   // a few units of the double-word precision of the unit-norm matrix
+    inverse_iteration_dw(sh0, nk, down, lam, E->x, E->U, E->mult, E->rpiv, E->swp, E->cur, E->nxt, tiny);
     // z = Q x with Q = H_0 H_1 ... (reflectors applied last-first)
     for (int k = nk - 3; k >= 0; --k) {
-        const double b = sbeta[k];
-        if (b == 0.0) continue;
+        const double bk = sbeta[k];
+        if (bk == 0.0) continue;
         const double* v = sV + k * LDS;
-        double sr = 0.0, si = 0.0;
-        for (int i = k + 1 + lane; i < nk; i += 32) { sr += v[i] * x[i].re; si += v[i] * x[i].im; }
-        sr = warp_sum(sr) * b;
-        si = warp_sum(si) * b;
+        dw sr = dw_make(0.0f), si = dw_make(0.0f);
+        for (int i = k + 1 + lane; i < nk; i += 32) {
+            const dw vi = dw_from_double(v[i]);
+            sr = dw_add(sr, dw_mul(vi, E->x[i].re));
+            si = dw_add(si, dw_mul(vi, E->x[i].im));
+        }
+        const dw b = dw_from_double(bk);
+        sr = dw_mul(warp_sum_dw(sr), b);
+        si = dw_mul(warp_sum_dw(si), b);
         __syncwarp();
-        for (int i = k + 1 + lane; i < nk; i += 32) { x[i].re -= sr * v[i]; x[i].im -= si * v[i]; }
+        for (int i = k + 1 + lane; i < nk; i += 32) {
+            const dw vi = dw_from_double(v[i]);
+            E->x[i].re = dw_sub(E->x[i].re, dw_mul(sr, vi));
+            E->x[i].im = dw_sub(E->x[i].im, dw_mul(si, vi));
+        }
         __syncwarp();
     }
-    // y = L^{-T} z  (back substitution with the lower factor L)
+    // y = L^{-T} z: column-oriented back substitution with the lower factor L
+    // (scaled to unit norm; y then carries the inverse scale, undone below)
+    const double ld = ldexp(1.0, -(ln > 0.0 ? ilogb(ln) : 0));
+    for (int i = lane; i < nk; i += 32) { E->yr[i] = E->x[i].re; E->yi[i] = E->x[i].im; }
+    __syncwarp();
     for (int i = nk - 1; i >= 0; --i) {
-        double sr = 0.0, si = 0.0;
-        for (int l = i + 1 + lane; l < nk; l += 32) {
-            sr += sL[l * LDS + i] * syr[l];
-            si += sL[l * LDS + i] * syi[l];
+        const dw rl = dw_div(dw_make(1.0f), dw_from_double(sL[i * LDS + i] * ld));
+        const dw yr = dw_mul(E->yr[i], rl), yi = dw_mul(E->yi[i], rl);
+        __syncwarp();
+        for (int j = lane; j < i; j += 32) {
+            const dw l = dw_from_double(sL[i * LDS + j] * ld);
+            E->yr[j] = dw_sub(E->yr[j], dw_mul(l, yr));
+            E->yi[j] = dw_sub(E->yi[j], dw_mul(l, yi));
         }
-        sr = warp_sum(sr);
-        si = warp_sum(si);
-        if (lane == 0) {
-            syr[i] = (x[i].re - sr) / sL[i * LDS + i];
-            syi[i] = (x[i].im - si) / sL[i * LDS + i];
-        }
+        if (lane == 0) { E->yr[i] = yr; E->yi[i] = yi; }
         __syncwarp();
     }
     double* yr = a.work + (size_t)u * MAXM;
     double* yi = a.work + (size_t)MAXM * MAXM + (size_t)u * MAXM;
     for (int i = lane; i < nk; i += 32) {
-        yr[i] = syr[i];
-        yi[i] = syi[i];
+        yr[i] = dw_to_double(E->yr[i]) * ld;
+        yi[i] = dw_to_double(E->yi[i]) * ld;
     }
 }
 

@@ -86,8 +86,8 @@ __device__ void stage_dw(dw* sz, dw* su, dw* sq, const double* rz, const double*
     }
 }
 
-// 768 threads: thread t owns tile t of gram_tile (output g = 0: Z^T Z,
-// written for ti <= tj and mirrored; 1: U^T Q; 2: Q^T Z); at most 648 tiles
+// 768 threads: thread t owns tile t of gram_tile (outputs g = 0: Z^T Z and
+// 1: U^T Q written for ti <= tj and mirrored; 2: Q^T Z); at most 528 tiles
 // (mp <= 64), every thread fetches and stages.  The rows of the next chunk
 // are copied asynchronously while the current one is multiplied.
 __global__ void __launch_bounds__(kDwThreads, 1) k_gram_dw(int64_t n, int m, int mp, int nb, FamD Z, FamD AZ, FamD Q,
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_gram_dw(int64_t n, int m, int
             if (i < m && j < m) {
                 const double v = (double)hi[x * 4 + y] + (double)lo[x * 4 + y];
                 out[i * m + j] = v;
-                if (g == 0) out[j * m + i] = v;
+                if (g <= 1) out[j * m + i] = v;
             }
         }
 }

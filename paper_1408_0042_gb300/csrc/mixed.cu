@@ -162,8 +162,8 @@ __device__ __forceinline__ void put_tile(double* G, int m, int i0, int j0, const
         }
 }
 
-// 768 threads: thread t owns tile t of gram_tile (output g = 0: Z^T Z,
-// written for ti <= tj and mirrored; 1: U^T Q; 2: Q^T Z); at most 648 tiles
+// 768 threads: thread t owns tile t of gram_tile (outputs g = 0: Z^T Z and
+// 1: U^T Q written for ti <= tj and mirrored; 2: Q^T Z); at most 528 tiles
 // (mp <= 64).  One tile per thread keeps ~70 registers, and all 24 warps
 // stage, which hides the latency of the staging loads.
 constexpr int kGramMxThreads = 768;
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kGramMxThreads, 1) k_gram_mx(int64_t n, int m,
     cp_async_wait_all();
     if (!act) return;
     double* out = partial + (int64_t)blockIdx.x * 3 * m * m + (int64_t)g * m * m;
-    put_tile(out, m, 4 * ti, 4 * tj, hi, lo, g == 0);
+    put_tile(out, m, 4 * ti, 4 * tj, hi, lo, g <= 1);
 }
 
 // out[j] = sum_b partial[b * width + j], fixed order, many CTAs
@@ -397,6 +397,55 @@ __global__ void __launch_bounds__(kSt) k_lap32(Ln g, const float* __restrict__ x
     if (o2) o2[row * ld2 + c] = a - sig * xv;
 }
 
+// the same with four consecutive columns per thread (16-byte loads and
+// stores; nc, the leading dimensions and the base addresses multiples of 4
+// floats): a CTA covers 1024 elements of one x-line
+template <bool D3>
+__global__ void __launch_bounds__(kSt) k_lap32v(Ln g, const float* __restrict__ x, int64_t ldx, float* __restrict__ ax,
+                                                int64_t ldax, float* __restrict__ o1, int64_t ld1,
+                                                const double* __restrict__ lam, float* __restrict__ o2, int64_t ld2,
+                                                float sig) {
+    const int nq = g.nc >> 2;
+    const int t = blockIdx.x * kSt + threadIdx.x;
+    if (t >= g.nx * nq) return;
+    const int ix = t / nq, c = (t - ix * nq) * 4;
+    const int iy = blockIdx.y, iz = blockIdx.z;
+    const int64_t row = ((int64_t)iz * g.ny + iy) * g.nx + ix;
+    const float* xp = x + row * ldx + c;
+    const int64_t sy = ldx * g.nx, sz = sy * g.ny;
+    const float4 xv = *reinterpret_cast<const float4*>(xp);
+    float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    // differences x_c - x_nb per direction, summed in the order of k_lap32
+    auto diff = [&](bool in, int64_t off) -> float4 {
+        if (!in) return xv;
+        const float4 nb = *reinterpret_cast<const float4*>(xp + off);
+        return make_float4(xv.x - nb.x, xv.y - nb.y, xv.z - nb.z, xv.w - nb.w);
+    };
+    const float4 a0 = diff(ix > 0, -ldx), a1 = diff(ix < g.nx - 1, ldx);
+    const float4 b0 = diff(iy > 0, -sy), b1 = diff(iy < g.ny - 1, sy);
+    s.x = (a0.x + a1.x) + (b0.x + b1.x);
+    s.y = (a0.y + a1.y) + (b0.y + b1.y);
+    s.z = (a0.z + a1.z) + (b0.z + b1.z);
+    s.w = (a0.w + a1.w) + (b0.w + b1.w);
+    if (D3) {
+        const float4 c0 = diff(iz > 0, -sz), c1 = diff(iz < g.nz - 1, sz);
+        s.x += c0.x + c1.x;
+        s.y += c0.y + c1.y;
+        s.z += c0.z + c1.z;
+        s.w += c0.w + c1.w;
+    }
+    const float4 a = make_float4(g.ih2 * s.x, g.ih2 * s.y, g.ih2 * s.z, g.ih2 * s.w);
+    if (ax) *reinterpret_cast<float4*>(ax + row * ldax + c) = a;
+    if (o1) {
+        const float l0 = (float)lam[c], l1 = (float)lam[c + 1], l2 = (float)lam[c + 2], l3 = (float)lam[c + 3];
+        *reinterpret_cast<float4*>(o1 + row * ld1 + c) =
+            make_float4(a.x - l0 * xv.x, a.y - l1 * xv.y, a.z - l2 * xv.z, a.w - l3 * xv.w);
+    }
+    if (o2)
+        *reinterpret_cast<float4*>(o2 + row * ld2 + c) =
+            make_float4(a.x - sig * xv.x, a.y - sig * xv.y, a.z - sig * xv.z, a.w - sig * xv.w);
+}
+
 // Y (FP64, ldy) = X (FP32, ldx), n x nc
 __global__ void k_widen(int64_t n, int nc, const float* __restrict__ X, int64_t ldx, double* __restrict__ Y,
                         int64_t ldy) {
@@ -472,6 +521,16 @@ cudaError_t lap32_apply_shifts(const Grid& g, int nc, const float* x, int64_t ld
                                int64_t ld1, const double* lam, float* o2, int64_t ld2, double sig, cudaStream_t s) {
     if (nc <= 0) return cudaSuccess;
     Ln L{(int)g.nx, (int)g.ny, (int)g.nz, nc, (float)g.inv_h2()};
+    auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const bool vec = nc % 4 == 0 && ldx % 4 == 0 && a16(x) && (!ax || (ldax % 4 == 0 && a16(ax))) &&
+                     (!o1 || (ld1 % 4 == 0 && a16(o1))) && (!o2 || (ld2 % 4 == 0 && a16(o2)));
+    if (vec) {
+        dim3 gv((unsigned)((g.nx * (nc / 4) + kSt - 1) / kSt), (unsigned)g.ny, (unsigned)g.nz);
+        if (g.d == 3) k_lap32v<true><<<gv, kSt, 0, s>>>(L, x, ldx, ax, ldax, o1, ld1, lam, o2, ld2, (float)sig);
+        else k_lap32v<false><<<gv, kSt, 0, s>>>(L, x, ldx, ax, ldax, o1, ld1, lam, o2, ld2, (float)sig);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     dim3 gr((unsigned)((g.nx * nc + kSt - 1) / kSt), (unsigned)g.ny, (unsigned)g.nz);
     if (g.d == 3) k_lap32<true><<<gr, kSt, 0, s>>>(L, x, ldx, ax, ldax, o1, ld1, lam, o2, ld2, (float)sig);
     else k_lap32<false><<<gr, kSt, 0, s>>>(L, x, ldx, ax, ldax, o1, ld1, lam, o2, ld2, (float)sig);

@@ -57,9 +57,9 @@ struct HostStatus {
     int pad;
 };
 
-// flops of one multi-Gram pass over an n x m trial basis: Z^T Z (upper
-// triangle), U^T Q and Q^T Z
-double gram_flops(int64_t n, int m) { return 2.0 * (double)n * (m * (m + 1) / 2.0 + 2.0 * m * m); }
+// flops of one multi-Gram pass over an n x m trial basis: Z^T Z and U^T Q
+// (upper triangles; both symmetric) and Q^T Z
+double gram_flops(int64_t n, int m) { return 2.0 * (double)n * ((double)m * (m + 1) + (double)m * m); }
 
 // Algorithmic HBM bytes of one preconditioner application on nc columns of
 // eb-byte elements: for AV-MG 14.25 passes per level above the coarsest (the
@@ -466,7 +466,15 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
                     PLHR_TRY_CUDA(cudaMemcpy2DAsync(V + j2, sizeof(double) * kp, Rc + j2, sizeof(double) * kp,
                                                     sizeof(double), n, cudaMemcpyDeviceToDevice, s));
         }
-        if (np) PLHR_TRY_CUDA(widen_block(n, kp, P32, kp, P, kp, s));
+        if (np) {
+            PLHR_TRY_CUDA(widen_block(n, kp, P32, kp, P, kp, s));
+            // a restarted column drops its search direction too: the old
+            // direction would bring the FP32 guard content straight back into
+            // the first FP64 projection, ahead of what the random column holds
+            for (int j2 = 0; j2 < kp; ++j2)
+                if (restart[j2])
+                    PLHR_TRY_CUDA(cudaMemset2DAsync(P + j2, sizeof(double) * kp, 0, sizeof(double), n, s));
+        }
         PLHR_TRY_CUDA(lap_apply_shifts(g, kp, V, kp, AV, kp, nullptr, 0, nullptr, X3, kp, sigma, s));
         if (T) PLHR_TRY(applyT(kp, X3, kp, QV));
         if (np) {
@@ -741,26 +749,32 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         }
 
         // -------------------------------------------- Grams over Z = [V W S P] (or [V W P]), AZ, Q (steps 6-7)
-        const int nb = (sv ? 3 : 2) + (np ? 1 : 0);
-        const int m = kp + (sv ? 2 : 1) * na + np;
-        last_m = m;
-        Blk<const double> zb[4] = {{V, kp, kp}, {W, na, na}, {S, lds, na}, {P, kp, np}};
-        Blk<const double> ab[4] = {{AV, kp, kp}, {AW, na, na}, {AS, na, na}, {AP, kp, np}};
-        Blk<const double> qb[4] = {{QV, kp, kp}, {QW, ldqw, na}, {QS, na, na}, {QP, kp, np}};
-        Blk<const double> bzb[4] = {{BV, kp, kp}, {BW, na, na}, {BS, na, na}, {BP, kp, np}};
-        if (!sv) {   // drop the S family: [V W P]
-            zb[2] = zb[3];
-            ab[2] = ab[3];
-            qb[2] = qb[3];
-            bzb[2] = bzb[3];
-        }
-        PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
+        // Recovery when the projected problem fails: first the carried images
+        // T(A - sigma B)V, T(A - sigma B)P are recomputed explicitly (they may
+        // have drifted), then the step is taken without the P block (a restart
+        // of the search directions, trial space [V W S]).
+        int nb = 0, m = 0, np_use = np;
+        Blk<const double> zb[4], ab[4], qb[4], bzb[4];
         DenseArgs da;
-        da.m = m; da.kp = kp; da.nv = kp;
-        da.Gzz = grams; da.Guq = grams + m * m; da.Gqz = grams + 2 * m * m;
-        da.colscale = colscale; da.work = dwork; da.Cp = Cp; da.Cvv = Cvv; da.tags = tags; da.tag_partner = partner;
-        da.xi = xi; da.out_int = dstat + 3; da.clk = nullptr;
-        for (int pass = 0; pass < 2; ++pass) {
+        PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
+        for (int pass = 0; pass < 3; ++pass) {
+            nb = (sv ? 3 : 2) + (np_use ? 1 : 0);
+            m = kp + (sv ? 2 : 1) * na + np_use;
+            last_m = m;
+            zb[0] = {V, kp, kp}; zb[1] = {W, na, na}; zb[2] = {S, lds, na}; zb[3] = {P, kp, np_use};
+            ab[0] = {AV, kp, kp}; ab[1] = {AW, na, na}; ab[2] = {AS, na, na}; ab[3] = {AP, kp, np_use};
+            qb[0] = {QV, kp, kp}; qb[1] = {QW, ldqw, na}; qb[2] = {QS, na, na}; qb[3] = {QP, kp, np_use};
+            bzb[0] = {BV, kp, kp}; bzb[1] = {BW, na, na}; bzb[2] = {BS, na, na}; bzb[3] = {BP, kp, np_use};
+            if (!sv) {   // drop the S family: [V W P]
+                zb[2] = zb[3];
+                ab[2] = ab[3];
+                qb[2] = qb[3];
+                bzb[2] = bzb[3];
+            }
+            da.m = m; da.kp = kp; da.nv = kp;
+            da.Gzz = grams; da.Guq = grams + m * m; da.Gqz = grams + 2 * m * m;
+            da.colscale = colscale; da.work = dwork; da.Cp = Cp; da.Cvv = Cvv; da.tags = tags; da.tag_partner = partner;
+            da.xi = xi; da.out_int = dstat + 3; da.clk = nullptr;
             {
                 PhaseScope ps(PH_GRAM, s, gram_flops(n, m), 8.0 * n * m * ((thq ? 3 : 2) + (hasB ? 1 : 0)));
                 if (dwf)
@@ -776,15 +790,18 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             }
             PLHR_TRY_CUDA(cudaMemcpyAsync(hs->dense, dstat + 3, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
             PLHR_TRY_CUDA(cudaStreamSynchronize(s));
-            if (hs->dense[0] == kDenseOK || !thq || pass == 1) break;
-            // recovery: the carried images T(A - sigma B)V, T(A - sigma B)P have
-            // drifted; recompute them explicitly and project again
-            PLHR_TRY(prod(kp, V, kp, AV, kp, BV, kp, nullptr, 0, nullptr, X3, kp));
-            PLHR_TRY(applyT(kp, X3, kp, QV));
-            if (np) {
-                PLHR_TRY(prod(kp, P, kp, AP, kp, BP, kp, nullptr, 0, nullptr, X3, kp));
-                PLHR_TRY(applyT(kp, X3, kp, QP));
+            if (hs->dense[0] == kDenseOK) break;
+            if (pass == 0 && thq) {
+                PLHR_TRY(prod(kp, V, kp, AV, kp, BV, kp, nullptr, 0, nullptr, X3, kp));
+                PLHR_TRY(applyT(kp, X3, kp, QV));
+                if (np) {
+                    PLHR_TRY(prod(kp, P, kp, AP, kp, BP, kp, nullptr, 0, nullptr, X3, kp));
+                    PLHR_TRY(applyT(kp, X3, kp, QP));
+                }
+                continue;
             }
+            if (np_use == 0) break;
+            np_use = 0;
         }
         last_kept = hs->dense[1];
         if (hs->dense[0] != kDenseOK) {

@@ -24,20 +24,26 @@ def plhr():
 SIGMA = 1068.5711114200
 
 
-def _blocks(n, ncols, seed, dtype, strided):
+def _blocks(n, ncols, seed, dtype, strided, cs=None):
     """Random blocks shaped like the solver's families: Z of unit-order
     entries, AZ ~ sigma-sized (so that U = AZ - sigma Z has no systematic
-    cancellation), Q smaller; block 2 lives in a wider array (ld > ncols)."""
+    cancellation), and Q = T U for a positive diagonal T (rows scaled by
+    weights in [0.5, 1.5] x 1e-3), so that U^T Q is symmetric as in the solver
+    (U^T T U); block 2 lives in a wider array (ld > ncols).  cs: the column
+    scales the kernels apply (Q is built from U of the scaled columns and
+    unscaled again, so that the scaled U^T Q is symmetric)."""
     rng = np.random.default_rng(seed)
-    out = []
-    for fam_scale in (1.0, SIGMA, 1e-3):
-        fam = []
+    Zs, As = [], []
+    for fam_scale, fam in ((1.0, Zs), (SIGMA, As)):
         for b, nc in enumerate(ncols):
             wide = nc + (3 if (strided and b == 2) else 0)
-            X = (rng.standard_normal((n, wide)) * fam_scale).astype(dtype)
-            fam.append(X)
-        out.append(fam)
-    return out
+            fam.append((rng.standard_normal((n, wide)) * fam_scale).astype(dtype))
+    wts = 1e-3 * rng.uniform(0.5, 1.5, n)[:, None]
+    Qs = []
+    for Z, A in zip(Zs, As):
+        U = A.astype(np.float64) - SIGMA * Z.astype(np.float64)
+        Qs.append((wts * U).astype(dtype))
+    return Zs, As, Qs
 
 
 def _ref(Zs, As, Qs, ncols, cs, sigma, f32):
