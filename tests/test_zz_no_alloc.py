@@ -87,6 +87,30 @@ def test_noalloc_matches_allocating_entry_point_on_consecutive_calls(lib):
         np.testing.assert_allclose(got["Cvv"], ref["Cvv"], rtol=1e-12, atol=1e-14 * np.abs(ref["Cvv"]).max())
 
 
+def test_noalloc_call_leaves_device_free_memory_unchanged(lib):
+    """After its first call on the device, a call with the caller's buffers in
+    place allocates nothing: the device's free memory is the same before and
+    after it (both read after a synchronise)."""
+    p, L = lib
+    Gzz, Guq, Gqz, cs, nv = _problem(14, 16, 48)
+    m, kp = Gzz.shape[0], nv
+    ins = [_dev(Gzz), _dev(Guq), _dev(Gqz), _dev(cs)]
+    outs = [torch.zeros((m, kp), dtype=torch.float64, device="cuda"),
+            torch.zeros((nv, kp), dtype=torch.float64, device="cuda"),
+            torch.zeros(kp, dtype=torch.int32, device="cuda"), torch.zeros(kp, dtype=torch.int32, device="cuda"),
+            torch.zeros(2 * kp, dtype=torch.float64, device="cuda"), torch.zeros(3, dtype=torch.int32, device="cuda")]
+    ptrs = [ctypes.c_void_p(t.data_ptr()) for t in ins + outs]
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.plhr_tharm_extract_noalloc(m, kp, nv, *ptrs, stream) == 0     # set-up call
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert L.plhr_tharm_extract_noalloc(m, kp, nv, *ptrs, stream) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert int(outs[5][0].item()) == 0
+
+
 def test_noalloc_rejects_basis_beyond_its_scratch(lib):
     p, L = lib
     buf = torch.zeros(65 * 65, dtype=torch.float64, device="cuda")
