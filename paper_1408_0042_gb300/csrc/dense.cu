@@ -263,29 +263,41 @@ __device__ __forceinline__ void house3(dw x, dw y, dw z, int nr, dw& u1, dw& u2,
 // H, eigenvalues only: every transformation is applied to the active window
 // rows/columns l..hi alone (no Schur vectors, no full Schur form), which is
 // all the eigenvalues need.  Deflated 1x1 and 2x2 diagonal blocks remain.
-// One warp.  The iteration runs in double-word arithmetic on H scaled by a
+// kFrancisThreads threads (two warps, on two sub-partitions): in a bulge step
+// each thread updates one column (left reflection) and then one row (right
+// reflection), so a step costs one short double-word chain per side instead of
+// two per lane in one warp; the reflector itself is formed redundantly by
+// every thread.  The iteration runs in double-word arithmetic on H scaled by a
 // power of two to unit norm (H is converted in place: a double and a
 // double-word value take the same 8 bytes) and is converted back at the end.
-// Returns false if the iteration does not converge; sweeps (optional) gets
-// the number of QR sweeps and of bulge steps.
+// Every entry is updated by the same operations in the same order as with
+// one warp, so the result does not depend on the thread count.  Returns false
+// if the iteration does not converge; sweeps (optional) gets the number of QR
+// sweeps and of bulge steps.
+constexpr int kFrancisThreads = 64;
+static_assert(kFrancisThreads >= MAXM, "one column / row per thread");
+
 __device__ __noinline__ bool francis_eigenvalues(double* Hd, int n, long long* sweeps) {
-    const int lane = threadIdx.x & 31;
+    __shared__ double red[kFrancisThreads / 32];
+    const int t = threadIdx.x;
     double anorm = 0.0;
-    for (int i = lane; i < n * n; i += 32) {
+    for (int i = t; i < n * n; i += kFrancisThreads) {
         int r = i / n, c = i % n;
         if (c >= r - 1) anorm = fmax(anorm, fabs(Hd[r * LDS + c]));
     }
     anorm = warp_max(anorm);
+    if ((t & 31) == 0) red[t >> 5] = anorm;
+    __syncthreads();
+    for (int w = 0; w < kFrancisThreads / 32; ++w) anorm = fmax(anorm, red[w]);
     const int ex = anorm > 0.0 ? ilogb(anorm) : 0;
     const double down = ldexp(1.0, -ex), up = ldexp(1.0, ex);
     dw* H = reinterpret_cast<dw*>(Hd);
-    wsync();
-    for (int i = lane; i < n * n; i += 32) {
+    for (int i = t; i < n * n; i += kFrancisThreads) {
         int r = i / n, c = i % n;
         double v = (c >= r - 1) ? Hd[r * LDS + c] * down : 0.0;
         H[r * LDS + c] = dw_from_double(v);
     }
-    wsync();
+    __syncthreads();
     // negligible subdiagonal: relative to the neighbouring diagonal, or to
     // ||H|| (= 1 to 2 after scaling; normwise backward stable).  Only the
     // eigenvalues of largest modulus are used, and they keep full relative
@@ -305,9 +317,9 @@ __device__ __noinline__ bool francis_eigenvalues(double* Hd, int n, long long* s
             if (fabsf(H[l * LDS + l - 1].hi) <= eps * s) break;
             --l;
         }
-        wsync();
-        if (l > 0 && lane == 0) H[l * LDS + l - 1] = zero;
-        wsync();
+        __syncthreads();
+        if (l > 0 && t == 0) H[l * LDS + l - 1] = zero;
+        __syncthreads();
         if (l >= hi - 1) {          // 1x1 or 2x2 block converged
             hi = l - 1;
             its = 0;
@@ -325,9 +337,9 @@ __device__ __noinline__ bool francis_eigenvalues(double* Hd, int n, long long* s
                 if (v < vm) { vm = v; jm = j; }
             }
             if (vm <= 1e-7f * hnorm) {
-                wsync();
-                if (lane == 0) H[jm * LDS + jm - 1] = zero;
-                wsync();
+                __syncthreads();
+                if (t == 0) H[jm * LDS + jm - 1] = zero;
+                __syncthreads();
                 its = 0;
                 continue;
             }
@@ -335,98 +347,81 @@ __device__ __noinline__ bool francis_eigenvalues(double* Hd, int n, long long* s
         if (++total_its > 100 * n) { ok = false; break; }
         ++its;
         total_steps += hi - l;
-        dw s, t;
+        dw s, tt;
         if (its % 10 == 0) {
             dw w = dw_add(dw_make(fabsf(H[hi * LDS + hi - 1].hi)), dw_make(fabsf(H[(hi - 1) * LDS + hi - 2].hi)));
             s = dw_mul_f(w, 1.5f);
-            t = dw_mul(w, w);
+            tt = dw_mul(w, w);
         } else {
             dw a = H[(hi - 1) * LDS + hi - 1], b = H[(hi - 1) * LDS + hi], c = H[hi * LDS + hi - 1],
                d = H[hi * LDS + hi];
             s = dw_add(a, d);
-            t = dw_sub(dw_mul(a, d), dw_mul(b, c));
+            tt = dw_sub(dw_mul(a, d), dw_mul(b, c));
         }
         dw h00 = H[l * LDS + l], h01 = H[l * LDS + l + 1], h10 = H[(l + 1) * LDS + l],
            h11 = H[(l + 1) * LDS + l + 1], h21 = H[(l + 2) * LDS + l + 1];
         // first column of (H - s1 I)(H - s2 I)
-        dw x = dw_add(dw_add(dw_mul(h00, dw_sub(h00, s)), dw_mul(h01, h10)), t);
+        dw x = dw_add(dw_add(dw_mul(h00, dw_sub(h00, s)), dw_mul(h01, h10)), tt);
         dw y = dw_mul(h10, dw_sub(dw_add(h00, h11), s));
         dw z = dw_mul(h10, h21);
-        // every lane has read the shift and the first bulge column before any
-        // lane writes (lanes of a warp need not run in lockstep)
-        wsync();
+        // every thread has read the shift and the first bulge column before
+        // any thread writes
+        __syncthreads();
         for (int k = l; k <= hi - 1; ++k) {
             const int nr = (k < hi - 1) ? 3 : 2;
             dw u1, u2, tau;
             house3(x, y, z, nr, u1, u2, tau);
             if (!dw_is_zero(tau)) {
-                // left: rows k..k+2, columns c0..hi (a lane holds c and c + 32,
-                // both updated in one pass for instruction-level parallelism)
+                // left: rows k..k+2, column c0 + t
                 const int c0 = k > l ? k - 1 : l;
                 {
-                    const int ca = c0 + lane, cb = ca + 32;
-                    const bool va = ca <= hi, vb = cb <= hi;
-                    dw a0 = zero, a1 = zero, a2 = zero, b0 = zero, b1 = zero, b2 = zero;
-                    if (va) { a0 = H[k * LDS + ca]; a1 = H[(k + 1) * LDS + ca]; if (nr == 3) a2 = H[(k + 2) * LDS + ca]; }
-                    if (vb) { b0 = H[k * LDS + cb]; b1 = H[(k + 1) * LDS + cb]; if (nr == 3) b2 = H[(k + 2) * LDS + cb]; }
-                    dw sa = dw_mul(dw_add(dw_add(a0, dw_mul(u1, a1)), dw_mul(u2, a2)), tau);
-                    dw sb = dw_mul(dw_add(dw_add(b0, dw_mul(u1, b1)), dw_mul(u2, b2)), tau);
-                    if (va) {
+                    const int ca = c0 + t;
+                    if (ca <= hi) {
+                        const dw a0 = H[k * LDS + ca], a1 = H[(k + 1) * LDS + ca];
+                        const dw a2 = nr == 3 ? H[(k + 2) * LDS + ca] : zero;
+                        const dw sa = dw_mul(dw_add(dw_add(a0, dw_mul(u1, a1)), dw_mul(u2, a2)), tau);
                         H[k * LDS + ca] = dw_sub(a0, sa);
                         H[(k + 1) * LDS + ca] = dw_sub(a1, dw_mul(sa, u1));
                         if (nr == 3) H[(k + 2) * LDS + ca] = dw_sub(a2, dw_mul(sa, u2));
                     }
-                    if (vb) {
-                        H[k * LDS + cb] = dw_sub(b0, sb);
-                        H[(k + 1) * LDS + cb] = dw_sub(b1, dw_mul(sb, u1));
-                        if (nr == 3) H[(k + 2) * LDS + cb] = dw_sub(b2, dw_mul(sb, u2));
-                    }
                 }
-                wsync();
-                // right: columns k..k+2, rows l..min(k+3, hi)
+                __syncthreads();
+                // right: columns k..k+2, row l + t (rows l..min(k+3, hi))
                 const int r1 = (k + 3 < hi) ? k + 3 : hi;
                 {
-                    const int ra = l + lane, rb = ra + 32;
-                    const bool va = ra <= r1, vb = rb <= r1;
-                    dw a0 = zero, a1 = zero, a2 = zero, b0 = zero, b1 = zero, b2 = zero;
-                    if (va) { a0 = H[ra * LDS + k]; a1 = H[ra * LDS + k + 1]; if (nr == 3) a2 = H[ra * LDS + k + 2]; }
-                    if (vb) { b0 = H[rb * LDS + k]; b1 = H[rb * LDS + k + 1]; if (nr == 3) b2 = H[rb * LDS + k + 2]; }
-                    dw sa = dw_mul(dw_add(dw_add(a0, dw_mul(u1, a1)), dw_mul(u2, a2)), tau);
-                    dw sb = dw_mul(dw_add(dw_add(b0, dw_mul(u1, b1)), dw_mul(u2, b2)), tau);
-                    if (va) {
+                    const int ra = l + t;
+                    if (ra <= r1) {
+                        const dw a0 = H[ra * LDS + k], a1 = H[ra * LDS + k + 1];
+                        const dw a2 = nr == 3 ? H[ra * LDS + k + 2] : zero;
+                        const dw sa = dw_mul(dw_add(dw_add(a0, dw_mul(u1, a1)), dw_mul(u2, a2)), tau);
                         H[ra * LDS + k] = dw_sub(a0, sa);
                         H[ra * LDS + k + 1] = dw_sub(a1, dw_mul(sa, u1));
                         if (nr == 3) H[ra * LDS + k + 2] = dw_sub(a2, dw_mul(sa, u2));
                     }
-                    if (vb) {
-                        H[rb * LDS + k] = dw_sub(b0, sb);
-                        H[rb * LDS + k + 1] = dw_sub(b1, dw_mul(sb, u1));
-                        if (nr == 3) H[rb * LDS + k + 2] = dw_sub(b2, dw_mul(sb, u2));
-                    }
                 }
-                wsync();
+                __syncthreads();
             }
-            if (k > l && lane == 0) {
+            if (k > l && t == 0) {
                 H[(k + 1) * LDS + k - 1] = zero;
                 if (nr == 3) H[(k + 2) * LDS + k - 1] = zero;
             }
-            wsync();
+            __syncthreads();
             if (k < hi - 1) {
                 x = H[(k + 1) * LDS + k];
                 y = H[(k + 2) * LDS + k];
                 z = (k < hi - 2) ? H[(k + 3) * LDS + k] : zero;
             }
-            wsync();
+            __syncthreads();
         }
     }
-    wsync();
-    for (int i = lane; i < n * n; i += 32) {
+    __syncthreads();
+    for (int i = t; i < n * n; i += kFrancisThreads) {
         int r = i / n, c = i % n;
         dw v = H[r * LDS + c];
         Hd[r * LDS + c] = (c >= r - 1) ? dw_to_double(v) * up : 0.0;
     }
-    if (sweeps && lane == 0) { sweeps[0] = total_its; sweeps[1] = total_steps; }
-    wsync();
+    if (sweeps && t == 0) { sweeps[0] = total_its; sweeps[1] = total_steps; }
+    __syncthreads();
     return ok;
 }
 
@@ -580,7 +575,7 @@ __device__ __forceinline__ Smem* state_of(const DenseArgs& a) {
 }
 
 // The dense stage runs as five launches: phase 0 of k_extract (up to the
-// Hessenberg form, state saved to global scratch), k_francis (one warp: the
+// Hessenberg form, state saved to global scratch), k_francis (two warps: the
 // eigenvalues), phase 1 (selection, state saved), k_eigvec (one CTA per
 // selected unit, in parallel), phase 2 (orthogonalisation, Y', coefficients).
 // The eigenvalue iteration measured 2x slower per bulge step when run inside
@@ -1029,21 +1024,21 @@ __global__ void __launch_bounds__(32) k_eigvec(DenseArgs a) {
     }
 }
 
-// Eigenvalues of the saved Hessenberg form (one warp; see k_extract).  The
+// Eigenvalues of the saved Hessenberg form (two warps; see k_extract).  The
 // stage clocks 3 and 4 and the sweep counts come from this launch.
-__global__ void __launch_bounds__(32) k_francis(DenseArgs a) {
+__global__ void __launch_bounds__(kFrancisThreads) k_francis(DenseArgs a) {
     extern __shared__ __align__(16) double shh[];
     Smem* G = state_of(a);
     if (G->ints[6]) return;
     const int nk = G->ints[0];
-    const int lane = threadIdx.x;
-    for (int i = lane; i < nk * LDS; i += 32) shh[i] = G->H[i];
-    __syncwarp();
-    if (a.clk && lane == 0) a.clk[3] = clock64();
+    const int t = threadIdx.x;
+    for (int i = t; i < nk * LDS; i += kFrancisThreads) shh[i] = G->H[i];
+    __syncthreads();
+    if (a.clk && t == 0) a.clk[3] = clock64();
     const bool conv = francis_eigenvalues(shh, nk, a.clk ? a.clk + 9 : nullptr);
-    if (a.clk && lane == 0) a.clk[4] = clock64();
-    for (int i = lane; i < nk * LDS; i += 32) G->H[i] = shh[i];
-    if (lane == 0) G->ints[2] = conv ? 1 : 0;
+    if (a.clk && t == 0) a.clk[4] = clock64();
+    for (int i = t; i < nk * LDS; i += kFrancisThreads) G->H[i] = shh[i];
+    if (t == 0) G->ints[2] = conv ? 1 : 0;
 }
 
 }  // namespace
@@ -1066,7 +1061,7 @@ cudaError_t dense_extract(const DenseArgs& a, cudaStream_t s) {
     e = cudaFuncSetAttribute(k_eigvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)she);
     if (e != cudaSuccess) return e;
     k_extract<<<1, NT, shm, s>>>(a, 0);
-    k_francis<<<1, 32, shf, s>>>(a);
+    k_francis<<<1, kFrancisThreads, shf, s>>>(a);
     k_extract<<<1, NT, shm, s>>>(a, 1);
     k_eigvec<<<a.kp, 32, she, s>>>(a);
     k_extract<<<1, NT, shm, s>>>(a, 2);
