@@ -29,6 +29,15 @@ struct G3 {
 };
 
 __device__ __forceinline__ void unflat(int64_t row, const G3& g, int64_t& ix, int64_t& iy, int64_t& iz) {
+    if ((uint64_t)row <= 0xffffffffull) {   // 32-bit divisions (the grid fits: nx, ny < 2^32)
+        const unsigned r = (unsigned)row, nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+        const unsigned t = r / nx;
+        ix = r - t * nx;
+        const unsigned z = t / ny;
+        iy = t - z * ny;
+        iz = z;
+        return;
+    }
     ix = row % g.nx;
     int64_t t = row / g.nx;
     iy = t % g.ny;
@@ -62,8 +71,9 @@ __global__ void __launch_bounds__(kT) k_rich_lap(G3 g, int nc, double ih2, doubl
                                                  const double* __restrict__ win, const double* __restrict__ r,
                                                  int64_t ldr, double* __restrict__ wout, int64_t total) {
     GRID_LOOP(total) {
-        int64_t row = e / nc;
-        int c = (int)(e - row * nc);
+        int64_t row;
+        int c;
+        split_index(e, nc, row, c);
         double rv = r[row * ldr + c];
         double v;
         if (win) {
@@ -84,8 +94,9 @@ template <bool D3>
 __global__ void __launch_bounds__(kT) k_shifted(G3 g, int nc, double ih2, double sig, const double* __restrict__ x,
                                                 double* __restrict__ t, int64_t total) {
     GRID_LOOP(total) {
-        int64_t row = e / nc;
-        int c = (int)(e - row * nc);
+        int64_t row;
+        int c;
+        split_index(e, nc, row, c);
         int64_t ix, iy, iz;
         unflat(row, g, ix, iy, iz);
         const double* xp = x + row * nc + c;
@@ -101,8 +112,9 @@ __global__ void __launch_bounds__(kT) k_poly_step(G3 g, int nc, double ih2, doub
                                                   const double* __restrict__ t, const double* __restrict__ r,
                                                   int64_t ldr, double* __restrict__ out, int64_t total) {
     GRID_LOOP(total) {
-        int64_t row = e / nc;
-        int c = (int)(e - row * nc);
+        int64_t row;
+        int c;
+        split_index(e, nc, row, c);
         int64_t ix, iy, iz;
         unflat(row, g, ix, iy, iz);
         const double* tp = t + row * nc + c;
@@ -120,8 +132,9 @@ __global__ void __launch_bounds__(kT) k_resid_lap(G3 g, int nc, double ih2, doub
                                                   const double* __restrict__ r, int64_t ldr,
                                                   double* __restrict__ out, int64_t total) {
     GRID_LOOP(total) {
-        int64_t row = e / nc;
-        int c = (int)(e - row * nc);
+        int64_t row;
+        int c;
+        split_index(e, nc, row, c);
         int64_t ix, iy, iz;
         unflat(row, g, ix, iy, iz);
         if (SHIFT)
@@ -154,8 +167,9 @@ template <bool D3>
 __global__ void __launch_bounds__(kT) k_prolong_add(G3 gf, G3 gc, int nc, int lin, const double* __restrict__ wc,
                                                     double* __restrict__ wf, int64_t total) {
     GRID_LOOP(total) {
-        int64_t row = e / nc;
-        int c = (int)(e - row * nc);
+        int64_t row;
+        int c;
+        split_index(e, nc, row, c);
         int64_t ix, iy, iz;
         unflat(row, gf, ix, iy, iz);
         int64_t xi[2], yi[2], zi[2];
@@ -194,8 +208,9 @@ template <bool D3>
 __global__ void __launch_bounds__(kT) k_restrict(G3 gf, G3 gc, int nc, int lin, const double* __restrict__ f,
                                                  double* __restrict__ rc, int64_t total) {
     GRID_LOOP(total) {
-        int64_t row = e / nc;
-        int c = (int)(e - row * nc);
+        int64_t row;
+        int c;
+        split_index(e, nc, row, c);
         int64_t ix, iy, iz;
         unflat(row, gc, ix, iy, iz);
         int64_t xi[4], yi[4], zi[4];

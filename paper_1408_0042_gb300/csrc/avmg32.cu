@@ -488,8 +488,10 @@ cudaError_t vcycle(const MGHierarchy& H, int l, int nc, bool v4, const Tr* r, in
 __global__ void k_narrow_rhs(int64_t n, int nc, const double* __restrict__ r, int64_t ldr, float* __restrict__ r32) {
     const int64_t total = n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e / nc;
-        r32[e] = f64_to_f32_rn(r[row * ldr + (e - row * nc)]);
+        int64_t row;
+        int cc;
+        split_index(e, nc, row, cc);
+        r32[e] = f64_to_f32_rn(r[row * ldr + cc]);
     }
 }
 

@@ -39,26 +39,37 @@ __device__ __forceinline__ bool pos_of(const Ld& g, Pos& p) {
 }
 
 // L x at p (leading dimension nc), zero outside: 2d x_c - sum of the
-// neighbours (48 bits leave ample room for the cancellation); xc receives x
+// neighbours, summed lazily (48 bits leave ample room for the cancellation);
+// xc receives x
 template <bool D3>
 __device__ __forceinline__ dw lapd(dw& xc, const dw* __restrict__ xp, const Ld& g, const Pos& p) {
     const int ld = g.nc, sy = ld * g.nx, sz = sy * g.ny;
     xc = xp[0];
-    const dw zero = dw_make(0.0f);
-    dw s = dw_add(p.ix > 0 ? xp[-ld] : zero, p.ix < g.nx - 1 ? xp[ld] : zero);
-    s = dw_add(s, dw_add(p.iy > 0 ? xp[-sy] : zero, p.iy < g.ny - 1 ? xp[sy] : zero));
-    if (D3) s = dw_add(s, dw_add(p.iz > 0 ? xp[-sz] : zero, p.iz < g.nz - 1 ? xp[sz] : zero));
-    return dw_sub(dw_mul_f(xc, D3 ? 6.0f : 4.0f), s);
+    dwacc s = {0.0f, 0.0f};
+    if (p.ix > 0) dwacc_sub(s, xp[-ld]);
+    if (p.ix < g.nx - 1) dwacc_sub(s, xp[ld]);
+    if (p.iy > 0) dwacc_sub(s, xp[-sy]);
+    if (p.iy < g.ny - 1) dwacc_sub(s, xp[sy]);
+    if (D3) {
+        if (p.iz > 0) dwacc_sub(s, xp[-sz]);
+        if (p.iz < g.nz - 1) dwacc_sub(s, xp[sz]);
+    }
+    dwacc_add_mul_f(s, xc, D3 ? 6.0f : 4.0f);
+    return dwacc_result(s);
 }
 
-// w = 2 om r - om^2 L r  (first two sweeps from w = 0, B = L)
+// w = 2 om r - om^2 L r  (first two sweeps from w = 0, B = L); om2x = 2 om,
+// om2ih2 = om^2 / h^2
 template <bool D3>
-__global__ void __launch_bounds__(kT) k_rich2(Ld g, dw om, dw om2, const dw* __restrict__ r, dw* __restrict__ w) {
+__global__ void __launch_bounds__(kT) k_rich2(Ld g, dw om2x, dw om2ih2, const dw* __restrict__ r, dw* __restrict__ w) {
     Pos p;
     if (!pos_of(g, p)) return;
     dw rc;
     const dw l = lapd<D3>(rc, r + p.row * g.nc + p.c, g, p);
-    w[p.row * g.nc + p.c] = dw_sub(dw_mul(dw_add(om, om), rc), dw_mul(om2, dw_mul(g.ih2, l)));
+    dwacc a = {0.0f, 0.0f};
+    dwacc_add_mul(a, om2x, rc);
+    dwacc_add_mul(a, dw_neg(om2ih2), l);
+    w[p.row * g.nc + p.c] = dwacc_result(a);
 }
 
 // w = om r
@@ -69,16 +80,19 @@ __global__ void __launch_bounds__(kT) k_scale(Ld g, dw om, const dw* __restrict_
     w[e] = dw_mul(om, r[e]);
 }
 
-// wout = win + om (r - L win)
+// wout = win + om (r - L win) = win + om r - (om / h^2) L' win; omih2 = om / h^2
 template <bool D3>
-__global__ void __launch_bounds__(kT) k_rich(Ld g, dw om, const dw* __restrict__ win, const dw* __restrict__ r,
-                                             dw* __restrict__ wout) {
+__global__ void __launch_bounds__(kT) k_rich(Ld g, dw om, dw omih2, const dw* __restrict__ win,
+                                             const dw* __restrict__ r, dw* __restrict__ wout) {
     Pos p;
     if (!pos_of(g, p)) return;
     const int64_t e = p.row * g.nc + p.c;
     dw wc;
     const dw l = lapd<D3>(wc, win + e, g, p);
-    wout[e] = dw_add(wc, dw_mul(om, dw_sub(r[e], dw_mul(g.ih2, l))));
+    dwacc a = dwacc_of(wc);
+    dwacc_add_mul(a, om, r[e]);
+    dwacc_add_mul(a, dw_neg(omih2), l);
+    wout[e] = dwacc_result(a);
 }
 
 // t = L x - sig x
@@ -89,7 +103,10 @@ __global__ void __launch_bounds__(kT) k_shifted(Ld g, dw sig, const dw* __restri
     const int64_t e = p.row * g.nc + p.c;
     dw xc;
     const dw l = lapd<D3>(xc, x + e, g, p);
-    t[e] = dw_sub(dw_mul(g.ih2, l), dw_mul(sig, xc));
+    dwacc a = {0.0f, 0.0f};
+    dwacc_add_mul(a, g.ih2, l);
+    dwacc_add_mul(a, dw_neg(sig), xc);
+    t[e] = dwacc_result(a);
 }
 
 // B w = ((L - sig) t + c^2 w) / (2c), t = (L - sig) w;
@@ -119,7 +136,9 @@ __global__ void __launch_bounds__(kT) k_resid(Ld g, const dw* __restrict__ w, co
     const int64_t e = p.row * g.nc + p.c;
     dw wc;
     const dw l = lapd<D3>(wc, w + e, g, p);
-    out[e] = dw_sub(r[e], dw_mul(g.ih2, l));
+    dwacc a = dwacc_of(r[e]);
+    dwacc_add_mul(a, dw_neg(g.ih2), l);
+    out[e] = dwacc_result(a);
 }
 
 // 1D cell-centred prolongation weights (constant: 1; linear: 3/4 and 1/4) and
@@ -168,13 +187,13 @@ __global__ void __launch_bounds__(kT) k_prolong_add(Ld gf, Ld gc, int lin, const
     zi[0] = 0; zw[0] = 1.0f;
     if (D3) nzw = pw(lin, p.iz, gc.nz, zi, zw);
     const int64_t e = p.row * gf.nc + p.c;
-    dw acc = wf[e];
+    dwacc acc = dwacc_of(wf[e]);
     for (int a = 0; a < nzw; ++a)
         for (int b = 0; b < nyw; ++b) {
             const dw* line = wc + ((int64_t)zi[a] * gc.ny + yi[b]) * gc.nx * gc.nc + p.c;
-            for (int q = 0; q < nxw; ++q) acc = dw_add(acc, dw_mul_f(line[(int64_t)xi[q] * gc.nc], zw[a] * yw[b] * xw[q]));
+            for (int q = 0; q < nxw; ++q) dwacc_add_mul_f(acc, line[(int64_t)xi[q] * gc.nc], zw[a] * yw[b] * xw[q]);
         }
-    wf[e] = acc;
+    wf[e] = dwacc_result(acc);
 }
 
 // rc = R f   (over the coarse level)
@@ -190,13 +209,13 @@ __global__ void __launch_bounds__(kT) k_restrict(Ld gf, Ld gc, int lin, const dw
     int nzw = 1;
     zi[0] = 0; zw[0] = 1.0f;
     if (D3) nzw = rw(lin, p.iz, gf.nz, zi, zw);
-    dw acc = dw_make(0.0f);
+    dwacc acc = {0.0f, 0.0f};
     for (int a = 0; a < nzw; ++a)
         for (int b = 0; b < nyw; ++b) {
             const dw* line = f + ((int64_t)zi[a] * gf.ny + yi[b]) * gf.nx * gf.nc + p.c;
-            for (int q = 0; q < nxw; ++q) acc = dw_add(acc, dw_mul_f(line[(int64_t)xi[q] * gf.nc], zw[a] * yw[b] * xw[q]));
+            for (int q = 0; q < nxw; ++q) dwacc_add_mul_f(acc, line[(int64_t)xi[q] * gf.nc], zw[a] * yw[b] * xw[q]);
         }
-    rc[p.row * gc.nc + p.c] = acc;
+    rc[p.row * gc.nc + p.c] = dwacc_result(acc);
 }
 
 // coarsest solve, one CTA per column: out = S diag(1/|mu_i + mu_j + mu_k - sig|) S^T in
@@ -277,15 +296,19 @@ __global__ void __launch_bounds__(kT) k_coarse_sep(int d, int nx, int ny, int nz
 __global__ void k_to_dw(int64_t n, int nc, const double* __restrict__ x, int64_t ldx, dw* __restrict__ y) {
     const int64_t total = n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e / nc;
-        y[e] = dw_split_trunc(x[row * ldx + (e - row * nc)]);
+        int64_t row;
+        int cc;
+        split_index(e, nc, row, cc);
+        y[e] = dw_split_trunc(x[row * ldx + cc]);
     }
 }
 __global__ void k_from_dw(int64_t n, int nc, const dw* __restrict__ x, double* __restrict__ y, int64_t ldy) {
     const int64_t total = n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e / nc;
-        y[row * ldy + (e - row * nc)] = dw_to_double_fast(x[e]);
+        int64_t row;
+        int cc;
+        split_index(e, nc, row, cc);
+        y[row * ldy + cc] = dw_to_double_fast(x[e]);
     }
 }
 
@@ -312,7 +335,7 @@ void sweep(const MGLevel& L, dw sig, int nc, const dw* win, const dw* r, dw* tmp
     const dim3 gr = grid_of(L.g, nc);
     const bool d3 = L.g.d == 3;
     if (!L.poly) {
-        PLHR_LD(k_rich, gr, g, dw_host(L.omega), win, r, wout);
+        PLHR_LD(k_rich, gr, g, dw_host(L.omega), dw_host(L.omega * L.g.inv_h2()), win, r, wout);
         return;
     }
     PLHR_LD(k_shifted, gr, g, sig, win, tmp);
@@ -348,7 +371,7 @@ cudaError_t vcycle(const MGHierarchy& H, int l, int nc, const dw* r, dw* out, co
     dw* nxt = bf.w1;
     int done;
     if (!L.poly && H.nu >= 2) {
-        PLHR_LD(k_rich2, gr, g, om, dw_host(L.omega * L.omega), r, cur);
+        PLHR_LD(k_rich2, gr, g, dw_host(2.0 * L.omega), dw_host(L.omega * L.omega * L.g.inv_h2()), r, cur);
         done = 2;
     } else {
         k_scale<<<gr, kT, 0, s>>>(g, om, r, cur);

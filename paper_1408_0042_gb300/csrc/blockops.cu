@@ -34,8 +34,9 @@ __global__ void __launch_bounds__(kThreads) k_residual(int64_t n, int kp, const 
     const int c = (int)(e0 % kp);
     const double s = sc[c], l = lam[c];
     double rr = 0.0, bb = 0.0;
-    for (int64_t e = e0; e < total; e += stride) {
-        int64_t row = e / kp;
+    const int64_t drow = stride / kp;   // the stride is a multiple of kp: the column stays c
+    int64_t row = e0 / kp;
+    for (int64_t e = e0; e < total; e += stride, row += drow) {
         double v = V[row * ldv + c];
         double r = s * (AV[row * ldav + c] - l * v);
         R[row * ldr + c] = r;
@@ -381,8 +382,9 @@ __global__ void k_gather(int64_t n, const double* __restrict__ X, int64_t ldx, c
                          double* __restrict__ Y, int64_t ldy) {
     int64_t total = n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = e / nc;
-        int j = (int)(e - r * nc);
+        int64_t r;
+        int j;
+        split_index(e, nc, r, j);
         Y[r * ldy + j] = X[r * ldx + idx[j]];
     }
 }
@@ -397,8 +399,9 @@ __device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t i) {
 __global__ void k_seeded(int64_t n, int kc, uint64_t seed, double* X, int64_t ldx) {
     int64_t total = n * kc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = e / kc;
-        int j = (int)(e - r * kc);
+        int64_t r;
+        int j;
+        split_index(e, kc, r, j);
         uint64_t x = splitmix_out(seed, (uint64_t)e + 1);
         X[r * ldx + j] = (double)(x >> 11) * 0x1.0p-53 - 0.5;
     }
@@ -431,8 +434,9 @@ __global__ void __launch_bounds__(256) k_shift_combine(int64_t n, int nc, const 
                                                        int64_t ld2) {
     const int64_t total = n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / nc;
-        const int c = (int)(e - i * nc);
+        int64_t i;
+        int c;
+        split_index(e, nc, i, c);
         const double a = AX[i * ldax + c], b = BX[i * ldbx + c];
         if (o1) o1[i * ld1 + c] = a - lam[c] * b;
         if (o2) o2[i * ld2 + c] = a - sig * b;
@@ -474,8 +478,9 @@ __global__ void __launch_bounds__(256) k_coldots(int64_t n, int kc, const double
     const int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = (int)(e0 % kc);
     double a = 0.0, b = 0.0;
-    for (int64_t e = e0; e < total; e += stride) {
-        int64_t row = e / kc;
+    const int64_t drow = stride / kc;   // the stride is a multiple of kc: the column stays c
+    int64_t row = e0 / kc;
+    for (int64_t e = e0; e < total; e += stride, row += drow) {
         double x = X[row * ldx + c];
         a = fma(x, Y[row * ldy + c], a);
         b = fma(x, x, b);

@@ -20,8 +20,9 @@ __global__ void __launch_bounds__(256) k_csr_axpby(CsrData A, int nc, const doub
                                                    double* __restrict__ y, int64_t ldy, double alpha, double beta) {
     const int64_t total = A.n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e / nc;
-        const int c = (int)(e - row * nc);
+        int64_t row;
+        int c;
+        split_index(e, nc, row, c);
         double v = alpha * row_dot(A, row, x, ldx, c);
         if (beta != 0.0) v = fma(beta, x[row * ldx + c], v);
         y[row * ldy + c] = v;
@@ -34,8 +35,9 @@ __global__ void __launch_bounds__(256) k_csr_shifts(CsrData A, int nc, const dou
                                                     double* __restrict__ o2, int64_t ld2, double sig) {
     const int64_t total = A.n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e / nc;
-        const int c = (int)(e - row * nc);
+        int64_t row;
+        int c;
+        split_index(e, nc, row, c);
         const double a = row_dot(A, row, x, ldx, c);
         const double xv = x[row * ldx + c];
         if (ax) ax[row * ldax + c] = a;

@@ -164,6 +164,37 @@ __device__ __forceinline__ void dw_fma_acc(float& hi, float& lo, const dw& a, co
     lo = __fadd_rn(lo, __fadd_rn(s.lo, __fadd_rn(pl, cr)));
 }
 
+// Lazily normalised double-word sum: the high part takes each term's high
+// part through TwoSum (exact), every low-order term (the TwoSum error, the
+// product's error and cross terms, the operands' low parts) is added to the
+// low part in FP32, and the pair is normalised once at the end.  For the
+// handful of terms of a stencil, a transfer or an update it carries about
+// 2^-46 of the sum of |terms| (the accurate pairwise sum's error class) in
+// half its instructions.
+struct dwacc {
+    float hi, lo;
+};
+__device__ __forceinline__ dwacc dwacc_of(dw a) { return {a.hi, a.lo}; }
+// s += a
+__device__ __forceinline__ void dwacc_add(dwacc& s, dw a) {
+    const dw t = dw_two_sum(s.hi, a.hi);
+    s.hi = t.hi;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, a.lo));
+}
+// s -= a
+__device__ __forceinline__ void dwacc_sub(dwacc& s, dw a) { dwacc_add(s, dw_neg(a)); }
+// s += a w (w FP32)
+__device__ __forceinline__ void dwacc_add_mul_f(dwacc& s, dw a, float w) {
+    const float ph = __fmul_rn(a.hi, w);
+    const float pl = __fmaf_rn(a.hi, w, -ph);
+    const dw t = dw_two_sum(s.hi, ph);
+    s.hi = t.hi;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, __fmaf_rn(a.lo, w, pl)));
+}
+// s += a b (double-word operands)
+__device__ __forceinline__ void dwacc_add_mul(dwacc& s, dw a, dw b) { dw_fma_acc(s.hi, s.lo, a, b); }
+__device__ __forceinline__ dw dwacc_result(dwacc s) { return dw_two_sum(s.hi, s.lo); }
+
 // FP64 -> FP32 rounding (to nearest, ties to even: the conversion
 // instruction's result) by integer operations on the encodings, for normal
 // FP32 results; other inputs take the conversion instruction

@@ -243,25 +243,61 @@ constexpr int kUpRows = 32;
 // With an FP64 F_0 and an FP64 Vout, the F_0 part of Vout is summed in
 // double-word arithmetic (V keeps ~48-bit accuracy: A amplifies rounding noise
 // in V by ||A|| / lambda, and FP64 FMAs would make the kernel FP64-pipe
-// bound); all other sums are FP32.  Every output row depends only on the same
-// input row and a chunk is staged before any of its rows is written (in place
-// allowed: Vout may be F_0, Pout may be F_{nb-1}).
+// bound), accumulated as in the double-word update (exact products of the
+// high parts, TwoSum on the high sum); all other sums are FP32.  Every output
+// row depends only on the same input row and a chunk is staged before any of
+// its rows is written (in place allowed: Vout may be F_0, Pout may be
+// F_{nb-1}).
+//
+// Shared memory (byte offsets rounded up to 16): csw [kp][kp] and zw
+// [rows][kp] double-word, then cpt [kp][cs] (C_P transposed, rows padded
+// with zeros to mp = m rounded up to 4, row stride cs = mp + 4 so that the
+// 16-byte loads of consecutive columns j fall in different banks), csf
+// [kp][kp], zf [rows][mp] (the staged rows, zero past m): a row segment and
+// a coefficient segment of 4 consecutive i are one 16-byte load each.
+struct UpMxLayout {
+    int mp, cs;
+    size_t zw, cpt, csf, zf, bytes;
+};
+__host__ __device__ inline size_t up16(size_t b) { return (b + 15) & ~(size_t)15; }
+__host__ __device__ inline UpMxLayout up_mx_layout(int m, int kp) {
+    UpMxLayout L;
+    L.mp = (m + 3) / 4 * 4;
+    L.cs = L.mp + 4;
+    L.zw = sizeof(dw) * kp * kp;
+    L.cpt = up16(L.zw + sizeof(dw) * kUpRows * kp);
+    L.csf = up16(L.cpt + sizeof(float) * kp * L.cs);
+    L.zf = up16(L.csf + sizeof(float) * kp * kp);
+    L.bytes = L.zf + sizeof(float) * kUpRows * L.mp;
+    return L;
+}
+
 __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int nb, FamMx F,
                                                    const double* __restrict__ Cp, const double* __restrict__ Cvv,
                                                    void* __restrict__ Vout, int vo64, int64_t ldvo,
                                                    void* __restrict__ Pout, int po64, int64_t ldpo) {
     extern __shared__ __align__(16) unsigned char raw[];
+    const UpMxLayout L = up_mx_layout(m, kp);
+    const int mp = L.mp;
     dw* csw = reinterpret_cast<dw*>(raw);                    // [kp][kp]  C_VV + C_P (V rows), double-word
-    dw* zw = csw + kp * kp;                                  // [rows][kp] V rows, double-word
-    float* cpf = reinterpret_cast<float*>(zw + kUpRows * kp);   // [m][kp]
-    float* csf = cpf + m * kp;                               // [kp][kp]
-    float* zf = csf + kp * kp;                               // [rows][m]
+    dw* zw = reinterpret_cast<dw*>(raw + L.zw);              // [rows][kp] V rows, double-word
+    float* cpt = reinterpret_cast<float*>(raw + L.cpt);      // [kp][cs] C_P transposed
+    float* csf = reinterpret_cast<float*>(raw + L.csf);      // [kp][kp]
+    float* zf = reinterpret_cast<float*>(raw + L.zf);        // [rows][mp]
     const bool v64 = F.f64[0] && vo64;
-    for (int t = threadIdx.x; t < m * kp; t += blockDim.x) cpf[t] = (float)Cp[t];
+    const int cs = L.cs;
+    for (int t = threadIdx.x; t < kp * cs; t += blockDim.x) {
+        const int jj = t / cs, i = t - jj * cs;
+        cpt[t] = i < m ? (float)Cp[i * kp + jj] : 0.0f;
+    }
     for (int t = threadIdx.x; t < kp * kp; t += blockDim.x) {
         const double v = Cvv[t] + Cp[t];     // V rows of C_P are the first kp rows
         csw[t] = dw_from_double(v);
         csf[t] = (float)v;
+    }
+    for (int t = threadIdx.x; t < kUpRows * (mp - m); t += blockDim.x) {
+        const int r = t / (mp - m), i = m + t - r * (mp - m);
+        zf[r * mp + i] = 0.0f;
     }
     // thread t owns column j = t % kp of rows t / kp and t / kp + kUpRows / 2
     // (kp <= 16): two independent sums sharing the coefficient loads, each
@@ -269,6 +305,7 @@ __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int
     constexpr int kHalfUp = kUpRows / 2;
     const int r0 = threadIdx.x / kp, j = threadIdx.x - r0 * kp;
     const bool own = r0 < kHalfUp;
+    const float* cj = cpt + j * cs;
     const int64_t nchunks = (n + kUpRows - 1) / kUpRows;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const int64_t row0 = ch * kUpRows;
@@ -284,9 +321,9 @@ __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int
                 if (b == 0 && v64) {
                     const dw v = dw_from_double_fast(ldv(F, 0, row, c));
                     zw[r * kp + c] = v;
-                    zf[r * m + c] = v.hi;
+                    zf[r * mp + c] = v.hi;
                 } else {
-                    zf[r * m + F.off[b] + c] = ldf(F, b, row, c);
+                    zf[r * mp + F.off[b] + c] = ldf(F, b, row, c);
                 }
             }
         }
@@ -295,18 +332,29 @@ __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int
         // rows ra = r0 and rb = r0 + kUpRows / 2 (rb = ra, not stored, past nrows)
         const bool two = r0 + kHalfUp < nrows;
         const int ra = r0, rb = two ? r0 + kHalfUp : r0;
-        const float* za = zf + ra * m;
-        const float* zb = zf + rb * m;
+        const float* za = zf + ra * mp;
+        const float* zb = zf + rb * mp;
         float resta = 0.0f, restb = 0.0f, pva = 0.0f, pvb = 0.0f;
-        for (int i = kp; i < m; ++i) {
-            const float c = cpf[i * kp + j];
+        // i = kp .. m - 1 (then zeros to mp), in order
+        int i = kp;
+        for (; i < mp && (i & 3); ++i) {
+            const float c = cj[i];
             resta = fmaf(za[i], c, resta);
             restb = fmaf(zb[i], c, restb);
         }
-        for (int i = 0; i < kp; ++i) {
-            const float c = cpf[i * kp + j];
-            pva = fmaf(za[i], c, pva);
-            pvb = fmaf(zb[i], c, pvb);
+        for (; i < mp; i += 4) {
+            const float4 c4 = *reinterpret_cast<const float4*>(cj + i);
+            const float4 a4 = *reinterpret_cast<const float4*>(za + i);
+            const float4 b4 = *reinterpret_cast<const float4*>(zb + i);
+            resta = fmaf(a4.x, c4.x, resta); restb = fmaf(b4.x, c4.x, restb);
+            resta = fmaf(a4.y, c4.y, resta); restb = fmaf(b4.y, c4.y, restb);
+            resta = fmaf(a4.z, c4.z, resta); restb = fmaf(b4.z, c4.z, restb);
+            resta = fmaf(a4.w, c4.w, resta); restb = fmaf(b4.w, c4.w, restb);
+        }
+        for (int q = 0; q < kp; ++q) {
+            const float c = cj[q];
+            pva = fmaf(za[q], c, pva);
+            pvb = fmaf(zb[q], c, pvb);
         }
         const int64_t rowa = row0 + ra, rowb = row0 + rb;
         const float pa = pva + resta, pb = pvb + restb;
@@ -320,20 +368,20 @@ __global__ void __launch_bounds__(256) k_update_mx(int64_t n, int m, int kp, int
         if (v64) {
             const dw* zra = zw + ra * kp;
             const dw* zrb = zw + rb * kp;
-            dw va = dw_make(resta), vb = dw_make(restb);
-            for (int i = 0; i < kp; ++i) {
-                const dw c = csw[i * kp + j];
-                va = dw_add(va, dw_mul(zra[i], c));
-                vb = dw_add(vb, dw_mul(zrb[i], c));
+            float vha = resta, vla = 0.0f, vhb = restb, vlb = 0.0f;
+            for (int q = 0; q < kp; ++q) {
+                const dw c = csw[q * kp + j];
+                dw_fma_acc(vha, vla, zra[q], c);
+                dw_fma_acc(vhb, vlb, zrb[q], c);
             }
-            static_cast<double*>(Vout)[rowa * ldvo + j] = dw_to_double_fast(va);
-            if (two) static_cast<double*>(Vout)[rowb * ldvo + j] = dw_to_double_fast(vb);
+            static_cast<double*>(Vout)[rowa * ldvo + j] = dw_to_double_fast(dw{vha, vla});
+            if (two) static_cast<double*>(Vout)[rowb * ldvo + j] = dw_to_double_fast(dw{vhb, vlb});
         } else {
             float va = 0.0f, vb = 0.0f;
-            for (int i = 0; i < kp; ++i) {
-                const float c = csf[i * kp + j];
-                va = fmaf(za[i], c, va);
-                vb = fmaf(zb[i], c, vb);
+            for (int q = 0; q < kp; ++q) {
+                const float c = csf[q * kp + j];
+                va = fmaf(za[q], c, va);
+                vb = fmaf(zb[q], c, vb);
             }
             va += resta;
             vb += restb;
@@ -451,8 +499,9 @@ __global__ void k_widen(int64_t n, int nc, const float* __restrict__ X, int64_t 
                         int64_t ldy) {
     const int64_t total = n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = e / nc;
-        const int c = (int)(e - r * nc);
+        int64_t r;
+        int c;
+        split_index(e, nc, r, c);
         Y[r * ldy + c] = f32_to_f64_bits(X[r * ldx + c]);
     }
 }
@@ -462,8 +511,9 @@ __global__ void k_narrow(int64_t n, int nc, const double* __restrict__ X, int64_
                          int64_t ldy) {
     const int64_t total = n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = e / nc;
-        const int c = (int)(e - r * nc);
+        int64_t r;
+        int c;
+        split_index(e, nc, r, c);
         Y[r * ldy + c] = f64_to_f32_rn(X[r * ldx + c]);
     }
 }
@@ -504,7 +554,7 @@ cudaError_t block_update_mx(int64_t n, int nb, const BlkMx* F, int kp, const dou
     FamMx FF = fam_mx(F, nb);
     int m = 0;
     for (int i = 0; i < nb; ++i) m += F[i].nc;
-    const size_t shm = sizeof(dw) * (kp * kp + kUpRows * kp) + sizeof(float) * (m * kp + kp * kp + kUpRows * m);
+    const size_t shm = up_mx_layout(m, kp).bytes;
     k_update_mx<<<sm_count() * 4, 256, shm, s>>>(n, m, kp, nb, FF, Cp, Cvv, Vout, vo64, ldvo, Pout, po64, ldpo);
     count_launches(1);
     return cudaGetLastError();

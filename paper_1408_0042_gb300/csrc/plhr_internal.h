@@ -240,3 +240,21 @@ inline int64_t prec_workspace_doubles(const plhr_prec* T, int nc) {
 plhr_status prec_apply64(const plhr_prec* T, int nc, const double* r, int64_t ldr, double* w, double* work,
                          cudaStream_t s);
 }  // namespace plhr
+
+#ifdef __CUDACC__
+namespace plhr {
+// row = e / nc and col = e - row nc for a flat index e of a row-major n x nc
+// block: a 32-bit division while e fits in 32 bits (a 64-bit division is a
+// long instruction sequence on the GPU), the 64-bit one past that
+__device__ __forceinline__ void split_index(int64_t e, int nc, int64_t& row, int& col) {
+    if ((uint64_t)e <= 0xffffffffull) {
+        const unsigned q = (unsigned)e / (unsigned)nc;
+        row = (int64_t)q;
+        col = (int)((unsigned)e - q * (unsigned)nc);
+    } else {
+        row = e / nc;
+        col = (int)(e - row * nc);
+    }
+}
+}  // namespace plhr
+#endif

@@ -15,8 +15,9 @@ __global__ void __launch_bounds__(256) k_diag(int64_t n, int nc, const double* _
                                               int64_t ldw) {
     const int64_t total = n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / nc;
-        const int c = (int)(e - i * nc);
+        int64_t i;
+        int c;
+        split_index(e, nc, i, c);
         w[i * ldw + c] = d[i] * r[i * ldr + c];
     }
 }

@@ -109,8 +109,9 @@ __global__ void __launch_bounds__(256) k_q1(Q1Geo g, int nc, int stiff, double s
                                             const double* __restrict__ lam, double* __restrict__ o2, int64_t ld2,
                                             double alpha, double beta, double sig, int64_t total) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e / nc;
-        const int c = (int)(e - row * nc);
+        int64_t row;
+        int c;
+        split_index(e, nc, row, c);
         const int64_t ix = row % g.nx, t = row / g.nx, iy = t % g.ny, iz = t / g.ny;
         double ya, yb;
         if (MODE == Q1_PAIR) {
@@ -146,8 +147,9 @@ struct BlochGeo {
 __global__ void __launch_bounds__(256) k_bloch(BlochGeo g, int nc, const double2* __restrict__ x, int64_t ldx,
                                                double2* __restrict__ y, int64_t ldy, int64_t total) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e / nc;
-        const int c = (int)(e - row * nc);
+        int64_t row;
+        int c;
+        split_index(e, nc, row, c);
         const int64_t ix = row % g.nx, t = row / g.nx, iy = t % g.ny, iz = t / g.ny;
         const int64_t n[3] = {g.nx, g.ny, g.nz}, i[3] = {ix, iy, iz}, st[3] = {1, g.nx, g.nx * g.ny};
         const double2 xc = x[row * ldx + c];

@@ -47,8 +47,10 @@ double tpa(double x) {
 __global__ void __launch_bounds__(kT) k_split(int64_t total, int nc, const double* __restrict__ r, int64_t ldr,
                                               dw* __restrict__ x) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t pt = e / nc;
-        x[e] = dw_from_double_fast(r[pt * ldr + (e - pt * nc)]);
+        int64_t pt;
+        int cc;
+        split_index(e, nc, pt, cc);
+        x[e] = dw_from_double_fast(r[pt * ldr + cc]);
     }
 }
 

@@ -126,3 +126,23 @@ def test_lap3d_128cube_mixed_full(plhr):
     Vn = V.cpu().numpy()
     assert np.all(_residuals(w, lam, Vn) <= w.tol * 1.0001)
     assert np.abs(Vn.T @ Vn - np.eye(w.k)).max() <= 1e-12
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("offset", [1, 2, 3, 4])
+def test_lap3d_128cube_mixed_other_start_blocks(plhr, offset):
+    """The 128^3 mixed solve from four other seeded start blocks: each
+    returns the closed-form set of the 10 eigenvalues nearest sigma (the
+    triple at 1061.03 included), not a converged set with one member of a
+    degenerate cluster replaced by a farther eigenvalue."""
+    w = wl.lap3d_128cube_k10()
+    A = plhr.Operator.laplacian(w.dims, w.h)
+    T = plhr.AVMG(A, w.sigma, levels=w.mg_levels, nu=w.mg_nu, transfer=1, coarse=1)
+    v0 = torch.from_numpy(wl.start_block(w.n, w.kprime, w.seed + 1000 * offset)).cuda()
+    lam, V, info = plhr.solve(A, w.sigma, w.k, T=T, tol=w.tol, maxit=w.maxit, v_init=v0, guard=w.guard,
+                              precision=plhr.PRECISION_MIXED)
+    assert info["converged"], info
+    cf = wl.lap_closed_form(w.dims, w.h)
+    want = cf[np.lexsort((cf, np.abs(cf - w.sigma)))][: w.k]
+    assert np.allclose(np.sort(lam), np.sort(want), rtol=1e-10)
+    assert info["max_rel_residual"] <= w.tol
