@@ -78,6 +78,7 @@ struct ColTc {
     const float* q[64];
     int64_t ldz[64], lda[64], ldq[64];
     int is_u[64];
+    int quad[3][16];      // columns 4q .. 4q + 3 of the family contiguous and 16-byte aligned in every row
 };
 
 // The column table in shared memory: indexing the kernel-parameter copy with
@@ -87,7 +88,10 @@ struct ColSh {
     const float* p[3][64];    // Z, AZ, Q
     int64_t ld[3][64];
     int is_u[64];
+    int quad[3][16];
 };
+
+static_assert(512 + sizeof(ColSh) <= (size_t)kMetaBytes, "column table fits the meta area");
 
 // TwoSum fold of 16 values into (hi, lo)
 __device__ __forceinline__ void fold16(float* hi, float* lo, const float* v) {
@@ -106,22 +110,32 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
 // Start the asynchronous copies of the raw rows row0 .. row0 + 31 (those
 // below n) of the Z, AZ and (with has_q) Q families into raw[row][192]:
 // element (r, j) of family f at raw[r * 192 + 64 f + j].  Thread t < 384
-// copies column j of family f for one half of the rows (consecutive threads
-// take consecutive columns, so a warp reads contiguous row segments); the
-// addresses advance by one row stride per copy.
+// copies the column quad 4q .. 4q + 3 of family f for 4 rows (consecutive
+// threads take consecutive quads, so a warp reads contiguous 256-byte row
+// segments): one 16-byte copy per row when the quad is contiguous and aligned
+// in memory, else one 4-byte copy per element.
 __device__ __forceinline__ void fetch_tc(float* raw, int64_t n, int64_t row0, int m, const ColSh& C, int has_q) {
     const int t = threadIdx.x;
-    if (t >= 2 * kPanelRows) return;
-    const int half = t / kPanelRows, fj = t - half * kPanelRows;
-    const int f = fj >> 6, j = fj & 63;
-    if (j >= m || (f == 2 && !has_q)) return;
-    const int64_t r0 = row0 + half * (kTcK / 2);
-    const int cnt = (int)(n - r0 < kTcK / 2 ? n - r0 : kTcK / 2);
-    const int64_t ld = C.ld[f][j];
-    const float* src = C.p[f][j] + r0 * ld;
-    float* dst = raw + half * (kTcK / 2) * kRawStride + fj;
-#pragma unroll 4
-    for (int r = 0; r < cnt; ++r, src += ld, dst += kRawStride) cp_async4(dst, src);
+    if (t >= 3 * 16 * (kTcK / 4)) return;
+    const int f = t / (16 * (kTcK / 4)), rem = t - f * (16 * (kTcK / 4));
+    const int qd = rem & 15, part = rem >> 4;
+    const int j0 = 4 * qd;
+    if (j0 >= m || (f == 2 && !has_q)) return;
+    const int64_t r0 = row0 + part * 4;
+    const int cnt = (int)(n - r0 < 4 ? n - r0 : 4);
+    float* dst = raw + part * 4 * kRawStride + 64 * f + j0;
+    if (C.quad[f][qd]) {
+        const int64_t ld = C.ld[f][j0];
+        const float* src = C.p[f][j0] + r0 * ld;
+        for (int r = 0; r < cnt; ++r, src += ld, dst += kRawStride) cp_async16(dst, src);
+        return;
+    }
+    for (int j = j0; j < j0 + 4 && j < m; ++j) {
+        const int64_t ld = C.ld[f][j];
+        const float* src = C.p[f][j] + r0 * ld;
+        float* d = dst + (j - j0);
+        for (int r = 0; r < cnt; ++r, src += ld, d += kRawStride) cp_async4(d, src);
+    }
 }
 
 // Convert the chunk of grid points row0 .. row0 + 31 (raw rows in shared
@@ -189,6 +203,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(int64_t n, int m, con
         cols.ld[2][tid] = C.ldq[tid];
         cols.is_u[tid] = C.is_u[tid];
     }
+    if (tid < 48) cols.quad[tid / 16][tid % 16] = C.quad[tid / 16][tid % 16];
     if (tid == 0) {
         for (int i = 0; i < 6; ++i) tc::mbar_init(&bars[i], 1);
         tc::mbar_init_fence();
@@ -379,6 +394,22 @@ cudaError_t multi_gram_tc(int64_t n, int nb, const BlkMx* Z, const BlkMx* AZ, co
         }
     }
     if (m == 0) return cudaSuccess;
+    // column quads that one 16-byte copy per row can fetch: same block (the
+    // pointers consecutive, the same leading dimension), aligned base, leading
+    // dimension a multiple of 4 floats
+    {
+        const float* const* ptr[3] = {C.z, C.a, C.q};
+        const int64_t* ldv[3] = {C.ldz, C.lda, C.ldq};
+        for (int f = 0; f < 3; ++f)
+            for (int q = 0; q < 16; ++q) {
+                const int j0 = 4 * q;
+                bool ok = j0 + 3 < m && ptr[f][j0] != nullptr;
+                for (int c = 1; ok && c < 4; ++c)
+                    ok = ptr[f][j0 + c] == ptr[f][j0] + c && ldv[f][j0 + c] == ldv[f][j0];
+                ok = ok && (reinterpret_cast<uintptr_t>(ptr[f][j0]) & 15) == 0 && ldv[f][j0] % 4 == 0;
+                C.quad[f][q] = ok ? 1 : 0;
+            }
+    }
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
