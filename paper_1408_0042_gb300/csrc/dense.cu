@@ -177,52 +177,110 @@ __device__ bool bchol_lower(double* A, int n, int* flag) {
 // Householder reduction of H (n x n) to upper Hessenberg form.  The reflector
 // of step k, I - beta_k v v^T with v = (0,..,0, v_{k+1}, .., v_{n-1}), is kept
 // in row k of Vh and beta[k] (beta = 0: identity).
-__device__ void bhessenberg(double* H, double* Vh, double* beta, int n, double* red) {
+//
+// The reduction runs in double-word arithmetic on H scaled by a power of two
+// to unit norm: its transformations are orthogonal, so it is as accurate as
+// the double-word QR iteration that follows it, and the FP64 form (one
+// dependent FP64 chain per column, each warp instruction holding the FP64 pipe
+// for 64 cycles) cost about a million cycles at n = 64.  Every column and row
+// belongs to a pair of threads that split its sum over i by parity (lazily
+// normalised double-word sums, combined by one shuffle).  v and beta describe
+// the same reflector at any scale, so only H is scaled back; H, Vh and beta
+// are FP64 again on return.
+__device__ void bhessenberg(double* Hd, double* Vhd, double* betad, int n, double* red) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const dw zero = dw_make(0.0f);
+    double an = 0.0;
+    for (int i = tid; i < n * n; i += NT) an = fmax(an, fabs(Hd[(i / n) * LDS + i % n]));
+    an = warp_max(an);
+    if (lane == 0) red[warp] = an;
+    bsync();
+    for (int w = 0; w < NT / 32; ++w) an = fmax(an, red[w]);
+    bsync();
+    const int ex = an > 0.0 ? ilogb(an) : 0;
+    const double down = ldexp(1.0, -ex), up = ldexp(1.0, ex);
+    dw* H = reinterpret_cast<dw*>(Hd);
+    dw* V = reinterpret_cast<dw*>(Vhd);
+    dw* B = reinterpret_cast<dw*>(betad);
+    for (int i = tid; i < n * n; i += NT) {
+        const int r = i / n, c = i % n;
+        H[r * LDS + c] = dw_from_double_fast(Hd[r * LDS + c] * down);
+    }
+    bsync();
+    float* redf = reinterpret_cast<float*>(red);
+    const int own = tid >> 1, half = tid & 1;
     for (int k = 0; k < n - 2; ++k) {
         // ||x||^2 for x = H[k+1:n, k]  (warp 0)
         if (warp == 0) {
-            double ss = 0.0;
-            for (int i = k + 1 + lane; i < n; i += 32) ss += H[i * LDS + k] * H[i * LDS + k];
-            ss = warp_sum(ss);
-            if (lane == 0) red[0] = ss;
+            dwacc acc = {0.0f, 0.0f};
+            for (int i = k + 1 + lane; i < n; i += 32) {
+                const dw x = H[i * LDS + k];
+                dwacc_add_mul(acc, x, x);
+            }
+            dw ss = dwacc_result(acc);
+            for (int o = 16; o > 0; o >>= 1)
+                ss = dw_add(ss, dw{__shfl_xor_sync(0xffffffffu, ss.hi, o), __shfl_xor_sync(0xffffffffu, ss.lo, o)});
+            if (lane == 0) { redf[0] = ss.hi; redf[1] = ss.lo; }
         }
         bsync();
-        const double ss = red[0];
-        const double x0 = H[(k + 1) * LDS + k];
-        double alpha = sqrt(ss);
-        if (x0 > 0) alpha = -alpha;
-        const double vv = ss - x0 * x0 + (x0 - alpha) * (x0 - alpha);
-        const bool skip = (alpha == 0.0) || (vv == 0.0);
-        const double b = skip ? 0.0 : 2.0 / vv;
-        for (int i = tid; i < n; i += NT) Vh[k * LDS + i] = (i <= k || skip) ? 0.0 : (i == k + 1 ? x0 - alpha : H[i * LDS + k]);
-        if (tid == 0) beta[k] = b;
+        const dw ss = {redf[0], redf[1]};
+        const dw x0 = H[(k + 1) * LDS + k];
+        dw alpha = dw_sqrt(ss);
+        if (x0.hi > 0.0f) alpha = dw_neg(alpha);
+        // v_{k+1} = x0 - alpha, v^T v = 2 (ss - x0 alpha) (alpha^2 = ss, no
+        // cancellation: -x0 alpha >= 0), beta = 2 / v^T v
+        const dw den = dw_sub(ss, dw_mul(x0, alpha));
+        const bool skip = dw_is_zero(alpha) || !(den.hi > 0.0f);
+        const dw b = skip ? zero : dw_div(dw_make(1.0f), den);
+        for (int i = tid; i < n; i += NT)
+            V[k * LDS + i] = (i <= k || skip) ? zero : (i == k + 1 ? dw_sub(x0, alpha) : H[i * LDS + k]);
+        if (tid == 0) B[k] = b;
         bsync();
         if (!skip) {
-            const double* v = Vh + k * LDS;
-            const int own = spread_second() ? n : spread_index();
-            // H <- (I - b v v^T) H : one column per thread
-            if (own < n) {
+            const dw* v = V + k * LDS;
+            // H <- (I - b v v^T) H : column c = own (columns below k are zero in rows > k)
+            {
                 const int c = own;
-                double s = 0.0;
-                for (int i = k + 1; i < n; ++i) s += v[i] * H[i * LDS + c];
-                s *= b;
-                for (int i = k + 1; i < n; ++i) H[i * LDS + c] -= s * v[i];
+                const bool act = c < n && c >= k;
+                dwacc acc = {0.0f, 0.0f};
+                if (act)
+                    for (int i = k + 1 + half; i < n; i += 2) dwacc_add_mul(acc, v[i], H[i * LDS + c]);
+                dw sv = dwacc_result(acc);
+                sv = dw_add(sv, dw{__shfl_xor_sync(0xffffffffu, sv.hi, 1), __shfl_xor_sync(0xffffffffu, sv.lo, 1)});
+                sv = dw_mul(sv, b);
+                if (act)
+                    for (int i = k + 1 + half; i < n; i += 2) H[i * LDS + c] = dw_sub(H[i * LDS + c], dw_mul(sv, v[i]));
             }
             bsync();
-            // H <- H (I - b v v^T) : one row per thread
-            if (own < n) {
+            // H <- H (I - b v v^T) : row r = own
+            {
                 const int r = own;
-                double s = 0.0;
-                for (int i = k + 1; i < n; ++i) s += H[r * LDS + i] * v[i];
-                s *= b;
-                for (int i = k + 1; i < n; ++i) H[r * LDS + i] -= s * v[i];
+                const bool act = r < n;
+                dwacc acc = {0.0f, 0.0f};
+                if (act)
+                    for (int i = k + 1 + half; i < n; i += 2) dwacc_add_mul(acc, H[r * LDS + i], v[i]);
+                dw sv = dwacc_result(acc);
+                sv = dw_add(sv, dw{__shfl_xor_sync(0xffffffffu, sv.hi, 1), __shfl_xor_sync(0xffffffffu, sv.lo, 1)});
+                sv = dw_mul(sv, b);
+                if (act)
+                    for (int i = k + 1 + half; i < n; i += 2) H[r * LDS + i] = dw_sub(H[r * LDS + i], dw_mul(sv, v[i]));
             }
             bsync();
-            for (int i = k + 2 + tid; i < n; i += NT) H[i * LDS + k] = 0.0;
+            for (int i = k + 2 + tid; i < n; i += NT) H[i * LDS + k] = zero;
         }
         bsync();
     }
+    // back to FP64 (each entry converted in place by the thread that reads it)
+    for (int i = tid; i < n * n; i += NT) {
+        const int r = i / n, c = i % n;
+        Hd[r * LDS + c] = dw_to_double(H[r * LDS + c]) * up;
+    }
+    for (int i = tid; i < (n - 2) * n; i += NT) {
+        const int r = i / n, c = i % n;
+        Vhd[r * LDS + c] = dw_to_double(V[r * LDS + c]);
+    }
+    for (int i = tid; i < n - 2; i += NT) betad[i] = dw_to_double(B[i]);
+    bsync();
 }
 
 // ---------------------------------------------------------------- eigenvalues (one warp)
@@ -617,6 +675,7 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
         }
         bsync();
         bchol_drop(S.A, m, S.keep, drop_tols[attempt]);
+        STAMP(11);
         if (tid == 0) {
             int q = 0, qv = 0;
             for (int j = 0; j < m; ++j)
@@ -648,7 +707,9 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
         }
         bsync();
         // ---- 2. the pencil in the B-orthonormal basis, via tau = 1/xi
+        STAMP(12);
         bcongruence2(S.A, S.B, S.H, nk);
+        STAMP(13);
         for (int i = tid; i < nk * nk; i += NT) {
             int r = i / nk, c = i % nk;
             if (c > r) {
@@ -692,6 +753,7 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
     STAMP(2);
     // ---- 3. eigenvalues of C: Hessenberg form, then Francis QR on a copy
     bhessenberg(S.H, S.Vh, S.beta, nk, S.red);
+    STAMP(14);
     for (int i = tid; i < nk * LDS; i += NT) S.H0[i] = S.H[i];
     if (tid == 0) S.ints[6] = 0;
     bsync();
