@@ -32,25 +32,6 @@ constexpr int MAXM = kDenseMaxM;
 constexpr int LDS = MAXM + 1;     // shared row stride: column accesses hit distinct banks
 constexpr int NT = 128;           // threads of the extraction CTA
 
-struct cplx {
-    double re, im;
-};
-__device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
-__device__ __forceinline__ cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
-__device__ __forceinline__ cplx cscale(cplx a, double s) { return {a.re * s, a.im * s}; }
-__device__ __forceinline__ double cabs1(cplx a) { return fabs(a.re) + fabs(a.im); }
-__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
-    // Smith's algorithm
-    if (fabs(b.re) >= fabs(b.im)) {
-        double r = b.im / b.re, d = b.re + b.im * r;
-        return {(a.re + a.im * r) / d, (a.im - a.re * r) / d};
-    } else {
-        double r = b.re / b.im, d = b.im + b.re * r;
-        return {(a.re * r + a.im) / d, (a.im * r - a.re) / d};
-    }
-}
-
 __device__ __forceinline__ void wsync() { __syncwarp(); }
 __device__ __forceinline__ void bsync() { __syncthreads(); }
 
@@ -632,6 +613,53 @@ __device__ __forceinline__ Smem* state_of(const DenseArgs& a) {
     return reinterpret_cast<Smem*>(a.work + kWorkMainDoubles);
 }
 
+// X <- L^{-1} X L^{-T} for the n x n block X (stride LDS, FP64 in and out)
+// and the lower triangular L (FP64), in double-word arithmetic; Lw (n x LDS
+// double-word) and rinv (n double-word values) are scratch.  Block-wide.
+__device__ void dense_csolve_dw(double* Xd, const double* L, double* Lwd, double* rinvd, int n) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    dw* X = reinterpret_cast<dw*>(Xd);
+    dw* Lw = reinterpret_cast<dw*>(Lwd);
+    dw* rinv = reinterpret_cast<dw*>(rinvd);
+    for (int i = tid; i < n * n; i += NT) {
+        const int r = i / n, c = i % n;
+        X[r * LDS + c] = dw_from_double_fast(Xd[r * LDS + c]);
+        if (c <= r) Lw[r * LDS + c] = dw_from_double_fast(L[r * LDS + c]);
+    }
+    bsync();
+    for (int i = tid; i < n; i += NT) rinv[i] = dw_div(dw_make(1.0f), Lw[i * LDS + i]);
+    bsync();
+    const int own = tid >> 1, half = tid & 1;
+    const bool act = own < n;
+    // columns: X[i][c] = (X[i][c] - sum_{l<i} L[i][l] X[l][c]) / L[i][i]
+    for (int i = 0; i < n; ++i) {
+        dwacc acc = {0.0f, 0.0f};
+        if (act)
+            for (int l = half; l < i; l += 2) dwacc_add_mul(acc, Lw[i * LDS + l], X[l * LDS + own]);
+        dw sv = dwacc_result(acc);
+        sv = dw_add(sv, dw{__shfl_xor_sync(0xffffffffu, sv.hi, 1), __shfl_xor_sync(0xffffffffu, sv.lo, 1)});
+        if (act && half == 0) X[i * LDS + own] = dw_mul(dw_sub(X[i * LDS + own], sv), rinv[i]);
+        __syncwarp();
+    }
+    bsync();
+    // rows: X[r][j] = (X[r][j] - sum_{l<j} X[r][l] L[j][l]) / L[j][j]
+    for (int j = 0; j < n; ++j) {
+        dwacc acc = {0.0f, 0.0f};
+        if (act)
+            for (int l = half; l < j; l += 2) dwacc_add_mul(acc, X[own * LDS + l], Lw[j * LDS + l]);
+        dw sv = dwacc_result(acc);
+        sv = dw_add(sv, dw{__shfl_xor_sync(0xffffffffu, sv.hi, 1), __shfl_xor_sync(0xffffffffu, sv.lo, 1)});
+        if (act && half == 0) X[own * LDS + j] = dw_mul(dw_sub(X[own * LDS + j], sv), rinv[j]);
+        __syncwarp();
+    }
+    bsync();
+    for (int i = tid; i < n * n; i += NT) {
+        const int r = i / n, c = i % n;
+        Xd[r * LDS + c] = dw_to_double(X[r * LDS + c]);
+    }
+    (void)lane;
+}
+
 // The dense stage runs as five launches: phase 0 of k_extract (up to the
 // Hessenberg form, state saved to global scratch), k_francis (two warps: the
 // eigenvalues), phase 1 (selection, state saved), k_eigvec (one CTA per
@@ -730,25 +758,15 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
         if (tid == 0) { a.out_int[0] = kDenseBreakdown; a.out_int[1] = nk; a.out_int[2] = 0; state_of(a)->ints[6] = 1; }
         return;
     }
-    // C = L^{-1} G_R L^{-T}: L Y = G_R by columns, then C L^T = Y by rows
-    const int own = spread_second() ? nk : spread_index();
-    if (own < nk) {
-        const int c = own;
-        for (int i = 0; i < nk; ++i) {
-            double sv = S.H[i * LDS + c];
-            for (int l = 0; l < i; ++l) sv -= S.B[i * LDS + l] * S.H[l * LDS + c];
-            S.H[i * LDS + c] = sv / S.B[i * LDS + i];
-        }
-    }
-    bsync();
-    if (own < nk) {
-        const int r = own;
-        for (int j = 0; j < nk; ++j) {
-            double sv = S.H[r * LDS + j];
-            for (int l = 0; l < j; ++l) sv -= S.H[r * LDS + l] * S.B[j * LDS + l];
-            S.H[r * LDS + j] = sv / S.B[j * LDS + j];
-        }
-    }
+    // C = L^{-1} G_R L^{-T}: L Y = G_R by columns, then C L^T = Y by rows, in
+    // double-word arithmetic (L is the Cholesky factor of the SPD G_L in the
+    // B-orthonormal basis; its condition is the square root of G_L's, so the
+    // solves lose little; in FP64 each dependent chain held a warp's FP64 pipe
+    // for 64 cycles per step).  A pair of threads owns a column (then a row)
+    // and splits each inner sum by parity; L (double-word) goes into the
+    // H0 array, free until the Hessenberg form is copied there, the
+    // reciprocals of its diagonal into red.
+    dense_csolve_dw(S.H, S.B, S.H0, S.red, nk);
     bsync();
     STAMP(2);
     // ---- 3. eigenvalues of C: Hessenberg form, then Francis QR on a copy
@@ -911,7 +929,9 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
         }
     }
     bsync();
-    // ---- Y' = [Y0 YR yR~ YI] (kept basis), column tags
+    // ---- Y' = [Y0 YR yR~ YI] (kept basis), column tags: thread 0 assigns the
+    // columns of each unit (keep: real part, nclose: imaginary part or -1;
+    // both free after the cluster step), then every thread copies entries
     if (tid == 0) {
         int nreal = 0, npair = 0;
         bool has_cut = false;
@@ -923,23 +943,27 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
         int col = 0, pr = 0;
         const int base_R = nreal, base_cut = nreal + npair, base_I = nreal + npair + (has_cut ? 1 : 0);
         for (int u = 0; u < nsel; ++u) {
-            const double* yr = Yre + u * MAXM;
-            const double* yi = Yim + u * MAXM;
             if (S.kind[u] == 0) {
-                for (int i = 0; i < nk; ++i) Yp[col * MAXM + i] = yr[i];
+                S.keep[u] = col; S.nclose[u] = -1;
                 a.tags[col] = 0; a.tag_partner[col] = -1;
                 ++col;
             } else if (S.kind[u] == 2) {
                 const int cr = base_R + pr, ci = base_I + pr;
-                for (int i = 0; i < nk; ++i) { Yp[cr * MAXM + i] = yr[i]; Yp[ci * MAXM + i] = yi[i]; }
+                S.keep[u] = cr; S.nclose[u] = ci;
                 a.tags[cr] = 1; a.tag_partner[cr] = ci;
                 a.tags[ci] = 3; a.tag_partner[ci] = cr;
                 ++pr;
             } else {
-                for (int i = 0; i < nk; ++i) Yp[base_cut * MAXM + i] = yr[i];
+                S.keep[u] = base_cut; S.nclose[u] = -1;
                 a.tags[base_cut] = 2; a.tag_partner[base_cut] = -1;
             }
         }
+    }
+    bsync();
+    for (int idx = tid; idx < nsel * nk; idx += NT) {
+        const int u = idx / nk, i = idx - u * nk;
+        Yp[S.keep[u] * MAXM + i] = Yre[u * MAXM + i];
+        if (S.nclose[u] >= 0) Yp[S.nclose[u] * MAXM + i] = Yim[u * MAXM + i];
     }
     __threadfence_block();
     bsync();
@@ -948,23 +972,33 @@ __global__ void __launch_bounds__(NT) k_extract(DenseArgs a, int phase) {
     // upper triangular with the V columns first, so
     //   P_new = Z-hat[:, rest] Y'_rest = Z diag(colscale t) R^{-1} [0; Y'_rest]
     //   V_new - P_new = Z-hat[:, V] Y'_V = Z_V diag(colscale t) R_VV^{-1} Y'_V
-    // column j = 4 warp + (lane & 3): lanes 0..3 solve for Wr, lanes 4..7 for
-    // Wv, so the 2 kp solves run on all four sub-partitions
+    // Four lanes per solve split each inner sum (l mod 4) and combine it by two
+    // shuffles: column j = 4 warp + (g & 3) of lane group g = lane / 4, groups
+    // 0..3 solve for Wr and 4..7 for Wv, all in one instruction stream (an
+    // FP64 warp instruction costs the same whatever its active lanes, so a
+    // quarter of the terms per lane is a quarter of the time); the diagonal's
+    // reciprocals are formed once, in parallel.
     static_assert(MAXKP <= 16, "four warps of four columns");
+    for (int i = tid; i < nk; i += NT) S.red[i] = 1.0 / S.A[i * LDS + i];
+    bsync();
     {
-        const int j = warp * 4 + (lane & 3);
-        if (lane < 4 && j < kp) {
-            for (int i = nk - 1; i >= 0; --i) {
-                double sv = (i >= nvk) ? Yp[j * MAXM + i] : 0.0;
-                for (int l = i + 1; l < nk; ++l) sv -= S.A[i * LDS + l] * Wr[j * MAXM + l];
-                Wr[j * MAXM + i] = sv / S.A[i * LDS + i];
+        const int g4 = lane & 3, grp = lane >> 2;
+        const int j = warp * 4 + (grp & 3);
+        const bool isv = grp >= 4;
+        double* W = isv ? Wv : Wr;
+        const int lim = isv ? nvk : nk;
+        for (int i = nk - 1; i >= 0; --i) {
+            const bool act = j < kp && i < lim;
+            double part = 0.0;
+            if (act)
+                for (int l = i + 1 + g4; l < lim; l += 4) part = fma(-S.A[i * LDS + l], W[j * MAXM + l], part);
+            part += __shfl_xor_sync(0xffffffffu, part, 1);
+            part += __shfl_xor_sync(0xffffffffu, part, 2);
+            if (act && g4 == 0) {
+                const double y = (isv || i >= nvk) ? Yp[j * MAXM + i] : 0.0;
+                W[j * MAXM + i] = (y + part) * S.red[i];
             }
-        } else if (lane >= 4 && lane < 8 && j < kp) {
-            for (int i = nvk - 1; i >= 0; --i) {
-                double sv = Yp[j * MAXM + i];
-                for (int l = i + 1; l < nvk; ++l) sv -= S.A[i * LDS + l] * Wv[j * MAXM + l];
-                Wv[j * MAXM + i] = sv / S.A[i * LDS + i];
-            }
+            __syncwarp();
         }
     }
     for (int i = tid; i < m * kp; i += NT) a.Cp[i] = 0.0;
