@@ -233,7 +233,10 @@ __global__ void __launch_bounds__(kT) k_restrict(G3 gf, G3 gc, int nc, int lin, 
 // memory, or in global scratch (gwork, 2 n0 doubles per column) when the
 // coarsest grid is too large for it
 // (S[point][mode] per axis, orthonormal).
-__global__ void __launch_bounds__(kT) k_coarse_sep(int d, int64_t nx, int64_t ny, int64_t nz, int nc,
+// coarsest level: 1024 threads per column (each output is still one thread's
+// sum in a fixed order); the transforms of one column are latency-bound
+constexpr int kTC = 1024;
+__global__ void __launch_bounds__(kTC) k_coarse_sep(int d, int64_t nx, int64_t ny, int64_t nz, int nc,
                                                    const double* __restrict__ Sx, const double* __restrict__ Sy,
                                                    const double* __restrict__ Sz, const double* __restrict__ mx,
                                                    const double* __restrict__ my, const double* __restrict__ mz,
@@ -390,7 +393,7 @@ cudaError_t coarse_solve(const MGHierarchy& H, int nc, const double* in, int64_t
         cudaError_t e = cudaFuncSetAttribute(k_coarse_sep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;
     }
-    k_coarse_sep<<<nc, kT, shm, s>>>(g.d, g.nx, g.ny, g.nz, nc, H.d_basis[0], H.d_basis[1],
+    k_coarse_sep<<<nc, kTC, shm, s>>>(g.d, g.nx, g.ny, g.nz, nc, H.d_basis[0], H.d_basis[1],
                                      g.d == 3 ? H.d_basis[2] : H.d_basis[1], H.d_mu[0], H.d_mu[1],
                                      g.d == 3 ? H.d_mu[2] : H.d_mu[1], H.sigma, H.indefinite, in, ldi, out, ldo,
                                      global ? gwork : nullptr);

@@ -304,10 +304,108 @@ __global__ void __launch_bounds__(kT) k_restrict(Lv gf, Lv gc, int lin, const fl
     vst<VW>(rc + p.row * gc.nc + p.c, acc);
 }
 
+// The transfers one grid line per CTA, separably (as in the double-word
+// form): the y-z interpolation (prolongation) or y-z sums (restriction) of
+// one line of all columns go to shared memory, then the x taps.  VW
+// consecutive columns per thread.
+template <bool D3, int VW>
+__global__ void __launch_bounds__(kT) k_prolong_line(Lv gf, Lv gc, int lin, const float* __restrict__ wc,
+                                                     float* __restrict__ wf) {
+    extern __shared__ float ush32[];   // [coarse x][column]
+    const int iy = blockIdx.x, iz = blockIdx.y;
+    int yi[2], zi[2];
+    float yw[2], zw[2];
+    const int nyw = pw(lin, iy, gc.ny, yi, yw);
+    int nzw = 1;
+    zi[0] = 0; zw[0] = 1.0f;
+    if (D3) nzw = pw(lin, iz, gc.nz, zi, zw);
+    const int nc = gf.nc, nq = gf.nq;
+    float acc[VW], v[VW];
+    for (int t = threadIdx.x; t < gc.nx * nq; t += blockDim.x) {
+        const int X = t / nq, c = (t - X * nq) * VW;
+#pragma unroll
+        for (int e = 0; e < VW; ++e) acc[e] = 0.0f;
+        for (int a = 0; a < nzw; ++a)
+            for (int b = 0; b < nyw; ++b) {
+                vld<VW>(v, wc + (((int64_t)zi[a] * gc.ny + yi[b]) * gc.nx + X) * nc + c);
+                const float wt = zw[a] * yw[b];
+#pragma unroll
+                for (int e = 0; e < VW; ++e) acc[e] += wt * v[e];
+            }
+        vst<VW>(ush32 + X * nc + c, acc);
+    }
+    __syncthreads();
+    const int64_t row0 = ((int64_t)iz * gf.ny + iy) * gf.nx;
+    for (int t = threadIdx.x; t < gf.nx * nq; t += blockDim.x) {
+        const int x = t / nq, c = (t - x * nq) * VW;
+        int xi[2];
+        float xw[2];
+        const int nxw = pw(lin, x, gc.nx, xi, xw);
+        float* dst = wf + (row0 + x) * nc + c;
+        vld<VW>(acc, dst);
+        for (int q = 0; q < nxw; ++q) {
+            vld<VW>(v, ush32 + xi[q] * nc + c);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) acc[e] += xw[q] * v[e];
+        }
+        vst<VW>(dst, acc);
+    }
+}
+
+template <bool D3, int VW>
+__global__ void __launch_bounds__(kT) k_restrict_line(Lv gf, Lv gc, int lin, const float* __restrict__ f,
+                                                      float* __restrict__ rc) {
+    extern __shared__ float tsh32[];   // [fine x][column]
+    const int J = blockIdx.x, K = blockIdx.y;
+    int yi[4], zi[4];
+    float yw[4], zw[4];
+    const int nyw = rw(lin, J, gf.ny, yi, yw);
+    int nzw = 1;
+    zi[0] = 0; zw[0] = 1.0f;
+    if (D3) nzw = rw(lin, K, gf.nz, zi, zw);
+    const int nc = gf.nc, nq = gf.nq;
+    float acc[VW], v[VW];
+    for (int t = threadIdx.x; t < gf.nx * nq; t += blockDim.x) {
+        const int x = t / nq, c = (t - x * nq) * VW;
+#pragma unroll
+        for (int e = 0; e < VW; ++e) acc[e] = 0.0f;
+        for (int a = 0; a < nzw; ++a)
+            for (int b = 0; b < nyw; ++b) {
+                vld<VW>(v, f + (((int64_t)zi[a] * gf.ny + yi[b]) * gf.nx + x) * nc + c);
+                const float wt = zw[a] * yw[b];
+#pragma unroll
+                for (int e = 0; e < VW; ++e) acc[e] += wt * v[e];
+            }
+        vst<VW>(tsh32 + x * nc + c, acc);
+    }
+    __syncthreads();
+    const int64_t row0 = ((int64_t)K * gc.ny + J) * gc.nx;
+    for (int t = threadIdx.x; t < gc.nx * nq; t += blockDim.x) {
+        const int X = t / nq, c = (t - X * nq) * VW;
+        int xi[4];
+        float xw[4];
+        const int nxw = rw(lin, X, gf.nx, xi, xw);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) acc[e] = 0.0f;
+        for (int q = 0; q < nxw; ++q) {
+            vld<VW>(v, tsh32 + xi[q] * nc + c);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) acc[e] += xw[q] * v[e];
+        }
+        vst<VW>(rc + (row0 + X) * nc + c, acc);
+    }
+}
+
+// the line kernels keep one x-line of all columns in shared memory
+constexpr size_t kLineSmemMax = 48 * 1024;
+
 // Coarsest solve, one CTA per column: out = S diag(1/|mu_i + mu_j + mu_k - sig|) S^T in,
 // S = Sx (x) Sy (x) Sz, applied one axis at a time through shared memory.
+// coarsest level: 1024 threads per column (each output is still one thread's
+// sum in a fixed order); the transforms of one column are latency-bound
+constexpr int kTC = 1024;
 template <typename Tr>
-__global__ void __launch_bounds__(kT) k_coarse_sep(int d, int nx, int ny, int nz, int nc, const float* __restrict__ Sx,
+__global__ void __launch_bounds__(kTC) k_coarse_sep(int d, int nx, int ny, int nz, int nc, const float* __restrict__ Sx,
                                                    const float* __restrict__ Sy, const float* __restrict__ Sz,
                                                    const float* __restrict__ mx, const float* __restrict__ my,
                                                    const float* __restrict__ mz, float sig,
@@ -411,7 +509,7 @@ cudaError_t coarse(const MGHierarchy& H, int nc, const Tr* r, int64_t ldr, float
         cudaError_t e = cudaFuncSetAttribute(k_coarse_sep<Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;
     }
-    k_coarse_sep<Tr><<<nc, kT, shm, s>>>(g.d, (int)g.nx, (int)g.ny, (int)g.nz, nc, H.f_basis[0], H.f_basis[1],
+    k_coarse_sep<Tr><<<nc, kTC, shm, s>>>(g.d, (int)g.nx, (int)g.ny, (int)g.nz, nc, H.f_basis[0], H.f_basis[1],
                                         g.d == 3 ? H.f_basis[2] : H.f_basis[1], H.f_mu[0], H.f_mu[1],
                                         g.d == 3 ? H.f_mu[2] : H.f_mu[1], (float)H.sigma, r, ldr, out);
     count_launches(1);
@@ -467,12 +565,38 @@ cudaError_t vcycle(const MGHierarchy& H, int l, int nc, bool v4, const Tr* r, in
         PLHR_L4(k_shifted, Tr, gr, g, sig, cur, b.tmp);
         PLHR_L4(k_poly, Tr, gr, g, sig, (float)L.c, om, 1, cur, b.tmp, r, ldr, nxt);
     }
-    PLHR_L4(k_restrict, float, grc, g, gc, H.linear, nxt, b.rc);
+    if (sizeof(float) * L.g.nx * nc <= kLineSmemMax && Lc.g.ny <= 65535 && Lc.g.nz <= 65535) {
+        const dim3 gl((unsigned)Lc.g.ny, (unsigned)Lc.g.nz);
+        const size_t sh = sizeof(float) * L.g.nx * nc;
+        if (d3) {
+            if (v4) k_restrict_line<true, 4><<<gl, kT, sh, s>>>(g, gc, H.linear, nxt, b.rc);
+            else k_restrict_line<true, 1><<<gl, kT, sh, s>>>(g, gc, H.linear, nxt, b.rc);
+        } else {
+            if (v4) k_restrict_line<false, 4><<<gl, kT, sh, s>>>(g, gc, H.linear, nxt, b.rc);
+            else k_restrict_line<false, 1><<<gl, kT, sh, s>>>(g, gc, H.linear, nxt, b.rc);
+        }
+        count_launches(1);
+    } else {
+        PLHR_L4(k_restrict, float, grc, g, gc, H.linear, nxt, b.rc);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = vcycle<float>(H, l - 1, nc, v4, b.rc, nc, b.wc, B, s);
     if (e != cudaSuccess) return e;
-    PLHR_L4(k_prolong_add, float, gr, g, gc, H.linear, b.wc, cur);
+    if (sizeof(float) * Lc.g.nx * nc <= kLineSmemMax && L.g.ny <= 65535 && L.g.nz <= 65535) {
+        const dim3 gl((unsigned)L.g.ny, (unsigned)L.g.nz);
+        const size_t sh = sizeof(float) * Lc.g.nx * nc;
+        if (d3) {
+            if (v4) k_prolong_line<true, 4><<<gl, kT, sh, s>>>(g, gc, H.linear, b.wc, cur);
+            else k_prolong_line<true, 1><<<gl, kT, sh, s>>>(g, gc, H.linear, b.wc, cur);
+        } else {
+            if (v4) k_prolong_line<false, 4><<<gl, kT, sh, s>>>(g, gc, H.linear, b.wc, cur);
+            else k_prolong_line<false, 1><<<gl, kT, sh, s>>>(g, gc, H.linear, b.wc, cur);
+        }
+        count_launches(1);
+    } else {
+        PLHR_L4(k_prolong_add, float, gr, g, gc, H.linear, b.wc, cur);
+    }
     // post-smoothing; the last sweep writes out
     for (int i = 0; i < H.nu; ++i) {
         float* dst = (i == H.nu - 1) ? out : nxt;

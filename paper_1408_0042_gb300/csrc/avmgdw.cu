@@ -218,8 +218,90 @@ __global__ void __launch_bounds__(kT) k_restrict(Ld gf, Ld gc, int lin, const dw
     rc[p.row * gc.nc + p.c] = dwacc_result(acc);
 }
 
-// coarsest solve, one CTA per column: out = S diag(1/|mu_i + mu_j + mu_k - sig|) S^T in
-__global__ void __launch_bounds__(kT) k_coarse_sep(int d, int nx, int ny, int nz, int nc, const dw* __restrict__ Sx,
+// The transfers one grid line per CTA, separably.  Prolongation (one fine
+// x-line): the y-z interpolation of the coarse values under the line, once
+// per coarse x (up to 4 taps), then the x interpolation (2 taps), 4 instead
+// of 8 double-word multiply-adds per fine value.  Restriction (one coarse
+// x-line): the y-z sums of the fine values, once per fine x (up to 16 taps),
+// then the x taps (up to 4), 36 instead of 64 per coarse value.  The partial
+// line is kept in shared memory.
+template <bool D3>
+__global__ void __launch_bounds__(kT) k_prolong_line(Ld gf, Ld gc, int lin, const dw* __restrict__ wc,
+                                                     dw* __restrict__ wf) {
+    extern __shared__ dw ush[];   // [coarse x][column]
+    const int iy = blockIdx.x, iz = blockIdx.y;
+    int yi[2], zi[2];
+    float yw[2], zw[2];
+    const int nyw = pw(lin, iy, gc.ny, yi, yw);
+    int nzw = 1;
+    zi[0] = 0; zw[0] = 1.0f;
+    if (D3) nzw = pw(lin, iz, gc.nz, zi, zw);
+    const int nc = gf.nc, nu = gc.nx * nc;
+    for (int t = threadIdx.x; t < nu; t += blockDim.x) {
+        const int X = t / nc, c = t - X * nc;
+        dwacc acc = {0.0f, 0.0f};
+        for (int a = 0; a < nzw; ++a)
+            for (int b = 0; b < nyw; ++b)
+                dwacc_add_mul_f(acc, wc[(((int64_t)zi[a] * gc.ny + yi[b]) * gc.nx + X) * nc + c], zw[a] * yw[b]);
+        ush[t] = dwacc_result(acc);
+    }
+    __syncthreads();
+    const int nf = gf.nx * nc;
+    const int64_t row0 = ((int64_t)iz * gf.ny + iy) * gf.nx;
+    for (int t = threadIdx.x; t < nf; t += blockDim.x) {
+        const int x = t / nc, c = t - x * nc;
+        int xi[2];
+        float xw[2];
+        const int nxw = pw(lin, x, gc.nx, xi, xw);
+        const int64_t e = (row0 + x) * nc + c;
+        dwacc acc = dwacc_of(wf[e]);
+        for (int q = 0; q < nxw; ++q) dwacc_add_mul_f(acc, ush[xi[q] * nc + c], xw[q]);
+        wf[e] = dwacc_result(acc);
+    }
+}
+
+template <bool D3>
+__global__ void __launch_bounds__(kT) k_restrict_line(Ld gf, Ld gc, int lin, const dw* __restrict__ f,
+                                                      dw* __restrict__ rc) {
+    extern __shared__ dw tsh[];   // [fine x][column]
+    const int J = blockIdx.x, K = blockIdx.y;
+    int yi[4], zi[4];
+    float yw[4], zw[4];
+    const int nyw = rw(lin, J, gf.ny, yi, yw);
+    int nzw = 1;
+    zi[0] = 0; zw[0] = 1.0f;
+    if (D3) nzw = rw(lin, K, gf.nz, zi, zw);
+    const int nc = gf.nc, nt = gf.nx * nc;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const int x = t / nc, c = t - x * nc;
+        dwacc acc = {0.0f, 0.0f};
+        for (int a = 0; a < nzw; ++a)
+            for (int b = 0; b < nyw; ++b)
+                dwacc_add_mul_f(acc, f[(((int64_t)zi[a] * gf.ny + yi[b]) * gf.nx + x) * nc + c], zw[a] * yw[b]);
+        tsh[t] = dwacc_result(acc);
+    }
+    __syncthreads();
+    const int no = gc.nx * nc;
+    const int64_t row0 = ((int64_t)K * gc.ny + J) * gc.nx;
+    for (int t = threadIdx.x; t < no; t += blockDim.x) {
+        const int X = t / nc, c = t - X * nc;
+        int xi[4];
+        float xw[4];
+        const int nxw = rw(lin, X, gf.nx, xi, xw);
+        dwacc acc = {0.0f, 0.0f};
+        for (int q = 0; q < nxw; ++q) dwacc_add_mul_f(acc, tsh[xi[q] * nc + c], xw[q]);
+        rc[(row0 + X) * nc + c] = dwacc_result(acc);
+    }
+}
+
+// the line kernels keep one x-line of all columns in shared memory
+constexpr size_t kLineSmemMax = 48 * 1024;
+
+// coarsest solve, one CTA of 1024 threads per column:
+// out = S diag(1/|mu_i + mu_j + mu_k - sig|) S^T in.  Each output is still one
+// thread's sum in a fixed order; the transforms of one column are latency-bound.
+constexpr int kTC = 1024;
+__global__ void __launch_bounds__(kTC) k_coarse_sep(int d, int nx, int ny, int nz, int nc, const dw* __restrict__ Sx,
                                                    const dw* __restrict__ Sy, const dw* __restrict__ Sz,
                                                    const dw* __restrict__ mx, const dw* __restrict__ my,
                                                    const dw* __restrict__ mz, dw sig, const dw* __restrict__ in,
@@ -355,7 +437,7 @@ cudaError_t vcycle(const MGHierarchy& H, int l, int nc, const dw* r, dw* out, co
                           reinterpret_cast<const dw*>(H.w_basis[g0.d == 3 ? 2 : 1])};
         const dw* mu[3] = {reinterpret_cast<const dw*>(H.w_mu[0]), reinterpret_cast<const dw*>(H.w_mu[1]),
                            reinterpret_cast<const dw*>(H.w_mu[g0.d == 3 ? 2 : 1])};
-        k_coarse_sep<<<nc, kT, shm, s>>>(g0.d, (int)g0.nx, (int)g0.ny, (int)g0.nz, nc, b[0], b[1], b[2], mu[0], mu[1],
+        k_coarse_sep<<<nc, kTC, shm, s>>>(g0.d, (int)g0.nx, (int)g0.ny, (int)g0.nz, nc, b[0], b[1], b[2], mu[0], mu[1],
                                         mu[2], dw_host(H.sigma), r, out);
         count_launches(1);
         return cudaGetLastError();
@@ -388,12 +470,28 @@ cudaError_t vcycle(const MGHierarchy& H, int l, int nc, const dw* r, dw* out, co
         PLHR_LD(k_shifted, gr, g, sig, cur, bf.tmp);
         PLHR_LD(k_poly, gr, g, sig, dw_host(L.c * L.c), dw_host(0.5 / L.c), om, 1, cur, bf.tmp, r, nxt);
     }
-    PLHR_LD(k_restrict, grc, g, gc, H.linear, nxt, bf.rc);
+    if (sizeof(dw) * L.g.nx * nc <= kLineSmemMax && Lc.g.ny <= 65535 && Lc.g.nz <= 65535) {
+        const dim3 gl((unsigned)Lc.g.ny, (unsigned)Lc.g.nz);
+        const size_t sh = sizeof(dw) * L.g.nx * nc;
+        if (d3) k_restrict_line<true><<<gl, kT, sh, s>>>(g, gc, H.linear, nxt, bf.rc);
+        else k_restrict_line<false><<<gl, kT, sh, s>>>(g, gc, H.linear, nxt, bf.rc);
+        count_launches(1);
+    } else {
+        PLHR_LD(k_restrict, grc, g, gc, H.linear, nxt, bf.rc);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = vcycle(H, l - 1, nc, bf.rc, bf.wc, B, s);
     if (e != cudaSuccess) return e;
-    PLHR_LD(k_prolong_add, gr, g, gc, H.linear, bf.wc, cur);
+    if (sizeof(dw) * Lc.g.nx * nc <= kLineSmemMax && L.g.ny <= 65535 && L.g.nz <= 65535) {
+        const dim3 gl((unsigned)L.g.ny, (unsigned)L.g.nz);
+        const size_t sh = sizeof(dw) * Lc.g.nx * nc;
+        if (d3) k_prolong_line<true><<<gl, kT, sh, s>>>(g, gc, H.linear, bf.wc, cur);
+        else k_prolong_line<false><<<gl, kT, sh, s>>>(g, gc, H.linear, bf.wc, cur);
+        count_launches(1);
+    } else {
+        PLHR_LD(k_prolong_add, gr, g, gc, H.linear, bf.wc, cur);
+    }
     for (int i = 0; i < H.nu; ++i) {
         dw* dst = (i == H.nu - 1) ? out : nxt;
         sweep(L, sig, nc, cur, r, bf.tmp, dst, s);

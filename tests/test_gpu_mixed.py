@@ -36,11 +36,13 @@ def _residuals(w, lam, V):
 # O(levels * nu) FP32 roundings per entry, each about 6e-8 of the entries it
 # combines; 2e-5 of the largest output entry bounds that for these sizes.
 # nc = 5: one column per thread; nc = 8, 12: four columns per thread (16-byte
-# accesses)
+# accesses).  The transfers stage one grid line of all columns in shared
+# memory where it fits in 48 KB; the 1024-point lines of 12 and 13 columns do
+# not (point-wise transfers on the finest level, line transfers below).
 @pytest.mark.parametrize("dims,levels,sigma,transfer,coarse,nc", [
     ((16, 16, 16), 1, 300.0, 0, 0, 5), ((16, 16, 16), 3, 900.0, 1, 1, 5), ((16, 16, 16), 3, 2500.0, 1, 1, 8),
     ((32, 24, 16), 3, 700.0, 0, 0, 12), ((32, 24, 16), 3, 700.0, 1, 1, 8), ((32, 24), 3, 700.0, 1, 1, 5),
-    ((32, 24), 3, 700.0, 0, 0, 4)])
+    ((32, 24), 3, 700.0, 0, 0, 4), ((1024, 8), 3, 700.0, 1, 1, 13), ((1024, 8), 3, 700.0, 1, 1, 12)])
 def test_avmg_f32_matches_oracle(plhr, dims, levels, sigma, transfer, coarse, nc):
     h = 1.0 / (max(dims) + 1)
     A = plhr.Operator.laplacian(dims, h)
@@ -53,10 +55,11 @@ def test_avmg_f32_matches_oracle(plhr, dims, levels, sigma, transfer, coarse, nc
 
 
 # double-word arithmetic (unit roundoff 2^-48): the V-cycle matches the FP64
-# oracle to ~1e-13 of its largest entry
+# oracle to ~1e-13 of its largest entry (1024 x 8: point-wise transfers on the
+# two finer levels, line transfers on the coarsest pair)
 @pytest.mark.parametrize("dims,levels,sigma,transfer,coarse,nc", [
     ((16, 16, 16), 1, 300.0, 0, 0, 3), ((16, 16, 16), 3, 900.0, 1, 1, 5), ((16, 16, 16), 3, 2500.0, 1, 1, 4),
-    ((32, 24, 16), 3, 700.0, 0, 0, 7), ((32, 24), 3, 700.0, 1, 1, 5)])
+    ((32, 24, 16), 3, 700.0, 0, 0, 7), ((32, 24), 3, 700.0, 1, 1, 5), ((1024, 8), 3, 700.0, 1, 1, 13)])
 def test_avmg_dw_matches_oracle(plhr, dims, levels, sigma, transfer, coarse, nc):
     h = 1.0 / (max(dims) + 1)
     A = plhr.Operator.laplacian(dims, h)
