@@ -8,7 +8,7 @@ arithmetic), preconditioner = 4-level AV-MG V-cycle with 2 pre/post smoothing
 steps.  A step is one complete solve from the seeded starting block to
 convergence (all k relative residuals <= 1e-8 after the final Rayleigh-Ritz),
 by default in the mixed-precision form (FP32 blocks and V-cycles until the k
-residuals reach 1e-5, then FP64); one all-FP64 solve is timed beside it.
+residuals reach 1e-6, then FP64); one all-FP64 solve is timed beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--precision mixed|f64] [--no-f64-compare]
@@ -795,7 +795,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "f64"], default="mixed")
-    ap.add_argument("--switch-tol", type=float, default=1e-5,
+    ap.add_argument("--switch-tol", type=float, default=1e-6,
                     help="mixed form: residual level where the FP32 phase hands over to the double-word phase")
     ap.add_argument("--no-f64-compare", action="store_true",
                     help="skip the all-FP64 solve timed beside the mixed-precision steps")

@@ -259,7 +259,7 @@ typedef struct {
                                   nearest sigma are all below switch_tol (or have stopped
                                   improving for 25 iterations below 1e-5), then continues in
                                   FP64 with the images recomputed explicitly and the columns beyond the
-                                  k nearest restarted from seeded random vectors (default 1e-5) */
+                                  k nearest restarted from seeded random vectors (default 1e-6) */
     int extraction;            /* 0: T-harmonic Rayleigh-Ritz (Section 3.1, default); 1: harmonic
                                   (T = I in the Petrov-Galerkin condition, Section 5.1's
                                   comparison).  extraction 1 and s_vectors 0 (the trial space

@@ -565,7 +565,7 @@ def gram(form, Z, AZ, Q=None, sigma=0.0, colscale=None, stream=None):
 
 def solve(A: Operator, sigma: float, k: int, T: AVMG | None = None, tol: float = 1e-8, maxit: int = 1000,
           v_init=None, seed: int = 20140801, history: bool = False, precision: int = PRECISION_F64,
-          stream=None, raise_on_notconv: bool = False, guard: int = 1, switch_tol: float = 1e-5,
+          stream=None, raise_on_notconv: bool = False, guard: int = 1, switch_tol: float = 1e-6,
           extraction: str = "tharm", s_vectors: bool = True, B: Operator | None = None,
           tensor_cores: bool = True):
     """k eigenpairs of A v = lambda v nearest sigma with k + guard block

@@ -89,7 +89,7 @@ extern "C" void plhr_options_default(plhr_options* o) {
     o->soft_lock = 1;
     o->seed = 20140801ull;
     o->guard = 1;
-    o->switch_tol = 1e-5;
+    o->switch_tol = 1e-6;
     o->extraction = 0;
     o->tensor_cores = 1;
 }

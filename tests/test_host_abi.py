@@ -44,7 +44,7 @@ def test_option_defaults(p):
     lib.plhr_options_default(ctypes.byref(o))
     assert (o.maxit, o.precision, o.real_arithmetic, o.s_vectors, o.soft_lock) == (1000, p.PRECISION_F64, 1, 1, 1)
     assert (o.guard, o.extraction, o.seed) == (1, 0, 20140801)
-    assert o.switch_tol == 1e-5 and not o.v_init and not o.history
+    assert o.switch_tol == 1e-6 and not o.v_init and not o.history
     g = p.MGOpts()
     lib.plhr_mg_opts_default(ctypes.byref(g))
     assert (g.levels, g.nu, g.transfer, g.coarse) == (1, 2, 0, 0)
