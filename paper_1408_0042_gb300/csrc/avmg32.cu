@@ -653,18 +653,22 @@ cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const double* r, int64_t
     // an FP64 right-hand side is read by four fine-level kernels: round it to
     // FP32 once (one pass) so that every level kernel streams FP32
     if (nc <= 0) return cudaSuccess;
-    const int64_t n = H.lev.back().g.n();
-    float* r32 = work + (mg_workspace_floats(H, nc) - n * nc);
-    k_narrow_rhs<<<grid_size_for(n * nc, 256, sm_count() * 8), 256, 0, s>>>(n, nc, r, ldr, r32);
-    count_launches(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return run<float>(H, nc, r32, nc, w, work, s);
+    return mg_graphed(H, 1, nc, r, ldr, w, nc, work, s, [&](cudaStream_t st) -> cudaError_t {
+        const int64_t n = H.lev.back().g.n();
+        float* r32 = work + (mg_workspace_floats(H, nc) - n * nc);
+        k_narrow_rhs<<<grid_size_for(n * nc, 256, sm_count() * 8), 256, 0, st>>>(n, nc, r, ldr, r32);
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return run<float>(H, nc, r32, nc, w, work, st);
+    });
 }
 
 cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const float* r, int64_t ldr, float* w, float* work,
                           cudaStream_t s) {
-    return run<float>(H, nc, r, ldr, w, work, s);
+    if (nc <= 0) return cudaSuccess;
+    return mg_graphed(H, 0, nc, r, ldr, w, nc, work, s,
+                      [&](cudaStream_t st) -> cudaError_t { return run<float>(H, nc, r, ldr, w, work, st); });
 }
 
 }  // namespace plhr

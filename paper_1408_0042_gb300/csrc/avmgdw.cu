@@ -530,16 +530,18 @@ cudaError_t mg_vcycle_dw(const MGHierarchy& H, int nc, const double* r, int64_t 
     }
     dw* rdw = p; p += n * nc;
     dw* wdw = p;
-    const int blocks = grid_size_for(n * nc, 256, sm_count() * 8);
-    k_to_dw<<<blocks, 256, 0, s>>>(n, nc, r, ldr, rdw);
-    count_launches(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = vcycle(H, top, nc, rdw, wdw, B, s);
-    if (e != cudaSuccess) return e;
-    k_from_dw<<<blocks, 256, 0, s>>>(n, nc, wdw, w, ldw);
-    count_launches(1);
-    return cudaGetLastError();
+    return mg_graphed(H, 2, nc, r, ldr, w, ldw, work_v, s, [&](cudaStream_t st) -> cudaError_t {
+        const int blocks = grid_size_for(n * nc, 256, sm_count() * 8);
+        k_to_dw<<<blocks, 256, 0, st>>>(n, nc, r, ldr, rdw);
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = vcycle(H, top, nc, rdw, wdw, B, st);
+        if (e != cudaSuccess) return e;
+        k_from_dw<<<blocks, 256, 0, st>>>(n, nc, wdw, w, ldw);
+        count_launches(1);
+        return cudaGetLastError();
+    });
 }
 
 }  // namespace plhr

@@ -352,6 +352,8 @@ plhr_status plhr_prec_avmg(plhr_prec** out, const plhr_op* A, double sigma, cons
 void plhr_prec_destroy(plhr_prec* T) {
     if (!T) return;
     cudaDeviceSynchronize();   // queued V-cycles may still read the hierarchy and workspace
+    mg_release_graphs(T->H);
+    if (T->H.capture) cudaStreamDestroy(T->H.capture);
     for (int a = 0; a < 3; ++a) {
         if (T->sp.d_S[a]) cudaFree(T->sp.d_S[a]);
         if (T->sp.d_St[a]) cudaFree(T->sp.d_St[a]);
@@ -377,6 +379,7 @@ plhr_status prec_reserve(plhr_prec* T, int nc, int64_t extra_doubles) {
     if (need <= T->work_doubles) return PLHR_OK;
     if (T->work) {
         cudaDeviceSynchronize();
+        mg_release_graphs(T->H);   // they hold the old workspace's addresses
         cudaFree(T->work);
         T->work = nullptr;
         T->work_doubles = 0;
@@ -394,6 +397,7 @@ plhr_status prec_reserve32(plhr_prec* T, int nc, int64_t extra_floats) {
     if (need <= T->work_floats) return PLHR_OK;
     if (T->work32) {
         cudaDeviceSynchronize();
+        mg_release_graphs(T->H);
         cudaFree(T->work32);
         T->work32 = nullptr;
         T->work_floats = 0;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include "plhr.h"
@@ -156,7 +157,33 @@ struct MGHierarchy {
     float* w_basis[3] = {nullptr, nullptr, nullptr};   // double-word (hi, lo) copies for the
     float* w_mu[3] = {nullptr, nullptr, nullptr};      // double-word V-cycle
     int64_t n0[3] = {1, 1, 1};
+    // V-cycles captured as CUDA graphs, keyed by their arguments, and replayed
+    // instead of issuing their ~35 launches again (mg_graphed)
+    struct Graph {
+        int kind, nc;
+        const void* r;
+        int64_t ldr;
+        const void* w;
+        int64_t ldw;
+        const void* work;
+        cudaGraphExec_t exec;
+        int launches;
+    };
+    mutable std::vector<Graph> graphs;
+    mutable cudaStream_t capture = nullptr;   // non-default stream the captures run on
 };
+
+// Run body (the launches of one V-cycle, issued on the stream it is given)
+// on s: the first call with a given (kind, nc, r, ldr, w, ldw, work) captures
+// it into a CUDA graph, later calls replay the graph.  Falls back to issuing
+// body on s directly when a capture fails or the cache is full.  The launch
+// counter counts the graph's kernels on every replay.
+cudaError_t mg_graphed(const MGHierarchy& H, int kind, int nc, const void* r, int64_t ldr, const void* w,
+                       int64_t ldw, const void* work, cudaStream_t s,
+                       const std::function<cudaError_t(cudaStream_t)>& body);
+// Destroy the captured graphs (the hierarchy's buffers or workspace change
+// or go away).
+void mg_release_graphs(const MGHierarchy& H);
 
 // Largest coarsest grid (points) of the FP32 and double-word V-cycles, whose
 // coarsest solve stages the grid in shared memory (the FP64 cycle takes any

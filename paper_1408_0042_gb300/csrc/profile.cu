@@ -1,4 +1,5 @@
-// Launch counter and CUDA-event phase timers exposed through the C ABI.
+// Launch counter and CUDA-event phase timers exposed through the C ABI, and
+// the CUDA-graph replay of V-cycles (whose launch counts it keeps).
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -91,3 +92,60 @@ void plhr_profile_bytes(double* bytes) {
 }
 
 }  // extern "C"
+
+namespace plhr {
+
+namespace {
+constexpr size_t kMaxGraphs = 64;   // distinct V-cycle argument sets kept per hierarchy (oldest dropped)
+}
+
+cudaError_t mg_graphed(const MGHierarchy& H, int kind, int nc, const void* r, int64_t ldr, const void* w,
+                       int64_t ldw, const void* work, cudaStream_t s,
+                       const std::function<cudaError_t(cudaStream_t)>& body) {
+    for (const MGHierarchy::Graph& g : H.graphs)
+        if (g.kind == kind && g.nc == nc && g.r == r && g.ldr == ldr && g.w == w && g.ldw == ldw && g.work == work) {
+            count_launches(g.launches);
+            return cudaGraphLaunch(g.exec, s);
+        }
+    if (H.graphs.size() >= kMaxGraphs) {
+        // a replay of the oldest may still be queued: the executable graph is
+        // released once that work completes (cudaGraphExecDestroy defers it)
+        cudaGraphExecDestroy(H.graphs.front().exec);
+        H.graphs.erase(H.graphs.begin());
+    }
+    if (!H.capture && cudaStreamCreateWithFlags(&H.capture, cudaStreamNonBlocking) != cudaSuccess) {
+        H.capture = nullptr;
+        cudaGetLastError();
+        return body(s);
+    }
+    // capture (nothing runs): the launches the body counts are taken back and
+    // counted again for each replay
+    const long long before = g_launches.load();
+    if (cudaStreamBeginCapture(H.capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return body(s);
+    }
+    const cudaError_t eb = body(H.capture);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(H.capture, &graph);
+    const int nl = (int)(g_launches.load() - before);
+    g_launches.fetch_sub(nl);
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ei = cudaErrorUnknown;
+    if (eb == cudaSuccess && ee == cudaSuccess && graph) ei = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        return body(s);
+    }
+    H.graphs.push_back({kind, nc, r, ldr, w, ldw, work, exec, nl});
+    count_launches(nl);
+    return cudaGraphLaunch(exec, s);
+}
+
+void mg_release_graphs(const MGHierarchy& H) {
+    for (const MGHierarchy::Graph& g : H.graphs) cudaGraphExecDestroy(g.exec);
+    H.graphs.clear();
+}
+
+}  // namespace plhr

@@ -149,3 +149,28 @@ def test_lap3d_128cube_mixed_other_start_blocks(plhr, offset):
     want = cf[np.lexsort((cf, np.abs(cf - w.sigma)))][: w.k]
     assert np.allclose(np.sort(lam), np.sort(want), rtol=1e-10)
     assert info["max_rel_residual"] <= w.tol
+
+
+@pytest.mark.parametrize("form", ["f32", "dw"])
+def test_vcycle_replay_reads_new_input(plhr, form):
+    """A V-cycle is captured once per argument set (a CUDA graph) and replayed
+    afterwards: applied again to new values in the same buffers, it returns
+    the V-cycle of the new values, equal to the oracle's."""
+    dims, levels, sigma = (16, 16, 16), 3, 900.0
+    h = 1.0 / (max(dims) + 1)
+    A = plhr.Operator.laplacian(dims, h)
+    T = plhr.AVMG(A, sigma, levels=levels, nu=2, transfer=1, coarse=1)
+    ref = oavmg.AVMG(dims, h, sigma, levels, nu=2, transfer="linear", coarse="fine_spectrum")
+    nc = 8
+    dt = torch.float32 if form == "f32" else torch.float64
+    R = torch.empty((A.n, nc), dtype=dt, device="cuda")
+    W = torch.empty((A.n, nc), dtype=dt, device="cuda")
+    apply = T.apply_f32 if form == "f32" else T.apply_dw
+    tol = 2e-5 if form == "f32" else 1e-12
+    for seed in (23, 24, 25):
+        Rn = wl.uniform_block(A.n, nc, seed)
+        if form == "f32":
+            Rn = Rn.astype(np.float32).astype(np.float64)
+        R.copy_(torch.from_numpy(Rn))
+        apply(R, out=W)
+        assert _rel(W.double().cpu().numpy(), ref(Rn)) <= tol
