@@ -140,23 +140,26 @@ __device__ __forceinline__ void fetch_tc(float* raw, int64_t n, int64_t row0, in
 
 // Convert the chunk of grid points row0 .. row0 + 31 (raw rows in shared
 // memory) into the panel at buf.  Task t: panel row mr (column j of U, Z or
-// Q) and core-matrix column ki (8 consecutive grid points): 8 values, three
-// 16-byte slice stores.
+// Q) and half hf of core-matrix column ki (4 consecutive grid points): 4
+// values, three 8-byte slice stores.  1536 tasks: three per thread, so the
+// barrier after the staging waits for no thread with more work than the rest.
+static_assert(kPanelRows * (kTcK / 4) % kTcThreads == 0, "staging tasks divide evenly");
 __device__ __forceinline__ void stage_tc(unsigned char* buf, const float* raw, int64_t n, int64_t row0, int m,
                                          const ColSh& C, int has_q, float sigf, const float* cscf) {
-    for (int t = threadIdx.x; t < kPanelRows * (kTcK / 8); t += kTcThreads) {
-        const int mr = t % kPanelRows, ki = t / kPanelRows;
+    for (int t = threadIdx.x; t < kPanelRows * (kTcK / 4); t += kTcThreads) {
+        const int mr = t % kPanelRows, kq = t / kPanelRows;
+        const int ki = kq >> 1, hf = kq & 1;
         const int part = mr >> 6, j = mr & 63;
-        float x[8];
+        float x[4];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) x[r] = 0.0f;
+        for (int r = 0; r < 4; ++r) x[r] = 0.0f;
         if (j < m) {
             const float sf = cscf[j];
             const bool isu = C.is_u[j] != 0;
-            const float* rr = raw + (8 * ki) * kRawStride;
+            const float* rr = raw + (4 * kq) * kRawStride;
 #pragma unroll
-            for (int r = 0; r < 8; ++r, rr += kRawStride) {
-                if (row0 + 8 * ki + r >= n) break;
+            for (int r = 0; r < 4; ++r, rr += kRawStride) {
+                if (row0 + 4 * kq + r >= n) break;
                 if (part == 1) {
                     x[r] = rr[j] * sf;
                 } else if (part == 2 && has_q) {
@@ -167,16 +170,13 @@ __device__ __forceinline__ void stage_tc(unsigned char* buf, const float* raw, i
                 }
             }
         }
-        __nv_bfloat16 s0[8], s1[8], s2[8];
+        __nv_bfloat16 s0[4], s1[4], s2[4];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) tc::split3(x[r], s0[r], s1[r], s2[r]);
-        const int off = (ki * (kPanelRows / 8) + (mr >> 3)) * kCoreBytes + (mr & 7) * 16;
-        *reinterpret_cast<uint4*>(buf + off) =
-            make_uint4(pack2(s0[0], s0[1]), pack2(s0[2], s0[3]), pack2(s0[4], s0[5]), pack2(s0[6], s0[7]));
-        *reinterpret_cast<uint4*>(buf + kSliceBytes + off) =
-            make_uint4(pack2(s1[0], s1[1]), pack2(s1[2], s1[3]), pack2(s1[4], s1[5]), pack2(s1[6], s1[7]));
-        *reinterpret_cast<uint4*>(buf + 2 * kSliceBytes + off) =
-            make_uint4(pack2(s2[0], s2[1]), pack2(s2[2], s2[3]), pack2(s2[4], s2[5]), pack2(s2[6], s2[7]));
+        for (int r = 0; r < 4; ++r) tc::split3(x[r], s0[r], s1[r], s2[r]);
+        const int off = (ki * (kPanelRows / 8) + (mr >> 3)) * kCoreBytes + (mr & 7) * 16 + 8 * hf;
+        *reinterpret_cast<uint2*>(buf + off) = make_uint2(pack2(s0[0], s0[1]), pack2(s0[2], s0[3]));
+        *reinterpret_cast<uint2*>(buf + kSliceBytes + off) = make_uint2(pack2(s1[0], s1[1]), pack2(s1[2], s1[3]));
+        *reinterpret_cast<uint2*>(buf + 2 * kSliceBytes + off) = make_uint2(pack2(s2[0], s2[1]), pack2(s2[2], s2[3]));
     }
 }
 
