@@ -608,14 +608,15 @@ cudaError_t vcycle(const MGHierarchy& H, int l, int nc, bool v4, const Tr* r, in
 }
 #undef PLHR_L4
 
-// r32 (dense, n x nc) = r (FP64, leading dimension ldr)
-__global__ void k_narrow_rhs(int64_t n, int nc, const double* __restrict__ r, int64_t ldr, float* __restrict__ r32) {
+// r32 (n x nc, leading dimension ldo) = r (FP64, leading dimension ldr)
+__global__ void k_narrow_rhs(int64_t n, int nc, const double* __restrict__ r, int64_t ldr, float* __restrict__ r32,
+                             int64_t ldo) {
     const int64_t total = n * nc;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         int64_t row;
         int cc;
         split_index(e, nc, row, cc);
-        r32[e] = f64_to_f32_rn(r[row * ldr + cc]);
+        r32[row * ldo + cc] = f64_to_f32_rn(r[row * ldr + cc]);
     }
 }
 
@@ -656,12 +657,33 @@ cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const double* r, int64_t
     return mg_graphed(H, 1, nc, r, ldr, w, nc, work, s, [&](cudaStream_t st) -> cudaError_t {
         const int64_t n = H.lev.back().g.n();
         float* r32 = work + (mg_workspace_floats(H, nc) - n * nc);
-        k_narrow_rhs<<<grid_size_for(n * nc, 256, sm_count() * 8), 256, 0, st>>>(n, nc, r, ldr, r32);
+        k_narrow_rhs<<<grid_size_for(n * nc, 256, sm_count() * 8), 256, 0, st>>>(n, nc, r, ldr, r32, nc);
         count_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         return run<float>(H, nc, r32, nc, w, work, st);
     });
+}
+
+cudaError_t mg_vcycle_f32_pair(const MGHierarchy& H, int nc1, const double* r1, int64_t ldr1, int nc2,
+                               const double* r2, int64_t ldr2, float* w, float* work, cudaStream_t s) {
+    // both right-hand sides narrowed side by side, then one cycle of
+    // nc1 + nc2 columns: the coarse levels cost one cycle instead of two
+    const int nc = nc1 + nc2;
+    if (nc1 <= 0 || nc2 <= 0) return cudaErrorInvalidValue;
+    return mg_graphed(
+        H, 3, nc1, r1, ldr1, w, nc, work, s,
+        [&](cudaStream_t st) -> cudaError_t {
+            const int64_t n = H.lev.back().g.n();
+            float* r32 = work + (mg_workspace_floats(H, nc) - n * nc);
+            k_narrow_rhs<<<grid_size_for(n * nc1, 256, sm_count() * 8), 256, 0, st>>>(n, nc1, r1, ldr1, r32, nc);
+            k_narrow_rhs<<<grid_size_for(n * nc2, 256, sm_count() * 8), 256, 0, st>>>(n, nc2, r2, ldr2, r32 + nc1, nc);
+            count_launches(2);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            return run<float>(H, nc, r32, nc, w, work, st);
+        },
+        r2, ldr2, nc2);
 }
 
 cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const float* r, int64_t ldr, float* w, float* work,

@@ -166,6 +166,9 @@ struct MGHierarchy {
         const void* w;
         int64_t ldw;
         const void* work;
+        const void* r2;   // second right-hand side (paired cycles), else null
+        int64_t ldr2;
+        int nc2;
         cudaGraphExec_t exec;
         int launches;
     };
@@ -180,7 +183,8 @@ struct MGHierarchy {
 // counter counts the graph's kernels on every replay.
 cudaError_t mg_graphed(const MGHierarchy& H, int kind, int nc, const void* r, int64_t ldr, const void* w,
                        int64_t ldw, const void* work, cudaStream_t s,
-                       const std::function<cudaError_t(cudaStream_t)>& body);
+                       const std::function<cudaError_t(cudaStream_t)>& body, const void* r2 = nullptr,
+                       int64_t ldr2 = 0, int nc2 = 0);
 // Destroy the captured graphs (the hierarchy's buffers or workspace change
 // or go away).
 void mg_release_graphs(const MGHierarchy& H);
@@ -219,6 +223,10 @@ cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const double* r, int64_t
                           cudaStream_t s);
 cudaError_t mg_vcycle_f32(const MGHierarchy& H, int nc, const float* r, int64_t ldr, float* w, float* work,
                           cudaStream_t s);
+// w (n x (nc1 + nc2), dense) = [T r1 | T r2] in one FP32 cycle of nc1 + nc2
+// columns (r1, r2 FP64; work: mg_workspace_floats(H, nc1 + nc2))
+cudaError_t mg_vcycle_f32_pair(const MGHierarchy& H, int nc1, const double* r1, int64_t ldr1, int nc2,
+                               const double* r2, int64_t ldr2, float* w, float* work, cudaStream_t s);
 int64_t mg_workspace_floats(const MGHierarchy& H, int nc);
 
 // Double-word V-cycle (same cycle; hi + lo FP32 pairs, ~48-bit arithmetic on

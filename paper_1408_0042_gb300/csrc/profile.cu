@@ -101,9 +101,11 @@ constexpr size_t kMaxGraphs = 64;   // distinct V-cycle argument sets kept per h
 
 cudaError_t mg_graphed(const MGHierarchy& H, int kind, int nc, const void* r, int64_t ldr, const void* w,
                        int64_t ldw, const void* work, cudaStream_t s,
-                       const std::function<cudaError_t(cudaStream_t)>& body) {
+                       const std::function<cudaError_t(cudaStream_t)>& body, const void* r2, int64_t ldr2,
+                       int nc2) {
     for (const MGHierarchy::Graph& g : H.graphs)
-        if (g.kind == kind && g.nc == nc && g.r == r && g.ldr == ldr && g.w == w && g.ldw == ldw && g.work == work) {
+        if (g.kind == kind && g.nc == nc && g.r == r && g.ldr == ldr && g.w == w && g.ldw == ldw && g.work == work &&
+            g.r2 == r2 && g.ldr2 == ldr2 && g.nc2 == nc2) {
             count_launches(g.launches);
             return cudaGraphLaunch(g.exec, s);
         }
@@ -138,7 +140,7 @@ cudaError_t mg_graphed(const MGHierarchy& H, int kind, int nc, const void* r, in
         cudaGetLastError();
         return body(s);
     }
-    H.graphs.push_back({kind, nc, r, ldr, w, ldw, work, exec, nl});
+    H.graphs.push_back({kind, nc, r, ldr, w, ldw, work, r2, ldr2, nc2, exec, nl});
     count_launches(nl);
     return cudaGraphLaunch(exec, s);
 }

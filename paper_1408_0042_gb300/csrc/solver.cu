@@ -246,16 +246,17 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     big32.s = s;
     float *W32 = nullptr, *AW32 = nullptr, *SQ32 = nullptr, *X2_32 = nullptr, *AS32 = nullptr, *X3_32 = nullptr,
           *QS32 = nullptr, *P32 = nullptr, *AP32 = nullptr, *QP32 = nullptr, *QV32 = nullptr, *V32 = nullptr,
-          *U32 = nullptr;
+          *U32 = nullptr, *WQ32 = nullptr;
     if (mx) {
-        if (cudaMallocAsync(&big32.p, sizeof(float) * 15 * nk, s) != cudaSuccess) {
-            set_error("plhr_solve: device allocation of %.1f MB failed", 4e-6 * 15.0 * (double)nk);
+        if (cudaMallocAsync(&big32.p, sizeof(float) * 17 * nk, s) != cudaSuccess) {
+            set_error("plhr_solve: device allocation of %.1f MB failed", 4e-6 * 17.0 * (double)nk);
             return PLHR_ENOMEM;
         }
         float* f = big32.p;
         W32 = f; f += nk; AW32 = f; f += nk; SQ32 = f; f += 2 * nk; X2_32 = f; f += 2 * nk; AS32 = f; f += nk;
         X3_32 = f; f += nk; QS32 = f; f += nk; P32 = f; f += nk; AP32 = f; f += nk; QP32 = f; f += nk;
         QV32 = f; f += nk; V32 = f; f += nk; U32 = f; f += nk;
+        WQ32 = f; f += 2 * nk;   // [W | Q_V] from one paired V-cycle (leading dimension na + kp)
         if (T) PLHR_TRY(prec_reserve32(T, 2 * kp, 0));
         if (T) PLHR_TRY(prec_reserve_dw(T, 2 * kp));
     }
@@ -312,6 +313,14 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         if (nc == 0) return PLHR_OK;
         PhaseScope ps(PH_VCYCLE32, s, (double)n * nc, prec_bytes(T, n, nc, 4));
         PLHR_TRY_CUDA(mg_vcycle_f32(T->H, nc, r, ldr, w, T->work32, s));
+        return PLHR_OK;
+    };
+    // w (ld nc1 + nc2) = [T r1 | T r2], one FP32 V-cycle of nc1 + nc2 columns
+    auto applyT32_pair = [&](int nc1, const double* r1, int64_t ldr1, int nc2, const double* r2, int64_t ldr2,
+                             float* w) -> plhr_status {
+        const int nc = nc1 + nc2;
+        PhaseScope ps(PH_VCYCLE32, s, (double)n * nc, prec_bytes(T, n, nc, 4));
+        PLHR_TRY_CUDA(mg_vcycle_f32_pair(T->H, nc1, r1, ldr1, nc2, r2, ldr2, w, T->work32, s));
         return PLHR_OK;
     };
 
@@ -627,12 +636,33 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
         }
         if (mx) {
             // ---------------------------------------- the same step in the FP32 form
-            if (T) PLHR_TRY(applyT32(na, Ract, ldra, W32));
-            else PLHR_TRY_CUDA(narrow_block(n, na, Ract, ldra, W32, na, s));
+            // W = T(AV - V Lambda) and, with T, Q_V = T(A V - sigma V) explicitly:
+            // carrying Q_V (and Q_P below) through the update would mix the FP32
+            // V-cycle's rounding of different iterations into one image, and the
+            // projected pencil (built from Q = T U) would lose consistency below
+            // ~1e-5.  Both right-hand sides are ready here, so they share one
+            // V-cycle when the 16-byte column groups allow it.
+            float* Wp = W32;
+            int64_t ldw = na;
+            float* QVp = QV32;
+            int64_t ldqv = kp;
+            // FP32 copies of V and U_V = A V - sigma V (formed in FP64) for the Gram
+            PLHR_TRY_CUDA(prepare_v_mx(n, kp, V, AV, sigma, V32, U32, T ? X3 : nullptr, s));
+            if (T && na % 4 == 0 && kp % 4 == 0) {
+                PLHR_TRY(applyT32_pair(na, Ract, ldra, kp, (const double*)X3, kp, WQ32));
+                Wp = WQ32;
+                QVp = WQ32 + na;
+                ldw = ldqv = na + kp;
+            } else if (T) {
+                PLHR_TRY(applyT32(na, Ract, ldra, W32));
+                PLHR_TRY(applyT32(kp, (const double*)X3, kp, QV32));
+            } else {
+                PLHR_TRY_CUDA(narrow_block(n, na, Ract, ldra, W32, na, s));
+            }
             float* X2in = T ? X2_32 : SQ32;
             {
                 PhaseScope ps(PH_STENCIL, s, (double)n * na, 4.0 * n * na * (T ? 4 : 3));
-                PLHR_TRY_CUDA(lap32_apply_shifts(g, na, W32, na, AW32, na, X2in, T ? 2 * na : na, lam_act,
+                PLHR_TRY_CUDA(lap32_apply_shifts(g, na, Wp, ldw, AW32, na, X2in, T ? 2 * na : na, lam_act,
                                                  T ? X2in + na : nullptr, 2 * na, sigma, s));
             }
             const float* S32 = SQ32;
@@ -645,27 +675,17 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
                                                  na, sigma, s));
             }
             if (T) PLHR_TRY(applyT32(na, (const float*)X3_32, na, QS32));
-            // FP32 copies of V and U_V = A V - sigma V (formed in FP64) for the Gram
-            PLHR_TRY_CUDA(prepare_v_mx(n, kp, V, AV, sigma, V32, U32, T ? X3 : nullptr, s));
-            if (T) {
-                // Q_V = T(A V - sigma V) and Q_P = T(A P - sigma P) explicitly: carrying
-                // them through the update would mix the FP32 V-cycle's rounding of
-                // different iterations into one image, and the projected pencil
-                // (built from Q = T U) would lose consistency below ~1e-5
-                PLHR_TRY(applyT32(kp, (const double*)X3, kp, QV32));
-                if (np) {
-                    PLHR_TRY_CUDA(lap32_apply_shifts(g, kp, P32, kp, AP32, kp, nullptr, 0, nullptr, X3_32, kp, sigma,
-                                                     s));
-                    PLHR_TRY(applyT32(kp, (const float*)X3_32, kp, QP32));
-                }
+            if (T && np) {
+                PLHR_TRY_CUDA(lap32_apply_shifts(g, kp, P32, kp, AP32, kp, nullptr, 0, nullptr, X3_32, kp, sigma, s));
+                PLHR_TRY(applyT32(kp, (const float*)X3_32, kp, QP32));
             }
             const int nb = np ? 4 : 3;
             const int m = kp + 2 * na + np;
             last_m = m;
-            BlkMx zb[4] = {{V32, kp, kp, 0}, {W32, na, na, 0}, {S32, lds, na, 0}, {P32, kp, np, 0}};
+            BlkMx zb[4] = {{V32, kp, kp, 0}, {Wp, ldw, na, 0}, {S32, lds, na, 0}, {P32, kp, np, 0}};
             BlkMx ab[4] = {{U32, kp, kp, 0, 1}, {AW32, na, na, 0}, {AS32, na, na, 0}, {AP32, kp, np, 0}};
-            BlkMx ub[4] = {{V, kp, kp, 1}, {W32, na, na, 0}, {S32, lds, na, 0}, {P32, kp, np, 0}};
-            BlkMx qb[4] = {{QV32, kp, kp, 0}, {QW32, 2 * na, na, 0}, {QS32, na, na, 0}, {QP32, kp, np, 0}};
+            BlkMx ub[4] = {{V, kp, kp, 1}, {Wp, ldw, na, 0}, {S32, lds, na, 0}, {P32, kp, np, 0}};
+            BlkMx qb[4] = {{QVp, ldqv, kp, 0}, {QW32, 2 * na, na, 0}, {QS32, na, na, 0}, {QP32, kp, np, 0}};
             PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
             DenseArgs da;
             da.m = m; da.kp = kp; da.nv = kp;

@@ -57,10 +57,11 @@ def _solve(plhr, w, maxit, tensor_cores, seed=None):
 # n = 252 (2D 18 x 14), 2145 (3D 15 x 13 x 11), 39304 (3D 34^3): none is a
 # multiple of 32 or 64
 @pytest.mark.parametrize("tensor_cores", [True, False])
-# (guard: the multiplicity of the cluster just outside the wanted set)
+# (guard: the multiplicity of the cluster just outside the wanted set; with
+# k + guard a multiple of 4, W and Q_V share one V-cycle)
 @pytest.mark.parametrize("dims,k,gap,prec,levels,maxit,guard", [
     ((18, 14), 4, 30, "avmg", 2, 2000, 1), ((15, 13, 11), 4, 40, "none", 1, 4000, 1),
-    ((34, 34, 34), 4, 60, "avmg", 2, 1500, 6)])
+    ((34, 34, 34), 4, 60, "avmg", 2, 1500, 6), ((34, 34, 34), 6, 60, "avmg", 2, 1500, 6)])
 def test_mixed_solve_ragged_n(plhr, tensor_cores, dims, k, gap, prec, levels, maxit, guard):
     w = _workload(dims, k, gap, prec, levels, guard=guard)
     assert w.n % 32 != 0
