@@ -246,17 +246,18 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
     big32.s = s;
     float *W32 = nullptr, *AW32 = nullptr, *SQ32 = nullptr, *X2_32 = nullptr, *AS32 = nullptr, *X3_32 = nullptr,
           *QS32 = nullptr, *P32 = nullptr, *AP32 = nullptr, *QP32 = nullptr, *QV32 = nullptr, *V32 = nullptr,
-          *U32 = nullptr, *WQ32 = nullptr;
+          *U32 = nullptr, *WQ32 = nullptr, *QSP32 = nullptr;
     if (mx) {
-        if (cudaMallocAsync(&big32.p, sizeof(float) * 17 * nk, s) != cudaSuccess) {
-            set_error("plhr_solve: device allocation of %.1f MB failed", 4e-6 * 17.0 * (double)nk);
+        if (cudaMallocAsync(&big32.p, sizeof(float) * 19 * nk, s) != cudaSuccess) {
+            set_error("plhr_solve: device allocation of %.1f MB failed", 4e-6 * 19.0 * (double)nk);
             return PLHR_ENOMEM;
         }
         float* f = big32.p;
         W32 = f; f += nk; AW32 = f; f += nk; SQ32 = f; f += 2 * nk; X2_32 = f; f += 2 * nk; AS32 = f; f += nk;
         X3_32 = f; f += nk; QS32 = f; f += nk; P32 = f; f += nk; AP32 = f; f += nk; QP32 = f; f += nk;
         QV32 = f; f += nk; V32 = f; f += nk; U32 = f; f += nk;
-        WQ32 = f; f += 2 * nk;   // [W | Q_V] from one paired V-cycle (leading dimension na + kp)
+        WQ32 = f; f += 2 * nk;    // [W | Q_V] from one paired V-cycle (leading dimension na + kp)
+        QSP32 = f; f += 2 * nk;   // [Q_S | Q_P] likewise
         if (T) PLHR_TRY(prec_reserve32(T, 2 * kp, 0));
         if (T) PLHR_TRY(prec_reserve_dw(T, 2 * kp));
     }
@@ -669,15 +670,34 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             const int64_t lds = T ? 2 * na : na;
             if (T) PLHR_TRY(applyT32(2 * na, (const float*)X2_32, 2 * na, SQ32));
             const float* QW32 = SQ32 + na;
+            // Q_S = T(A S - sigma S) and Q_P = T(A P - sigma P) from one V-cycle too
+            // when both widths allow it: their inputs go side by side into X2_32
+            // (free once the cycle above has read it)
+            const bool pair_sp = T && np && na % 4 == 0 && kp % 4 == 0;
+            const int64_t ldsp = na + kp;
+            float* QSp = QS32;
+            float* QPp = QP32;
+            int64_t ldqs = na, ldqp = kp;
             {
                 PhaseScope ps(PH_STENCIL, s, (double)n * na, 4.0 * n * na * (T ? 3 : 2));
-                PLHR_TRY_CUDA(lap32_apply_shifts(g, na, S32, lds, AS32, na, nullptr, 0, nullptr, T ? X3_32 : nullptr,
-                                                 na, sigma, s));
+                PLHR_TRY_CUDA(lap32_apply_shifts(g, na, S32, lds, AS32, na, nullptr, 0, nullptr,
+                                                 T ? (pair_sp ? X2_32 : X3_32) : nullptr, pair_sp ? ldsp : na, sigma,
+                                                 s));
             }
-            if (T) PLHR_TRY(applyT32(na, (const float*)X3_32, na, QS32));
-            if (T && np) {
-                PLHR_TRY_CUDA(lap32_apply_shifts(g, kp, P32, kp, AP32, kp, nullptr, 0, nullptr, X3_32, kp, sigma, s));
-                PLHR_TRY(applyT32(kp, (const float*)X3_32, kp, QP32));
+            if (pair_sp) {
+                PLHR_TRY_CUDA(lap32_apply_shifts(g, kp, P32, kp, AP32, kp, nullptr, 0, nullptr, X2_32 + na, ldsp,
+                                                 sigma, s));
+                PLHR_TRY(applyT32(na + kp, (const float*)X2_32, ldsp, QSP32));
+                QSp = QSP32;
+                QPp = QSP32 + na;
+                ldqs = ldqp = ldsp;
+            } else {
+                if (T) PLHR_TRY(applyT32(na, (const float*)X3_32, na, QS32));
+                if (T && np) {
+                    PLHR_TRY_CUDA(
+                        lap32_apply_shifts(g, kp, P32, kp, AP32, kp, nullptr, 0, nullptr, X3_32, kp, sigma, s));
+                    PLHR_TRY(applyT32(kp, (const float*)X3_32, kp, QP32));
+                }
             }
             const int nb = np ? 4 : 3;
             const int m = kp + 2 * na + np;
@@ -685,7 +705,7 @@ extern "C" plhr_status plhr_solve(const plhr_op* A, const plhr_op* B, double sig
             BlkMx zb[4] = {{V32, kp, kp, 0}, {Wp, ldw, na, 0}, {S32, lds, na, 0}, {P32, kp, np, 0}};
             BlkMx ab[4] = {{U32, kp, kp, 0, 1}, {AW32, na, na, 0}, {AS32, na, na, 0}, {AP32, kp, np, 0}};
             BlkMx ub[4] = {{V, kp, kp, 1}, {Wp, ldw, na, 0}, {S32, lds, na, 0}, {P32, kp, np, 0}};
-            BlkMx qb[4] = {{QVp, ldqv, kp, 0}, {QW32, 2 * na, na, 0}, {QS32, na, na, 0}, {QP32, kp, np, 0}};
+            BlkMx qb[4] = {{QVp, ldqv, kp, 0}, {QW32, 2 * na, na, 0}, {QSp, ldqs, na, 0}, {QPp, ldqp, np, 0}};
             PLHR_TRY_CUDA(cudaMemcpyAsync(colscale, scale, sizeof(double) * kp, cudaMemcpyDeviceToDevice, s));
             DenseArgs da;
             da.m = m; da.kp = kp; da.nv = kp;
