@@ -219,7 +219,13 @@ plhr_status plhr_prec_apply(plhr_prec* T, int ncols, const double* R, int64_t ld
                             double* W, int64_t ldw, void* stream);
 /* The same V-cycle in FP32 storage and arithmetic (the form the mixed-precision
  * solve uses): W = T R for FP32 blocks.  Workspace as for plhr_prec_apply.
- * AV-MG only (PLHR_EINVAL for a TPA preconditioner). */
+ * AV-MG only (PLHR_EINVAL for a TPA preconditioner).  This form and the
+ * double-word one below run the cycle as a CUDA graph: the first call with a
+ * given (ncols, R, ldr, W, ldw) captures the cycle's launches on a stream T
+ * owns (nothing runs during the capture) and launches the graph on `stream`;
+ * later calls with the same arguments replay it.  T keeps up to 64 graphs
+ * (the oldest is dropped) and releases them when its workspace is
+ * reallocated or T is destroyed. */
 plhr_status plhr_prec_apply_f32(plhr_prec* T, int ncols, const float* R, int64_t ldr,
                                 float* W, int64_t ldw, void* stream);
 /* The same V-cycle with double-word storage and arithmetic (hi + lo FP32
