@@ -225,7 +225,8 @@ plhr_status plhr_prec_apply(plhr_prec* T, int ncols, const double* R, int64_t ld
  * owns (nothing runs during the capture) and launches the graph on `stream`;
  * later calls with the same arguments replay it.  T keeps up to 64 graphs
  * (the oldest is dropped) and releases them when its workspace is
- * reallocated or T is destroyed. */
+ * reallocated or T is destroyed.  Do not call these two while `stream` is
+ * itself being captured into a graph. */
 plhr_status plhr_prec_apply_f32(plhr_prec* T, int ncols, const float* R, int64_t ldr,
                                 float* W, int64_t ldw, void* stream);
 /* The same V-cycle with double-word storage and arithmetic (hi + lo FP32
